@@ -1,0 +1,140 @@
+/*
+ * FP64 CPU oracle for Lyman-alpha skewer synthesis (arXiv 2310.18996).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / --impl reference legs of bench.py may load this library.
+ * It shares no code, header, table or constant generator with the CUDA
+ * library in paper_2310_18996_gb300/, and neither side includes the other.
+ *
+ * Every routine is a plain, slow, direct transcription of a definition:
+ * quadrature for the cosmology, the Philox4x32-10 round function, the
+ * Box-Muller map, an O(N^2) discrete Fourier transform, trilinear weights
+ * written out corner by corner, and straight loops for the statistics.
+ * All floating point is double precision; box values are FP32 inputs that
+ * are promoted on read.
+ */
+#ifndef MK_ORACLE_H
+#define MK_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_C_OVER_H0 2997.92458 /* c / H0 in Mpc/h (H0 = 100 h km/s/Mpc) */
+#define ORC_MAX_NODES 32
+#define ORC_MAX_ZBINS 32
+#define ORC_MAX_KBINS 64
+#define ORC_NSUM 10
+
+/* Everything the method needs to turn a catalogue and a box into skewers. */
+typedef struct orc_cfg {
+  double omega_m;    /* flat LCDM, Omega_L = 1 - Omega_M, no radiation (Table 1) */
+  double lambda_lya; /* Lya rest wavelength [Angstrom] */
+  /* box: n^3 cells of side `cell`, x fastest, periodic; origin = corner */
+  int32_t n;
+  double cell;
+  double origin[3]; /* box corner in the observer frame [Mpc/h]; observer at 0 */
+  /* line-of-sight pixels */
+  double dr;               /* pixel length [Mpc/h] (Sec. 2.3: 0.2) */
+  double lrf_min, lrf_max; /* rest-frame forest window [Angstrom] */
+  double lobs_min;         /* observed-frame lower cut [Angstrom], <= 0: none */
+  int32_t n_min, n_max;    /* skewers shorter than n_min get n = 0; n_max > 0
+                              truncates at the blue end */
+  /* small-scale field (Sec. 2.3): segments of n_fft pixels */
+  int32_t n_fft;
+  const double *p_s; /* n_fft/2+1 samples P_S(k_m), k_m = 2 pi m/(n_fft dr) */
+  uint32_t seed;
+} orc_cfg;
+
+/* FGPA parameter nodes (Sec. 2.5: tuned at a few z, interpolated between). */
+typedef struct orc_nodes {
+  int32_t count;
+  double z[ORC_MAX_NODES];
+  double ln_a[ORC_MAX_NODES];
+  double b[ORC_MAX_NODES];
+  double c[ORC_MAX_NODES];
+} orc_nodes;
+
+/* Statistic binning: n_z redshift bins [z_lo + i dz, z_lo + (i+1) dz). */
+typedef struct orc_bins {
+  int32_t n_z;
+  double z_lo, dz;
+  int32_t n_k;   /* equal-count linear k bins over m = 1..n_fft/2 */
+  int32_t n_fft; /* P1D segment length in output pixels */
+} orc_bins;
+
+/* Raw FP64 sums and the finalised statistics. Sum index order:
+   0 n, 1 F, 2 F^2, 3 d, 4 e, 5 d^2, 6 e^2, 7 d e, 8 F d, 9 F e
+   where d = delta_tot and e = eta (both growth scaled). */
+typedef struct orc_stats {
+  double sums[ORC_MAX_ZBINS][ORC_NSUM];
+  double p1d_sum[ORC_MAX_ZBINS][ORC_MAX_KBINS];
+  double n_seg[ORC_MAX_ZBINS];
+  double mean_flux[ORC_MAX_ZBINS];
+  double sigma_f[ORC_MAX_ZBINS];
+  double p1d_f[ORC_MAX_ZBINS][ORC_MAX_KBINS];
+  double p1d_df[ORC_MAX_ZBINS][ORC_MAX_KBINS];
+  double b_f[ORC_MAX_ZBINS];
+  double beta_f[ORC_MAX_ZBINS];
+} orc_stats;
+
+/* ---- cosmology (Table 1, flat LCDM) ---- */
+double orc_hubble_e(double omega_m, double z);
+double orc_comoving_distance(double omega_m, double z);
+double orc_z_of_distance(double omega_m, double r);
+double orc_growth(double omega_m, double z);
+
+/* ---- Philox4x32-10 (Salmon et al. 2011) and Box-Muller ---- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+void orc_box_muller(uint32_t xu1, uint32_t xu2, double *e1, double *e2);
+
+/* ---- discrete Fourier transforms, O(N^2) ---- */
+void orc_dft_forward_real(const double *x, int32_t n, double *re, double *im);
+void orc_dft_inverse_hermitian(const double *re, const double *im, int32_t n, double *x);
+
+/* ---- geometry of one quasar line of sight ---- */
+int orc_geometry(const orc_cfg *cfg, const double q[3], int32_t *j_lo, int32_t *npix,
+                 double *z_q);
+double orc_pixel_z(const orc_cfg *cfg, int64_t j);
+
+/* ---- trilinear interpolation of a periodic box (c in cell units) ---- */
+double orc_trilinear(const float *box, int32_t n, const double c[3]);
+
+/* ---- small-scale modes and field of one segment ---- */
+void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double *re,
+                           double *im);
+void orc_small_scale_segment(const orc_cfg *cfg, uint64_t id, int32_t seg, double *out);
+
+/* ---- one skewer: growth-scaled delta_L, eta and delta_S per pixel ---- */
+int orc_skewer_fields(const orc_cfg *cfg, const float *dbox, const float *ebox,
+                      const double q[3], uint64_t id, int32_t j_lo, int32_t npix,
+                      double *delta_lg, double *eta_g, double *delta_s);
+
+/* ---- FGPA parameters at z and the transform ---- */
+void orc_fgpa_params(const orc_nodes *nodes, double z, double *a, double *b, double *c);
+double orc_fgpa(double a, double b, double c, double delta, double eta);
+
+/* ---- batch driver: geometry, fields, flux, rebin; ragged outputs ----
+   offsets has nq+1 entries. Pass NULL outputs to size only. Returns total
+   fine pixels (>= 0) or -1 on error. */
+int64_t orc_run_skewers(const orc_cfg *cfg, const float *dbox, const float *ebox,
+                        const double *qpos, const uint64_t *ids, int64_t nq,
+                        const orc_nodes *nodes, int32_t rebin, int32_t *j_lo,
+                        int32_t *npix, int64_t *offsets, double *delta_tot, double *eta,
+                        double *flux_fine, int64_t *offsets_out, double *flux_out,
+                        int32_t n_threads);
+
+/* ---- statistics over ragged flux (output resolution R) ---- */
+void orc_stats_zero(orc_stats *st);
+int orc_stats_accumulate(const orc_cfg *cfg, const orc_bins *bins, int32_t rebin,
+                         const int32_t *j_lo, const int64_t *offsets_fine,
+                         const int64_t *offsets_out, int64_t nq, const double *flux_out,
+                         const double *delta_fine, const double *eta_fine, orc_stats *st);
+void orc_stats_finalize(const orc_bins *bins, orc_stats *st);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
