@@ -1,0 +1,255 @@
+/*
+ * mockskewer: GB300 (sm_103a) library for Lyman-alpha forest skewer synthesis,
+ * the transmission step of the mock method of Etourneau, Le Goff, Rich et al.,
+ * "Mock data sets for the eBOSS and DESI Lyman-alpha forest surveys"
+ * (arXiv 2310.18996).
+ *
+ * For every quasar line of sight the library
+ *   1. places pixels of length dr on the line from the quasar to the observer
+ *      over the rest-frame forest window (Sec. 2.3, pixels of 0.2 Mpc/h; the
+ *      pixel wavelength uses the unperturbed redshift, Sec. 2.4),
+ *   2. interpolates the density box delta and the line-of-sight
+ *      velocity-gradient box eta_par at each pixel (Sec. 2.3; trilinear),
+ *   3. scales both by the linear growth factor G(z) of the pixel (Sec. 2.1),
+ *   4. adds the small-scale field delta_S, an independent Gaussian
+ *      realisation per line of sight with power P_S (Sec. 2.3),
+ *   5. applies the FGPA, F = exp[-a(z) exp(b(z) g)], g = delta + c(z) eta_par
+ *      (Eq. FGPA, Sec. 2.4), with a, b, c interpolated between redshift nodes
+ *      (Sec. 2.6),
+ *   6. rebins to spectral pixels, and
+ *   7. accumulates FP64 statistics: mean flux and sigma_F per z bin, the 1D
+ *      flux power spectrum P1D (Sec. 2.6, Sec. 4.1 for delta_F = F/Fbar - 1),
+ *      and the regression of F on (delta, eta) that gives b_F and beta_F.
+ *
+ * Conventions common to every call
+ *   - Distances are comoving Mpc/h, wavelengths Angstrom.  The observer sits
+ *     at the origin of the frame in which quasar positions are given.
+ *   - Pixel J of the global grid is centred at comoving distance (J + 1/2) dr.
+ *     A skewer holds the consecutive pixels j_lo .. j_lo + n - 1 whose centres
+ *     r satisfy r_lo <= r < r_hi, r_lo/r_hi the distances of the forest
+ *     window's ends; pixel 0 is the bluest (nearest the observer).
+ *   - Ragged per-pixel arrays are dense: skewer i owns entries
+ *     offsets[i] .. offsets[i+1] - 1, offsets[i+1] - offsets[i] = n_i.
+ *   - "d_" arguments are device pointers on the context's device, "h_"
+ *     arguments host pointers.  Large buffers are always allocated and owned
+ *     by the caller; the library owns only its tables, a statistics
+ *     workspace, captured graphs and a device error word.
+ *   - Calls are asynchronous on the context's stream unless stated.  Device
+ *     side range failures (an output larger than its stated capacity, a
+ *     pixel outside the redshift tables) set the error word; the next
+ *     synchronising call (mk_sync, mk_stats, mk_run, a size query) returns
+ *     MK_ERANGE and clears it.
+ *   - Return codes: MK_OK = 0, or one of the MK_E* codes below.  No call
+ *     aborts or throws; mk_last_error() gives the message of the last failure.
+ */
+#ifndef MOCKSKEWER_H
+#define MOCKSKEWER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MK_OK 0
+#define MK_EINVAL 1   /* bad argument: NULL pointer, size, unsupported option */
+#define MK_ECUDA 2    /* a CUDA runtime call failed */
+#define MK_ENOMEM 3   /* the library could not allocate its own workspace */
+#define MK_ETIMEOUT 4 /* a bounded device wait gave up */
+#define MK_ERANGE 5   /* a device-side bound check failed */
+
+#define MK_MAX_NODES 32
+#define MK_MAX_ZBINS 32
+#define MK_MAX_KBINS 64
+#define MK_NSUM 10
+
+#define MK_BOX_PLANAR 0      /* two FP32 arrays, delta and eta, index x + n (y + n z) */
+#define MK_BOX_INTERLEAVED 1 /* one FP32 array of (delta, eta) pairs, same index order */
+
+/* mk_run flags */
+#define MK_STORE_FIELDS 1u /* write delta_tot and eta (pre-FGPA skewers) */
+#define MK_STORE_FLUX 2u   /* write F */
+#define MK_STATS 4u        /* accumulate and return statistics */
+
+typedef struct mk_ctx mk_ctx; /* opaque, library-owned */
+typedef struct mk_box mk_box; /* opaque, refers to caller-owned device memory */
+
+/* Flat LCDM cosmology (Table 1: Omega_M = 0.3147); Omega_L = 1 - Omega_M. */
+typedef struct mk_cosmo {
+  double omega_m;
+  double lambda_lya; /* Lya rest wavelength [Angstrom], 1215.67 */
+} mk_cosmo;
+
+/* Box of n^3 cubic cells (n a power of two, 2..2048), periodic. */
+typedef struct mk_box_desc {
+  int32_t n;
+  int32_t layout;   /* MK_BOX_PLANAR or MK_BOX_INTERLEAVED */
+  double cell;      /* cell side [Mpc/h] */
+  double origin[3]; /* corner of the box in the observer frame [Mpc/h] */
+} mk_box_desc;
+
+/* One quasar: position in the observer frame and a catalogue id that keys its
+   small-scale noise (the same id gives the same delta_S in any batch). */
+typedef struct mk_qso {
+  double pos[3];
+  uint64_t id;
+} mk_qso;
+
+/* Per-skewer record written by mk_make_skewers / mk_run (device memory). */
+typedef struct mk_skewer {
+  int64_t offset;  /* first pixel in the ragged arrays */
+  int32_t n;       /* pixels */
+  int32_t j_lo;    /* global index of pixel 0 */
+  int64_t p0[3];   /* cell coordinate of pixel 0 minus 1/2, fixed point 2^-44 */
+  int64_t step[3]; /* per-pixel step of that coordinate, fixed point 2^-44 */
+  uint64_t id;
+} mk_skewer;
+
+typedef struct mk_skewer_params {
+  double dr;               /* pixel length [Mpc/h] (paper: 0.2) */
+  double lrf_min, lrf_max; /* rest-frame forest window [Angstrom] (1040, 1200) */
+  double lobs_min;         /* observed-frame lower cut [Angstrom]; <= 0: none */
+  int32_t n_min;           /* skewers with fewer pixels get n = 0 */
+  int32_t n_max;           /* > 0: keep at most n_max pixels, dropping blue ones */
+  int32_t n_fft;           /* delta_S segment length: power of two, 256..2048 */
+  uint32_t seed;           /* small-scale noise seed */
+  const double *h_p_s;     /* n_fft/2 + 1 values P_S(k_m), k_m = 2 pi m/(n_fft dr) */
+} mk_skewer_params;
+
+/* FGPA nodes: ln a, b, c at increasing z, linear in z between nodes, clamped
+   outside (Sec. 2.6 tunes at a few z_t and interpolates). */
+typedef struct mk_fgpa_nodes {
+  int32_t count; /* 1..MK_MAX_NODES */
+  double z[MK_MAX_NODES];
+  double ln_a[MK_MAX_NODES];
+  double b[MK_MAX_NODES];
+  double c[MK_MAX_NODES];
+} mk_fgpa_nodes;
+
+/* Statistic bins: n_z redshift bins [z_lo + i dz, z_lo + (i+1) dz); P1D on
+   segments of n_fft output pixels aligned to the skewer start (incomplete
+   tail segments dropped), modes m = 1..n_fft/2 in n_k equal-count bins. */
+typedef struct mk_stat_bins {
+  int32_t n_z;   /* 1..MK_MAX_ZBINS */
+  double z_lo, dz;
+  int32_t n_k;   /* divides n_fft/2, <= MK_MAX_KBINS */
+  int32_t n_fft; /* power of two, 256..2048 */
+} mk_stat_bins;
+
+/* Statistics (host memory).  sums[z][i], i = 0 count, 1 F, 2 F^2, 3 d, 4 e,
+   5 d^2, 6 e^2, 7 d e, 8 F d, 9 F e, with d = delta_tot and e = eta of the
+   pixel.  p1d_sum: sum over segments of (dr_out/N) |X_m|^2 per k bin.
+   mean_flux = F-bar, sigma_f, p1d_f = P1D_F (per mode average), p1d_df =
+   P1D_F / F-bar^2, b_f = k_d/F-bar and beta_f = k_e/k_d from the least squares
+   fit F ~ F0 + k_d d + k_e e in each z bin. */
+typedef struct mk_stats_out {
+  double sums[MK_MAX_ZBINS][MK_NSUM];
+  double p1d_sum[MK_MAX_ZBINS][MK_MAX_KBINS];
+  double n_seg[MK_MAX_ZBINS];
+  double mean_flux[MK_MAX_ZBINS];
+  double sigma_f[MK_MAX_ZBINS];
+  double p1d_f[MK_MAX_ZBINS][MK_MAX_KBINS];
+  double p1d_df[MK_MAX_ZBINS][MK_MAX_KBINS];
+  double b_f[MK_MAX_ZBINS];
+  double beta_f[MK_MAX_ZBINS];
+} mk_stats_out;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on `device` using `cuda_stream` (a cudaStream_t, borrowed;
+   NULL = legacy default stream).  Builds the cosmology tables of `cosmo`
+   (Sec. 2, Table 1) on the host in FP64.  Synchronous.  *out is NULL on error. */
+int mk_create(mk_ctx **out, int device, void *cuda_stream, const mk_cosmo *cosmo);
+
+/* Release everything the context owns (not caller buffers).  NULL is a no-op. */
+void mk_destroy(mk_ctx *ctx);
+
+/* Message of the last failing call on this context ("" if none).  The string
+   is owned by the context and valid until its next call. */
+const char *mk_last_error(const mk_ctx *ctx);
+
+/* Change the stream later calls are issued on (borrowed). */
+int mk_set_stream(mk_ctx *ctx, void *cuda_stream);
+
+/* Wait for the context's stream and report (then clear) device-side errors. */
+int mk_sync(mk_ctx *ctx);
+
+/* ---------------------------------------------------------------- boxes */
+
+/* Register a box held in caller-owned device memory (Sec. 2.1: the density
+   box delta_m and the velocity-gradient box, here the single line-of-sight
+   component eta_par).  MK_BOX_PLANAR: d_delta and d_eta each n^3 floats.
+   MK_BOX_INTERLEAVED: d_delta holds 2 n^3 floats (delta, eta) per cell and
+   d_eta must be NULL.  The memory must outlive the box.  Synchronous. */
+int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float *d_delta,
+                const float *d_eta);
+void mk_free_box(mk_box *box);
+
+/* Interleave two planar boxes into d_out (2 n_voxels floats, caller-owned). */
+int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float *d_eta,
+                float *d_out);
+
+/* ---------------------------------------------------------------- skewers */
+
+/* Pre-FGPA skewers (Eq. gfield inputs).  Always computes the geometry of the
+   n_qso quasars in d_qso: d_sk (n_qso records) and d_offsets (n_qso + 1).
+   If h_total_px is not NULL the call synchronises and stores the total pixel
+   count there (a size query).  If d_delta_out and d_eta_out are not NULL it
+   also writes, per pixel, delta_tot = G delta_L + delta_S and eta = G eta_par
+   (FP32, ragged, capacity_px entries available); otherwise they are ignored.
+   delta_S of segment s (pixels s n_fft .. s n_fft + n_fft - 1 of a skewer) is
+   the inverse real DFT (1/N normalisation) of modes
+   X_m = A_m (e1 + i e2)/sqrt(2), 0 < m < N/2, X_{N/2} = A e1, X_0 = 0,
+   A_m = sqrt(N P_S(k_m)/dr), with (e1, e2) the Box-Muller normals of
+   Philox4x32-10 words: counter (m >> 1, s, id >> 32, 0), key (seed, id),
+   words (0,1) for even m and (2,3) for odd m. */
+int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
+                    const mk_skewer_params *params, mk_skewer *d_sk, int64_t *d_offsets,
+                    float *d_delta_out, float *d_eta_out, int64_t capacity_px,
+                    int64_t *h_total_px);
+
+/* FGPA and rebin (Eq. FGPA): F = exp[-a exp(b (delta + c eta))] per fine
+   pixel, then the mean of `rebin` consecutive pixels (incomplete tail
+   dropped).  Writes d_offsets_out (n_sk + 1 entries, floor(n_i/rebin) per
+   skewer) and d_flux (capacity_out entries). */
+int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+            const float *d_delta, const float *d_eta, const mk_fgpa_nodes *nodes,
+            int32_t rebin, float *d_flux, int64_t *d_offsets_out, int64_t capacity_out);
+
+/* Statistics of ragged flux at output resolution `rebin` (d_offsets_out from
+   mk_flux).  d_delta / d_eta are the fine-resolution fields (averaged over
+   the same pixels) or NULL (their sums are then zero).  The z of an output
+   pixel is the mean z of its fine pixels; a P1D segment's z is the mean over
+   the segment.  Synchronous: fills *h_out. */
+int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+             const int64_t *d_offsets_out, const float *d_flux, int32_t rebin,
+             const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
+             mk_stats_out *h_out);
+
+/* The whole path in one pass (rebin 1): geometry, gather, growth, delta_S,
+   FGPA and statistics in one persistent kernel, skipping the stores that
+   `flags` does not ask for.  P1D segments coincide with delta_S segments
+   (bins->n_fft must equal params->n_fft).  d_delta_out / d_eta_out /
+   d_flux_out may be NULL when not stored.  With MK_STATS the call
+   synchronises and fills *h_out; otherwise it is asynchronous. */
+int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
+           const mk_skewer_params *params, const mk_fgpa_nodes *nodes,
+           const mk_stat_bins *bins, uint32_t flags, mk_skewer *d_sk, int64_t *d_offsets,
+           float *d_delta_out, float *d_eta_out, float *d_flux_out, int64_t capacity_px,
+           mk_stats_out *h_out);
+
+/* ---------------------------------------------------------------- timing */
+
+/* When on (non-zero), the library records CUDA events on the context's
+   stream around its main kernel: the skewer pass of mk_make_skewers and
+   mk_run, the statistics pass of mk_stats. */
+int mk_set_timing(mk_ctx *ctx, int on);
+
+/* GPU time in milliseconds of the last timed main-kernel launch.  Waits for
+   that launch to finish.  MK_EINVAL if nothing was timed. */
+int mk_last_kernel_ms(mk_ctx *ctx, double *ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,327 @@
+"""GB300-native Lyman-alpha skewer synthesis (arXiv 2310.18996).
+
+Thin ctypes binding over ``libmockskewer.so`` (declared in
+``include/mockskewer.h``).  This module only marshals arguments: every step
+of the path runs in the library's CUDA kernels.  PyTorch supplies device
+memory and the stream.  There is no CPU fallback: importing succeeds without
+a GPU, but creating a :class:`Context` needs the compiled library and a CUDA
+device and raises otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
+MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
+BOX_PLANAR, BOX_INTERLEAVED = 0, 1
+STORE_FIELDS, STORE_FLUX, STATS = 1, 2, 4
+
+EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
+           "mk_free_box", "mk_pack_box", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
+           "mk_set_timing", "mk_last_kernel_ms"]
+
+
+class MkError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mockskewer error {code}: {msg}")
+        self.code = code
+
+
+class Cosmo(C.Structure):
+    _fields_ = [("omega_m", C.c_double), ("lambda_lya", C.c_double)]
+
+
+class BoxDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("layout", C.c_int32), ("cell", C.c_double),
+                ("origin", C.c_double * 3)]
+
+
+class SkewerParams(C.Structure):
+    _fields_ = [("dr", C.c_double), ("lrf_min", C.c_double), ("lrf_max", C.c_double),
+                ("lobs_min", C.c_double), ("n_min", C.c_int32), ("n_max", C.c_int32),
+                ("n_fft", C.c_int32), ("seed", C.c_uint32), ("h_p_s", C.POINTER(C.c_double))]
+
+
+class FgpaNodes(C.Structure):
+    _fields_ = [("count", C.c_int32), ("z", C.c_double * MAX_NODES),
+                ("ln_a", C.c_double * MAX_NODES), ("b", C.c_double * MAX_NODES),
+                ("c", C.c_double * MAX_NODES)]
+
+
+class StatBins(C.Structure):
+    _fields_ = [("n_z", C.c_int32), ("z_lo", C.c_double), ("dz", C.c_double),
+                ("n_k", C.c_int32), ("n_fft", C.c_int32)]
+
+
+class StatsOut(C.Structure):
+    _fields_ = [
+        ("sums", (C.c_double * NSUM) * MAX_ZBINS),
+        ("p1d_sum", (C.c_double * MAX_KBINS) * MAX_ZBINS),
+        ("n_seg", C.c_double * MAX_ZBINS),
+        ("mean_flux", C.c_double * MAX_ZBINS),
+        ("sigma_f", C.c_double * MAX_ZBINS),
+        ("p1d_f", (C.c_double * MAX_KBINS) * MAX_ZBINS),
+        ("p1d_df", (C.c_double * MAX_KBINS) * MAX_ZBINS),
+        ("b_f", C.c_double * MAX_ZBINS),
+        ("beta_f", C.c_double * MAX_ZBINS),
+    ]
+
+
+SKEWER_BYTES = 72  # sizeof(mk_skewer)
+QSO_DTYPE = np.dtype([("pos", np.float64, 3), ("id", np.uint64)])  # mk_qso, 32 bytes
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libmockskewer.so (building it in-tree if needed); raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            vp, i32, i64, u32 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32
+            P = C.POINTER
+            sig = {
+                "mk_create": (C.c_int, [P(vp), C.c_int, vp, P(Cosmo)]),
+                "mk_destroy": (None, [vp]),
+                "mk_last_error": (C.c_char_p, [vp]),
+                "mk_set_stream": (C.c_int, [vp, vp]),
+                "mk_sync": (C.c_int, [vp]),
+                "mk_load_box": (C.c_int, [vp, P(vp), P(BoxDesc), vp, vp]),
+                "mk_free_box": (None, [vp]),
+                "mk_pack_box": (C.c_int, [vp, i64, vp, vp, vp]),
+                "mk_make_skewers": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), vp, vp, vp, vp,
+                                              i64, P(i64)]),
+                "mk_flux": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, P(FgpaNodes), i32, vp,
+                                      vp, i64]),
+                "mk_stats": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, i32, vp, vp,
+                                       P(StatBins), P(StatsOut)]),
+                "mk_run": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(FgpaNodes), P(StatBins),
+                                     u32, vp, vp, vp, vp, vp, i64, P(StatsOut)]),
+                "mk_set_timing": (C.c_int, [vp, C.c_int]),
+                "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ struct builders
+def skewer_params(w):
+    ps = np.ascontiguousarray(w["p_s"], dtype=np.float64)
+    p = SkewerParams(dr=w["dr"], lrf_min=w["lrf_min"], lrf_max=w["lrf_max"],
+                     lobs_min=w.get("lobs_min", 0.0), n_min=w.get("n_min", 0),
+                     n_max=w.get("n_max", 0), n_fft=w["n_fft"],
+                     seed=w["seed_noise"] & 0xFFFFFFFF,
+                     h_p_s=ps.ctypes.data_as(C.POINTER(C.c_double)))
+    p._keep = ps
+    return p
+
+
+def fgpa_nodes(w):
+    nd = FgpaNodes()
+    z = list(w["node_z"])
+    nd.count = len(z)
+    for i in range(len(z)):
+        nd.z[i], nd.ln_a[i], nd.b[i], nd.c[i] = z[i], w["node_ln_a"][i], w["node_b"][i], w["node_c"][i]
+    return nd
+
+
+def stat_bins(w):
+    return StatBins(n_z=w["n_zbins"], z_lo=w["z_bin_lo"], dz=w["dz_bin"], n_k=w["n_kbins"],
+                    n_fft=w["n_fft_p1d"])
+
+
+def stats_dict(st, n_z, n_k):
+    a = np.ctypeslib.as_array
+    return dict(sums=a(st.sums)[:n_z].copy(), p1d_sum=a(st.p1d_sum)[:n_z, :n_k].copy(),
+                n_seg=a(st.n_seg)[:n_z].copy(), mean_flux=a(st.mean_flux)[:n_z].copy(),
+                sigma_f=a(st.sigma_f)[:n_z].copy(), p1d_f=a(st.p1d_f)[:n_z, :n_k].copy(),
+                p1d_df=a(st.p1d_df)[:n_z, :n_k].copy(), b_f=a(st.b_f)[:n_z].copy(),
+                beta_f=a(st.beta_f)[:n_z].copy())
+
+
+def catalogue_tensor(pos, ids, device="cuda"):
+    """mk_qso records (pos FP64 x3, id) as a uint8 device tensor."""
+    import torch
+
+    rec = np.zeros(len(ids), dtype=QSO_DTYPE)
+    rec["pos"] = np.asarray(pos, dtype=np.float64)
+    rec["id"] = np.asarray(ids, dtype=np.uint64)
+    return torch.from_numpy(rec.view(np.uint8)).to(device)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+# ------------------------------------------------------------------ objects
+class Box:
+    def __init__(self, ctx, handle, desc, keep):
+        self._ctx, self.handle, self.desc, self._keep = ctx, handle, desc, keep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.mk_free_box(self.handle)
+            self.handle = None
+
+
+class Context:
+    """A library context on one CUDA device; calls run on torch's current stream."""
+
+    def __init__(self, device=0, omega_m=0.3147, lambda_lya=1215.67):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("mockskewer needs a CUDA device (no CPU fallback)")
+        self._torch = torch
+        self.device = device
+        L = lib()
+        h = C.c_void_p()
+        cos = Cosmo(omega_m=omega_m, lambda_lya=lambda_lya)
+        with torch.cuda.device(device):
+            rc = L.mk_create(C.byref(h), device, C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                             C.byref(cos))
+        if rc != MK_OK:
+            raise MkError(rc, "mk_create failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != MK_OK:
+            raise MkError(rc, lib().mk_last_error(self.h).decode())
+
+    def _stream(self):
+        s = self._torch.cuda.current_stream(self.device).cuda_stream
+        self._check(lib().mk_set_stream(self.h, C.c_void_p(s)))
+
+    def sync(self):
+        self._check(lib().mk_sync(self.h))
+
+    def set_timing(self, on=True):
+        self._check(lib().mk_set_timing(self.h, 1 if on else 0))
+
+    def last_kernel_ms(self):
+        ms = C.c_double()
+        self._check(lib().mk_last_kernel_ms(self.h, C.byref(ms)))
+        return ms.value
+
+    # boxes
+    def load_box(self, w, delta, eta=None, layout=None):
+        """Register a box (torch float32 tensors on the device) with the recipe's geometry."""
+        if layout is None:
+            layout = BOX_PLANAR if eta is not None else BOX_INTERLEAVED
+        desc = BoxDesc(n=w["n"], layout=layout, cell=w["cell"])
+        for d in range(3):
+            desc.origin[d] = w["origin"][d]
+        h = C.c_void_p()
+        self._check(lib().mk_load_box(self.h, C.byref(h), C.byref(desc), _ptr(delta), _ptr(eta)))
+        return Box(self, h, desc, (delta, eta))
+
+    def pack_box(self, delta, eta):
+        out = self._torch.empty(delta.numel() * 2, dtype=self._torch.float32, device=delta.device)
+        self._stream()
+        self._check(lib().mk_pack_box(self.h, delta.numel(), _ptr(delta), _ptr(eta), _ptr(out)))
+        return out
+
+    # skewers
+    def plan(self, box, qso, n_qso, w):
+        """Geometry only: (skewer records, offsets, total pixels)."""
+        torch = self._torch
+        sk = torch.empty(max(n_qso, 1) * SKEWER_BYTES, dtype=torch.uint8, device=qso.device)
+        off = torch.empty(n_qso + 1, dtype=torch.int64, device=qso.device)
+        total = C.c_int64()
+        p = skewer_params(w)
+        self._stream()
+        self._check(lib().mk_make_skewers(self.h, box.handle, _ptr(qso), n_qso, C.byref(p), _ptr(sk),
+                                          _ptr(off), None, None, 0, C.byref(total)))
+        return sk, off, total.value
+
+    def make_skewers(self, box, qso, n_qso, w):
+        """Pre-FGPA skewers: dict(sk, offsets, delta, eta) as device tensors."""
+        torch = self._torch
+        sk, off, total = self.plan(box, qso, n_qso, w)
+        d = torch.empty(max(total, 1), dtype=torch.float32, device=qso.device)
+        e = torch.empty(max(total, 1), dtype=torch.float32, device=qso.device)
+        p = skewer_params(w)
+        self._stream()
+        self._check(lib().mk_make_skewers(self.h, box.handle, _ptr(qso), n_qso, C.byref(p), _ptr(sk),
+                                          _ptr(off), _ptr(d), _ptr(e), total, None))
+        return dict(sk=sk, offsets=off, delta=d[:total], eta=e[:total], total=total)
+
+    def flux(self, w, sk, n_sk, delta, eta, rebin=1, nodes=None, capacity=None):
+        torch = self._torch
+        total = delta.numel()
+        cap = total // rebin if capacity is None else capacity
+        f = torch.empty(max(cap, 1), dtype=torch.float32, device=delta.device)
+        off = torch.empty(n_sk + 1, dtype=torch.int64, device=delta.device)
+        p = skewer_params(w)
+        nd = fgpa_nodes(w) if nodes is None else nodes
+        self._stream()
+        self._check(lib().mk_flux(self.h, C.byref(p), _ptr(sk), n_sk, _ptr(delta), _ptr(eta), C.byref(nd),
+                                  rebin, _ptr(f), _ptr(off), cap))
+        return f, off
+
+    def stats(self, w, sk, n_sk, offsets_out, flux, rebin=1, delta=None, eta=None):
+        p = skewer_params(w)
+        b = stat_bins(w)
+        st = StatsOut()
+        self._stream()
+        self._check(lib().mk_stats(self.h, C.byref(p), _ptr(sk), n_sk, _ptr(offsets_out), _ptr(flux),
+                                   rebin, _ptr(delta), _ptr(eta), C.byref(b), C.byref(st)))
+        return stats_dict(st, b.n_z, b.n_k)
+
+    def run(self, box, qso, n_qso, w, flags=STATS, capacity=0, outputs=None, nodes=None):
+        """The fused path; returns (stats dict or None, dict of device tensors)."""
+        torch = self._torch
+        o = dict(outputs or {})
+        if "sk" not in o:
+            o["sk"] = torch.empty(max(n_qso, 1) * SKEWER_BYTES, dtype=torch.uint8, device=qso.device)
+            o["offsets"] = torch.empty(n_qso + 1, dtype=torch.int64, device=qso.device)
+        if (flags & (STORE_FIELDS | STORE_FLUX)) and capacity == 0:
+            _, _, capacity = self.plan(box, qso, n_qso, w)
+        if flags & STORE_FIELDS and "delta" not in o:
+            o["delta"] = torch.empty(max(capacity, 1), dtype=torch.float32, device=qso.device)
+            o["eta"] = torch.empty(max(capacity, 1), dtype=torch.float32, device=qso.device)
+        if flags & STORE_FLUX and "flux" not in o:
+            o["flux"] = torch.empty(max(capacity, 1), dtype=torch.float32, device=qso.device)
+        p = skewer_params(w)
+        nd = fgpa_nodes(w) if nodes is None else nodes
+        b = stat_bins(w)
+        st = StatsOut()
+        self._stream()
+        self._check(lib().mk_run(self.h, box.handle, _ptr(qso), n_qso, C.byref(p), C.byref(nd),
+                                 C.byref(b), flags, _ptr(o["sk"]), _ptr(o["offsets"]),
+                                 _ptr(o.get("delta")), _ptr(o.get("eta")), _ptr(o.get("flux")),
+                                 capacity, C.byref(st)))
+        return (stats_dict(st, b.n_z, b.n_k) if flags & STATS else None), o
+
+
+def skewer_records(sk, n):
+    """Host view of mk_skewer records (offset, n, j_lo, p0[3], step[3], id)."""
+    dt = np.dtype([("offset", np.int64), ("n", np.int32), ("j_lo", np.int32),
+                   ("p0", np.int64, 3), ("step", np.int64, 3), ("id", np.uint64)])
+    assert dt.itemsize == SKEWER_BYTES
+    return sk[: n * SKEWER_BYTES].cpu().numpy().view(dt)

@@ -1,0 +1,740 @@
+// C-ABI of the skewer-synthesis library: context, tables, entry points.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mockskewer.h"
+#include "mk_kernels.h"
+
+using namespace mk;
+
+namespace {
+
+constexpr double kCH = 2997.92458;  // c/H0 [Mpc/h]
+constexpr double kZMax = 12.0;      // redshift range of the tables
+constexpr double kDcStep = 1.0 / 512.0;
+
+// ------------------------------------------------------------------ host cosmology
+// Flat LCDM, Omega_L = 1 - Omega_M (Table 1).  D_C is tabulated on a uniform
+// z grid by composite Simpson integration of c/(H0 E); values between nodes
+// come from cubic Hermite interpolation with the exact slopes.  The growth
+// factor solves the linear growth equation in ln a by classical RK4.
+struct HostCosmo {
+  double om = 0.3147;
+  std::vector<double> dc, slope;  // on z_i = i kDcStep
+  std::vector<double> lna, gD, gDp;  // growth D(ln a) and dD/dln a
+  double lna0 = 0.0, dlna = 0.0, d_today = 1.0;
+
+  double e(double z) const {
+    const double zp = 1.0 + z;
+    return std::sqrt(om * zp * zp * zp + (1.0 - om));
+  }
+
+  void build(double omega_m) {
+    om = omega_m;
+    const int n = static_cast<int>(kZMax / kDcStep) + 2;
+    dc.assign(n, 0.0);
+    slope.assign(n, 0.0);
+    const int sub = 32;  // Simpson panels per table step
+    for (int i = 0; i < n; ++i) {
+      const double z = i * kDcStep;
+      slope[i] = kCH / e(z);
+      if (i == 0) continue;
+      const double a = z - kDcStep, hh = kDcStep / sub;
+      double s = kCH / e(a) + kCH / e(z);
+      for (int k = 1; k < sub; ++k) s += (k & 1 ? 4.0 : 2.0) * kCH / e(a + k * hh);
+      dc[i] = dc[i - 1] + s * hh / 3.0;
+    }
+    // growth: y = (D, D'), ' = d/dln a;  D'' + (2 - 1.5 Om(a)) D' - 1.5 Om(a) D = 0
+    // starting deep in matter domination where D = a is the growing mode.
+    const int steps = 24000;
+    lna0 = std::log(1e-4);
+    dlna = -lna0 / steps;
+    lna.resize(steps + 1);
+    gD.resize(steps + 1);
+    gDp.resize(steps + 1);
+    auto om_a = [&](double x) {
+      const double a3 = std::exp(3.0 * x);
+      return om / (om + (1.0 - om) * a3);
+    };
+    auto rhs = [&](double x, double d, double dp, double &dd, double &ddp) {
+      const double w = om_a(x);
+      dd = dp;
+      ddp = -(2.0 - 1.5 * w) * dp + 1.5 * w * d;
+    };
+    double x = lna0, d = std::exp(lna0), dp = d;
+    for (int s = 0; s <= steps; ++s) {
+      lna[s] = x;
+      gD[s] = d;
+      gDp[s] = dp;
+      if (s == steps) break;
+      double k1d, k1p, k2d, k2p, k3d, k3p, k4d, k4p;
+      rhs(x, d, dp, k1d, k1p);
+      rhs(x + 0.5 * dlna, d + 0.5 * dlna * k1d, dp + 0.5 * dlna * k1p, k2d, k2p);
+      rhs(x + 0.5 * dlna, d + 0.5 * dlna * k2d, dp + 0.5 * dlna * k2p, k3d, k3p);
+      rhs(x + dlna, d + dlna * k3d, dp + dlna * k3p, k4d, k4p);
+      d += dlna / 6.0 * (k1d + 2 * k2d + 2 * k3d + k4d);
+      dp += dlna / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p);
+      x += dlna;
+    }
+    d_today = gD[steps];
+  }
+
+  static double hermite(double y0, double y1, double s0, double s1, double h, double t) {
+    const double t2 = t * t, t3 = t2 * t;
+    return (2 * t3 - 3 * t2 + 1) * y0 + (t3 - 2 * t2 + t) * h * s0 + (-2 * t3 + 3 * t2) * y1 +
+           (t3 - t2) * h * s1;
+  }
+
+  double distance(double z) const {
+    double s = z / kDcStep;
+    int i = static_cast<int>(std::floor(s));
+    if (i < 0) i = 0;
+    if (i > static_cast<int>(dc.size()) - 2) i = static_cast<int>(dc.size()) - 2;
+    return hermite(dc[i], dc[i + 1], slope[i], slope[i + 1], kDcStep, s - i);
+  }
+
+  double z_of(double r) const {
+    int lo = 0, hi = static_cast<int>(dc.size()) - 1;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) / 2;
+      if (dc[mid] <= r) lo = mid; else hi = mid;
+    }
+    double z = (lo + (r - dc[lo]) / (dc[hi] - dc[lo])) * kDcStep;
+    for (int it = 0; it < 5; ++it) z -= (distance(z) - r) / (kCH / e(z));
+    return z;
+  }
+
+  double growth(double z) const {
+    const double x = -std::log1p(z);
+    double s = (x - lna0) / dlna;
+    int i = static_cast<int>(std::floor(s));
+    if (i < 0) i = 0;
+    if (i > static_cast<int>(gD.size()) - 2) i = static_cast<int>(gD.size()) - 2;
+    return hermite(gD[i], gD[i + 1], gDp[i], gDp[i + 1], dlna, s - i) / d_today;
+  }
+};
+
+}  // namespace
+
+// ====================================================================== context
+struct mk_box {
+  mk_box_desc desc;
+  const float *d;
+  const float *e;
+  int lgn;
+};
+
+struct mk_ctx {
+  int device = 0;
+  int sms = 0;
+  cudaStream_t stream = nullptr;
+  mk_cosmo cosmo{};
+  std::string err;
+  HostCosmo cos;
+  double2 *d_dc = nullptr;
+  int n_dc = 0;
+  int *d_err = nullptr;
+  int *h_err = nullptr;  // pinned
+  // pixel tables (per dr)
+  double dr = -1.0;
+  int32_t j_max = 0;
+  double *d_zpix = nullptr, *d_cumz = nullptr;
+  float *d_gpix = nullptr;
+  float4 *d_pixtab = nullptr;
+  int16_t *d_zbin = nullptr;
+  bool pixtab_valid = false;
+  mk_fgpa_nodes nodes_key{};
+  bool zbin_valid = false;
+  mk_stat_bins bins_key{};
+  // small-scale amplitudes and twiddles
+  float *d_amp = nullptr;
+  std::vector<double> amp_key;
+  float2 *d_tw[4] = {nullptr, nullptr, nullptr, nullptr};  // N = 256, 512, 1024, 2048
+  // workspaces
+  int64_t *d_cnt_px = nullptr, *d_cnt_seg = nullptr, *d_segoff = nullptr;
+  int64_t cnt_cap = 0;
+  void *d_scan_ws = nullptr;
+  size_t scan_cap = 0;
+  double *d_partials = nullptr;
+  size_t partials_cap = 0;  // doubles
+  mk_stats_out *d_stats = nullptr, *h_stats = nullptr;
+  int64_t *h_total = nullptr;  // pinned
+  int skewer_threads = 256;
+  bool timing = false;
+  bool timed = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+int fail(mk_ctx *ctx, int code, const char *fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof(msg), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess) return fail(ctx, MK_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+int grow(mk_ctx *ctx, void **p, size_t *cap, size_t need) {
+  if (*cap >= need && *p) return MK_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, MK_ENOMEM, "device allocation of %zu bytes failed", need);
+  }
+  *cap = need;
+  return MK_OK;
+}
+
+int ensure_counts(mk_ctx *ctx, int64_t n) {
+  if (ctx->cnt_cap >= n + 1 && ctx->d_cnt_px) return MK_OK;
+  cudaFree(ctx->d_cnt_px);
+  cudaFree(ctx->d_cnt_seg);
+  cudaFree(ctx->d_segoff);
+  ctx->d_cnt_px = ctx->d_cnt_seg = ctx->d_segoff = nullptr;
+  ctx->cnt_cap = 0;
+  const size_t bytes = sizeof(int64_t) * static_cast<size_t>(n + 1);
+  if (cudaMalloc(&ctx->d_cnt_px, bytes) != cudaSuccess || cudaMalloc(&ctx->d_cnt_seg, bytes) != cudaSuccess ||
+      cudaMalloc(&ctx->d_segoff, bytes) != cudaSuccess)
+    return fail(ctx, MK_ENOMEM, "count workspace (%lld skewers)", static_cast<long long>(n));
+  ctx->cnt_cap = n + 1;
+  return grow(ctx, &ctx->d_scan_ws, &ctx->scan_cap, scan_workspace_bytes(n));
+}
+
+int ensure_pixel_tables(mk_ctx *ctx, double dr) {
+  if (ctx->dr == dr && ctx->d_zpix) return MK_OK;
+  const double rmax = ctx->cos.distance(kZMax - 2 * kDcStep);
+  const int32_t jmax = static_cast<int32_t>(std::floor(rmax / dr)) - 1;
+  std::vector<double> z(jmax), cz(jmax + 1);
+  std::vector<float> g(jmax);
+  cz[0] = 0.0;
+  for (int32_t j = 0; j < jmax; ++j) {
+    z[j] = ctx->cos.z_of((j + 0.5) * dr);
+    g[j] = static_cast<float>(ctx->cos.growth(z[j]));
+    cz[j + 1] = cz[j] + z[j];
+  }
+  cudaFree(ctx->d_zpix);
+  cudaFree(ctx->d_cumz);
+  cudaFree(ctx->d_gpix);
+  cudaFree(ctx->d_pixtab);
+  cudaFree(ctx->d_zbin);
+  ctx->d_zpix = ctx->d_cumz = nullptr;
+  ctx->d_gpix = nullptr;
+  ctx->d_pixtab = nullptr;
+  ctx->d_zbin = nullptr;
+  if (cudaMalloc(&ctx->d_zpix, sizeof(double) * jmax) != cudaSuccess ||
+      cudaMalloc(&ctx->d_cumz, sizeof(double) * (jmax + 1)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_gpix, sizeof(float) * jmax) != cudaSuccess ||
+      cudaMalloc(&ctx->d_pixtab, sizeof(float4) * jmax) != cudaSuccess ||
+      cudaMalloc(&ctx->d_zbin, sizeof(int16_t) * jmax) != cudaSuccess)
+    return fail(ctx, MK_ENOMEM, "pixel tables");
+  CK(cudaMemcpy(ctx->d_zpix, z.data(), sizeof(double) * jmax, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_cumz, cz.data(), sizeof(double) * (jmax + 1), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->d_gpix, g.data(), sizeof(float) * jmax, cudaMemcpyHostToDevice));
+  ctx->dr = dr;
+  ctx->j_max = jmax;
+  ctx->pixtab_valid = false;
+  ctx->zbin_valid = false;
+  return MK_OK;
+}
+
+int tw_slot(int n_fft) {
+  switch (n_fft) {
+    case 256: return 0;
+    case 512: return 1;
+    case 1024: return 2;
+    case 2048: return 3;
+  }
+  return -1;
+}
+
+int ensure_twiddles(mk_ctx *ctx, int n_fft) {
+  const int slot = tw_slot(n_fft);
+  if (ctx->d_tw[slot]) return MK_OK;
+  std::vector<float2> tw(n_fft);
+  for (int k = 0; k < n_fft; ++k) {
+    const double a = 2.0 * M_PI * k / n_fft;
+    tw[k] = make_float2(static_cast<float>(std::cos(a)), static_cast<float>(-std::sin(a)));
+  }
+  CK(cudaMalloc(&ctx->d_tw[slot], sizeof(float2) * n_fft));
+  CK(cudaMemcpy(ctx->d_tw[slot], tw.data(), sizeof(float2) * n_fft, cudaMemcpyHostToDevice));
+  return MK_OK;
+}
+
+int ensure_amp(mk_ctx *ctx, const mk_skewer_params *p) {
+  const int m = p->n_fft / 2;
+  std::vector<double> key(m + 3);
+  key[0] = p->n_fft;
+  key[1] = p->dr;
+  for (int i = 0; i <= m; ++i) key[i + 2] = p->h_p_s[i];
+  if (key == ctx->amp_key && ctx->d_amp) return MK_OK;
+  std::vector<float> amp(m + 1);
+  for (int i = 0; i <= m; ++i) {
+    const double ps = p->h_p_s[i];
+    if (!(ps >= 0.0)) return fail(ctx, MK_EINVAL, "P_S[%d] must be >= 0", i);
+    amp[i] = static_cast<float>(std::sqrt(p->n_fft * ps / p->dr) / p->n_fft);
+  }
+  amp[0] = 0.f;
+  cudaFree(ctx->d_amp);
+  ctx->d_amp = nullptr;
+  CK(cudaMalloc(&ctx->d_amp, sizeof(float) * (m + 1)));
+  CK(cudaMemcpy(ctx->d_amp, amp.data(), sizeof(float) * (m + 1), cudaMemcpyHostToDevice));
+  ctx->amp_key = key;
+  return MK_OK;
+}
+
+int check_params(mk_ctx *ctx, const mk_skewer_params *p, bool need_ps) {
+  if (!p) return fail(ctx, MK_EINVAL, "params is NULL");
+  if (!(p->dr > 0.0) || p->dr > 100.0) return fail(ctx, MK_EINVAL, "dr must be in (0, 100]");
+  if (!(p->lrf_min > 0.0) || !(p->lrf_max > p->lrf_min)) return fail(ctx, MK_EINVAL, "bad forest window");
+  if (p->n_min < 0 || p->n_max < 0) return fail(ctx, MK_EINVAL, "n_min/n_max must be >= 0");
+  if (tw_slot(p->n_fft) < 0) return fail(ctx, MK_EINVAL, "n_fft must be 256, 512, 1024 or 2048");
+  if (need_ps && !p->h_p_s) return fail(ctx, MK_EINVAL, "h_p_s is NULL");
+  return MK_OK;
+}
+
+int check_nodes(mk_ctx *ctx, const mk_fgpa_nodes *nd) {
+  if (!nd || nd->count < 1 || nd->count > MK_MAX_NODES) return fail(ctx, MK_EINVAL, "bad FGPA node count");
+  for (int i = 1; i < nd->count; ++i)
+    if (!(nd->z[i] > nd->z[i - 1])) return fail(ctx, MK_EINVAL, "FGPA node z must increase");
+  return MK_OK;
+}
+
+int check_bins(mk_ctx *ctx, const mk_stat_bins *b) {
+  if (!b || b->n_z < 1 || b->n_z > MK_MAX_ZBINS) return fail(ctx, MK_EINVAL, "bad n_z");
+  if (!(b->dz > 0.0)) return fail(ctx, MK_EINVAL, "dz must be > 0");
+  if (tw_slot(b->n_fft) < 0) return fail(ctx, MK_EINVAL, "bins n_fft must be 256, 512, 1024 or 2048");
+  if (b->n_k < 1 || b->n_k > MK_MAX_KBINS || (b->n_fft / 2) % b->n_k)
+    return fail(ctx, MK_EINVAL, "n_k must divide n_fft/2 and be <= %d", MK_MAX_KBINS);
+  return MK_OK;
+}
+
+int ensure_pixtab(mk_ctx *ctx, const mk_fgpa_nodes *nd) {
+  if (ctx->pixtab_valid && std::memcmp(&ctx->nodes_key, nd, sizeof(*nd)) == 0) return MK_OK;
+  CK(launch_pixtab(ctx->d_zpix, ctx->d_gpix, ctx->j_max, *nd, ctx->d_pixtab, ctx->stream));
+  ctx->nodes_key = *nd;
+  ctx->pixtab_valid = true;
+  return MK_OK;
+}
+
+int ensure_zbin(mk_ctx *ctx, const mk_stat_bins *b) {
+  if (ctx->zbin_valid && std::memcmp(&ctx->bins_key, b, sizeof(*b)) == 0) return MK_OK;
+  CK(launch_zbin(ctx->d_zpix, ctx->j_max, b->z_lo, b->dz, b->n_z, ctx->d_zbin, ctx->stream));
+  ctx->bins_key = *b;
+  ctx->zbin_valid = true;
+  return MK_OK;
+}
+
+int read_error_word(mk_ctx *ctx) {
+  CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int e = *ctx->h_err;
+  if (e) {
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (e & ERR_TIMEOUT) return fail(ctx, MK_ETIMEOUT, "a device wait timed out");
+    if (e & ERR_CAPACITY) return fail(ctx, MK_ERANGE, "output larger than the stated capacity");
+    return fail(ctx, MK_ERANGE, "pixel outside the redshift tables (z > %.1f)", kZMax);
+  }
+  return MK_OK;
+}
+
+int time_begin(mk_ctx *ctx) {
+  if (ctx->timing) CK(cudaEventRecord(ctx->ev0, ctx->stream));
+  return MK_OK;
+}
+
+int time_end(mk_ctx *ctx) {
+  if (ctx->timing) {
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    ctx->timed = true;
+  }
+  return MK_OK;
+}
+
+// persistent grids: as many resident CTAs as the SMs hold
+int skewer_grid(mk_ctx *ctx, int n_fft, int layout, int threads, int acc_doubles) {
+  return ctx->sms * skewer_blocks_per_sm(n_fft, layout, threads, acc_doubles);
+}
+
+int stats_grid(mk_ctx *ctx, int n_fft, int threads, int acc_doubles) {
+  return ctx->sms * stats_blocks_per_sm(n_fft, threads, acc_doubles);
+}
+
+int run_geometry(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, const mk_skewer_params *p,
+                 mk_skewer *d_sk, int64_t *d_offsets) {
+  GeomParams G{};
+  G.tab = DcTable{ctx->d_dc, ctx->n_dc, kDcStep, ctx->cosmo.omega_m};
+  G.lambda_lya = ctx->cosmo.lambda_lya;
+  G.dr = p->dr;
+  G.lrf_min = p->lrf_min;
+  G.lrf_max = p->lrf_max;
+  G.lobs_min = p->lobs_min;
+  G.n_min = p->n_min;
+  G.n_max = p->n_max;
+  for (int d = 0; d < 3; ++d) G.origin[d] = box->desc.origin[d];
+  G.cell = box->desc.cell;
+  G.j_max = ctx->j_max;
+  G.n_fft = p->n_fft;
+  G.rebin = 0;
+  CK(launch_geometry(d_qso, n_qso, G, d_sk, ctx->d_cnt_px, ctx->d_cnt_seg, ctx->d_err, ctx->stream));
+  CK(launch_scan(ctx->d_cnt_px, ctx->d_cnt_seg, n_qso, d_offsets, ctx->d_segoff, d_sk, ctx->d_scan_ws,
+                 ctx->stream));
+  return MK_OK;
+}
+
+SkewerParams skewer_params(mk_ctx *ctx, const mk_box *box, const mk_skewer *d_sk, int64_t n, const mk_skewer_params *p) {
+  SkewerParams S{};
+  S.sk = d_sk;
+  S.segoff = ctx->d_segoff;
+  S.n_sk = n;
+  S.box_d = box->d;
+  S.box_e = box->e;
+  S.lgn = box->lgn;
+  S.pixtab = ctx->d_pixtab;
+  S.zbin = ctx->d_zbin;
+  S.cumz = ctx->d_cumz;
+  S.amp = ctx->d_amp;
+  S.tw = ctx->d_tw[tw_slot(p->n_fft)];
+  S.seed = p->seed;
+  S.j_max = ctx->j_max;
+  S.err = ctx->d_err;
+  S.dr = p->dr;
+  return S;
+}
+
+int finish_stats(mk_ctx *ctx, int nparts, const mk_stat_bins *b, mk_stats_out *h_out) {
+  CK(launch_finalize(ctx->d_partials, nparts, b->n_z, b->n_k, b->n_fft, ctx->d_stats, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(mk_stats_out), cudaMemcpyDeviceToHost, ctx->stream));
+  int rc = read_error_word(ctx);  // synchronises
+  if (rc) return rc;
+  std::memcpy(h_out, ctx->h_stats, sizeof(mk_stats_out));
+  return MK_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int mk_create(mk_ctx **out, int device, void *cuda_stream, const mk_cosmo *cosmo) {
+  mk_ctx *ctx = nullptr;
+  if (!out) return MK_EINVAL;
+  *out = nullptr;
+  if (!cosmo || !(cosmo->omega_m > 0.0) || cosmo->omega_m > 1.0 || !(cosmo->lambda_lya > 0.0))
+    return MK_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return MK_ECUDA;
+  ctx = new mk_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->cosmo = *cosmo;
+  ctx->cos.build(cosmo->omega_m);
+  int rc = MK_OK;
+  do {
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { rc = MK_ECUDA; break; }
+    ctx->sms = prop.multiProcessorCount;
+    ctx->n_dc = static_cast<int>(ctx->cos.dc.size());
+    std::vector<double2> tab(ctx->n_dc);
+    for (int i = 0; i < ctx->n_dc; ++i) tab[i] = make_double2(ctx->cos.dc[i], ctx->cos.slope[i]);
+    if (cudaMalloc(&ctx->d_dc, sizeof(double2) * ctx->n_dc) != cudaSuccess ||
+        cudaMemcpy(ctx->d_dc, tab.data(), sizeof(double2) * ctx->n_dc, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_err, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_total, sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_stats, sizeof(mk_stats_out)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_stats, sizeof(mk_stats_out)) != cudaSuccess) {
+      rc = MK_ENOMEM;
+      break;
+    }
+  } while (0);
+  if (rc != MK_OK) {
+    mk_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return MK_OK;
+}
+
+void mk_destroy(mk_ctx *ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->d_dc);
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_err);
+  cudaFreeHost(ctx->h_total);
+  cudaFree(ctx->d_zpix);
+  cudaFree(ctx->d_cumz);
+  cudaFree(ctx->d_gpix);
+  cudaFree(ctx->d_pixtab);
+  cudaFree(ctx->d_zbin);
+  cudaFree(ctx->d_amp);
+  for (auto *p : ctx->d_tw) cudaFree(p);
+  cudaFree(ctx->d_cnt_px);
+  cudaFree(ctx->d_cnt_seg);
+  cudaFree(ctx->d_segoff);
+  cudaFree(ctx->d_scan_ws);
+  cudaFree(ctx->d_partials);
+  cudaFree(ctx->d_stats);
+  cudaFreeHost(ctx->h_stats);
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  delete ctx;
+}
+
+const char *mk_last_error(const mk_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int mk_set_stream(mk_ctx *ctx, void *cuda_stream) {
+  if (!ctx) return MK_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return MK_OK;
+}
+
+int mk_sync(mk_ctx *ctx) {
+  if (!ctx) return MK_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  return read_error_word(ctx);
+}
+
+int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float *d_delta, const float *d_eta) {
+  if (!ctx || !out) return MK_EINVAL;
+  *out = nullptr;
+  if (!desc) return fail(ctx, MK_EINVAL, "desc is NULL");
+  const int n = desc->n;
+  if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
+  if (!(desc->cell > 0.0)) return fail(ctx, MK_EINVAL, "cell must be > 0");
+  if (desc->layout == MK_BOX_PLANAR) {
+    if (!d_delta || !d_eta) return fail(ctx, MK_EINVAL, "planar box needs d_delta and d_eta");
+  } else if (desc->layout == MK_BOX_INTERLEAVED) {
+    if (!d_delta || d_eta) return fail(ctx, MK_EINVAL, "interleaved box: d_delta holds pairs, d_eta must be NULL");
+    if (reinterpret_cast<uintptr_t>(d_delta) % 8) return fail(ctx, MK_EINVAL, "interleaved box must be 8-byte aligned");
+  } else {
+    return fail(ctx, MK_EINVAL, "unknown layout %d", desc->layout);
+  }
+  mk_box *b = new mk_box();
+  b->desc = *desc;
+  b->d = d_delta;
+  b->e = d_eta;
+  b->lgn = 0;
+  while ((1 << b->lgn) < n) ++b->lgn;
+  *out = b;
+  return MK_OK;
+}
+
+void mk_free_box(mk_box *box) { delete box; }
+
+int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float *d_eta, float *d_out) {
+  if (!ctx) return MK_EINVAL;
+  if (n_voxels < 0 || !d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_pack(d_delta, d_eta, n_voxels, d_out, ctx->sms, ctx->stream));
+  return MK_OK;
+}
+
+int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
+                    const mk_skewer_params *params, mk_skewer *d_sk, int64_t *d_offsets, float *d_delta_out,
+                    float *d_eta_out, int64_t capacity_px, int64_t *h_total_px) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_params(ctx, params, d_delta_out != nullptr);
+  if (rc) return rc;
+  if (!box || n_qso < 0 || (n_qso > 0 && !d_qso) || !d_sk || !d_offsets)
+    return fail(ctx, MK_EINVAL, "bad box, catalogue or skewer arguments");
+  if ((d_delta_out == nullptr) != (d_eta_out == nullptr))
+    return fail(ctx, MK_EINVAL, "d_delta_out and d_eta_out go together");
+  CK(cudaSetDevice(ctx->device));
+  if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_qso))) return rc;
+  if ((rc = run_geometry(ctx, box, d_qso, n_qso, params, d_sk, d_offsets))) return rc;
+  if (h_total_px) {
+    CK(cudaMemcpyAsync(ctx->h_total, d_offsets + n_qso, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    if ((rc = read_error_word(ctx))) return rc;
+    *h_total_px = *ctx->h_total;
+  }
+  if (!d_delta_out) return MK_OK;
+  if ((rc = ensure_twiddles(ctx, params->n_fft)) || (rc = ensure_amp(ctx, params))) return rc;
+  // the growth factor is the only table entry this pass reads
+  mk_fgpa_nodes unit{};
+  unit.count = 1;
+  unit.z[0] = 0.0;
+  if (!ctx->pixtab_valid && (rc = ensure_pixtab(ctx, &unit))) return rc;
+  SkewerParams S = skewer_params(ctx, box, d_sk, n_qso, params);
+  S.delta_out = d_delta_out;
+  S.eta_out = d_eta_out;
+  S.flux_out = nullptr;
+  S.capacity = capacity_px;
+  S.do_stats = 0;
+  const int grid = skewer_grid(ctx, params->n_fft, box->desc.layout, ctx->skewer_threads, 0);
+  if ((rc = time_begin(ctx))) return rc;
+  CK(launch_skewer(S, params->n_fft, box->desc.layout, grid, ctx->skewer_threads, ctx->stream));
+  return time_end(ctx);
+}
+
+int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk, const float *d_delta,
+            const float *d_eta, const mk_fgpa_nodes *nodes, int32_t rebin, float *d_flux, int64_t *d_offsets_out,
+            int64_t capacity_out) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_params(ctx, params, false);
+  if (rc || (rc = check_nodes(ctx, nodes))) return rc;
+  if (rebin < 1 || rebin > 4096) return fail(ctx, MK_EINVAL, "rebin must be in [1, 4096]");
+  if (n_sk < 0 || (n_sk > 0 && (!d_sk || !d_delta || !d_eta || !d_flux)) || !d_offsets_out)
+    return fail(ctx, MK_EINVAL, "bad flux arguments");
+  CK(cudaSetDevice(ctx->device));
+  if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_sk)) ||
+      (rc = ensure_pixtab(ctx, nodes)))
+    return rc;
+  CK(launch_out_counts(d_sk, n_sk, rebin, ctx->d_cnt_px, ctx->stream));
+  CK(launch_scan(ctx->d_cnt_px, nullptr, n_sk, d_offsets_out, nullptr, nullptr, ctx->d_scan_ws, ctx->stream));
+  FluxParams F{};
+  F.sk = d_sk;
+  F.off_out = d_offsets_out;
+  F.n_sk = n_sk;
+  F.delta = d_delta;
+  F.eta = d_eta;
+  F.pixtab = ctx->d_pixtab;
+  F.rebin = rebin;
+  F.j_max = ctx->j_max;
+  F.flux = d_flux;
+  F.capacity = capacity_out;
+  F.err = ctx->d_err;
+  CK(launch_flux(F, ctx->sms, ctx->stream));
+  return MK_OK;
+}
+
+int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+             const int64_t *d_offsets_out, const float *d_flux, int32_t rebin, const float *d_delta,
+             const float *d_eta, const mk_stat_bins *bins, mk_stats_out *h_out) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_params(ctx, params, false);
+  if (rc || (rc = check_bins(ctx, bins))) return rc;
+  if (rebin < 1 || rebin > 4096) return fail(ctx, MK_EINVAL, "rebin must be in [1, 4096]");
+  if (!h_out || n_sk < 0 || (n_sk > 0 && (!d_sk || !d_offsets_out || !d_flux)))
+    return fail(ctx, MK_EINVAL, "bad stats arguments");
+  if ((d_delta == nullptr) != (d_eta == nullptr)) return fail(ctx, MK_EINVAL, "d_delta and d_eta go together");
+  CK(cudaSetDevice(ctx->device));
+  if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_sk)) ||
+      (rc = ensure_twiddles(ctx, bins->n_fft)) || (rc = ensure_zbin(ctx, bins)))
+    return rc;
+  const int threads = 256;
+  const StatLayout L{bins->n_z, bins->n_k};
+  const int grid = stats_grid(ctx, bins->n_fft, threads, L.size());
+  if ((rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
+                 sizeof(double) * static_cast<size_t>(grid) * L.size())))
+    return rc;
+  if (n_sk > 0) CK(launch_seg_counts(d_offsets_out, n_sk, bins->n_fft, ctx->d_cnt_seg, ctx->stream));
+  CK(launch_scan(ctx->d_cnt_seg, nullptr, n_sk, ctx->d_segoff, nullptr, nullptr, ctx->d_scan_ws, ctx->stream));
+  StatParams P{};
+  P.sk = d_sk;
+  P.off_out = d_offsets_out;
+  P.segoff = ctx->d_segoff;
+  P.n_sk = n_sk;
+  P.flux = d_flux;
+  P.delta = d_delta;
+  P.eta = d_eta;
+  P.rebin = rebin;
+  P.zbin = ctx->d_zbin;
+  P.cumz = ctx->d_cumz;
+  P.tw = ctx->d_tw[tw_slot(bins->n_fft)];
+  P.j_max = ctx->j_max;
+  P.n_z = bins->n_z;
+  P.n_k = bins->n_k;
+  P.z_lo = bins->z_lo;
+  P.dz = bins->dz;
+  P.dr = params->dr;
+  P.partials = ctx->d_partials;
+  P.err = ctx->d_err;
+  if ((rc = time_begin(ctx))) return rc;
+  CK(launch_stats(P, bins->n_fft, grid, threads, ctx->stream));
+  if ((rc = time_end(ctx))) return rc;
+  return finish_stats(ctx, grid, bins, h_out);
+}
+
+int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, const mk_skewer_params *params,
+           const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, uint32_t flags, mk_skewer *d_sk,
+           int64_t *d_offsets, float *d_delta_out, float *d_eta_out, float *d_flux_out, int64_t capacity_px,
+           mk_stats_out *h_out) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_params(ctx, params, true);
+  if (rc || (rc = check_nodes(ctx, nodes))) return rc;
+  const bool stats = flags & MK_STATS;
+  if (stats) {
+    if ((rc = check_bins(ctx, bins))) return rc;
+    if (bins->n_fft != params->n_fft) return fail(ctx, MK_EINVAL, "fused statistics need bins n_fft == n_fft");
+    if (!h_out) return fail(ctx, MK_EINVAL, "h_out is NULL");
+  }
+  if (!box || n_qso < 0 || (n_qso > 0 && !d_qso) || !d_sk || !d_offsets)
+    return fail(ctx, MK_EINVAL, "bad box, catalogue or skewer arguments");
+  if ((flags & MK_STORE_FIELDS) && (!d_delta_out || !d_eta_out))
+    return fail(ctx, MK_EINVAL, "MK_STORE_FIELDS needs d_delta_out and d_eta_out");
+  if ((flags & MK_STORE_FLUX) && !d_flux_out) return fail(ctx, MK_EINVAL, "MK_STORE_FLUX needs d_flux_out");
+  CK(cudaSetDevice(ctx->device));
+  if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_qso)) ||
+      (rc = ensure_twiddles(ctx, params->n_fft)) || (rc = ensure_amp(ctx, params)) ||
+      (rc = ensure_pixtab(ctx, nodes)))
+    return rc;
+  if (stats && (rc = ensure_zbin(ctx, bins))) return rc;
+  const StatLayout L{stats ? bins->n_z : 0, stats ? bins->n_k : 0};
+  const int grid = skewer_grid(ctx, params->n_fft, box->desc.layout, ctx->skewer_threads, L.size());
+  if (stats && (rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
+                          sizeof(double) * static_cast<size_t>(grid) * L.size())))
+    return rc;
+  if ((rc = run_geometry(ctx, box, d_qso, n_qso, params, d_sk, d_offsets))) return rc;
+  SkewerParams S = skewer_params(ctx, box, d_sk, n_qso, params);
+  S.delta_out = (flags & MK_STORE_FIELDS) ? d_delta_out : nullptr;
+  S.eta_out = (flags & MK_STORE_FIELDS) ? d_eta_out : nullptr;
+  S.flux_out = (flags & MK_STORE_FLUX) ? d_flux_out : nullptr;
+  S.capacity = capacity_px;
+  S.do_stats = stats ? 1 : 0;
+  if (stats) {
+    S.n_z = bins->n_z;
+    S.n_k = bins->n_k;
+    S.z_lo = bins->z_lo;
+    S.dz = bins->dz;
+    S.partials = ctx->d_partials;
+  }
+  if ((rc = time_begin(ctx))) return rc;
+  CK(launch_skewer(S, params->n_fft, box->desc.layout, grid, ctx->skewer_threads, ctx->stream));
+  if ((rc = time_end(ctx))) return rc;
+  if (!stats) return MK_OK;
+  return finish_stats(ctx, grid, bins, h_out);
+}
+
+int mk_set_timing(mk_ctx *ctx, int on) {
+  if (!ctx) return MK_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  if (on && !ctx->ev0) {
+    CK(cudaEventCreate(&ctx->ev0));
+    CK(cudaEventCreate(&ctx->ev1));
+  }
+  ctx->timing = on != 0;
+  ctx->timed = false;
+  return MK_OK;
+}
+
+int mk_last_kernel_ms(mk_ctx *ctx, double *ms) {
+  if (!ctx || !ms) return MK_EINVAL;
+  if (!ctx->timed) return fail(ctx, MK_EINVAL, "no timed launch");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaEventSynchronize(ctx->ev1));
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, ctx->ev0, ctx->ev1));
+  *ms = t;
+  return MK_OK;
+}
+
+}  // extern "C"

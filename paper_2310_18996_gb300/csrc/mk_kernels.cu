@@ -1,0 +1,714 @@
+// Kernels of the skewer-synthesis path (sm_103a) and their host launchers.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "mk_device.cuh"
+#include "mk_kernels.h"
+
+namespace mk {
+
+// =================================================================== geometry
+// D_C(z) by cubic Hermite interpolation of the FP64 table (values + slopes).
+__device__ __forceinline__ double dc_eval(const DcTable &T, double z) {
+  double s = z / T.h;
+  int i = static_cast<int>(floor(s));
+  i = max(0, min(i, T.n - 2));
+  const double t = s - i;
+  const double2 a = T.dc[i], b = T.dc[i + 1];
+  const double t2 = t * t, t3 = t2 * t;
+  return (2.0 * t3 - 3.0 * t2 + 1.0) * a.x + (t3 - 2.0 * t2 + t) * T.h * a.y +
+         (-2.0 * t3 + 3.0 * t2) * b.x + (t3 - t2) * T.h * b.y;
+}
+
+__device__ __forceinline__ double dc_slope(const DcTable &T, double z) {
+  const double zp = 1.0 + z;
+  return 2997.92458 / sqrt(T.omega_m * zp * zp * zp + (1.0 - T.omega_m));
+}
+
+// z(r): bracket by bisection on the tabulated values, then Newton.
+__device__ double z_of_dc(const DcTable &T, double r) {
+  int lo = 0, hi = T.n - 1;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (T.dc[mid].x <= r) lo = mid; else hi = mid;
+  }
+  const double2 a = T.dc[lo], b = T.dc[hi];
+  double z = (lo + (r - a.x) / (b.x - a.x)) * T.h;
+  for (int it = 0; it < 4; ++it) z -= (dc_eval(T, z) - r) / dc_slope(T, z);
+  return z;
+}
+
+__global__ void k_geometry(const mk_qso *__restrict__ q, int64_t nq, GeomParams P, mk_skewer *sk,
+                           int64_t *cnt_px, int64_t *cnt_seg, int *err) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i >= nq) return;
+  const mk_qso Q = q[i];
+  mk_skewer s;
+  s.offset = 0;
+  s.n = 0;
+  s.j_lo = 0;
+  s.id = Q.id;
+  for (int d = 0; d < 3; ++d) s.p0[d] = s.step[d] = 0;
+  const double r = sqrt(Q.pos[0] * Q.pos[0] + Q.pos[1] * Q.pos[1] + Q.pos[2] * Q.pos[2]);
+  if (r > 0.0) {
+    const double zmax = (P.tab.n - 2) * P.tab.h;
+    const double zq = z_of_dc(P.tab, r);
+    double z_lo = (1.0 + zq) * P.lrf_min / P.lambda_lya - 1.0;
+    const double z_hi = (1.0 + zq) * P.lrf_max / P.lambda_lya - 1.0;
+    if (P.lobs_min > 0.0) z_lo = fmax(z_lo, P.lobs_min / P.lambda_lya - 1.0);
+    z_lo = fmax(z_lo, 0.0);
+    int64_t jl = 0, n = 0;
+    if (z_hi > z_lo) {
+      if (z_hi >= zmax) {
+        raise_error(err, ERR_RANGE);
+      } else {
+        const double r_lo = dc_eval(P.tab, z_lo), r_hi = dc_eval(P.tab, z_hi);
+        jl = static_cast<int64_t>(ceil(r_lo / P.dr - 0.5));
+        const int64_t jh = static_cast<int64_t>(ceil(r_hi / P.dr - 0.5));
+        n = jh > jl ? jh - jl : 0;
+        if (P.n_max > 0 && n > P.n_max) {
+          jl = jh - P.n_max;
+          n = P.n_max;
+        }
+        if (n < P.n_min) n = 0;
+        if (n > 0 && (jl < 0 || jl + n > P.j_max)) {
+          raise_error(err, ERR_RANGE);
+          n = 0;
+        }
+      }
+    }
+    s.n = static_cast<int32_t>(n);
+    s.j_lo = static_cast<int32_t>(jl);
+    const double rc = (static_cast<double>(jl) + 0.5) * P.dr;
+    for (int d = 0; d < 3; ++d) {
+      const double u = Q.pos[d] / r;
+      const double c0 = (rc * u - P.origin[d]) / P.cell - 0.5;
+      s.p0[d] = llrint(c0 * 0x1p44);
+      s.step[d] = llrint(P.dr * u / P.cell * 0x1p44);
+    }
+  }
+  sk[i] = s;
+  cnt_px[i] = P.rebin > 0 ? s.n / P.rebin : s.n;
+  cnt_seg[i] = P.n_fft > 0 ? (s.n + P.n_fft - 1) / P.n_fft : 0;
+}
+
+// =================================================================== scan
+// Exclusive prefix sums of two int64 sequences (pixels, segments) in three
+// passes over tiles of SCAN_TILE elements.
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+struct Pair {
+  int64_t a, b;
+};
+
+__device__ __forceinline__ Pair block_exclusive_scan(Pair v, Pair *sh, Pair &total) {
+  const int t = threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+    Pair add = {0, 0};
+    if (t >= off) add = sh[t - off];
+    __syncthreads();
+    sh[t].a += add.a;
+    sh[t].b += add.b;
+    __syncthreads();
+  }
+  total = sh[SCAN_THREADS - 1];
+  Pair ex = {sh[t].a - v.a, sh[t].b - v.b};
+  __syncthreads();
+  return ex;
+}
+
+__global__ void k_scan_tiles(const int64_t *a, const int64_t *b, int64_t n, Pair *tile_sum) {
+  __shared__ Pair sh[SCAN_THREADS];
+  const int64_t base = blockIdx.x * static_cast<int64_t>(SCAN_TILE) + threadIdx.x * SCAN_ITEMS;
+  Pair v = {0, 0};
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) {
+      v.a += a[base + k];
+      v.b += b ? b[base + k] : 0;
+    }
+  }
+  Pair tot;
+  block_exclusive_scan(v, sh, tot);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_tile_sums(Pair *tile_sum, int64_t ntiles) {
+  __shared__ Pair sh[SCAN_THREADS];
+  Pair carry = {0, 0};
+  for (int64_t base = 0; base < ntiles; base += SCAN_THREADS) {
+    const int64_t i = base + threadIdx.x;
+    Pair v = (i < ntiles) ? tile_sum[i] : Pair{0, 0};
+    Pair tot;
+    Pair ex = block_exclusive_scan(v, sh, tot);
+    if (i < ntiles) tile_sum[i] = Pair{ex.a + carry.a, ex.b + carry.b};
+    carry.a += tot.a;
+    carry.b += tot.b;
+  }
+}
+
+__global__ void k_scan_apply(const int64_t *a, const int64_t *b, int64_t n, const Pair *tile_sum,
+                             int64_t *out_a, int64_t *out_b, mk_skewer *sk) {
+  __shared__ Pair sh[SCAN_THREADS];
+  const int64_t base = blockIdx.x * static_cast<int64_t>(SCAN_TILE) + threadIdx.x * SCAN_ITEMS;
+  Pair v = {0, 0};
+  int64_t va[SCAN_ITEMS], vb[SCAN_ITEMS];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    va[k] = (base + k < n) ? a[base + k] : 0;
+    vb[k] = (base + k < n && b) ? b[base + k] : 0;
+    v.a += va[k];
+    v.b += vb[k];
+  }
+  Pair tot;
+  Pair ex = block_exclusive_scan(v, sh, tot);
+  const Pair ts = tile_sum[blockIdx.x];
+  int64_t ra = ts.a + ex.a, rb = ts.b + ex.b;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    if (base + k < n) {
+      out_a[base + k] = ra;
+      if (out_b) out_b[base + k] = rb;
+      if (sk) sk[base + k].offset = ra;
+    }
+    ra += va[k];
+    rb += vb[k];
+  }
+  // the thread holding element n - 1 writes the totals at index n
+  if (base <= n - 1 && n - 1 < base + SCAN_ITEMS) {
+    out_a[n] = ra;
+    if (out_b) out_b[n] = rb;
+  }
+}
+
+// =================================================================== tables
+__global__ void k_pixtab(const double *__restrict__ zpix, const float *__restrict__ gpix, int32_t j_max,
+                         NodeParams nd, float4 *pixtab) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= j_max) return;
+  const double z = zpix[j];
+  double la, b, c;
+  const int k = nd.count;
+  if (z <= nd.z[0]) {
+    la = nd.ln_a[0]; b = nd.b[0]; c = nd.c[0];
+  } else if (z >= nd.z[k - 1]) {
+    la = nd.ln_a[k - 1]; b = nd.b[k - 1]; c = nd.c[k - 1];
+  } else {
+    int i = 0;
+    while (i + 2 < k && z >= nd.z[i + 1]) ++i;
+    const double w = (z - nd.z[i]) / (nd.z[i + 1] - nd.z[i]);
+    la = (1.0 - w) * nd.ln_a[i] + w * nd.ln_a[i + 1];
+    b = (1.0 - w) * nd.b[i] + w * nd.b[i + 1];
+    c = (1.0 - w) * nd.c[i] + w * nd.c[i + 1];
+  }
+  const double log2e = 1.4426950408889634;
+  pixtab[j] = make_float4(gpix[j], static_cast<float>(exp(la) * log2e), static_cast<float>(b * log2e),
+                          static_cast<float>(c));
+}
+
+__global__ void k_zbin(const double *__restrict__ zpix, int32_t j_max, double z_lo, double dz, int n_z,
+                       int16_t *zbin) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= j_max) return;
+  const double f = floor((zpix[j] - z_lo) / dz);
+  zbin[j] = static_cast<int16_t>(f < 0.0 ? -1 : (f >= n_z ? n_z : static_cast<int>(f)));
+}
+
+__global__ void k_pack(const float *__restrict__ d, const float *__restrict__ e, int64_t n, float2 *out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    out[i] = make_float2(d[i], e[i]);
+}
+
+__global__ void k_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) cnt[i] = sk[i].n / rebin;
+}
+
+__global__ void k_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt) {
+  const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (i < n) cnt[i] = (off[i + 1] - off[i] + n_fft - 1) / n_fft;
+}
+
+// =================================================================== shared-memory plan
+template <int N>
+struct TeamSmem {
+  static constexpr int T = N / 8;
+  static constexpr int BUF = N / 2 + 2;  // complex entries (N/2 + 1, padded even)
+  static constexpr int RED = (T / 32) * MK_NSUM;
+  static size_t bytes(int teams, int acc_doubles) {
+    return teams * (sizeof(double) * acc_doubles + sizeof(float2) * BUF + sizeof(float) * RED);
+  }
+};
+
+// largest i with a[i] <= v over a[0..n] (a non-decreasing)
+__device__ __forceinline__ int64_t upper_index(const int64_t *a, int64_t n, int64_t v) {
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void flush_partials(double *acc_all, int teams, int size, double *partials) {
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < size; idx += blockDim.x) {
+    double s = 0.0;
+    for (int tm = 0; tm < teams; ++tm) s += acc_all[tm * size + idx];
+    partials[static_cast<size_t>(blockIdx.x) * size + idx] = s;
+  }
+}
+
+// =================================================================== fused skewer kernel
+// One team per segment of N pixels: small-scale modes -> inverse real FFT ->
+// gather + growth per pixel -> FGPA -> stores -> pixel statistics -> forward
+// FFT of the flux -> P1D.  Teams take contiguous ranges of segments.
+template <int N, int LAYOUT>
+__global__ void __launch_bounds__(256) k_skewer(SkewerParams P) {
+  constexpr int T = N / 8;
+  using S = TeamSmem<N>;
+  const int teams = blockDim.x / T;
+  const int team = threadIdx.x / T, t = threadIdx.x % T;
+  const StatLayout L{P.n_z, P.n_k};
+  const int acc_size = P.do_stats ? L.size() : 0;
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *acc_all = reinterpret_cast<double *>(smem);
+  float2 *buf = reinterpret_cast<float2 *>(acc_all + teams * acc_size) + team * S::BUF;
+  float *red = reinterpret_cast<float *>(reinterpret_cast<float2 *>(acc_all + teams * acc_size) +
+                                         teams * S::BUF) + team * S::RED;
+  double *acc = acc_all + team * acc_size;
+  for (int i = t; i < acc_size; i += T) acc[i] = 0.0;
+
+  Twiddles<N> tw;
+  load_twiddles<N>(tw, P.tw, t);
+
+  const int64_t nunits = P.segoff[P.n_sk];
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
+  int64_t u = g * nunits / G;
+  const int64_t uend = (g + 1) * nunits / G;
+  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
+  const float *fbuf = reinterpret_cast<const float *>(buf);
+  team_sync<T>(team);
+
+  for (; u < uend; ++u) {
+    while (P.segoff[i + 1] <= u) ++i;
+    const int s = static_cast<int>(u - P.segoff[i]);
+    const mk_skewer sk = P.sk[i];
+    const int64_t j0 = static_cast<int64_t>(s) * N;
+    const int npx = static_cast<int>(min(static_cast<int64_t>(N), sk.n - j0));
+    if ((P.delta_out || P.flux_out) && sk.offset + sk.n > P.capacity) {
+      if (t == 0) raise_error(P.err, ERR_CAPACITY);
+      continue;
+    }
+    // ---- small-scale field of this segment
+    small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
+    team_sync<T>(team);
+    inverse_real_fft<N>(buf, tw, t, team);
+    float ds[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) ds[k] = fbuf[t + T * k];
+
+    // ---- gather, growth, FGPA
+    float dt[8], eg[8], f[8];
+    int zb[8];
+    int64_t px = sk.p0[0] + (j0 + t) * sk.step[0];
+    int64_t py = sk.p0[1] + (j0 + t) * sk.step[1];
+    int64_t pz = sk.p0[2] + (j0 + t) * sk.step[2];
+    const int64_t sx = T * sk.step[0], sy = T * sk.step[1], sz = T * sk.step[2];
+    const int64_t out0 = sk.offset + j0;
+    const int jb = sk.j_lo + static_cast<int>(j0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int p = t + T * k;
+      if (p < npx) {
+        const float2 de = gather<LAYOUT>(P.box_d, P.box_e, P.lgn, px, py, pz);
+        const float4 tb = __ldg(P.pixtab + jb + p);
+        dt[k] = fmaf(tb.x, de.x, ds[k]);
+        eg[k] = tb.x * de.y;
+        f[k] = fgpa(tb, dt[k], eg[k]);
+        zb[k] = P.do_stats ? __ldg(P.zbin + jb + p) : -1;
+        if (P.delta_out) {
+          P.delta_out[out0 + p] = dt[k];
+          P.eta_out[out0 + p] = eg[k];
+        }
+        if (P.flux_out) P.flux_out[out0 + p] = f[k];
+      } else {
+        dt[k] = eg[k] = f[k] = 0.f;
+        zb[k] = -1;
+      }
+      px += sx;
+      py += sy;
+      pz += sz;
+    }
+
+    // ---- statistics
+    if (P.do_stats) {
+      const int zf = __ldg(P.zbin + jb), zl = __ldg(P.zbin + jb + npx - 1);
+      accumulate_pixels<T>(acc, L, f, dt, eg, zb, zf, zl, red, t, team);
+      if (npx == N) {
+        const double zm = (P.cumz[jb + N] - P.cumz[jb]) / N;
+        const double fz = floor((zm - P.z_lo) / P.dz);
+        if (fz >= 0.0 && fz < P.n_z) {
+          float *fw = reinterpret_cast<float *>(buf);
+          team_sync<T>(team);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) fw[t + T * k] = f[k];
+          forward_packed_fft<N>(buf, tw, t, team);
+          float pk[4];
+          power_of_modes<N>(buf, P.tw, t, pk);
+          accumulate_p1d<N>(acc, L, pk, static_cast<float>(P.dr / N), static_cast<int>(fz), t);
+        }
+      }
+    }
+    team_sync<T>(team);
+  }
+  if (P.do_stats) flush_partials(acc_all, teams, acc_size, P.partials);
+}
+
+// =================================================================== flux kernel
+__global__ void __launch_bounds__(256) k_flux(FluxParams P) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t i = warp; i < P.n_sk; i += nwarps) {
+    const mk_skewer sk = P.sk[i];
+    const int64_t o = P.off_out[i];
+    const int64_t nout = P.off_out[i + 1] - o;
+    if (o + nout > P.capacity) {
+      if (lane == 0) raise_error(P.err, ERR_CAPACITY);
+      continue;
+    }
+    for (int64_t k = lane; k < nout; k += 32) {
+      float s = 0.f;
+      for (int r = 0; r < P.rebin; ++r) {
+        const int64_t j = k * P.rebin + r;
+        const float4 tb = __ldg(P.pixtab + sk.j_lo + j);
+        s += fgpa(tb, P.delta[sk.offset + j], P.eta[sk.offset + j]);
+      }
+      P.flux[o + k] = P.rebin == 1 ? s : s / static_cast<float>(P.rebin);
+    }
+  }
+}
+
+// =================================================================== statistics kernel
+template <int N>
+__global__ void __launch_bounds__(256) k_stats(StatParams P) {
+  constexpr int T = N / 8;
+  using S = TeamSmem<N>;
+  const int teams = blockDim.x / T;
+  const int team = threadIdx.x / T, t = threadIdx.x % T;
+  const StatLayout L{P.n_z, P.n_k};
+  const int acc_size = L.size();
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *acc_all = reinterpret_cast<double *>(smem);
+  float2 *buf = reinterpret_cast<float2 *>(acc_all + teams * acc_size) + team * S::BUF;
+  float *red = reinterpret_cast<float *>(reinterpret_cast<float2 *>(acc_all + teams * acc_size) +
+                                         teams * S::BUF) + team * S::RED;
+  double *acc = acc_all + team * acc_size;
+  for (int i = t; i < acc_size; i += T) acc[i] = 0.0;
+  Twiddles<N> tw;
+  load_twiddles<N>(tw, P.tw, t);
+
+  const int64_t nunits = P.segoff[P.n_sk];
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
+  int64_t u = g * nunits / G;
+  const int64_t uend = (g + 1) * nunits / G;
+  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
+  const int R = P.rebin;
+  team_sync<T>(team);
+
+  for (; u < uend; ++u) {
+    while (P.segoff[i + 1] <= u) ++i;
+    const int s = static_cast<int>(u - P.segoff[i]);
+    const mk_skewer sk = P.sk[i];
+    const int64_t o = P.off_out[i];
+    const int64_t nout = P.off_out[i + 1] - o;
+    const int64_t k0 = static_cast<int64_t>(s) * N;
+    const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
+    float f[8], d[8], e[8];
+    int zb[8];
+    auto zbin_of = [&](int64_t k) -> int {
+      const int64_t J = sk.j_lo + k * R;
+      if (R == 1) return __ldg(P.zbin + J);
+      const double fz = floor(((P.cumz[J + R] - P.cumz[J]) / R - P.z_lo) / P.dz);
+      return fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
+    };
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int p = t + T * q;
+      if (p < npx) {
+        const int64_t k = k0 + p;
+        f[q] = P.flux[o + k];
+        float ds = 0.f, es = 0.f;
+        if (P.delta) {
+          for (int r = 0; r < R; ++r) {
+            ds += P.delta[sk.offset + k * R + r];
+            es += P.eta[sk.offset + k * R + r];
+          }
+          if (R > 1) {
+            ds /= static_cast<float>(R);
+            es /= static_cast<float>(R);
+          }
+        }
+        d[q] = ds;
+        e[q] = es;
+        zb[q] = zbin_of(k);
+      } else {
+        f[q] = d[q] = e[q] = 0.f;
+        zb[q] = -1;
+      }
+    }
+    const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
+    accumulate_pixels<T>(acc, L, f, d, e, zb, zf, zl, red, t, team);
+    if (npx == N) {
+      const int64_t J0 = sk.j_lo + k0 * R;
+      const double zm = (P.cumz[J0 + static_cast<int64_t>(N) * R] - P.cumz[J0]) / (static_cast<double>(N) * R);
+      const double fz = floor((zm - P.z_lo) / P.dz);
+      if (fz >= 0.0 && fz < P.n_z) {
+        float *fw = reinterpret_cast<float *>(buf);
+        team_sync<T>(team);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) fw[t + T * q] = f[q];
+        forward_packed_fft<N>(buf, tw, t, team);
+        float pk[4];
+        power_of_modes<N>(buf, P.tw, t, pk);
+        accumulate_p1d<N>(acc, L, pk, static_cast<float>(R * P.dr / N), static_cast<int>(fz), t);
+      }
+    }
+    team_sync<T>(team);
+  }
+  flush_partials(acc_all, teams, acc_size, P.partials);
+}
+
+// =================================================================== finalize
+__global__ void k_finalize(const double *__restrict__ partials, int nparts, int n_z, int n_k, int n_fft,
+                           mk_stats_out *out) {
+  extern __shared__ double tot[];
+  const StatLayout L{n_z, n_k};
+  const int size = L.size();
+  for (int idx = threadIdx.x; idx < size; idx += blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += partials[static_cast<size_t>(c) * size + idx];
+    tot[idx] = s;
+  }
+  // zero the output struct
+  double *o = reinterpret_cast<double *>(out);
+  for (int idx = threadIdx.x; idx < static_cast<int>(sizeof(mk_stats_out) / sizeof(double)); idx += blockDim.x)
+    o[idx] = 0.0;
+  __syncthreads();
+  const double per_bin = static_cast<double>(n_fft / 2) / n_k;
+  for (int zb = threadIdx.x; zb < n_z; zb += blockDim.x) {
+    for (int i = 0; i < MK_NSUM; ++i) out->sums[zb][i] = tot[L.sums(zb, i)];
+    for (int k = 0; k < n_k; ++k) out->p1d_sum[zb][k] = tot[L.p1d(zb, k)];
+    const double ns = tot[L.nseg(zb)];
+    out->n_seg[zb] = ns;
+    const double *s = &tot[L.sums(zb, 0)];
+    const double n = s[0];
+    if (n <= 0.0) continue;
+    const double fbar = s[1] / n;
+    out->mean_flux[zb] = fbar;
+    const double varf = s[2] / n - fbar * fbar;
+    out->sigma_f[zb] = varf > 0.0 ? sqrt(varf) : 0.0;
+    const double md = s[3] / n, me = s[4] / n;
+    const double cdd = s[5] / n - md * md, cee = s[6] / n - me * me, cde = s[7] / n - md * me;
+    const double vfd = s[8] / n - fbar * md, vfe = s[9] / n - fbar * me;
+    const double det = cdd * cee - cde * cde;
+    if (det != 0.0) {
+      const double kd = (cee * vfd - cde * vfe) / det;
+      const double ke = (cdd * vfe - cde * vfd) / det;
+      out->b_f[zb] = kd / fbar;
+      out->beta_f[zb] = kd != 0.0 ? ke / kd : 0.0;
+    }
+    if (ns > 0.0) {
+      for (int k = 0; k < n_k; ++k) {
+        out->p1d_f[zb][k] = tot[L.p1d(zb, k)] / (ns * per_bin);
+        out->p1d_df[zb][k] = out->p1d_f[zb][k] / (fbar * fbar);
+      }
+    }
+  }
+}
+
+// =================================================================== launchers
+static int blocks_for(int64_t n, int threads) { return static_cast<int>((n + threads - 1) / threads); }
+
+cudaError_t launch_geometry(const mk_qso *q, int64_t nq, const GeomParams &P, mk_skewer *sk, int64_t *cnt_px,
+                            int64_t *cnt_seg, int *err, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  k_geometry<<<blocks_for(nq, 128), 128, 0, st>>>(q, nq, P, sk, cnt_px, cnt_seg, err);
+  return cudaGetLastError();
+}
+
+size_t scan_workspace_bytes(int64_t n) {
+  return sizeof(Pair) * static_cast<size_t>((n + SCAN_TILE - 1) / SCAN_TILE + 1);
+}
+
+cudaError_t launch_scan(const int64_t *a, const int64_t *b, int64_t n, int64_t *out_a, int64_t *out_b,
+                        mk_skewer *sk, void *ws, cudaStream_t st) {
+  if (n == 0) {
+    cudaError_t e = cudaMemsetAsync(out_a, 0, sizeof(int64_t), st);
+    if (e == cudaSuccess && out_b) e = cudaMemsetAsync(out_b, 0, sizeof(int64_t), st);
+    return e;
+  }
+  const int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  Pair *ts = static_cast<Pair *>(ws);
+  k_scan_tiles<<<static_cast<unsigned>(ntiles), SCAN_THREADS, 0, st>>>(a, b, n, ts);
+  k_scan_tile_sums<<<1, SCAN_THREADS, 0, st>>>(ts, ntiles);
+  k_scan_apply<<<static_cast<unsigned>(ntiles), SCAN_THREADS, 0, st>>>(a, b, n, ts, out_a, out_b, sk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, const NodeParams &nd,
+                          float4 *pixtab, cudaStream_t st) {
+  k_pixtab<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, gpix, j_max, nd, pixtab);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zbin(const double *zpix, int32_t j_max, double z_lo, double dz, int n_z, int16_t *zbin,
+                        cudaStream_t st) {
+  k_zbin<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, j_max, z_lo, dz, n_z, zbin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st) {
+  k_pack<<<sms * 8, 256, 0, st>>>(d, e, n, reinterpret_cast<float2 *>(out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_out_counts<<<blocks_for(n, 256), 256, 0, st>>>(sk, n, rebin, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_seg_counts<<<blocks_for(n, 256), 256, 0, st>>>(off, n, n_fft, cnt);
+  return cudaGetLastError();
+}
+
+template <int N, int LAYOUT>
+static cudaError_t skewer_dispatch(const SkewerParams &P, int grid, int threads, size_t smem, cudaStream_t st) {
+  auto kern = k_skewer<N, LAYOUT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+size_t skewer_smem_bytes(int n_fft, int threads, int acc_doubles) {
+  const int teams = threads / (n_fft / 8);
+  switch (n_fft) {
+    case 256: return TeamSmem<256>::bytes(teams, acc_doubles);
+    case 512: return TeamSmem<512>::bytes(teams, acc_doubles);
+    case 1024: return TeamSmem<1024>::bytes(teams, acc_doubles);
+    case 2048: return TeamSmem<2048>::bytes(teams, acc_doubles);
+  }
+  return 0;
+}
+
+template <int N, int LAYOUT>
+static int skewer_occ(int threads, size_t smem) {
+  int b = 0;
+  cudaFuncSetAttribute(k_skewer<N, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_skewer<N, LAYOUT>, threads, smem) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+int skewer_blocks_per_sm(int n_fft, int layout, int threads, int acc_doubles) {
+  const size_t smem = skewer_smem_bytes(n_fft, threads, acc_doubles);
+  const bool il = layout == MK_BOX_INTERLEAVED;
+  switch (n_fft) {
+    case 256: return il ? skewer_occ<256, 1>(threads, smem) : skewer_occ<256, 0>(threads, smem);
+    case 512: return il ? skewer_occ<512, 1>(threads, smem) : skewer_occ<512, 0>(threads, smem);
+    case 1024: return il ? skewer_occ<1024, 1>(threads, smem) : skewer_occ<1024, 0>(threads, smem);
+    case 2048: return il ? skewer_occ<2048, 1>(threads, smem) : skewer_occ<2048, 0>(threads, smem);
+  }
+  return 1;
+}
+
+template <int N>
+static int stats_occ(int threads, int acc_doubles) {
+  const size_t smem = TeamSmem<N>::bytes(threads / (N / 8), acc_doubles);
+  int b = 0;
+  cudaFuncSetAttribute(k_stats<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stats<N>, threads, smem) != cudaSuccess) return 1;
+  return b > 0 ? b : 1;
+}
+
+int stats_blocks_per_sm(int n_fft, int threads, int acc_doubles) {
+  switch (n_fft) {
+    case 256: return stats_occ<256>(threads, acc_doubles);
+    case 512: return stats_occ<512>(threads, acc_doubles);
+    case 1024: return stats_occ<1024>(threads, acc_doubles);
+    case 2048: return stats_occ<2048>(threads, acc_doubles);
+  }
+  return 1;
+}
+
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads,
+                          cudaStream_t st) {
+  const size_t smem = skewer_smem_bytes(n_fft, threads, P.do_stats ? StatLayout{P.n_z, P.n_k}.size() : 0);
+  if (layout == MK_BOX_INTERLEAVED) {
+    switch (n_fft) {
+      case 256: return skewer_dispatch<256, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
+      case 512: return skewer_dispatch<512, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
+      case 1024: return skewer_dispatch<1024, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
+      case 2048: return skewer_dispatch<2048, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
+    }
+  } else {
+    switch (n_fft) {
+      case 256: return skewer_dispatch<256, MK_BOX_PLANAR>(P, grid, threads, smem, st);
+      case 512: return skewer_dispatch<512, MK_BOX_PLANAR>(P, grid, threads, smem, st);
+      case 1024: return skewer_dispatch<1024, MK_BOX_PLANAR>(P, grid, threads, smem, st);
+      case 2048: return skewer_dispatch<2048, MK_BOX_PLANAR>(P, grid, threads, smem, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st) {
+  if (P.n_sk == 0) return cudaSuccess;
+  const int64_t warps = P.n_sk;
+  int grid = blocks_for(warps * 32, 256);
+  if (grid > sms * 16) grid = sms * 16;
+  k_flux<<<grid, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t stats_dispatch(const StatParams &P, int grid, int threads, cudaStream_t st) {
+  const size_t smem = TeamSmem<N>::bytes(threads / (N / 8), StatLayout{P.n_z, P.n_k}.size());
+  auto kern = k_stats<N>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st) {
+  switch (n_fft) {
+    case 256: return stats_dispatch<256>(P, grid, threads, st);
+    case 512: return stats_dispatch<512>(P, grid, threads, st);
+    case 1024: return stats_dispatch<1024>(P, grid, threads, st);
+    case 2048: return stats_dispatch<2048>(P, grid, threads, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_finalize(const double *partials, int nparts, int n_z, int n_k, int n_fft, mk_stats_out *out,
+                            cudaStream_t st) {
+  const size_t smem = sizeof(double) * StatLayout{n_z, n_k}.size();
+  cudaError_t e = cudaFuncSetAttribute(k_finalize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_finalize<<<1, 512, smem, st>>>(partials, nparts, n_z, n_k, n_fft, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mk

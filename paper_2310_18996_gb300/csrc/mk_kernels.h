@@ -1,0 +1,34 @@
+// Host-side launchers of the kernels in mk_kernels.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mk_params.h"
+
+namespace mk {
+
+cudaError_t launch_geometry(const mk_qso *q, int64_t nq, const GeomParams &P, mk_skewer *sk, int64_t *cnt_px,
+                            int64_t *cnt_seg, int *err, cudaStream_t st);
+size_t scan_workspace_bytes(int64_t n);
+// exclusive prefix sums (n + 1 outputs) of a (and b if not NULL); also
+// stores the pixel offset into sk[i].offset when sk is not NULL
+cudaError_t launch_scan(const int64_t *a, const int64_t *b, int64_t n, int64_t *out_a, int64_t *out_b,
+                        mk_skewer *sk, void *ws, cudaStream_t st);
+cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, const NodeParams &nd,
+                          float4 *pixtab, cudaStream_t st);
+cudaError_t launch_zbin(const double *zpix, int32_t j_max, double z_lo, double dz, int n_z, int16_t *zbin,
+                        cudaStream_t st);
+cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
+cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);
+cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st);
+int skewer_blocks_per_sm(int n_fft, int layout, int threads, int acc_doubles);
+int stats_blocks_per_sm(int n_fft, int threads, int acc_doubles);
+size_t skewer_smem_bytes(int n_fft, int threads, int acc_doubles);
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads,
+                          cudaStream_t st);
+cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);
+cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st);
+cudaError_t launch_finalize(const double *partials, int nparts, int n_z, int n_k, int n_fft, mk_stats_out *out,
+                            cudaStream_t st);
+
+}  // namespace mk

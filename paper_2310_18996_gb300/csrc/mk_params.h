@@ -1,0 +1,104 @@
+// Kernel parameter blocks shared by the host launch code and the kernels.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/mockskewer.h"
+
+namespace mk {
+
+// error bits of the device error word
+enum : int { ERR_RANGE = 1, ERR_CAPACITY = 2, ERR_TIMEOUT = 4 };
+
+// Cubic-Hermite table of D_C(z) on z_i = i h: values and slopes c/(H0 E(z_i)).
+struct DcTable {
+  const double2 *dc;  // {D_C(z_i), dD_C/dz(z_i)}
+  int n;              // entries
+  double h;           // z spacing
+  double omega_m;     // for E(z) in the Newton inversion
+};
+
+struct GeomParams {
+  DcTable tab;
+  double lambda_lya, dr, lrf_min, lrf_max, lobs_min;
+  int32_t n_min, n_max;
+  double origin[3], cell;
+  int32_t j_max;  // pixel tables cover J < j_max
+  int32_t n_fft;  // segment length for the segment count (0: none)
+  int32_t rebin;  // > 0: write floor(n / rebin) counts instead (flux offsets)
+};
+
+using NodeParams = mk_fgpa_nodes;
+
+// FP64 accumulators of one team in shared memory:
+//   sums[n_z][NSUM], p1d[n_z][n_k], nseg[n_z]
+struct StatLayout {
+  int n_z, n_k;
+  __host__ __device__ int sums(int zb, int i) const { return zb * MK_NSUM + i; }
+  __host__ __device__ int p1d(int zb, int k) const { return n_z * MK_NSUM + zb * n_k + k; }
+  __host__ __device__ int nseg(int zb) const { return n_z * (MK_NSUM + n_k) + zb; }
+  __host__ __device__ int size() const { return n_z * (MK_NSUM + n_k + 1); }
+};
+
+
+// Everything the fused / split skewer kernels read.
+struct SkewerParams {
+  const mk_skewer *sk;
+  const int64_t *segoff;  // exclusive prefix of segments per skewer, n_sk + 1
+  int64_t n_sk;
+  // box
+  const float *box_d;  // planar delta, or interleaved (delta, eta)
+  const float *box_e;  // planar eta or NULL
+  int32_t lgn;
+  // tables
+  const float4 *pixtab;  // per global pixel J: {G, a log2e, b log2e, c}
+  const int16_t *zbin;   // per J: z bin, -1 below, n_z above
+  const double *cumz;    // per J: sum_{J' < J} z_J'
+  const float *amp;      // A_m / N, m = 0..N/2
+  const float2 *tw;      // e^{-2 pi i k/N}, k < N
+  uint32_t seed;
+  int32_t j_max;
+  // outputs
+  float *delta_out, *eta_out, *flux_out;
+  int64_t capacity;
+  // statistics
+  int32_t do_stats;
+  int32_t n_z, n_k;
+  double z_lo, dz, dr;
+  double *partials;  // [gridDim.x][layout size]
+  int *err;
+};
+
+// Statistics pass over stored flux (any rebin).
+struct StatParams {
+  const mk_skewer *sk;
+  const int64_t *off_out;  // output offsets, n_sk + 1
+  const int64_t *segoff;   // prefix of ceil(n_out / N) per skewer
+  int64_t n_sk;
+  const float *flux;
+  const float *delta, *eta;  // fine fields or NULL
+  int32_t rebin;
+  const int16_t *zbin;
+  const double *cumz;
+  const float2 *tw;
+  int32_t j_max;
+  int32_t n_z, n_k;
+  double z_lo, dz, dr;
+  double *partials;
+  int *err;
+};
+
+struct FluxParams {
+  const mk_skewer *sk;
+  const int64_t *off_out;
+  int64_t n_sk;
+  const float *delta, *eta;
+  const float4 *pixtab;
+  int32_t rebin;
+  int32_t j_max;
+  float *flux;
+  int64_t capacity;
+  int *err;
+};
+
+}  // namespace mk

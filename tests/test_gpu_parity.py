@@ -1,0 +1,273 @@
+"""GPU path vs the FP64 oracle, element by element, through the C-ABI.
+
+Sizes: the 64^3 / 500-quasar workload in full (several FFT segments per
+skewer and a ragged tail), the 512^3 / 100k and 1024^3 / 1M workloads on
+sampled skewers in the launch configuration the benchmark times, plus
+edge cases (empty catalogue, zero-length skewers, capacity overflow, bad
+arguments, every supported FFT length, both box layouts).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import skewer_inputs as si
+from tests.parity_util import (TOL_STAT, assert_field_close, assert_flux_close, assert_stats_close,
+                               box_numpy, oracle_subset, ragged)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2310_18996_gb300 as mk  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = mk.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = si.workload("tiny")
+    d, e = box_numpy(w)
+    pos, ids = si.catalogue(w)
+    orc = oracle.run_skewers(w, d, e, pos, ids, n_threads=16)
+    st = oracle.stats(w, orc["j_lo"], orc["offsets"], orc["offsets_out"], orc["flux"], orc["delta"], orc["eta"])
+    dev = dict(d=torch.from_numpy(d).cuda(), e=torch.from_numpy(e).cuda(),
+               qso=mk.catalogue_tensor(pos, ids))
+    return dict(w=w, d=d, e=e, pos=pos, ids=ids, orc=orc, st=st, dev=dev)
+
+
+def records(sk, n):
+    return mk.skewer_records(sk, n)
+
+
+# ------------------------------------------------------------------ tiny workload, full
+def test_geometry_matches_oracle_exactly(ctx, tiny):
+    w, o = tiny["w"], tiny["orc"]
+    box = ctx.load_box(w, tiny["dev"]["d"], tiny["dev"]["e"])
+    sk, off, total = ctx.plan(box, tiny["dev"]["qso"], len(tiny["ids"]), w)
+    rec = records(sk, len(tiny["ids"]))
+    np.testing.assert_array_equal(rec["n"], o["npix"])
+    np.testing.assert_array_equal(rec["j_lo"], o["j_lo"])
+    np.testing.assert_array_equal(off.cpu().numpy(), o["offsets"])
+    np.testing.assert_array_equal(rec["offset"], o["offsets"][:-1])
+    assert total == o["offsets"][-1]
+
+
+@pytest.mark.parametrize("layout", ["planar", "interleaved"])
+def test_pre_fgpa_fields_match_oracle(ctx, tiny, layout):
+    w, o, dv = tiny["w"], tiny["orc"], tiny["dev"]
+    if layout == "planar":
+        box = ctx.load_box(w, dv["d"], dv["e"])
+    else:
+        box = ctx.load_box(w, ctx.pack_box(dv["d"], dv["e"]), None)
+    r = ctx.make_skewers(box, dv["qso"], len(tiny["ids"]), w)
+    ctx.sync()
+    assert_field_close(r["delta"].cpu().numpy(), o["delta"], "delta_tot")
+    assert_field_close(r["eta"].cpu().numpy(), o["eta"], "eta")
+
+
+@pytest.mark.parametrize("rebin", [1, 3])
+def test_flux_matches_oracle(ctx, tiny, rebin):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    f, off = ctx.flux(w, r["sk"], n, r["delta"], r["eta"], rebin=rebin)
+    o = tiny["orc"] if rebin == 1 else oracle.run_skewers(w, tiny["d"], tiny["e"], tiny["pos"], tiny["ids"],
+                                                          rebin=rebin, n_threads=16)
+    np.testing.assert_array_equal(off.cpu().numpy(), o["offsets_out"])
+    assert_flux_close(f[: o["offsets_out"][-1]].cpu().numpy(), o["flux"])
+    if rebin > 1:
+        st_o = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"],
+                            rebin=rebin)
+        st_g = ctx.stats(w, r["sk"], n, off, f, rebin=rebin, delta=r["delta"], eta=r["eta"])
+        assert_stats_close(st_g, st_o)
+
+
+def test_split_statistics_match_oracle(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    f, off = ctx.flux(w, r["sk"], n, r["delta"], r["eta"])
+    st = ctx.stats(w, r["sk"], n, off, f, delta=r["delta"], eta=r["eta"])
+    assert_stats_close(st, tiny["st"])
+    # without the fields the flux statistics are unchanged
+    st2 = ctx.stats(w, r["sk"], n, off, f)
+    np.testing.assert_array_equal(st2["mean_flux"], st["mean_flux"])
+    np.testing.assert_array_equal(st2["p1d_sum"], st["p1d_sum"])
+
+
+def test_fused_path_matches_split_path_and_oracle(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    st, o = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    f, off = ctx.flux(w, r["sk"], n, r["delta"], r["eta"])
+    tot = r["total"]
+    assert torch.equal(o["delta"][:tot], r["delta"]) and torch.equal(o["eta"][:tot], r["eta"])
+    assert torch.equal(o["flux"][:tot], f[:tot])
+    assert_stats_close(st, tiny["st"])
+    st_fast, _ = ctx.run(box, dv["qso"], n, w, flags=mk.STATS)
+    for k in ("sums", "p1d_sum", "n_seg"):
+        np.testing.assert_array_equal(st_fast[k], st[k])
+
+
+@pytest.mark.parametrize("n_fft", [512, 1024, 2048])
+def test_other_fft_lengths(ctx, tiny, n_fft):
+    w = si.shrink(tiny["w"], n_fft=n_fft)
+    idx = np.arange(0, 500, 7)
+    pos, ids = tiny["pos"][idx], tiny["ids"][idx]
+    o = oracle.run_skewers(w, tiny["d"], tiny["e"], pos, ids, n_threads=16)
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    box = ctx.load_box(w, tiny["dev"]["d"], tiny["dev"]["e"])
+    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w,
+                    flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
+    tot = o["offsets"][-1]
+    assert_field_close(g["delta"][:tot].cpu().numpy(), o["delta"], "delta_tot")
+    assert_field_close(g["eta"][:tot].cpu().numpy(), o["eta"], "eta")
+    assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
+    assert_stats_close(st, so, check_fields=False)
+
+
+def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
+    # zero box: delta_tot is delta_S; each segment's DFT over its amplitude gives
+    # back the oracle's modes
+    w = tiny["w"]
+    z = torch.zeros_like(tiny["dev"]["d"])
+    box = ctx.load_box(w, z, z)
+    idx = np.arange(5)
+    r = ctx.make_skewers(box, mk.catalogue_tensor(tiny["pos"][idx], tiny["ids"][idx]), 5, w)
+    ds = r["delta"].cpu().numpy().astype(np.float64)
+    off = r["offsets"].cpu().numpy()
+    N = w["n_fft"]
+    amp = np.sqrt(N * w["p_s"] / w["dr"])
+    for q in range(5):
+        x = ragged(ds, off, q)
+        for s in range(len(x) // N):
+            X = np.fft.rfft(x[s * N:(s + 1) * N])
+            ref = oracle.small_scale_modes(w, int(tiny["ids"][q]), s)
+            np.testing.assert_allclose(X[1:] / amp[1:], ref[1:] / amp[1:], atol=2e-5)
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_catalogue_and_zero_length_skewers(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    q0 = mk.catalogue_tensor(np.zeros((0, 3)), np.zeros(0, np.uint64))
+    st, o = ctx.run(box, q0, 0, w, flags=mk.STATS)
+    assert o["offsets"][0].item() == 0 and st["sums"].sum() == 0
+    # quasars too close (forest below z = 0) or at the observer give n = 0
+    pos = np.array([[10.0, 0.0, 0.0], [0.0, 0.0, 0.0], tiny["pos"][0]])
+    ids = np.array([7, 8, 9], np.uint64)
+    sk, off, total = ctx.plan(box, mk.catalogue_tensor(pos, ids), 3, w)
+    rec = records(sk, 3)
+    assert rec["n"][0] == 0 and rec["n"][1] == 0 and rec["n"][2] == tiny["orc"]["npix"][0]
+    r = ctx.make_skewers(box, mk.catalogue_tensor(pos, ids), 3, w)
+    o2 = oracle.run_skewers(w, tiny["d"], tiny["e"], pos, ids)
+    assert_field_close(r["delta"].cpu().numpy(), o2["delta"], "delta_tot")
+
+
+def test_capacity_overflow_is_reported_and_context_survives(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = 20
+    qso = mk.catalogue_tensor(tiny["pos"][:n], tiny["ids"][:n])
+    sk, off, total = ctx.plan(box, qso, n, w)
+    small = torch.empty(total // 2, dtype=torch.float32, device="cuda")
+    p = mk.skewer_params(w)
+    import ctypes as C
+    rc = mk.lib().mk_make_skewers(ctx.h, box.handle, C.c_void_p(qso.data_ptr()), n, C.byref(p),
+                                  C.c_void_p(sk.data_ptr()), C.c_void_p(off.data_ptr()),
+                                  C.c_void_p(small.data_ptr()), C.c_void_p(small.data_ptr()),
+                                  total // 2, None)
+    assert rc == mk.MK_OK
+    with pytest.raises(mk.MkError) as ei:
+        ctx.sync()
+    assert ei.value.code == mk.MK_ERANGE
+    ctx.sync()  # cleared
+    r = ctx.make_skewers(box, qso, n, w)
+    assert r["total"] == total
+
+
+def test_invalid_arguments(ctx, tiny):
+    w = si.shrink(tiny["w"], n_fft=300)
+    box = ctx.load_box(tiny["w"], tiny["dev"]["d"], tiny["dev"]["e"])
+    with pytest.raises(mk.MkError) as ei:
+        ctx.plan(box, tiny["dev"]["qso"], 10, w)
+    assert ei.value.code == mk.MK_EINVAL
+    bad = dict(tiny["w"])
+    bad["n"] = 48
+    with pytest.raises(mk.MkError):
+        ctx.load_box(bad, tiny["dev"]["d"], tiny["dev"]["e"])
+    nodes = mk.fgpa_nodes(tiny["w"])
+    nodes.z[3] = nodes.z[2]
+    with pytest.raises(mk.MkError):
+        ctx.run(box, tiny["dev"]["qso"], 10, tiny["w"], nodes=nodes)
+
+
+# ------------------------------------------------------------------ full-size workloads, sampled
+def _full_size_check(ctx, w, n_sample, seed, lognormal=False):
+    torch.cuda.empty_cache()
+    d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"], backend="torch")
+    dh = d.cpu().numpy()
+    pos, ids = si.catalogue(w, delta=dh if lognormal else None)
+    qso = mk.catalogue_tensor(pos, ids)
+    box = ctx.load_box(w, ctx.pack_box(d, e), None)
+    eh = e.cpu().numpy()
+    del d, e
+    st, g = ctx.run(box, qso, len(ids), w, flags=mk.STATS | mk.STORE_FLUX | mk.STORE_FIELDS)
+    rec = records(g["sk"], len(ids))
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(len(ids), n_sample, replace=False))
+    o = oracle_subset(w, dh, eh, pos, ids, idx)
+    np.testing.assert_array_equal(rec["n"][idx], o["npix"])
+    np.testing.assert_array_equal(rec["j_lo"][idx], o["j_lo"])
+    off = g["offsets"].cpu().numpy()
+    for k, q in enumerate(idx):
+        a, b = off[q], off[q + 1]
+        assert_field_close(g["delta"][a:b].cpu().numpy(), ragged(o["delta"], o["offsets"], k), f"delta q{q}")
+        assert_field_close(g["eta"][a:b].cpu().numpy(), ragged(o["eta"], o["offsets"], k), f"eta q{q}")
+        assert_flux_close(g["flux"][a:b].cpu().numpy(), ragged(o["flux"], o["offsets"], k), f"flux q{q}")
+    # whole-catalogue statistics: the fused pass equals the split pass over the
+    # stored fields, and the mean flux per z bin equals an FP64 reduction of
+    # the stored flux binned with the oracle's pixel redshifts
+    tot = int(off[-1])
+    st2 = ctx.stats(w, g["sk"], len(ids), g["offsets"], g["flux"], delta=g["delta"], eta=g["eta"])
+    np.testing.assert_array_equal(st2["sums"][:, 0], st["sums"][:, 0])
+    np.testing.assert_allclose(st2["sums"], st["sums"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(st2["p1d_sum"], st["p1d_sum"], rtol=1e-9)
+    jl = torch.from_numpy(rec["j_lo"].astype(np.int64)).cuda()
+    nn = torch.from_numpy(rec["n"].astype(np.int64)).cuda()
+    owner = torch.repeat_interleave(torch.arange(len(ids), device="cuda"), nn)
+    J = jl[owner] + (torch.arange(tot, device="cuda") - g["offsets"][:-1][owner])
+    jmax = int(J.max().item()) + 1
+    jmin = int(J.min().item())
+    zt = np.zeros(jmax)
+    for j in range(jmin, jmax):
+        zt[j] = oracle.pixel_z(w, j)
+    zb = torch.floor((torch.from_numpy(zt).cuda()[J] - w["z_bin_lo"]) / w["dz_bin"]).long()
+    ok = (zb >= 0) & (zb < w["n_zbins"])
+    fsum = torch.zeros(w["n_zbins"], dtype=torch.float64, device="cuda")
+    cnt = torch.zeros(w["n_zbins"], dtype=torch.float64, device="cuda")
+    fsum.index_add_(0, zb[ok], g["flux"][:tot][ok].double())
+    cnt.index_add_(0, zb[ok], torch.ones_like(fsum[zb[ok]]))
+    np.testing.assert_array_equal(cnt.cpu().numpy(), st["sums"][:, 0])
+    m = cnt.cpu().numpy() > 0
+    np.testing.assert_allclose(st["mean_flux"][m], (fsum / cnt).cpu().numpy()[m], rtol=TOL_STAT)
+    del g, box
+    torch.cuda.empty_cache()
+
+
+def test_scale_workload_sampled(ctx):
+    _full_size_check(ctx, si.workload("scale"), 24, 5, lognormal=True)
+
+
+def test_batched_workload_sampled(ctx):
+    _full_size_check(ctx, si.workload("batched"), 40, 6)
