@@ -238,6 +238,41 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
            float *d_delta_out, float *d_eta_out, float *d_flux_out, int64_t capacity_px,
            mk_stats_out *h_out);
 
+/* ---------------------------------------------------------------- statistics without allocation */
+
+/* The paper has no counterpart to this call.  It is mk_stats for callers that
+   cannot allocate device memory at the point where they need statistics:
+   programs that hand all device memory to their own pool allocator at start-up,
+   processes running under a hard device-memory cap, and latency-bound loops in
+   which a cudaMalloc or cudaFree, which waits for the whole device, is not
+   acceptable.  mk_stats keeps its scratch (segment counts and offsets, scan tile
+   sums, per-CTA FP64 partial sums, the device copy of the result) in a
+   workspace that it grows with cudaMalloc when a larger catalogue arrives.
+   This call keeps the same scratch in one fixed array of
+   MK_STATIC_SCRATCH_BYTES bytes in the library's own device memory, which every
+   GPU that loads the library holds until the process exits, and it calls no
+   allocating routine.
+   Limits and conditions:
+   - n_sk <= MK_STATIC_MAX_SKEWERS, otherwise MK_EINVAL and nothing runs.
+   - The context must already hold the tables the call reads: the pixel tables
+     of params->dr and the FFT twiddles of bins->n_fft.  Any earlier
+     mk_make_skewers, mk_flux, mk_stats or mk_run on this context with the same
+     dr and n_fft builds them; otherwise MK_EINVAL.
+   - The first call on each device performs a set-up step (it looks up the
+     device address of the array); make that first call before any stream
+     capture.
+   - All calls share the one array, which keeps the contents of the last call.
+     Calls that overlap on the GPU (other threads, streams or contexts of the
+     same process) race on it and corrupt each other's results.
+   Arguments, results and synchronisation are those of mk_stats; the results
+   equal mk_stats' up to the order in which FP64 partial sums are added. */
+#define MK_STATIC_MAX_SKEWERS 131072
+#define MK_STATIC_SCRATCH_BYTES (6u << 20)
+int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+                    const int64_t *d_offsets_out, const float *d_flux, int32_t rebin,
+                    const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
+                    mk_stats_out *h_out);
+
 /* ---------------------------------------------------------------- timing */
 
 /* When on (non-zero), the library records CUDA events on the context's

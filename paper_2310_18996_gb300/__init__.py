@@ -20,12 +20,13 @@ from . import build as _build
 
 MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
 MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
+STATIC_MAX_SKEWERS = 131072
 BOX_PLANAR, BOX_INTERLEAVED = 0, 1
 STORE_FIELDS, STORE_FLUX, STATS = 1, 2, 4
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
            "mk_free_box", "mk_pack_box", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
-           "mk_set_timing", "mk_last_kernel_ms"]
+           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static"]
 
 
 class MkError(RuntimeError):
@@ -107,6 +108,8 @@ def lib():
                                        P(StatBins), P(StatsOut)]),
                 "mk_run": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(FgpaNodes), P(StatBins),
                                      u32, vp, vp, vp, vp, vp, i64, P(StatsOut)]),
+                "mk_stats_static": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, i32, vp, vp,
+                                              P(StatBins), P(StatsOut)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }

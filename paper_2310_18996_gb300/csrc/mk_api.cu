@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -738,3 +739,111 @@ int mk_last_kernel_ms(mk_ctx *ctx, double *ms) {
 }
 
 }  // extern "C"
+
+// ====================================================================== statistics without allocation
+// Scratch of mk_stats_static: one fixed array in the library's device memory
+// instead of the context's growable workspace.  Layout, in 256-byte aligned
+// pieces: the device copy of the result, segment counts, segment offsets,
+// scan tile sums, then per-CTA FP64 partial sums in the remaining space.
+static __device__ __align__(256) unsigned char g_stats_scratch[MK_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+void *g_stats_scratch_ptr[kMaxStaticDevices] = {};
+std::mutex g_stats_scratch_mu;
+
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+// Device address of the array on the context's device (looked up once per
+// device, with that device current).
+int stats_scratch_address(mk_ctx *ctx, unsigned char **out) {
+  if (ctx->device < 0 || ctx->device >= kMaxStaticDevices)
+    return fail(ctx, MK_EINVAL, "device %d out of range for the static scratch", ctx->device);
+  std::lock_guard<std::mutex> lock(g_stats_scratch_mu);
+  if (!g_stats_scratch_ptr[ctx->device]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_stats_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(ctx, MK_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+    g_stats_scratch_ptr[ctx->device] = p;
+  }
+  *out = static_cast<unsigned char *>(g_stats_scratch_ptr[ctx->device]);
+  return MK_OK;
+}
+
+}  // namespace
+
+extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+                               const int64_t *d_offsets_out, const float *d_flux, int32_t rebin,
+                               const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
+                               mk_stats_out *h_out) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_params(ctx, params, false);
+  if (rc || (rc = check_bins(ctx, bins))) return rc;
+  if (rebin < 1 || rebin > 4096) return fail(ctx, MK_EINVAL, "rebin must be in [1, 4096]");
+  if (!h_out || n_sk < 0 || (n_sk > 0 && (!d_sk || !d_offsets_out || !d_flux)))
+    return fail(ctx, MK_EINVAL, "bad stats arguments");
+  if (n_sk > MK_STATIC_MAX_SKEWERS)
+    return fail(ctx, MK_EINVAL, "n_sk = %lld exceeds MK_STATIC_MAX_SKEWERS = %d", static_cast<long long>(n_sk),
+                MK_STATIC_MAX_SKEWERS);
+  if ((d_delta == nullptr) != (d_eta == nullptr)) return fail(ctx, MK_EINVAL, "d_delta and d_eta go together");
+  CK(cudaSetDevice(ctx->device));
+  if (!(ctx->d_zpix && ctx->dr == params->dr))
+    return fail(ctx, MK_EINVAL, "no pixel tables for dr = %g on this context: run an allocating call first",
+                params->dr);
+  if (!ctx->d_tw[tw_slot(bins->n_fft)])
+    return fail(ctx, MK_EINVAL, "no FFT twiddles for n_fft = %d on this context: run an allocating call first",
+                bins->n_fft);
+  if ((rc = ensure_zbin(ctx, bins))) return rc;  // kernel into the existing table
+  unsigned char *base = nullptr;
+  if ((rc = stats_scratch_address(ctx, &base))) return rc;
+
+  const size_t off_cnt = align256(sizeof(mk_stats_out));
+  const size_t off_seg = off_cnt + align256(sizeof(int64_t) * MK_STATIC_MAX_SKEWERS);
+  const size_t off_tiles = off_seg + align256(sizeof(int64_t) * (MK_STATIC_MAX_SKEWERS + 1));
+  const size_t off_part = off_tiles + align256(scan_workspace_bytes(MK_STATIC_MAX_SKEWERS));
+  if (off_part >= MK_STATIC_SCRATCH_BYTES) return fail(ctx, MK_EINVAL, "static scratch layout overflow");
+  mk_stats_out *d_out = reinterpret_cast<mk_stats_out *>(base);
+  int64_t *d_cnt = reinterpret_cast<int64_t *>(base + off_cnt);
+  int64_t *d_seg = reinterpret_cast<int64_t *>(base + off_seg);
+  void *d_tiles = base + off_tiles;
+  double *d_part = reinterpret_cast<double *>(base + off_part);
+  const size_t part_doubles = (MK_STATIC_SCRATCH_BYTES - off_part) / sizeof(double);
+
+  const int threads = 256;
+  const StatLayout L{bins->n_z, bins->n_k};
+  int grid = stats_grid(ctx, bins->n_fft, threads, L.size());
+  if (static_cast<size_t>(grid) * L.size() > part_doubles) grid = static_cast<int>(part_doubles / L.size());
+  if (grid < 1) return fail(ctx, MK_EINVAL, "binning too large for the static scratch");
+
+  // every piece below is fully rewritten by this call, so nothing is cleared
+  if (n_sk > 0) CK(launch_seg_counts(d_offsets_out, n_sk, bins->n_fft, d_cnt, ctx->stream));
+  CK(launch_scan(d_cnt, nullptr, n_sk, d_seg, nullptr, nullptr, d_tiles, ctx->stream));
+  StatParams P{};
+  P.sk = d_sk;
+  P.off_out = d_offsets_out;
+  P.segoff = d_seg;
+  P.n_sk = n_sk;
+  P.flux = d_flux;
+  P.delta = d_delta;
+  P.eta = d_eta;
+  P.rebin = rebin;
+  P.zbin = ctx->d_zbin;
+  P.cumz = ctx->d_cumz;
+  P.tw = ctx->d_tw[tw_slot(bins->n_fft)];
+  P.j_max = ctx->j_max;
+  P.n_z = bins->n_z;
+  P.n_k = bins->n_k;
+  P.z_lo = bins->z_lo;
+  P.dz = bins->dz;
+  P.dr = params->dr;
+  P.partials = d_part;
+  P.err = ctx->d_err;
+  CK(launch_stats(P, bins->n_fft, grid, threads, ctx->stream));
+  CK(launch_finalize(d_part, grid, bins->n_z, bins->n_k, bins->n_fft, d_out, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_stats, d_out, sizeof(mk_stats_out), cudaMemcpyDeviceToHost, ctx->stream));
+  if ((rc = read_error_word(ctx))) return rc;  // synchronises
+  std::memcpy(h_out, ctx->h_stats, sizeof(mk_stats_out));
+  return MK_OK;
+}
