@@ -129,10 +129,10 @@ def oracle_rate(w, dh, eh, pos, ids, target_s, threads):
     return px / dt, px, n, dt
 
 
-def make_inputs(w, rank, device):
+def make_inputs(w, rank, device, box_n=None, n_q=None):
     import torch
 
-    w = dict(w)
+    w = si.shrink(w, n=box_n, n_q=n_q)
     w["seed_cat"] = w["seed_cat"] + 7919 * rank
     d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"], backend="torch", device=device)
     pos, ids = si.catalogue(w)
@@ -187,7 +187,7 @@ def run_gb300(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local_rank)
     dev = f"cuda:{local_rank}"
-    w, d, e, pos, ids = make_inputs(si.workload(WORKLOAD), rank, dev)
+    w, d, e, pos, ids = make_inputs(si.workload(WORKLOAD), rank, dev, args.box_n, args.n_q)
     want_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
     dh = eh = None
     if want_cpu:
@@ -246,10 +246,11 @@ def run_gb300(args, rank, world, local_rank):
     # pinned memory, the pass, flux D2H into pinned memory (stats come back
     # inside mk_run)
     host_flux = torch.empty(total, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = 0 if args.no_e2e else max(3, args.steps // 2)
     qdev = torch.empty_like(qso)
     ctx.set_timing(False)
-    for it in range(e2e_steps + 1):
+    t0 = time.perf_counter()
+    for it in range(e2e_steps + 1 if e2e_steps else 0):
         if it == 1:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -257,7 +258,7 @@ def run_gb300(args, rank, world, local_rank):
         ctx.run(box, qdev, n_q, w, flags=flags, capacity=total, outputs=outs)
         host_flux.copy_(flux, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps
+    e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps if e2e_steps else float("nan")
     if dist:
         t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -277,8 +278,8 @@ def run_gb300(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "1024^3 box (delta+eta FP32, 8.6 GB interleaved), 1M quasars "
-                                   "z 1.8-4.0, 200-1500 px skewers, N_fft 256, fused persistent launch",
+            "config": {"workload": f"{w['n']}^3 box (delta+eta FP32, interleaved), {n_q} quasars "
+                                   "z 2.04-4.0, 200-1500 px skewers, N_fft 256, fused persistent launch",
                        "pixels_per_step_per_gpu": int(total), "skewers_per_gpu": n_q,
                        "l2": "inputs larger than L2 (8.6 GB box)",
                        "outputs": "flux stored + FP64 statistics"},
@@ -309,6 +310,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--box-n", type=int, default=None, help="smaller box (profiling runs)")
+    ap.add_argument("--n-q", type=int, default=None, help="fewer quasars (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -148,7 +148,7 @@ struct mk_ctx {
   double *d_zpix = nullptr, *d_cumz = nullptr;
   float *d_gpix = nullptr;
   float4 *d_pixtab = nullptr;
-  int16_t *d_zbin = nullptr;
+  int16_t *d_zbin = nullptr, *d_segzbin = nullptr;
   bool pixtab_valid = false;
   mk_fgpa_nodes nodes_key{};
   bool zbin_valid = false;
@@ -235,15 +235,17 @@ int ensure_pixel_tables(mk_ctx *ctx, double dr) {
   cudaFree(ctx->d_gpix);
   cudaFree(ctx->d_pixtab);
   cudaFree(ctx->d_zbin);
+  cudaFree(ctx->d_segzbin);
   ctx->d_zpix = ctx->d_cumz = nullptr;
   ctx->d_gpix = nullptr;
   ctx->d_pixtab = nullptr;
-  ctx->d_zbin = nullptr;
+  ctx->d_zbin = ctx->d_segzbin = nullptr;
   if (cudaMalloc(&ctx->d_zpix, sizeof(double) * jmax) != cudaSuccess ||
       cudaMalloc(&ctx->d_cumz, sizeof(double) * (jmax + 1)) != cudaSuccess ||
       cudaMalloc(&ctx->d_gpix, sizeof(float) * jmax) != cudaSuccess ||
       cudaMalloc(&ctx->d_pixtab, sizeof(float4) * jmax) != cudaSuccess ||
-      cudaMalloc(&ctx->d_zbin, sizeof(int16_t) * jmax) != cudaSuccess)
+      cudaMalloc(&ctx->d_zbin, sizeof(int16_t) * jmax) != cudaSuccess ||
+      cudaMalloc(&ctx->d_segzbin, sizeof(int16_t) * jmax) != cudaSuccess)
     return fail(ctx, MK_ENOMEM, "pixel tables");
   CK(cudaMemcpy(ctx->d_zpix, z.data(), sizeof(double) * jmax, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(ctx->d_cumz, cz.data(), sizeof(double) * (jmax + 1), cudaMemcpyHostToDevice));
@@ -336,7 +338,8 @@ int ensure_pixtab(mk_ctx *ctx, const mk_fgpa_nodes *nd) {
 
 int ensure_zbin(mk_ctx *ctx, const mk_stat_bins *b) {
   if (ctx->zbin_valid && std::memcmp(&ctx->bins_key, b, sizeof(*b)) == 0) return MK_OK;
-  CK(launch_zbin(ctx->d_zpix, ctx->j_max, b->z_lo, b->dz, b->n_z, ctx->d_zbin, ctx->stream));
+  CK(launch_zbin(ctx->d_zpix, ctx->d_cumz, ctx->j_max, b->z_lo, b->dz, b->n_z, b->n_fft, ctx->d_zbin,
+                 ctx->d_segzbin, ctx->stream));
   ctx->bins_key = *b;
   ctx->zbin_valid = true;
   return MK_OK;
@@ -370,12 +373,13 @@ int time_end(mk_ctx *ctx) {
 }
 
 // persistent grids: as many resident CTAs as the SMs hold
-int skewer_grid(mk_ctx *ctx, int n_fft, int layout, int threads, int acc_doubles) {
-  return ctx->sms * skewer_blocks_per_sm(n_fft, layout, threads, acc_doubles);
+int skewer_grid(mk_ctx *ctx, int n_fft, const mk_box *box, int threads, const mk_stat_bins *bins) {
+  return ctx->sms * skewer_blocks_per_sm(n_fft, box->desc.layout, box->lgn, threads, bins ? bins->n_z : 0,
+                                         bins ? bins->n_k : 0, bins != nullptr);
 }
 
-int stats_grid(mk_ctx *ctx, int n_fft, int threads, int acc_doubles) {
-  return ctx->sms * stats_blocks_per_sm(n_fft, threads, acc_doubles);
+int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads) {
+  return ctx->sms * stats_blocks_per_sm(bins->n_fft, threads, bins->n_z, bins->n_k);
 }
 
 int run_geometry(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, const mk_skewer_params *p,
@@ -415,8 +419,10 @@ SkewerParams skewer_params(mk_ctx *ctx, const mk_box *box, const mk_skewer *d_sk
   S.tw = ctx->d_tw[tw_slot(p->n_fft)];
   S.seed = p->seed;
   S.j_max = ctx->j_max;
+  S.segzbin = ctx->d_segzbin;
   S.err = ctx->d_err;
   S.dr = p->dr;
+  S.p1d_scale = static_cast<float>(p->dr / p->n_fft);
   return S;
 }
 
@@ -486,6 +492,7 @@ void mk_destroy(mk_ctx *ctx) {
   cudaFree(ctx->d_gpix);
   cudaFree(ctx->d_pixtab);
   cudaFree(ctx->d_zbin);
+  cudaFree(ctx->d_segzbin);
   cudaFree(ctx->d_amp);
   for (auto *p : ctx->d_tw) cudaFree(p);
   cudaFree(ctx->d_cnt_px);
@@ -580,7 +587,7 @@ int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t
   S.flux_out = nullptr;
   S.capacity = capacity_px;
   S.do_stats = 0;
-  const int grid = skewer_grid(ctx, params->n_fft, box->desc.layout, ctx->skewer_threads, 0);
+  const int grid = skewer_grid(ctx, params->n_fft, box, ctx->skewer_threads, nullptr);
   if ((rc = time_begin(ctx))) return rc;
   CK(launch_skewer(S, params->n_fft, box->desc.layout, grid, ctx->skewer_threads, ctx->stream));
   return time_end(ctx);
@@ -633,7 +640,7 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
     return rc;
   const int threads = 256;
   const StatLayout L{bins->n_z, bins->n_k};
-  const int grid = stats_grid(ctx, bins->n_fft, threads, L.size());
+  const int grid = stats_grid(ctx, bins, threads);
   if ((rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
                  sizeof(double) * static_cast<size_t>(grid) * L.size())))
     return rc;
@@ -649,6 +656,8 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
   P.eta = d_eta;
   P.rebin = rebin;
   P.zbin = ctx->d_zbin;
+  P.segzbin = ctx->d_segzbin;
+  P.p1d_scale = static_cast<float>(rebin * params->dr / bins->n_fft);
   P.cumz = ctx->d_cumz;
   P.tw = ctx->d_tw[tw_slot(bins->n_fft)];
   P.j_max = ctx->j_max;
@@ -690,7 +699,7 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
     return rc;
   if (stats && (rc = ensure_zbin(ctx, bins))) return rc;
   const StatLayout L{stats ? bins->n_z : 0, stats ? bins->n_k : 0};
-  const int grid = skewer_grid(ctx, params->n_fft, box->desc.layout, ctx->skewer_threads, L.size());
+  const int grid = skewer_grid(ctx, params->n_fft, box, ctx->skewer_threads, stats ? bins : nullptr);
   if (stats && (rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
                           sizeof(double) * static_cast<size_t>(grid) * L.size())))
     return rc;
@@ -813,7 +822,7 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
 
   const int threads = 256;
   const StatLayout L{bins->n_z, bins->n_k};
-  int grid = stats_grid(ctx, bins->n_fft, threads, L.size());
+  int grid = stats_grid(ctx, bins, threads);
   if (static_cast<size_t>(grid) * L.size() > part_doubles) grid = static_cast<int>(part_doubles / L.size());
   if (grid < 1) return fail(ctx, MK_EINVAL, "binning too large for the static scratch");
 
@@ -830,6 +839,8 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
   P.eta = d_eta;
   P.rebin = rebin;
   P.zbin = ctx->d_zbin;
+  P.segzbin = ctx->d_segzbin;
+  P.p1d_scale = static_cast<float>(rebin * params->dr / bins->n_fft);
   P.cumz = ctx->d_cumz;
   P.tw = ctx->d_tw[tw_slot(bins->n_fft)];
   P.j_max = ctx->j_max;

@@ -1,12 +1,14 @@
 // Device building blocks of the skewer-synthesis kernels (sm_103a).
 //
 // A "team" of T = N/8 threads owns one segment of N pixels of one skewer:
-// thread t holds pixels t + T i, i = 0..7, in registers, and the team shares
-// one buffer of N/2 + 1 complex values in shared memory for the FFTs.
+// thread t handles pixels t + T k, k = 0..7, and the team shares one buffer
+// of N/2 + 1 complex values in shared memory for the FFTs.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "mk_params.h"
 
@@ -35,14 +37,34 @@ __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1
   return c;
 }
 
-// ln(u) for u = (x + 1/2) 2^-32 without losing the small distance to 1:
-// the upper half of the range goes through log1p of the complement.
-__device__ __forceinline__ float log_uniform(uint32_t x) {
-  if (x & 0x80000000u) {
-    const float d = (__uint2float_rn(~x) + 0.5f) * 0x1p-32f;
-    return log1pf(-d);
-  }
-  return logf((__uint2float_rn(x) + 0.5f) * 0x1p-32f);
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// -ln(u) for u = (x + 1/2) 2^-32, branch-free and accurate in relative terms
+// over the whole range.  Below 1/2 the SFU log2 is accurate to ~2^-22
+// relative (|log2 u| >= 1).  Above, u = 1 - d with d = (~x + 1/2) 2^-32 known
+// exactly, and -ln(1 - d) = 2 atanh(s), s = d/(2 - d) <= 1/3, summed from the
+// Gregory series 2 (s + s^3/3 + ... + s^17/17) (truncation < 1e-10).
+__device__ __forceinline__ float neg_log_uniform(uint32_t x) {
+  const float u = (__uint2float_rn(x) + 0.5f) * 0x1p-32f;
+  const float lo = -0.69314718055994531f * lg2_approx(u);
+  const float d = (__uint2float_rn(~x) + 0.5f) * 0x1p-32f;
+  const float s = __fdividef(d, 2.0f - d);
+  const float s2 = s * s;
+  float p = 1.0f / 17.0f;
+  p = fmaf(p, s2, 1.0f / 15.0f);
+  p = fmaf(p, s2, 1.0f / 13.0f);
+  p = fmaf(p, s2, 1.0f / 11.0f);
+  p = fmaf(p, s2, 1.0f / 9.0f);
+  p = fmaf(p, s2, 1.0f / 7.0f);
+  p = fmaf(p, s2, 1.0f / 5.0f);
+  p = fmaf(p, s2, 1.0f / 3.0f);
+  p = fmaf(p, s2, 1.0f);
+  const float hi = 2.0f * s * p;
+  return (x & 0x80000000u) ? hi : lo;
 }
 
 // (cos, sin)(2 pi u), u = (x + 1/2) 2^-32: the angle is taken in (-pi, pi)
@@ -55,6 +77,8 @@ __device__ __forceinline__ float2 unit_phase(uint32_t x) {
   return make_float2(-c, -s);
 }
 
+__device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+
 // ------------------------------------------------------------------ complex helpers
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -62,9 +86,8 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-// multiply by +i (SIGN > 0) or -i (SIGN < 0)
 template <int SIGN>
-__device__ __forceinline__ float2 cmul_i(float2 a) {
+__device__ __forceinline__ float2 cmul_i(float2 a) {  // times +i (SIGN > 0) or -i
   return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
@@ -84,13 +107,20 @@ struct Fft {
   static constexpr int M = N / 2;  // complex points
   static constexpr int T = N / 8;  // threads per team (M/4)
   static constexpr int LOGM = (M == 128) ? 7 : (M == 256) ? 8 : (M == 512) ? 9 : 10;
-  static constexpr int P4 = LOGM / 2;        // radix-4 passes
+  static constexpr int P4 = LOGM / 2;          // radix-4 passes
   static constexpr bool R2 = (LOGM & 1) != 0;  // one radix-2 pass at the end
   static_assert(N == 256 || N == 512 || N == 1024 || N == 2048, "unsupported N");
 };
 
-// Per-thread twiddles, fixed for the kernel's lifetime (the thread's
-// butterfly index does not change between segments).  Stored for the
+// Shared-memory swizzle of complex index i: xor the low bits with 5 times
+// bits 4-5.  Every Stockham access pattern (strided reads t + r T, writes at
+// base + r Ns for Ns = 1, 4, 16, ..., the mode and power reads) then hits 16
+// distinct 8-byte slots per half warp.
+__device__ __forceinline__ int sw(int i) { return i ^ (5 * ((i >> 4) & 3)); }
+// float view: real value p of the packed sequence z_n = x_2n + i x_2n+1
+__device__ __forceinline__ int swf(int p) { return 2 * sw(p >> 1) + (p & 1); }
+
+// Per-thread twiddles, fixed for the kernel's lifetime.  Stored for the
 // forward sign e^{-i...}; the inverse uses conjugates.
 template <int N>
 struct Twiddles {
@@ -99,7 +129,7 @@ struct Twiddles {
   float2 wu[4];              // e^{-2 pi i k/N}, k = t + r T (real-FFT untangle)
 };
 
-// tw[k] = e^{-2 pi i k/N}, k < N (FP64-rounded table in global memory)
+// tab[k] = e^{-2 pi i k/N}, k < N (FP64-rounded table in global memory)
 template <int N>
 __device__ __forceinline__ void load_twiddles(Twiddles<N> &tw, const float2 *__restrict__ tab, int t) {
   constexpr int T = Fft<N>::T;
@@ -112,7 +142,6 @@ __device__ __forceinline__ void load_twiddles(Twiddles<N> &tw, const float2 *__r
     ns *= 4;
   }
   if constexpr (Fft<N>::R2) {
-    // Ns = M/2: angle 2 pi (j mod Ns)/M -> index 2 (j mod Ns)
     tw.w2[0] = tab[(2 * (t % ns)) % N];
     tw.w2[1] = tab[(2 * ((t + T) % ns)) % N];
   }
@@ -129,51 +158,49 @@ __device__ __forceinline__ void dft4(float2 &v0, float2 &v1, float2 &v2, float2 
   v3 = csub(b, d);
 }
 
-// Stockham passes 1.. on buf (pass 0 already applied by the caller, whose
-// outputs sit in v[] for butterfly j = t).  SIGN = -1 forward, +1 inverse.
-// On return buf holds the transform in natural order.
+// Stockham passes after pass 0 (whose butterfly j = t outputs are in v[]).
+// SIGN = -1 forward, +1 inverse.  On return buf holds the transform in
+// natural order (through the swizzle).
 template <int N, int SIGN>
 __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const Twiddles<N> &tw, int t,
                                            int team) {
   constexpr int T = Fft<N>::T;
   constexpr int M = Fft<N>::M;
-  // pass 0 (Ns = 1): outputs at 4 t + r
   team_sync<T>(team);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) buf[4 * t + r] = v[r];
+  for (int r = 0; r < 4; ++r) buf[sw(4 * t + r)] = v[r];
   int ns = 4;
 #pragma unroll
   for (int p = 1; p < Fft<N>::P4; ++p) {
     team_sync<T>(team);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) v[r] = buf[t + r * T];
+    for (int r = 0; r < 4; ++r) v[r] = buf[sw(t + r * T)];
 #pragma unroll
     for (int r = 1; r < 4; ++r) v[r] = cmul(v[r], SIGN < 0 ? tw.w4[p][r - 1] : cconj(tw.w4[p][r - 1]));
     dft4<SIGN>(v[0], v[1], v[2], v[3]);
-    const int jm = t % ns;
-    const int base = (t / ns) * ns * 4 + jm;
+    const int base = (t / ns) * ns * 4 + t % ns;
     team_sync<T>(team);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) buf[base + r * ns] = v[r];
+    for (int r = 0; r < 4; ++r) buf[sw(base + r * ns)] = v[r];
     ns *= 4;
   }
   if constexpr (Fft<N>::R2) {
     team_sync<T>(team);
-    float2 a0 = buf[t], b0 = buf[t + M / 2], a1 = buf[t + T], b1 = buf[t + T + M / 2];
+    float2 a0 = buf[sw(t)], b0 = buf[sw(t + M / 2)], a1 = buf[sw(t + T)], b1 = buf[sw(t + T + M / 2)];
     b0 = cmul(b0, SIGN < 0 ? tw.w2[0] : cconj(tw.w2[0]));
     b1 = cmul(b1, SIGN < 0 ? tw.w2[1] : cconj(tw.w2[1]));
     team_sync<T>(team);
-    buf[t] = cadd(a0, b0);
-    buf[t + M / 2] = csub(a0, b0);
-    buf[t + T] = cadd(a1, b1);
-    buf[t + T + M / 2] = csub(a1, b1);
+    buf[sw(t)] = cadd(a0, b0);
+    buf[sw(t + M / 2)] = csub(a0, b0);
+    buf[sw(t + T)] = cadd(a1, b1);
+    buf[sw(t + T + M / 2)] = csub(a1, b1);
   }
   team_sync<T>(team);
 }
 
 // Inverse real FFT of the Hermitian modes Y_0..Y_M held in buf (already
-// scaled by 1/N); on return the float view of buf holds the N real outputs
-// in pixel order.
+// scaled by 1/N); on return the float view holds the N real outputs
+// (pixel p at swf(p)).
 template <int N>
 __device__ __forceinline__ void inverse_real_fft(float2 *buf, const Twiddles<N> &tw, int t, int team) {
   constexpr int T = Fft<N>::T;
@@ -182,31 +209,31 @@ __device__ __forceinline__ void inverse_real_fft(float2 *buf, const Twiddles<N> 
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int k = t + r * T;
-    const float2 yk = buf[k];
-    const float2 ym = cconj(buf[M - k]);
+    const float2 yk = buf[sw(k)];
+    const float2 ym = cconj(buf[sw(M - k)]);
     // Z_k = (Y_k + conj Y_{M-k}) + i (Y_k - conj Y_{M-k}) e^{+2 pi i k/N}
     v[r] = cadd(cadd(yk, ym), cmul_i<1>(cmul(csub(yk, ym), cconj(tw.wu[r]))));
   }
-  dft4<1>(v[0], v[1], v[2], v[3]);  // pass 0: Ns = 1, no twiddle
+  dft4<1>(v[0], v[1], v[2], v[3]);
   fft_finish<N, 1>(buf, v, tw, t, team);
 }
 
-// Forward complex FFT of the N real values in the float view of buf
-// (z_n = x_{2n} + i x_{2n+1}); on return buf holds Z_0..Z_{M-1}.
+// Forward complex FFT of the N reals in the float view of buf; on return buf
+// holds Z_0..Z_{M-1}.
 template <int N>
 __device__ __forceinline__ void forward_packed_fft(float2 *buf, const Twiddles<N> &tw, int t, int team) {
   constexpr int T = Fft<N>::T;
   float2 v[4];
   team_sync<T>(team);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) v[r] = buf[t + r * T];
+  for (int r = 0; r < 4; ++r) v[r] = buf[sw(t + r * T)];
   dft4<-1>(v[0], v[1], v[2], v[3]);
   fft_finish<N, -1>(buf, v, tw, t, team);
 }
 
 // |X_k|^2 of the real input for k = 4t+1 .. 4t+4 after forward_packed_fft:
-// X_k = E_k + e^{-2 pi i k/N} O_k with E = (Z_k + conj Z_{M-k})/2,
-// O = (Z_k - conj Z_{M-k})/(2i); Z_M = Z_0.
+// X_k = E_k + e^{-2 pi i k/N} O_k, E = (Z_k + conj Z_{M-k})/2,
+// O = (Z_k - conj Z_{M-k})/(2i), Z_M = Z_0.
 template <int N>
 __device__ __forceinline__ void power_of_modes(const float2 *buf, const float2 *__restrict__ tab, int t,
                                                float (&pk)[4]) {
@@ -214,19 +241,20 @@ __device__ __forceinline__ void power_of_modes(const float2 *buf, const float2 *
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int k = 4 * t + 1 + r;
-    const float2 zk = buf[k & (M - 1)];
-    const float2 zm = cconj(buf[(M - k) & (M - 1)]);
+    const float2 zk = buf[sw(k & (M - 1))];
+    const float2 zm = cconj(buf[sw((M - k) & (M - 1))]);
     const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
     const float2 dd = csub(zk, zm);
-    const float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);  // (Z - conj Z')/(2i)
-    const float2 w = tab[k & (N - 1)];                          // e^{-2 pi i k/N}
+    const float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);
+    const float2 w = __ldg(tab + (k & (N - 1)));
     const float2 x = cadd(e, cmul(w, o));
     pk[r] = fmaf(x.x, x.x, x.y * x.y);
   }
 }
 
 // ------------------------------------------------------------------ small-scale modes
-// Writes Y_m = X_m/N for m = 0..M into buf (Philox words -> Box-Muller).
+// Y_m = X_m / N for m = 0..M into buf (Philox words -> Box-Muller):
+// X_m = A_m sqrt(-ln u1) e^{2 pi i u2} (= A (e1 + i e2)/sqrt 2), X_M = A e1.
 template <int N>
 __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__restrict__ amp, uint32_t seg,
                                                   uint64_t id, uint32_t seed, int t) {
@@ -239,15 +267,15 @@ __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__re
     const u32x4 w = philox4x32_10(u32x4{c, seg, id_hi, 0u}, seed, id_lo);
     const int m0 = 2 * c, m1 = 2 * c + 1;
     const float2 p0 = unit_phase(w.y), p1 = unit_phase(w.w);
-    const float r0 = sqrtf(-log_uniform(w.x)), r1 = sqrtf(-log_uniform(w.z));
-    const float a0 = amp[m0] * r0, a1 = amp[m1] * r1;
-    buf[m0] = (m0 == 0) ? make_float2(0.f, 0.f) : make_float2(a0 * p0.x, a0 * p0.y);
-    buf[m1] = make_float2(a1 * p1.x, a1 * p1.y);
+    const float a0 = __ldg(amp + m0) * sqrt_pos(neg_log_uniform(w.x));
+    const float a1 = __ldg(amp + m1) * sqrt_pos(neg_log_uniform(w.z));
+    buf[sw(m0)] = make_float2(a0 * p0.x, a0 * p0.y);  // amp[0] = 0 gives Y_0 = 0
+    buf[sw(m1)] = make_float2(a1 * p1.x, a1 * p1.y);
   }
-  if (t == 0) {  // Nyquist mode m = M from counter M/2, words (0, 1): real A e1
+  if (t == 0) {  // Nyquist mode m = M from counter M/2, words (0, 1)
     const u32x4 w = philox4x32_10(u32x4{static_cast<uint32_t>(M / 2), seg, id_hi, 0u}, seed, id_lo);
-    const float e1 = sqrtf(-2.0f * log_uniform(w.x)) * unit_phase(w.y).x;
-    buf[M] = make_float2(amp[M] * e1, 0.f);
+    const float e1 = sqrt_pos(2.0f * neg_log_uniform(w.x)) * unit_phase(w.y).x;
+    buf[sw(M)] = make_float2(__ldg(amp + M) * e1, 0.f);
   }
 }
 
@@ -262,8 +290,9 @@ __device__ __forceinline__ void split_coord(int64_t p, int mask, int &i0, int &i
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
-// Trilinear (delta, eta) at fixed-point coordinate (px, py, pz).
-template <int LAYOUT>
+// Trilinear (delta, eta) at fixed-point coordinate (px, py, pz).  BIG: box
+// with more than 2^30 cells (64-bit indices).
+template <int LAYOUT, bool BIG>
 __device__ __forceinline__ float2 gather(const float *__restrict__ d, const float *__restrict__ e, int lgn,
                                          int64_t px, int64_t py, int64_t pz) {
   const int mask = (1 << lgn) - 1;
@@ -272,20 +301,19 @@ __device__ __forceinline__ float2 gather(const float *__restrict__ d, const floa
   split_coord(px, mask, x0, x1, tx);
   split_coord(py, mask, y0, y1, ty);
   split_coord(pz, mask, z0, z1, tz);
-  // row index (z n + y) n in 64 bits: boxes up to 2048^3 cells
-  const size_t r00 = static_cast<size_t>((static_cast<uint32_t>(z0) << lgn) | static_cast<uint32_t>(y0)) << lgn;
-  const size_t r10 = static_cast<size_t>((static_cast<uint32_t>(z0) << lgn) | static_cast<uint32_t>(y1)) << lgn;
-  const size_t r01 = static_cast<size_t>((static_cast<uint32_t>(z1) << lgn) | static_cast<uint32_t>(y0)) << lgn;
-  const size_t r11 = static_cast<size_t>((static_cast<uint32_t>(z1) << lgn) | static_cast<uint32_t>(y1)) << lgn;
+  using I = typename std::conditional<BIG, size_t, uint32_t>::type;
+  const I zz0 = static_cast<I>(z0) << (2 * lgn), zz1 = static_cast<I>(z1) << (2 * lgn);
+  const I yy0 = static_cast<I>(y0) << lgn, yy1 = static_cast<I>(y1) << lgn;
+  const I r00 = zz0 | yy0, r10 = zz0 | yy1, r01 = zz1 | yy0, r11 = zz1 | yy1;
   float2 v[8];
   if constexpr (LAYOUT == MK_BOX_INTERLEAVED) {
     const float2 *b = reinterpret_cast<const float2 *>(d);
-    v[0] = __ldg(b + r00 + x0); v[1] = __ldg(b + r00 + x1);
-    v[2] = __ldg(b + r10 + x0); v[3] = __ldg(b + r10 + x1);
-    v[4] = __ldg(b + r01 + x0); v[5] = __ldg(b + r01 + x1);
-    v[6] = __ldg(b + r11 + x0); v[7] = __ldg(b + r11 + x1);
+    v[0] = __ldg(b + (r00 | x0)); v[1] = __ldg(b + (r00 | x1));
+    v[2] = __ldg(b + (r10 | x0)); v[3] = __ldg(b + (r10 | x1));
+    v[4] = __ldg(b + (r01 | x0)); v[5] = __ldg(b + (r01 | x1));
+    v[6] = __ldg(b + (r11 | x0)); v[7] = __ldg(b + (r11 | x1));
   } else {
-    const size_t idx[8] = {r00 + x0, r00 + x1, r10 + x0, r10 + x1, r01 + x0, r01 + x1, r11 + x0, r11 + x1};
+    const I idx[8] = {r00 | x0, r00 | x1, r10 | x0, r10 | x1, r01 | x0, r01 | x1, r11 | x0, r11 | x1};
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = make_float2(__ldg(d + idx[k]), __ldg(e + idx[k]));
   }
@@ -316,93 +344,131 @@ __device__ __forceinline__ float fgpa(float4 tab, float delta, float eta) {
 }
 
 // ------------------------------------------------------------------ statistics
-// Team-wide sum of v[NSUM]; the result is valid in thread t == 0.
-template <int T>
-__device__ __forceinline__ void team_reduce(float (&v)[MK_NSUM], float *red, int t, int team) {
-#pragma unroll
-  for (int i = 0; i < MK_NSUM; ++i) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+// Per-warp accumulators in shared memory, FP32 with Kahan compensation
+// (each slot has one writer lane), flushed to FP64 at the end of the kernel:
+//   sums[n_z][NSUM] (float2 {sum, compensation}), p1d[n_z][n_k] (float2),
+//   nseg[n_z] (uint32)
+struct WarpAcc {
+  float2 *sums, *p1d;
+  uint32_t *nseg;
+  __host__ __device__ static size_t bytes(int n_z, int n_k) {
+    return ((sizeof(float2) * n_z * (MK_NSUM + n_k) + sizeof(uint32_t) * n_z) + 15) / 16 * 16;
   }
-  if constexpr (T > 32) {
-    const int wid = t >> 5;
-    if ((t & 31) == 0) {
+  __device__ static WarpAcc at(unsigned char *base, int n_z, int n_k) {
+    WarpAcc a;
+    a.sums = reinterpret_cast<float2 *>(base);
+    a.p1d = a.sums + n_z * MK_NSUM;
+    a.nseg = reinterpret_cast<uint32_t *>(a.p1d + n_z * n_k);
+    return a;
+  }
+};
+
+__device__ __forceinline__ void kahan_add(float2 &acc, float x) {
+  const float y = x - acc.y;
+  const float t = acc.x + y;
+  acc.y = (t - acc.x) - y;
+  acc.x = t;
+}
+
+// Warp reduce-scatter of 16 values: afterwards lanes l and l + 16 hold the
+// warp total of v[l & 15].
+__device__ __forceinline__ float reduce_scatter16(float (&v)[16], int lane) {
 #pragma unroll
-      for (int i = 0; i < MK_NSUM; ++i) red[wid * MK_NSUM + i] = v[i];
-    }
-    team_sync<T>(team);
-    if (t == 0) {
+  for (int s = 8; s >= 1; s >>= 1) {
 #pragma unroll
-      for (int i = 0; i < MK_NSUM; ++i) {
-        float s = red[i];
-        for (int w = 1; w < T / 32; ++w) s += red[w * MK_NSUM + i];
-        v[i] = s;
-      }
+    for (int i = 0; i < s; ++i) {
+      const bool up = lane & s;
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
     }
-    team_sync<T>(team);
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
+// Warp reduce-scatter of 32 values: lane l holds the warp total of v[l].
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+#pragma unroll
+    for (int i = 0; i < s; ++i) {
+      const bool up = lane & s;
+      const float send = up ? v[i] : v[i + s];
+      const float keep = up ? v[i + s] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  return v[0];
+}
+
+// Pixel sums of one pixel: n, F, F^2, d, e, d^2, e^2, d e, F d, F e.
+__device__ __forceinline__ void add_pixel(float *a, float f, float d, float e) {
+  a[0] += 1.f;
+  a[1] += f;
+  a[2] = fmaf(f, f, a[2]);
+  a[3] += d;
+  a[4] += e;
+  a[5] = fmaf(d, d, a[5]);
+  a[6] = fmaf(e, e, a[6]);
+  a[7] = fmaf(d, e, a[7]);
+  a[8] = fmaf(f, d, a[8]);
+  a[9] = fmaf(f, e, a[9]);
+}
+
+// Flush the thread sums of bins zf (a0) and zf + 1 (a1) into the warp
+// accumulators (warp-uniform call).
+__device__ __forceinline__ void flush_pixel_sums(const WarpAcc &W, int n_z, int zf, bool two, const float *a0,
+                                                 const float *a1, int lane) {
+  if (!two) {
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = i < MK_NSUM ? a0[i] : 0.f;
+    const float s = reduce_scatter16(v, lane);
+    if (lane < MK_NSUM && zf >= 0 && zf < n_z) kahan_add(W.sums[zf * MK_NSUM + lane], s);
+  } else {
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = i < MK_NSUM ? a0[i] : (i < 2 * MK_NSUM ? a1[i - MK_NSUM] : 0.f);
+    const float s = reduce_scatter32(v, lane);
+    const int b = zf + (lane >= MK_NSUM ? 1 : 0);
+    if (lane < 2 * MK_NSUM && b >= 0 && b < n_z) kahan_add(W.sums[b * MK_NSUM + lane % MK_NSUM], s);
   }
 }
 
-// Pixel statistics of the team's 8 pixels per thread.  zb[i] is the
-// pixel's z bin (-1 below the range, n_z above, also for invalid pixels).
-template <int T>
-__device__ __forceinline__ void accumulate_pixels(double *acc, const StatLayout &L, const float (&f)[8],
-                                                  const float (&d)[8], const float (&e)[8],
-                                                  const int (&zb)[8], int zb_first, int zb_last, float *red,
-                                                  int t, int team) {
-  if (zb_first < 0) zb_first = 0;
-  if (zb_last > L.n_z - 1) zb_last = L.n_z - 1;
-  for (int b = zb_first; b <= zb_last; ++b) {
-    float v[MK_NSUM];
+// Pixel sums of bins beyond zf + 1 (only when a segment spans three or more
+// bins): the lanes that need it take turns adding into the warp accumulators.
+__device__ __forceinline__ void add_pixel_slow(const WarpAcc &W, int zb, float f, float d, float e) {
+  float a[MK_NSUM] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  add_pixel(a, f, d, e);
+  const unsigned active = __activemask();
+  const int lane = threadIdx.x & 31;
+  for (int l = 0; l < 32; ++l) {
+    if (((active >> l) & 1u) && l == lane) {
 #pragma unroll
-    for (int i = 0; i < MK_NSUM; ++i) v[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (zb[i] == b) {
-        v[0] += 1.f;
-        v[1] += f[i];
-        v[2] = fmaf(f[i], f[i], v[2]);
-        v[3] += d[i];
-        v[4] += e[i];
-        v[5] = fmaf(d[i], d[i], v[5]);
-        v[6] = fmaf(e[i], e[i], v[6]);
-        v[7] = fmaf(d[i], e[i], v[7]);
-        v[8] = fmaf(f[i], d[i], v[8]);
-        v[9] = fmaf(f[i], e[i], v[9]);
-      }
+      for (int i = 0; i < MK_NSUM; ++i) kahan_add(W.sums[zb * MK_NSUM + i], a[i]);
     }
-    team_reduce<T>(v, red, t, team);
-    if (t == 0) {
-#pragma unroll
-      for (int i = 0; i < MK_NSUM; ++i) acc[L.sums(b, i)] += static_cast<double>(v[i]);
-    }
+    __syncwarp(active);
   }
 }
 
-// Add the 4 mode powers of thread t (modes 4t+1..4t+4) to the P1D bins of z bin zb.
+// Add the 4 mode powers of thread t (modes 4t+1..4t+4) to the P1D bins of z
+// bin zb (warp-uniform call).  Every bin slot of a warp has one writer.
 template <int N>
-__device__ __forceinline__ void accumulate_p1d(double *acc, const StatLayout &L, const float (&pk)[4],
-                                               float scale, int zb, int t) {
+__device__ __forceinline__ void accumulate_p1d(const WarpAcc &W, int n_k, const float (&pk)[4], float scale,
+                                               int zb, int t) {
   constexpr int M = Fft<N>::M;
-  const int per_bin = M / L.n_k;  // modes per k bin
+  const int per_bin = M / n_k;
+  const int lane = t & 31;
   if (per_bin >= 4) {
     float s = (pk[0] + pk[1]) + (pk[2] + pk[3]);
-    const int group = per_bin / 4;  // threads sharing a bin (power of two <= 32)
-    for (int o = 1; o < group && o < 32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (group > 32) {
-      // only when n_k is tiny; fall back to one add per warp leader
-      if ((t & 31) == 0) atomicAdd(&acc[L.p1d(zb, (4 * t) / per_bin)], static_cast<double>(s * scale));
-    } else if ((t & (group - 1)) == 0) {
-      acc[L.p1d(zb, (4 * t) / per_bin)] += static_cast<double>(s * scale);
-    }
+    const int group = per_bin / 4;  // threads sharing a bin
+    const int g32 = group < 32 ? group : 32;
+    for (int o = 1; o < g32; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((lane & (g32 - 1)) == 0) kahan_add(W.p1d[zb * n_k + (4 * t) / per_bin], s * scale);
   } else {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int k = 4 * t + r;  // mode k+1, bin (k * n_k)/M
-      atomicAdd(&acc[L.p1d(zb, (k * L.n_k) / M)], static_cast<double>(pk[r] * scale));
-    }
+    for (int r = 0; r < 4; ++r) kahan_add(W.p1d[zb * n_k + ((4 * t + r) * n_k) / M], pk[r] * scale);
   }
-  if (t == 0) acc[L.nseg(zb)] += 1.0;
 }
 
 }  // namespace mk

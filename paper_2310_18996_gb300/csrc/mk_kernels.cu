@@ -209,12 +209,20 @@ __global__ void k_pixtab(const double *__restrict__ zpix, const float *__restric
                           static_cast<float>(c));
 }
 
-__global__ void k_zbin(const double *__restrict__ zpix, int32_t j_max, double z_lo, double dz, int n_z,
-                       int16_t *zbin) {
+__device__ __forceinline__ int16_t bin_of(double z, double z_lo, double dz, int n_z) {
+  const double f = floor((z - z_lo) / dz);
+  return static_cast<int16_t>(f < 0.0 ? -1 : (f >= n_z ? n_z : static_cast<int>(f)));
+}
+
+// Pixel z bins and, for segments of n_seg pixels starting at J, the z bin of
+// the segment's mean z (n_z where the segment leaves the tables).
+__global__ void k_zbin(const double *__restrict__ zpix, const double *__restrict__ cumz, int32_t j_max,
+                       double z_lo, double dz, int n_z, int n_seg, int16_t *zbin, int16_t *segzbin) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= j_max) return;
-  const double f = floor((zpix[j] - z_lo) / dz);
-  zbin[j] = static_cast<int16_t>(f < 0.0 ? -1 : (f >= n_z ? n_z : static_cast<int>(f)));
+  zbin[j] = bin_of(zpix[j], z_lo, dz, n_z);
+  segzbin[j] = (j + n_seg <= j_max) ? bin_of((cumz[j + n_seg] - cumz[j]) / n_seg, z_lo, dz, n_z)
+                                    : static_cast<int16_t>(n_z);
 }
 
 __global__ void k_pack(const float *__restrict__ d, const float *__restrict__ e, int64_t n, float2 *out) {
@@ -234,13 +242,15 @@ __global__ void k_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *
 }
 
 // =================================================================== shared-memory plan
+// Per CTA: per-warp statistic accumulators (when statistics are on), then one
+// FFT buffer of N/2 + 2 complex values per team.
 template <int N>
 struct TeamSmem {
   static constexpr int T = N / 8;
-  static constexpr int BUF = N / 2 + 2;  // complex entries (N/2 + 1, padded even)
-  static constexpr int RED = (T / 32) * MK_NSUM;
-  static size_t bytes(int teams, int acc_doubles) {
-    return teams * (sizeof(double) * acc_doubles + sizeof(float2) * BUF + sizeof(float) * RED);
+  static constexpr int BUF = N / 2 + 2;
+  static size_t bytes(int threads, int n_z, int n_k, bool stats) {
+    return (stats ? static_cast<size_t>(threads / 32) * WarpAcc::bytes(n_z, n_k) : 0) +
+           static_cast<size_t>(threads / T) * BUF * sizeof(float2);
   }
 };
 
@@ -254,34 +264,55 @@ __device__ __forceinline__ int64_t upper_index(const int64_t *a, int64_t n, int6
   return lo;
 }
 
-__device__ __forceinline__ void flush_partials(double *acc_all, int teams, int size, double *partials) {
+__device__ __forceinline__ void zero_warp_acc(unsigned char *base, size_t wbytes) {
+  float *f = reinterpret_cast<float *>(base);
+  for (size_t i = threadIdx.x & 31; i < wbytes / sizeof(float); i += 32) f[i] = 0.f;
+  __syncwarp();
+}
+
+// Sum the warps' compensated FP32 accumulators in FP64 and write this CTA's
+// partials in the StatLayout order.
+__device__ void flush_warp_partials(unsigned char *smem, int nwarps, size_t wbytes, int n_z, int n_k,
+                                    double *partials) {
   __syncthreads();
-  for (int idx = threadIdx.x; idx < size; idx += blockDim.x) {
+  const StatLayout L{n_z, n_k};
+  const int ns = n_z * MK_NSUM, np = n_z * n_k;
+  for (int idx = threadIdx.x; idx < L.size(); idx += blockDim.x) {
     double s = 0.0;
-    for (int tm = 0; tm < teams; ++tm) s += acc_all[tm * size + idx];
-    partials[static_cast<size_t>(blockIdx.x) * size + idx] = s;
+    for (int w = 0; w < nwarps; ++w) {
+      const WarpAcc A = WarpAcc::at(smem + w * wbytes, n_z, n_k);
+      if (idx < ns) {
+        const float2 v = A.sums[idx];
+        s += static_cast<double>(v.x) - static_cast<double>(v.y);
+      } else if (idx < ns + np) {
+        const float2 v = A.p1d[idx - ns];
+        s += static_cast<double>(v.x) - static_cast<double>(v.y);
+      } else {
+        s += static_cast<double>(A.nseg[idx - ns - np]);
+      }
+    }
+    partials[static_cast<size_t>(blockIdx.x) * L.size() + idx] = s;
   }
 }
 
 // =================================================================== fused skewer kernel
 // One team per segment of N pixels: small-scale modes -> inverse real FFT ->
-// gather + growth per pixel -> FGPA -> stores -> pixel statistics -> forward
-// FFT of the flux -> P1D.  Teams take contiguous ranges of segments.
-template <int N, int LAYOUT>
+// per pixel gather, growth, FGPA, stores and pixel sums -> forward FFT of the
+// flux -> P1D.  Teams take contiguous ranges of segments (all segments cost
+// the same); statistics go to per-warp compensated accumulators.
+template <int N, int LAYOUT, bool BIG>
 __global__ void __launch_bounds__(256) k_skewer(SkewerParams P) {
   constexpr int T = N / 8;
-  using S = TeamSmem<N>;
+  constexpr int BUF = TeamSmem<N>::BUF;
   const int teams = blockDim.x / T;
-  const int team = threadIdx.x / T, t = threadIdx.x % T;
-  const StatLayout L{P.n_z, P.n_k};
-  const int acc_size = P.do_stats ? L.size() : 0;
+  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
-  double *acc_all = reinterpret_cast<double *>(smem);
-  float2 *buf = reinterpret_cast<float2 *>(acc_all + teams * acc_size) + team * S::BUF;
-  float *red = reinterpret_cast<float *>(reinterpret_cast<float2 *>(acc_all + teams * acc_size) +
-                                         teams * S::BUF) + team * S::RED;
-  double *acc = acc_all + team * acc_size;
-  for (int i = t; i < acc_size; i += T) acc[i] = 0.0;
+  const size_t wbytes = P.do_stats ? WarpAcc::bytes(P.n_z, P.n_k) : 0;
+  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
+  float *fb = reinterpret_cast<float *>(buf);
+  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
+  if (P.do_stats) zero_warp_acc(smem + warp * wbytes, wbytes);
 
   Twiddles<N> tw;
   load_twiddles<N>(tw, P.tw, t);
@@ -292,7 +323,6 @@ __global__ void __launch_bounds__(256) k_skewer(SkewerParams P) {
   int64_t u = g * nunits / G;
   const int64_t uend = (g + 1) * nunits / G;
   int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
-  const float *fbuf = reinterpret_cast<const float *>(buf);
   team_sync<T>(team);
 
   for (; u < uend; ++u) {
@@ -309,38 +339,45 @@ __global__ void __launch_bounds__(256) k_skewer(SkewerParams P) {
     small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
     team_sync<T>(team);
     inverse_real_fft<N>(buf, tw, t, team);
-    float ds[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) ds[k] = fbuf[t + T * k];
 
-    // ---- gather, growth, FGPA
-    float dt[8], eg[8], f[8];
-    int zb[8];
+    // ---- per pixel: gather, growth, FGPA, stores, pixel sums
+    const int jb = sk.j_lo + static_cast<int>(j0);
+    int zf = 0, zl = 0;
+    if (P.do_stats) {
+      zf = __ldg(P.zbin + jb);
+      zl = __ldg(P.zbin + jb + npx - 1);
+    }
+    float a0[MK_NSUM], a1[MK_NSUM];
+#pragma unroll
+    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
     int64_t px = sk.p0[0] + (j0 + t) * sk.step[0];
     int64_t py = sk.p0[1] + (j0 + t) * sk.step[1];
     int64_t pz = sk.p0[2] + (j0 + t) * sk.step[2];
     const int64_t sx = T * sk.step[0], sy = T * sk.step[1], sz = T * sk.step[2];
     const int64_t out0 = sk.offset + j0;
-    const int jb = sk.j_lo + static_cast<int>(j0);
-#pragma unroll
+#pragma unroll 2
     for (int k = 0; k < 8; ++k) {
       const int p = t + T * k;
+      float f = 0.f;
       if (p < npx) {
-        const float2 de = gather<LAYOUT>(P.box_d, P.box_e, P.lgn, px, py, pz);
+        const float2 de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
         const float4 tb = __ldg(P.pixtab + jb + p);
-        dt[k] = fmaf(tb.x, de.x, ds[k]);
-        eg[k] = tb.x * de.y;
-        f[k] = fgpa(tb, dt[k], eg[k]);
-        zb[k] = P.do_stats ? __ldg(P.zbin + jb + p) : -1;
+        const float dt = fmaf(tb.x, de.x, fb[swf(p)]);
+        const float eg = tb.x * de.y;
+        f = fgpa(tb, dt, eg);
         if (P.delta_out) {
-          P.delta_out[out0 + p] = dt[k];
-          P.eta_out[out0 + p] = eg[k];
+          P.delta_out[out0 + p] = dt;
+          P.eta_out[out0 + p] = eg;
         }
-        if (P.flux_out) P.flux_out[out0 + p] = f[k];
-      } else {
-        dt[k] = eg[k] = f[k] = 0.f;
-        zb[k] = -1;
+        if (P.flux_out) P.flux_out[out0 + p] = f;
+        if (P.do_stats) {
+          const int zb = __ldg(P.zbin + jb + p);
+          if (zb == zf) add_pixel(a0, f, dt, eg);
+          else if (zb == zf + 1) add_pixel(a1, f, dt, eg);
+          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dt, eg);
+        }
       }
+      fb[swf(p)] = f;
       px += sx;
       py += sy;
       pz += sz;
@@ -348,26 +385,21 @@ __global__ void __launch_bounds__(256) k_skewer(SkewerParams P) {
 
     // ---- statistics
     if (P.do_stats) {
-      const int zf = __ldg(P.zbin + jb), zl = __ldg(P.zbin + jb + npx - 1);
-      accumulate_pixels<T>(acc, L, f, dt, eg, zb, zf, zl, red, t, team);
+      flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
       if (npx == N) {
-        const double zm = (P.cumz[jb + N] - P.cumz[jb]) / N;
-        const double fz = floor((zm - P.z_lo) / P.dz);
-        if (fz >= 0.0 && fz < P.n_z) {
-          float *fw = reinterpret_cast<float *>(buf);
-          team_sync<T>(team);
-#pragma unroll
-          for (int k = 0; k < 8; ++k) fw[t + T * k] = f[k];
+        const int zs = __ldg(P.segzbin + jb);
+        if (zs >= 0 && zs < P.n_z) {
           forward_packed_fft<N>(buf, tw, t, team);
           float pk[4];
           power_of_modes<N>(buf, P.tw, t, pk);
-          accumulate_p1d<N>(acc, L, pk, static_cast<float>(P.dr / N), static_cast<int>(fz), t);
+          accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
+          if (t == 0) W.nseg[zs] += 1u;
         }
       }
     }
     team_sync<T>(team);
   }
-  if (P.do_stats) flush_partials(acc_all, teams, acc_size, P.partials);
+  if (P.do_stats) flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
 }
 
 // =================================================================== flux kernel
@@ -399,18 +431,16 @@ __global__ void __launch_bounds__(256) k_flux(FluxParams P) {
 template <int N>
 __global__ void __launch_bounds__(256) k_stats(StatParams P) {
   constexpr int T = N / 8;
-  using S = TeamSmem<N>;
+  constexpr int BUF = TeamSmem<N>::BUF;
   const int teams = blockDim.x / T;
-  const int team = threadIdx.x / T, t = threadIdx.x % T;
-  const StatLayout L{P.n_z, P.n_k};
-  const int acc_size = L.size();
+  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
-  double *acc_all = reinterpret_cast<double *>(smem);
-  float2 *buf = reinterpret_cast<float2 *>(acc_all + teams * acc_size) + team * S::BUF;
-  float *red = reinterpret_cast<float *>(reinterpret_cast<float2 *>(acc_all + teams * acc_size) +
-                                         teams * S::BUF) + team * S::RED;
-  double *acc = acc_all + team * acc_size;
-  for (int i = t; i < acc_size; i += T) acc[i] = 0.0;
+  const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
+  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
+  float *fb = reinterpret_cast<float *>(buf);
+  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
+  zero_warp_acc(smem + warp * wbytes, wbytes);
   Twiddles<N> tw;
   load_twiddles<N>(tw, P.tw, t);
 
@@ -431,59 +461,64 @@ __global__ void __launch_bounds__(256) k_stats(StatParams P) {
     const int64_t nout = P.off_out[i + 1] - o;
     const int64_t k0 = static_cast<int64_t>(s) * N;
     const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
-    float f[8], d[8], e[8];
-    int zb[8];
-    auto zbin_of = [&](int64_t k) -> int {
-      const int64_t J = sk.j_lo + k * R;
+    auto zbin_of = [&](int64_t kk) -> int {
+      const int64_t J = sk.j_lo + kk * R;
       if (R == 1) return __ldg(P.zbin + J);
       const double fz = floor(((P.cumz[J + R] - P.cumz[J]) / R - P.z_lo) / P.dz);
       return fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
     };
+    const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
+    float a0[MK_NSUM], a1[MK_NSUM];
 #pragma unroll
+    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
+#pragma unroll 2
     for (int q = 0; q < 8; ++q) {
       const int p = t + T * q;
+      float f = 0.f;
       if (p < npx) {
-        const int64_t k = k0 + p;
-        f[q] = P.flux[o + k];
+        const int64_t kk = k0 + p;
+        f = P.flux[o + kk];
         float ds = 0.f, es = 0.f;
         if (P.delta) {
           for (int r = 0; r < R; ++r) {
-            ds += P.delta[sk.offset + k * R + r];
-            es += P.eta[sk.offset + k * R + r];
+            ds += P.delta[sk.offset + kk * R + r];
+            es += P.eta[sk.offset + kk * R + r];
           }
           if (R > 1) {
             ds /= static_cast<float>(R);
             es /= static_cast<float>(R);
           }
         }
-        d[q] = ds;
-        e[q] = es;
-        zb[q] = zbin_of(k);
-      } else {
-        f[q] = d[q] = e[q] = 0.f;
-        zb[q] = -1;
+        const int zb = zbin_of(kk);
+        if (zb == zf) add_pixel(a0, f, ds, es);
+        else if (zb == zf + 1) add_pixel(a1, f, ds, es);
+        else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, ds, es);
       }
+      fb[swf(p)] = f;
     }
-    const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
-    accumulate_pixels<T>(acc, L, f, d, e, zb, zf, zl, red, t, team);
+    flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
     if (npx == N) {
-      const int64_t J0 = sk.j_lo + k0 * R;
-      const double zm = (P.cumz[J0 + static_cast<int64_t>(N) * R] - P.cumz[J0]) / (static_cast<double>(N) * R);
-      const double fz = floor((zm - P.z_lo) / P.dz);
-      if (fz >= 0.0 && fz < P.n_z) {
-        float *fw = reinterpret_cast<float *>(buf);
-        team_sync<T>(team);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) fw[t + T * q] = f[q];
+      int zs;
+      if (R == 1) {
+        zs = __ldg(P.segzbin + sk.j_lo + k0);
+      } else {
+        const int64_t J0 = sk.j_lo + k0 * R;
+        const double zm =
+            (P.cumz[J0 + static_cast<int64_t>(N) * R] - P.cumz[J0]) / (static_cast<double>(N) * R);
+        const double fz = floor((zm - P.z_lo) / P.dz);
+        zs = fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
+      }
+      if (zs >= 0 && zs < P.n_z) {
         forward_packed_fft<N>(buf, tw, t, team);
         float pk[4];
         power_of_modes<N>(buf, P.tw, t, pk);
-        accumulate_p1d<N>(acc, L, pk, static_cast<float>(R * P.dr / N), static_cast<int>(fz), t);
+        accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
+        if (t == 0) W.nseg[zs] += 1u;
       }
     }
     team_sync<T>(team);
   }
-  flush_partials(acc_all, teams, acc_size, P.partials);
+  flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
 }
 
 // =================================================================== finalize
@@ -569,9 +604,9 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_zbin(const double *zpix, int32_t j_max, double z_lo, double dz, int n_z, int16_t *zbin,
-                        cudaStream_t st) {
-  k_zbin<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, j_max, z_lo, dz, n_z, zbin);
+cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
+                        int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st) {
+  k_zbin<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, cumz, j_max, z_lo, dz, n_z, n_seg, zbin, segzbin);
   return cudaGetLastError();
 }
 
@@ -592,84 +627,81 @@ cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t 
   return cudaGetLastError();
 }
 
-template <int N, int LAYOUT>
-static cudaError_t skewer_dispatch(const SkewerParams &P, int grid, int threads, size_t smem, cudaStream_t st) {
-  auto kern = k_skewer<N, LAYOUT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  kern<<<grid, threads, smem, st>>>(P);
-  return cudaGetLastError();
-}
-
-size_t skewer_smem_bytes(int n_fft, int threads, int acc_doubles) {
-  const int teams = threads / (n_fft / 8);
+size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats) {
   switch (n_fft) {
-    case 256: return TeamSmem<256>::bytes(teams, acc_doubles);
-    case 512: return TeamSmem<512>::bytes(teams, acc_doubles);
-    case 1024: return TeamSmem<1024>::bytes(teams, acc_doubles);
-    case 2048: return TeamSmem<2048>::bytes(teams, acc_doubles);
+    case 256: return TeamSmem<256>::bytes(threads, n_z, n_k, stats);
+    case 512: return TeamSmem<512>::bytes(threads, n_z, n_k, stats);
+    case 1024: return TeamSmem<1024>::bytes(threads, n_z, n_k, stats);
+    case 2048: return TeamSmem<2048>::bytes(threads, n_z, n_k, stats);
   }
   return 0;
 }
 
-template <int N, int LAYOUT>
-static int skewer_occ(int threads, size_t smem) {
-  int b = 0;
-  cudaFuncSetAttribute(k_skewer<N, LAYOUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_skewer<N, LAYOUT>, threads, smem) != cudaSuccess) return 1;
-  return b > 0 ? b : 1;
-}
-
-int skewer_blocks_per_sm(int n_fft, int layout, int threads, int acc_doubles) {
-  const size_t smem = skewer_smem_bytes(n_fft, threads, acc_doubles);
-  const bool il = layout == MK_BOX_INTERLEAVED;
+// Calls fn with the kernel instance for (N, layout, box size).
+template <typename F>
+static cudaError_t with_skewer_kernel(int n_fft, int layout, bool big, F &&fn) {
+#define MK_SK_CASE(NN)                                                                            \
+  case NN:                                                                                        \
+    if (layout == MK_BOX_INTERLEAVED)                                                             \
+      return big ? fn(k_skewer<NN, MK_BOX_INTERLEAVED, true>) : fn(k_skewer<NN, MK_BOX_INTERLEAVED, false>); \
+    return big ? fn(k_skewer<NN, MK_BOX_PLANAR, true>) : fn(k_skewer<NN, MK_BOX_PLANAR, false>);
   switch (n_fft) {
-    case 256: return il ? skewer_occ<256, 1>(threads, smem) : skewer_occ<256, 0>(threads, smem);
-    case 512: return il ? skewer_occ<512, 1>(threads, smem) : skewer_occ<512, 0>(threads, smem);
-    case 1024: return il ? skewer_occ<1024, 1>(threads, smem) : skewer_occ<1024, 0>(threads, smem);
-    case 2048: return il ? skewer_occ<2048, 1>(threads, smem) : skewer_occ<2048, 0>(threads, smem);
+    MK_SK_CASE(256)
+    MK_SK_CASE(512)
+    MK_SK_CASE(1024)
+    MK_SK_CASE(2048)
   }
-  return 1;
+#undef MK_SK_CASE
+  return cudaErrorInvalidValue;
 }
 
-template <int N>
-static int stats_occ(int threads, int acc_doubles) {
-  const size_t smem = TeamSmem<N>::bytes(threads / (N / 8), acc_doubles);
-  int b = 0;
-  cudaFuncSetAttribute(k_stats<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_stats<N>, threads, smem) != cudaSuccess) return 1;
-  return b > 0 ? b : 1;
-}
-
-int stats_blocks_per_sm(int n_fft, int threads, int acc_doubles) {
+template <typename F>
+static cudaError_t with_stats_kernel(int n_fft, F &&fn) {
   switch (n_fft) {
-    case 256: return stats_occ<256>(threads, acc_doubles);
-    case 512: return stats_occ<512>(threads, acc_doubles);
-    case 1024: return stats_occ<1024>(threads, acc_doubles);
-    case 2048: return stats_occ<2048>(threads, acc_doubles);
-  }
-  return 1;
-}
-
-cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads,
-                          cudaStream_t st) {
-  const size_t smem = skewer_smem_bytes(n_fft, threads, P.do_stats ? StatLayout{P.n_z, P.n_k}.size() : 0);
-  if (layout == MK_BOX_INTERLEAVED) {
-    switch (n_fft) {
-      case 256: return skewer_dispatch<256, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
-      case 512: return skewer_dispatch<512, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
-      case 1024: return skewer_dispatch<1024, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
-      case 2048: return skewer_dispatch<2048, MK_BOX_INTERLEAVED>(P, grid, threads, smem, st);
-    }
-  } else {
-    switch (n_fft) {
-      case 256: return skewer_dispatch<256, MK_BOX_PLANAR>(P, grid, threads, smem, st);
-      case 512: return skewer_dispatch<512, MK_BOX_PLANAR>(P, grid, threads, smem, st);
-      case 1024: return skewer_dispatch<1024, MK_BOX_PLANAR>(P, grid, threads, smem, st);
-      case 2048: return skewer_dispatch<2048, MK_BOX_PLANAR>(P, grid, threads, smem, st);
-    }
+    case 256: return fn(k_stats<256>);
+    case 512: return fn(k_stats<512>);
+    case 1024: return fn(k_stats<1024>);
+    case 2048: return fn(k_stats<2048>);
   }
   return cudaErrorInvalidValue;
+}
+
+template <typename K>
+static int occupancy(K kern, int threads, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem) != cudaSuccess || v < 1) return 1;
+  return v;
+}
+
+int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int threads, int n_z, int n_k, bool stats) {
+  const size_t smem = skewer_smem_bytes(n_fft, threads, n_z, n_k, stats);
+  int b = 1;
+  with_skewer_kernel(n_fft, layout, lgn > 10, [&](auto kern) {
+    b = occupancy(kern, threads, smem);
+    return cudaSuccess;
+  });
+  return b;
+}
+
+int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k) {
+  const size_t smem = skewer_smem_bytes(n_fft, threads, n_z, n_k, true);
+  int b = 1;
+  with_stats_kernel(n_fft, [&](auto kern) {
+    b = occupancy(kern, threads, smem);
+    return cudaSuccess;
+  });
+  return b;
+}
+
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads, cudaStream_t st) {
+  const size_t smem = skewer_smem_bytes(n_fft, threads, P.n_z, P.n_k, P.do_stats != 0);
+  return with_skewer_kernel(n_fft, layout, P.lgn > 10, [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, st>>>(P);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st) {
@@ -681,24 +713,14 @@ cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int N>
-static cudaError_t stats_dispatch(const StatParams &P, int grid, int threads, cudaStream_t st) {
-  const size_t smem = TeamSmem<N>::bytes(threads / (N / 8), StatLayout{P.n_z, P.n_k}.size());
-  auto kern = k_stats<N>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return e;
-  kern<<<grid, threads, smem, st>>>(P);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st) {
-  switch (n_fft) {
-    case 256: return stats_dispatch<256>(P, grid, threads, st);
-    case 512: return stats_dispatch<512>(P, grid, threads, st);
-    case 1024: return stats_dispatch<1024>(P, grid, threads, st);
-    case 2048: return stats_dispatch<2048>(P, grid, threads, st);
-  }
-  return cudaErrorInvalidValue;
+  const size_t smem = skewer_smem_bytes(n_fft, threads, P.n_z, P.n_k, true);
+  return with_stats_kernel(n_fft, [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, st>>>(P);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_finalize(const double *partials, int nparts, int n_z, int n_k, int n_fft, mk_stats_out *out,

@@ -16,14 +16,14 @@ cudaError_t launch_scan(const int64_t *a, const int64_t *b, int64_t n, int64_t *
                         mk_skewer *sk, void *ws, cudaStream_t st);
 cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, const NodeParams &nd,
                           float4 *pixtab, cudaStream_t st);
-cudaError_t launch_zbin(const double *zpix, int32_t j_max, double z_lo, double dz, int n_z, int16_t *zbin,
-                        cudaStream_t st);
+cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
+                        int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st);
 cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);
 cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st);
-int skewer_blocks_per_sm(int n_fft, int layout, int threads, int acc_doubles);
-int stats_blocks_per_sm(int n_fft, int threads, int acc_doubles);
-size_t skewer_smem_bytes(int n_fft, int threads, int acc_doubles);
+int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int threads, int n_z, int n_k, bool stats);
+int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k);
+size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
 cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads,
                           cudaStream_t st);
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);

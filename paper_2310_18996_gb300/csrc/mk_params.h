@@ -52,9 +52,10 @@ struct SkewerParams {
   int32_t lgn;
   // tables
   const float4 *pixtab;  // per global pixel J: {G, a log2e, b log2e, c}
-  const int16_t *zbin;   // per J: z bin, -1 below, n_z above
-  const double *cumz;    // per J: sum_{J' < J} z_J'
-  const float *amp;      // A_m / N, m = 0..N/2
+  const int16_t *zbin;     // per J: z bin, -1 below, n_z above
+  const int16_t *segzbin;  // per J: z bin of the mean z of pixels J .. J+N-1
+  const double *cumz;      // per J: sum_{J' < J} z_J'
+  const float *amp;        // A_m / N, m = 0..N/2
   const float2 *tw;      // e^{-2 pi i k/N}, k < N
   uint32_t seed;
   int32_t j_max;
@@ -65,6 +66,7 @@ struct SkewerParams {
   int32_t do_stats;
   int32_t n_z, n_k;
   double z_lo, dz, dr;
+  float p1d_scale;   // dr / N
   double *partials;  // [gridDim.x][layout size]
   int *err;
 };
@@ -79,11 +81,13 @@ struct StatParams {
   const float *delta, *eta;  // fine fields or NULL
   int32_t rebin;
   const int16_t *zbin;
+  const int16_t *segzbin;
   const double *cumz;
   const float2 *tw;
   int32_t j_max;
   int32_t n_z, n_k;
   double z_lo, dz, dr;
+  float p1d_scale;  // rebin dr / N
   double *partials;
   int *err;
 };
