@@ -70,6 +70,10 @@ extern "C" {
 #define MK_STORE_FIELDS 1u /* write delta_tot and eta (pre-FGPA skewers) */
 #define MK_STORE_FLUX 2u   /* write F */
 #define MK_STATS 4u        /* accumulate and return statistics */
+#define MK_AUTOTUNE 8u     /* time the admissible launch shapes on this call's inputs the first
+                              time a kernel variant runs, and keep the fastest for the context */
+#define MK_GRAPH 16u       /* run the step (geometry, scan, fused kernel, statistics readback)
+                              as a captured CUDA graph, re-captured when an argument changes */
 
 typedef struct mk_ctx mk_ctx; /* opaque, library-owned */
 typedef struct mk_box mk_box; /* opaque, refers to caller-owned device memory */
@@ -201,8 +205,10 @@ int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float
    the inverse real DFT (1/N normalisation) of modes
    X_m = A_m (e1 + i e2)/sqrt(2), 0 < m < N/2, X_{N/2} = A e1, X_0 = 0,
    A_m = sqrt(N P_S(k_m)/dr), with (e1, e2) the Box-Muller normals of
-   Philox4x32-10 words: counter (m >> 1, s, id >> 32, 0), key (seed, id),
-   words (0,1) for even m and (2,3) for odd m. */
+   Philox4x32-10 words: key (seed, id); for 0 < m < N/2 counter
+   (m >> 1, s, id >> 32, 0), words (0,1) for even m and (2,3) for odd m; the
+   Nyquist mode m = N/2 takes words (0,1) of counter 0, which no other mode
+   uses. */
 int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
                     const mk_skewer_params *params, mk_skewer *d_sk, int64_t *d_offsets,
                     float *d_delta_out, float *d_eta_out, int64_t capacity_px,
@@ -231,12 +237,27 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
    `flags` does not ask for.  P1D segments coincide with delta_S segments
    (bins->n_fft must equal params->n_fft).  d_delta_out / d_eta_out /
    d_flux_out may be NULL when not stored.  With MK_STATS the call
-   synchronises and fills *h_out; otherwise it is asynchronous. */
+   synchronises and fills *h_out; otherwise it is asynchronous.
+   MK_AUTOTUNE: the first call of a kernel variant (FFT length, box layout
+   and size, store/statistics flags) times each admissible launch shape
+   (CTA of 128 or 256 threads, compiler or four-CTA-per-SM occupancy) on its
+   own inputs and keeps the fastest for later calls.  MK_GRAPH: the step is
+   captured into a CUDA graph on the context stream (which must not be the
+   legacy default stream) and replayed while the arguments, tables and
+   workspaces stay the same; with timing on, the timed region is then the
+   whole graph. */
 int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
            const mk_skewer_params *params, const mk_fgpa_nodes *nodes,
            const mk_stat_bins *bins, uint32_t flags, mk_skewer *d_sk, int64_t *d_offsets,
            float *d_delta_out, float *d_eta_out, float *d_flux_out, int64_t capacity_px,
            mk_stats_out *h_out);
+
+/* Launch shape the context uses for a fused-kernel variant: *threads per CTA
+   and *occupancy target (1: compiler's register choice, 4: four CTAs per
+   SM).  MK_OK when the autotuner chose it, MK_ERANGE when it is the default
+   (still written). */
+int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box, uint32_t flags,
+                     int32_t *threads, int32_t *occupancy);
 
 /* ---------------------------------------------------------------- statistics without allocation */
 

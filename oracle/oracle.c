@@ -14,7 +14,8 @@
  *    takes the pixels with r_lo <= r_J < r_hi of its forest window;
  *  - interpolation: trilinear between voxel centres (i + 1/2) cell, periodic;
  *  - small-scale field: independent realisation per segment of n_fft pixels
- *    aligned to the skewer start, Philox4x32-10 noise, Box-Muller normals;
+ *    aligned to the skewer start, Philox4x32-10 noise, Box-Muller normals
+ *    (the Nyquist mode takes the counter-0 words that mode 0 leaves unused);
  *  - a, b, c: ln a, b, c linear in z between nodes, clamped at the ends;
  *  - rebin: box-car mean of R consecutive pixels, incomplete tail dropped.
  */
@@ -307,9 +308,11 @@ double orc_trilinear(const float *box, int32_t n, const double c[3]) {
 /* ------------------------------------------------------------------------ */
 /* Small-scale field delta_S (Sec. 2.3): Gaussian modes times sqrt(P_S),     */
 /* inverse Fourier transform.  Mode m of segment `seg` of quasar `id`:       */
-/*   Philox counter (m >> 1, seg, id >> 32, 0), key (seed, id & 0xffffffff); */
-/*   words (0,1) serve even m, words (2,3) odd m; Box-Muller gives (e1, e2); */
-/*   X_m = A_m (e1 + i e2)/sqrt(2) for 0 < m < n/2, X_{n/2} = A e1, X_0 = 0, */
+/*   Philox key (seed, id & 0xffffffff); for 0 < m < n/2 counter             */
+/*   (m >> 1, seg, id >> 32, 0), words (0,1) for even m and (2,3) for odd m; */
+/*   the Nyquist mode m = n/2 takes words (0,1) of counter 0, the pair no    */
+/*   other mode uses (X_0 = 0).  Box-Muller gives (e1, e2);                  */
+/*   X_m = A_m (e1 + i e2)/sqrt(2) for 0 < m < n/2, X_{n/2} = A e1,          */
 /*   A_m = sqrt(n P_S(k_m) / dr).                                            */
 /* ------------------------------------------------------------------------ */
 void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double *re,
@@ -318,11 +321,12 @@ void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double 
   re[0] = 0.0;
   im[0] = 0.0;
   for (int32_t m = 1; m <= n / 2; ++m) {
-    uint32_t ctr[4] = {(uint32_t)(m >> 1), (uint32_t)seg, (uint32_t)(id >> 32), 0u};
+    uint32_t c = (m < n / 2) ? (uint32_t)(m >> 1) : 0u;
+    uint32_t ctr[4] = {c, (uint32_t)seg, (uint32_t)(id >> 32), 0u};
     uint32_t key[2] = {cfg->seed, (uint32_t)(id & 0xffffffffu)};
     uint32_t w[4];
     orc_philox4x32_10(ctr, key, w);
-    int pair = (m & 1) ? 2 : 0;
+    int pair = (m < n / 2 && (m & 1)) ? 2 : 0;
     double e1, e2;
     orc_box_muller(w[pair], w[pair + 1], &e1, &e2);
     double amp = sqrt((double)n * cfg->p_s[m] / cfg->dr);

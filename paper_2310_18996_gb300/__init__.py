@@ -22,11 +22,11 @@ MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
 MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
 STATIC_MAX_SKEWERS = 131072
 BOX_PLANAR, BOX_INTERLEAVED = 0, 1
-STORE_FIELDS, STORE_FLUX, STATS = 1, 2, 4
+STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
            "mk_free_box", "mk_pack_box", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
-           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static"]
+           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config"]
 
 
 class MkError(RuntimeError):
@@ -110,6 +110,7 @@ def lib():
                                      u32, vp, vp, vp, vp, vp, i64, P(StatsOut)]),
                 "mk_stats_static": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, i32, vp, vp,
                                               P(StatBins), P(StatsOut)]),
+                "mk_launch_config": (C.c_int, [vp, i32, i32, i32, u32, P(i32), P(i32)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -225,6 +226,14 @@ class Context:
 
     def set_timing(self, on=True):
         self._check(lib().mk_set_timing(self.h, 1 if on else 0))
+
+    def launch_config(self, n_fft, layout=BOX_INTERLEAVED, big_box=False, flags=STATS):
+        """(threads, occupancy, tuned) of the fused kernel variant."""
+        t, o = C.c_int32(), C.c_int32()
+        rc = lib().mk_launch_config(self.h, n_fft, layout, 1 if big_box else 0, flags, C.byref(t), C.byref(o))
+        if rc not in (MK_OK, MK_ERANGE):
+            self._check(rc)
+        return t.value, o.value, rc == MK_OK
 
     def last_kernel_ms(self):
         ms = C.c_double()

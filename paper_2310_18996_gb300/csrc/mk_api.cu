@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -131,6 +132,11 @@ struct mk_box {
   int lgn;
 };
 
+struct LaunchCfg {
+  int threads;  // CTA size of the fused kernel
+  int minb;     // occupancy target of the instance (1 or 4)
+};
+
 struct mk_ctx {
   int device = 0;
   int sms = 0;
@@ -167,6 +173,12 @@ struct mk_ctx {
   mk_stats_out *d_stats = nullptr, *h_stats = nullptr;
   int64_t *h_total = nullptr;  // pinned
   int skewer_threads = 256;
+  // launch configurations chosen by the autotuner, per kernel variant
+  std::map<uint64_t, LaunchCfg> tuned;
+  // captured graph of the last mk_run with MK_GRAPH, and what it was made from
+  cudaGraphExec_t graph = nullptr;
+  std::vector<unsigned char> graph_key;
+  uint64_t generation = 0;  // bumped whenever a table or workspace moves
   bool timing = false;
   bool timed = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -192,6 +204,7 @@ int fail(mk_ctx *ctx, int code, const char *fmt, ...) {
 
 int grow(mk_ctx *ctx, void **p, size_t *cap, size_t need) {
   if (*cap >= need && *p) return MK_OK;
+  ++ctx->generation;
   if (*p) cudaFree(*p);
   *p = nullptr;
   *cap = 0;
@@ -205,6 +218,7 @@ int grow(mk_ctx *ctx, void **p, size_t *cap, size_t need) {
 
 int ensure_counts(mk_ctx *ctx, int64_t n) {
   if (ctx->cnt_cap >= n + 1 && ctx->d_cnt_px) return MK_OK;
+  ++ctx->generation;
   cudaFree(ctx->d_cnt_px);
   cudaFree(ctx->d_cnt_seg);
   cudaFree(ctx->d_segoff);
@@ -220,6 +234,7 @@ int ensure_counts(mk_ctx *ctx, int64_t n) {
 
 int ensure_pixel_tables(mk_ctx *ctx, double dr) {
   if (ctx->dr == dr && ctx->d_zpix) return MK_OK;
+  ++ctx->generation;
   const double rmax = ctx->cos.distance(kZMax - 2 * kDcStep);
   const int32_t jmax = static_cast<int32_t>(std::floor(rmax / dr)) - 1;
   std::vector<double> z(jmax), cz(jmax + 1);
@@ -270,6 +285,7 @@ int tw_slot(int n_fft) {
 int ensure_twiddles(mk_ctx *ctx, int n_fft) {
   const int slot = tw_slot(n_fft);
   if (ctx->d_tw[slot]) return MK_OK;
+  ++ctx->generation;
   std::vector<float2> tw(n_fft);
   for (int k = 0; k < n_fft; ++k) {
     const double a = 2.0 * M_PI * k / n_fft;
@@ -296,6 +312,7 @@ int ensure_amp(mk_ctx *ctx, const mk_skewer_params *p) {
   amp[0] = 0.f;
   cudaFree(ctx->d_amp);
   ctx->d_amp = nullptr;
+  ++ctx->generation;
   CK(cudaMalloc(&ctx->d_amp, sizeof(float) * (m + 1)));
   CK(cudaMemcpy(ctx->d_amp, amp.data(), sizeof(float) * (m + 1), cudaMemcpyHostToDevice));
   ctx->amp_key = key;
@@ -373,18 +390,30 @@ int time_end(mk_ctx *ctx) {
 }
 
 // persistent grids: as many resident CTAs as the SMs hold
-int skewer_grid(mk_ctx *ctx, int n_fft, const mk_box *box, int threads, const mk_stat_bins *bins) {
-  return ctx->sms * skewer_blocks_per_sm(n_fft, box->desc.layout, box->lgn, threads, bins ? bins->n_z : 0,
-                                         bins ? bins->n_k : 0, bins != nullptr);
+int skewer_grid(mk_ctx *ctx, int n_fft, const mk_box *box, LaunchCfg cfg, const mk_stat_bins *bins) {
+  return ctx->sms * skewer_blocks_per_sm(n_fft, box->desc.layout, box->lgn, cfg.minb, cfg.threads,
+                                         bins ? bins->n_z : 0, bins ? bins->n_k : 0, bins != nullptr);
+}
+
+// default launch: 256-thread CTAs, four per SM (measured faster than the
+// compiler's register choice on GB300 despite a few spilled words)
+LaunchCfg default_cfg(int n_fft) {
+  (void)n_fft;
+  return LaunchCfg{256, 4};
+}
+
+uint64_t tune_key(int n_fft, const mk_box *box, uint32_t flags) {
+  return (static_cast<uint64_t>(n_fft) << 32) | (static_cast<uint64_t>(box->desc.layout) << 16) |
+         (static_cast<uint64_t>(box->lgn > 10) << 8) | (flags & (MK_STORE_FIELDS | MK_STORE_FLUX | MK_STATS));
 }
 
 int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads) {
   return ctx->sms * stats_blocks_per_sm(bins->n_fft, threads, bins->n_z, bins->n_k);
 }
 
-int run_geometry(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, const mk_skewer_params *p,
-                 mk_skewer *d_sk, int64_t *d_offsets) {
-  GeomParams G{};
+GeomParams geom_params(mk_ctx *ctx, const mk_box *box, const mk_skewer_params *p) {
+  GeomParams G;
+  std::memset(&G, 0, sizeof(G));
   G.tab = DcTable{ctx->d_dc, ctx->n_dc, kDcStep, ctx->cosmo.omega_m};
   G.lambda_lya = ctx->cosmo.lambda_lya;
   G.dr = p->dr;
@@ -398,14 +427,25 @@ int run_geometry(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_
   G.j_max = ctx->j_max;
   G.n_fft = p->n_fft;
   G.rebin = 0;
+  return G;
+}
+
+int enqueue_geometry(mk_ctx *ctx, const GeomParams &G, const mk_qso *d_qso, int64_t n_qso, mk_skewer *d_sk,
+                     int64_t *d_offsets) {
   CK(launch_geometry(d_qso, n_qso, G, d_sk, ctx->d_cnt_px, ctx->d_cnt_seg, ctx->d_err, ctx->stream));
   CK(launch_scan(ctx->d_cnt_px, ctx->d_cnt_seg, n_qso, d_offsets, ctx->d_segoff, d_sk, ctx->d_scan_ws,
                  ctx->stream));
   return MK_OK;
 }
 
+int run_geometry(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, const mk_skewer_params *p,
+                 mk_skewer *d_sk, int64_t *d_offsets) {
+  return enqueue_geometry(ctx, geom_params(ctx, box, p), d_qso, n_qso, d_sk, d_offsets);
+}
+
 SkewerParams skewer_params(mk_ctx *ctx, const mk_box *box, const mk_skewer *d_sk, int64_t n, const mk_skewer_params *p) {
-  SkewerParams S{};
+  SkewerParams S;
+  std::memset(&S, 0, sizeof(S));
   S.sk = d_sk;
   S.segoff = ctx->d_segoff;
   S.n_sk = n;
@@ -502,6 +542,7 @@ void mk_destroy(mk_ctx *ctx) {
   cudaFree(ctx->d_partials);
   cudaFree(ctx->d_stats);
   cudaFreeHost(ctx->h_stats);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
   delete ctx;
@@ -587,9 +628,10 @@ int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t
   S.flux_out = nullptr;
   S.capacity = capacity_px;
   S.do_stats = 0;
-  const int grid = skewer_grid(ctx, params->n_fft, box, ctx->skewer_threads, nullptr);
+  const LaunchCfg cfg = default_cfg(params->n_fft);
+  const int grid = skewer_grid(ctx, params->n_fft, box, cfg, nullptr);
   if ((rc = time_begin(ctx))) return rc;
-  CK(launch_skewer(S, params->n_fft, box->desc.layout, grid, ctx->skewer_threads, ctx->stream));
+  CK(launch_skewer(S, params->n_fft, box->desc.layout, cfg.minb, grid, cfg.threads, ctx->stream));
   return time_end(ctx);
 }
 
@@ -681,6 +723,8 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, true);
   if (rc || (rc = check_nodes(ctx, nodes))) return rc;
+  if (flags & ~(MK_STORE_FIELDS | MK_STORE_FLUX | MK_STATS | MK_AUTOTUNE | MK_GRAPH))
+    return fail(ctx, MK_EINVAL, "unknown flags 0x%x", flags);
   const bool stats = flags & MK_STATS;
   if (stats) {
     if ((rc = check_bins(ctx, bins))) return rc;
@@ -692,6 +736,8 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
   if ((flags & MK_STORE_FIELDS) && (!d_delta_out || !d_eta_out))
     return fail(ctx, MK_EINVAL, "MK_STORE_FIELDS needs d_delta_out and d_eta_out");
   if ((flags & MK_STORE_FLUX) && !d_flux_out) return fail(ctx, MK_EINVAL, "MK_STORE_FLUX needs d_flux_out");
+  if ((flags & MK_GRAPH) && !ctx->stream)
+    return fail(ctx, MK_EINVAL, "MK_GRAPH needs a non-default stream (the legacy stream cannot be captured)");
   CK(cudaSetDevice(ctx->device));
   if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_qso)) ||
       (rc = ensure_twiddles(ctx, params->n_fft)) || (rc = ensure_amp(ctx, params)) ||
@@ -699,11 +745,14 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
     return rc;
   if (stats && (rc = ensure_zbin(ctx, bins))) return rc;
   const StatLayout L{stats ? bins->n_z : 0, stats ? bins->n_k : 0};
-  const int grid = skewer_grid(ctx, params->n_fft, box, ctx->skewer_threads, stats ? bins : nullptr);
-  if (stats && (rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
-                          sizeof(double) * static_cast<size_t>(grid) * L.size())))
-    return rc;
-  if ((rc = run_geometry(ctx, box, d_qso, n_qso, params, d_sk, d_offsets))) return rc;
+
+  // the launch shape: tuned, or tune now, or the default
+  const uint64_t key = tune_key(params->n_fft, box, flags);
+  LaunchCfg cfg = default_cfg(params->n_fft);
+  auto it = ctx->tuned.find(key);
+  if (it != ctx->tuned.end()) cfg = it->second;
+
+  const GeomParams G = geom_params(ctx, box, params);
   SkewerParams S = skewer_params(ctx, box, d_sk, n_qso, params);
   S.delta_out = (flags & MK_STORE_FIELDS) ? d_delta_out : nullptr;
   S.eta_out = (flags & MK_STORE_FIELDS) ? d_eta_out : nullptr;
@@ -715,13 +764,127 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
     S.n_k = bins->n_k;
     S.z_lo = bins->z_lo;
     S.dz = bins->dz;
-    S.partials = ctx->d_partials;
   }
-  if ((rc = time_begin(ctx))) return rc;
-  CK(launch_skewer(S, params->n_fft, box->desc.layout, grid, ctx->skewer_threads, ctx->stream));
-  if ((rc = time_end(ctx))) return rc;
+
+  // enqueue geometry, the fused kernel and (with statistics) their readback
+  auto enqueue = [&](LaunchCfg c, int grid, bool timed) -> int {
+    int r = enqueue_geometry(ctx, G, d_qso, n_qso, d_sk, d_offsets);
+    if (r) return r;
+    S.partials = ctx->d_partials;
+    if (timed && (r = time_begin(ctx))) return r;
+    CK(launch_skewer(S, params->n_fft, box->desc.layout, c.minb, grid, c.threads, ctx->stream));
+    if (timed && (r = time_end(ctx))) return r;
+    if (stats) {
+      CK(launch_finalize(ctx->d_partials, grid, bins->n_z, bins->n_k, bins->n_fft, ctx->d_stats, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(mk_stats_out), cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    return MK_OK;
+  };
+  auto ensure_partials = [&](int grid) -> int {
+    if (!stats) return MK_OK;
+    return grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
+                sizeof(double) * static_cast<size_t>(grid) * L.size());
+  };
+
+  if ((flags & MK_AUTOTUNE) && it == ctx->tuned.end()) {
+    // time every admissible shape on this call's inputs; outputs are rewritten
+    // by the final run below
+    const LaunchCfg cand[4] = {{256, 1}, {256, 4}, {128, 1}, {128, 4}};
+    cudaEvent_t a0, a1;
+    CK(cudaEventCreate(&a0));
+    CK(cudaEventCreate(&a1));
+    float best = 1e30f;
+    for (const LaunchCfg &c : cand) {
+      if (c.threads < params->n_fft / 8) continue;  // a team must fit in a CTA
+      const int grid = skewer_grid(ctx, params->n_fft, box, c, stats ? bins : nullptr);
+      if ((rc = ensure_partials(grid))) break;
+      if ((rc = enqueue_geometry(ctx, G, d_qso, n_qso, d_sk, d_offsets))) break;
+      S.partials = ctx->d_partials;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2 && rc == MK_OK; ++rep) {  // first launch warms caches
+        if (cudaEventRecord(a0, ctx->stream) != cudaSuccess ||
+            launch_skewer(S, params->n_fft, box->desc.layout, c.minb, grid, c.threads, ctx->stream) != cudaSuccess ||
+            cudaEventRecord(a1, ctx->stream) != cudaSuccess || cudaEventSynchronize(a1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, a0, a1) != cudaSuccess)
+          rc = fail(ctx, MK_ECUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+      }
+      if (rc) break;
+      if (ms < best) {
+        best = ms;
+        cfg = c;
+      }
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    if (rc) return rc;
+    ctx->tuned[key] = cfg;
+  }
+
+  const int grid = skewer_grid(ctx, params->n_fft, box, cfg, stats ? bins : nullptr);
+  if ((rc = ensure_partials(grid))) return rc;
+
+  if (flags & MK_GRAPH) {
+    // replay the captured step when nothing it depends on has changed
+    std::vector<unsigned char> gkey(sizeof(G) + sizeof(S) + 8 * sizeof(int64_t));
+    unsigned char *kp = gkey.data();
+    S.partials = ctx->d_partials;
+    std::memcpy(kp, &G, sizeof(G));
+    std::memcpy(kp + sizeof(G), &S, sizeof(S));
+    const int64_t extra[8] = {reinterpret_cast<int64_t>(d_qso), n_qso, reinterpret_cast<int64_t>(d_offsets),
+                              static_cast<int64_t>(ctx->generation), grid, cfg.threads * 16 + cfg.minb,
+                              static_cast<int64_t>(flags & ~MK_AUTOTUNE),
+                              stats ? (bins->n_z * 4096 + bins->n_k * 8 + (bins->n_fft >> 8)) : 0};
+    std::memcpy(kp + sizeof(G) + sizeof(S), extra, sizeof(extra));
+    if (!ctx->graph || gkey != ctx->graph_key) {
+      if (ctx->graph) {
+        cudaGraphExecDestroy(ctx->graph);
+        ctx->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue(cfg, grid, false);
+      const cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+      if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+      }
+      if (ce != cudaSuccess) return fail(ctx, MK_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+      const cudaError_t ie = cudaGraphInstantiate(&ctx->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) {
+        ctx->graph = nullptr;
+        return fail(ctx, MK_ECUDA, "graph instantiate: %s", cudaGetErrorString(ie));
+      }
+      ctx->graph_key = gkey;
+    }
+    if ((rc = time_begin(ctx))) return rc;
+    CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+    if ((rc = time_end(ctx))) return rc;
+  } else {
+    if ((rc = enqueue(cfg, grid, true))) return rc;
+  }
   if (!stats) return MK_OK;
-  return finish_stats(ctx, grid, bins, h_out);
+  CK(cudaStreamSynchronize(ctx->stream));
+  const int e = *ctx->h_err;
+  if (e) return read_error_word(ctx);
+  std::memcpy(h_out, ctx->h_stats, sizeof(mk_stats_out));
+  return MK_OK;
+}
+
+int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box, uint32_t flags,
+                     int32_t *threads, int32_t *occupancy) {
+  if (!ctx || !threads || !occupancy) return MK_EINVAL;
+  if (tw_slot(n_fft) < 0) return fail(ctx, MK_EINVAL, "bad n_fft");
+  mk_box b{};
+  b.desc.layout = layout;
+  b.lgn = big_box ? 11 : 10;
+  LaunchCfg c = default_cfg(n_fft);
+  auto it = ctx->tuned.find(tune_key(n_fft, &b, flags));
+  if (it != ctx->tuned.end()) c = it->second;
+  *threads = c.threads;
+  *occupancy = c.minb;
+  return it != ctx->tuned.end() ? MK_OK : MK_ERANGE;
 }
 
 int mk_set_timing(mk_ctx *ctx, int on) {

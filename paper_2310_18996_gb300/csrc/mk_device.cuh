@@ -255,6 +255,8 @@ __device__ __forceinline__ void power_of_modes(const float2 *buf, const float2 *
 // ------------------------------------------------------------------ small-scale modes
 // Y_m = X_m / N for m = 0..M into buf (Philox words -> Box-Muller):
 // X_m = A_m sqrt(-ln u1) e^{2 pi i u2} (= A (e1 + i e2)/sqrt 2), X_M = A e1.
+// Counter c serves modes 2c (words 0, 1) and 2c + 1 (words 2, 3); the words
+// of counter 0 that mode 0 (X_0 = 0) would use serve the Nyquist mode M.
 template <int N>
 __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__restrict__ amp, uint32_t seg,
                                                   uint64_t id, uint32_t seed, int t) {
@@ -265,18 +267,15 @@ __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__re
   for (int q = 0; q < 2; ++q) {
     const uint32_t c = t + q * T;  // modes 2c, 2c+1 (< M)
     const u32x4 w = philox4x32_10(u32x4{c, seg, id_hi, 0u}, seed, id_lo);
-    const int m0 = 2 * c, m1 = 2 * c + 1;
+    const bool nyq = (c == 0);
+    const int m0 = nyq ? M : 2 * c, m1 = 2 * c + 1;
     const float2 p0 = unit_phase(w.y), p1 = unit_phase(w.w);
-    const float a0 = __ldg(amp + m0) * sqrt_pos(neg_log_uniform(w.x));
+    const float a0 = __ldg(amp + m0) * sqrt_pos((nyq ? 2.0f : 1.0f) * neg_log_uniform(w.x));
     const float a1 = __ldg(amp + m1) * sqrt_pos(neg_log_uniform(w.z));
-    buf[sw(m0)] = make_float2(a0 * p0.x, a0 * p0.y);  // amp[0] = 0 gives Y_0 = 0
+    buf[sw(m0)] = make_float2(a0 * p0.x, nyq ? 0.f : a0 * p0.y);
     buf[sw(m1)] = make_float2(a1 * p1.x, a1 * p1.y);
   }
-  if (t == 0) {  // Nyquist mode m = M from counter M/2, words (0, 1)
-    const u32x4 w = philox4x32_10(u32x4{static_cast<uint32_t>(M / 2), seg, id_hi, 0u}, seed, id_lo);
-    const float e1 = sqrt_pos(2.0f * neg_log_uniform(w.x)) * unit_phase(w.y).x;
-    buf[sw(M)] = make_float2(__ldg(amp + M) * e1, 0.f);
-  }
+  if (t == 0) buf[sw(0)] = make_float2(0.f, 0.f);
 }
 
 // ------------------------------------------------------------------ fixed-point gather

@@ -241,167 +241,6 @@ __global__ void k_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *
   if (i < n) cnt[i] = (off[i + 1] - off[i] + n_fft - 1) / n_fft;
 }
 
-// =================================================================== shared-memory plan
-// Per CTA: per-warp statistic accumulators (when statistics are on), then one
-// FFT buffer of N/2 + 2 complex values per team.
-template <int N>
-struct TeamSmem {
-  static constexpr int T = N / 8;
-  static constexpr int BUF = N / 2 + 2;
-  static size_t bytes(int threads, int n_z, int n_k, bool stats) {
-    return (stats ? static_cast<size_t>(threads / 32) * WarpAcc::bytes(n_z, n_k) : 0) +
-           static_cast<size_t>(threads / T) * BUF * sizeof(float2);
-  }
-};
-
-// largest i with a[i] <= v over a[0..n] (a non-decreasing)
-__device__ __forceinline__ int64_t upper_index(const int64_t *a, int64_t n, int64_t v) {
-  int64_t lo = 0, hi = n;
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (a[mid] <= v) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ void zero_warp_acc(unsigned char *base, size_t wbytes) {
-  float *f = reinterpret_cast<float *>(base);
-  for (size_t i = threadIdx.x & 31; i < wbytes / sizeof(float); i += 32) f[i] = 0.f;
-  __syncwarp();
-}
-
-// Sum the warps' compensated FP32 accumulators in FP64 and write this CTA's
-// partials in the StatLayout order.
-__device__ void flush_warp_partials(unsigned char *smem, int nwarps, size_t wbytes, int n_z, int n_k,
-                                    double *partials) {
-  __syncthreads();
-  const StatLayout L{n_z, n_k};
-  const int ns = n_z * MK_NSUM, np = n_z * n_k;
-  for (int idx = threadIdx.x; idx < L.size(); idx += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < nwarps; ++w) {
-      const WarpAcc A = WarpAcc::at(smem + w * wbytes, n_z, n_k);
-      if (idx < ns) {
-        const float2 v = A.sums[idx];
-        s += static_cast<double>(v.x) - static_cast<double>(v.y);
-      } else if (idx < ns + np) {
-        const float2 v = A.p1d[idx - ns];
-        s += static_cast<double>(v.x) - static_cast<double>(v.y);
-      } else {
-        s += static_cast<double>(A.nseg[idx - ns - np]);
-      }
-    }
-    partials[static_cast<size_t>(blockIdx.x) * L.size() + idx] = s;
-  }
-}
-
-// =================================================================== fused skewer kernel
-// One team per segment of N pixels: small-scale modes -> inverse real FFT ->
-// per pixel gather, growth, FGPA, stores and pixel sums -> forward FFT of the
-// flux -> P1D.  Teams take contiguous ranges of segments (all segments cost
-// the same); statistics go to per-warp compensated accumulators.
-template <int N, int LAYOUT, bool BIG>
-__global__ void __launch_bounds__(256) k_skewer(SkewerParams P) {
-  constexpr int T = N / 8;
-  constexpr int BUF = TeamSmem<N>::BUF;
-  const int teams = blockDim.x / T;
-  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const size_t wbytes = P.do_stats ? WarpAcc::bytes(P.n_z, P.n_k) : 0;
-  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
-  float *fb = reinterpret_cast<float *>(buf);
-  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
-  if (P.do_stats) zero_warp_acc(smem + warp * wbytes, wbytes);
-
-  Twiddles<N> tw;
-  load_twiddles<N>(tw, P.tw, t);
-
-  const int64_t nunits = P.segoff[P.n_sk];
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
-  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
-  int64_t u = g * nunits / G;
-  const int64_t uend = (g + 1) * nunits / G;
-  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
-  team_sync<T>(team);
-
-  for (; u < uend; ++u) {
-    while (P.segoff[i + 1] <= u) ++i;
-    const int s = static_cast<int>(u - P.segoff[i]);
-    const mk_skewer sk = P.sk[i];
-    const int64_t j0 = static_cast<int64_t>(s) * N;
-    const int npx = static_cast<int>(min(static_cast<int64_t>(N), sk.n - j0));
-    if ((P.delta_out || P.flux_out) && sk.offset + sk.n > P.capacity) {
-      if (t == 0) raise_error(P.err, ERR_CAPACITY);
-      continue;
-    }
-    // ---- small-scale field of this segment
-    small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
-    team_sync<T>(team);
-    inverse_real_fft<N>(buf, tw, t, team);
-
-    // ---- per pixel: gather, growth, FGPA, stores, pixel sums
-    const int jb = sk.j_lo + static_cast<int>(j0);
-    int zf = 0, zl = 0;
-    if (P.do_stats) {
-      zf = __ldg(P.zbin + jb);
-      zl = __ldg(P.zbin + jb + npx - 1);
-    }
-    float a0[MK_NSUM], a1[MK_NSUM];
-#pragma unroll
-    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
-    int64_t px = sk.p0[0] + (j0 + t) * sk.step[0];
-    int64_t py = sk.p0[1] + (j0 + t) * sk.step[1];
-    int64_t pz = sk.p0[2] + (j0 + t) * sk.step[2];
-    const int64_t sx = T * sk.step[0], sy = T * sk.step[1], sz = T * sk.step[2];
-    const int64_t out0 = sk.offset + j0;
-#pragma unroll 2
-    for (int k = 0; k < 8; ++k) {
-      const int p = t + T * k;
-      float f = 0.f;
-      if (p < npx) {
-        const float2 de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
-        const float4 tb = __ldg(P.pixtab + jb + p);
-        const float dt = fmaf(tb.x, de.x, fb[swf(p)]);
-        const float eg = tb.x * de.y;
-        f = fgpa(tb, dt, eg);
-        if (P.delta_out) {
-          P.delta_out[out0 + p] = dt;
-          P.eta_out[out0 + p] = eg;
-        }
-        if (P.flux_out) P.flux_out[out0 + p] = f;
-        if (P.do_stats) {
-          const int zb = __ldg(P.zbin + jb + p);
-          if (zb == zf) add_pixel(a0, f, dt, eg);
-          else if (zb == zf + 1) add_pixel(a1, f, dt, eg);
-          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dt, eg);
-        }
-      }
-      fb[swf(p)] = f;
-      px += sx;
-      py += sy;
-      pz += sz;
-    }
-
-    // ---- statistics
-    if (P.do_stats) {
-      flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
-      if (npx == N) {
-        const int zs = __ldg(P.segzbin + jb);
-        if (zs >= 0 && zs < P.n_z) {
-          forward_packed_fft<N>(buf, tw, t, team);
-          float pk[4];
-          power_of_modes<N>(buf, P.tw, t, pk);
-          accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
-          if (t == 0) W.nseg[zs] += 1u;
-        }
-      }
-    }
-    team_sync<T>(team);
-  }
-  if (P.do_stats) flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
-}
-
 // =================================================================== flux kernel
 __global__ void __launch_bounds__(256) k_flux(FluxParams P) {
   const int lane = threadIdx.x & 31;
@@ -425,100 +264,6 @@ __global__ void __launch_bounds__(256) k_flux(FluxParams P) {
       P.flux[o + k] = P.rebin == 1 ? s : s / static_cast<float>(P.rebin);
     }
   }
-}
-
-// =================================================================== statistics kernel
-template <int N>
-__global__ void __launch_bounds__(256) k_stats(StatParams P) {
-  constexpr int T = N / 8;
-  constexpr int BUF = TeamSmem<N>::BUF;
-  const int teams = blockDim.x / T;
-  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
-  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
-  float *fb = reinterpret_cast<float *>(buf);
-  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
-  zero_warp_acc(smem + warp * wbytes, wbytes);
-  Twiddles<N> tw;
-  load_twiddles<N>(tw, P.tw, t);
-
-  const int64_t nunits = P.segoff[P.n_sk];
-  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
-  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
-  int64_t u = g * nunits / G;
-  const int64_t uend = (g + 1) * nunits / G;
-  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
-  const int R = P.rebin;
-  team_sync<T>(team);
-
-  for (; u < uend; ++u) {
-    while (P.segoff[i + 1] <= u) ++i;
-    const int s = static_cast<int>(u - P.segoff[i]);
-    const mk_skewer sk = P.sk[i];
-    const int64_t o = P.off_out[i];
-    const int64_t nout = P.off_out[i + 1] - o;
-    const int64_t k0 = static_cast<int64_t>(s) * N;
-    const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
-    auto zbin_of = [&](int64_t kk) -> int {
-      const int64_t J = sk.j_lo + kk * R;
-      if (R == 1) return __ldg(P.zbin + J);
-      const double fz = floor(((P.cumz[J + R] - P.cumz[J]) / R - P.z_lo) / P.dz);
-      return fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
-    };
-    const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
-    float a0[MK_NSUM], a1[MK_NSUM];
-#pragma unroll
-    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
-#pragma unroll 2
-    for (int q = 0; q < 8; ++q) {
-      const int p = t + T * q;
-      float f = 0.f;
-      if (p < npx) {
-        const int64_t kk = k0 + p;
-        f = P.flux[o + kk];
-        float ds = 0.f, es = 0.f;
-        if (P.delta) {
-          for (int r = 0; r < R; ++r) {
-            ds += P.delta[sk.offset + kk * R + r];
-            es += P.eta[sk.offset + kk * R + r];
-          }
-          if (R > 1) {
-            ds /= static_cast<float>(R);
-            es /= static_cast<float>(R);
-          }
-        }
-        const int zb = zbin_of(kk);
-        if (zb == zf) add_pixel(a0, f, ds, es);
-        else if (zb == zf + 1) add_pixel(a1, f, ds, es);
-        else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, ds, es);
-      }
-      fb[swf(p)] = f;
-    }
-    flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
-    if (npx == N) {
-      int zs;
-      if (R == 1) {
-        zs = __ldg(P.segzbin + sk.j_lo + k0);
-      } else {
-        const int64_t J0 = sk.j_lo + k0 * R;
-        const double zm =
-            (P.cumz[J0 + static_cast<int64_t>(N) * R] - P.cumz[J0]) / (static_cast<double>(N) * R);
-        const double fz = floor((zm - P.z_lo) / P.dz);
-        zs = fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
-      }
-      if (zs >= 0 && zs < P.n_z) {
-        forward_packed_fft<N>(buf, tw, t, team);
-        float pk[4];
-        power_of_modes<N>(buf, P.tw, t, pk);
-        accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
-        if (t == 0) W.nseg[zs] += 1u;
-      }
-    }
-    team_sync<T>(team);
-  }
-  flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
 }
 
 // =================================================================== finalize
@@ -627,82 +372,60 @@ cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ dispatch by FFT length
+#define MK_DECL(NN)                                                                                      \
+  size_t skewer_smem_bytes_##NN(int threads, int n_z, int n_k, bool stats);                              \
+  int skewer_blocks_per_sm_##NN(int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats); \
+  cudaError_t launch_skewer_##NN(const SkewerParams &P, int layout, int minb, int grid, int threads,      \
+                                 cudaStream_t st);                                                      \
+  int stats_blocks_per_sm_##NN(int threads, int n_z, int n_k);                                          \
+  cudaError_t launch_stats_##NN(const StatParams &P, int grid, int threads, cudaStream_t st);
+MK_DECL(256)
+MK_DECL(512)
+MK_DECL(1024)
+MK_DECL(2048)
+#undef MK_DECL
+
+#define MK_SWITCH(EXPR, FAIL)     \
+  switch (n_fft) {                \
+    case 256: return EXPR(256);   \
+    case 512: return EXPR(512);   \
+    case 1024: return EXPR(1024); \
+    case 2048: return EXPR(2048); \
+  }                               \
+  return FAIL;
+
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats) {
-  switch (n_fft) {
-    case 256: return TeamSmem<256>::bytes(threads, n_z, n_k, stats);
-    case 512: return TeamSmem<512>::bytes(threads, n_z, n_k, stats);
-    case 1024: return TeamSmem<1024>::bytes(threads, n_z, n_k, stats);
-    case 2048: return TeamSmem<2048>::bytes(threads, n_z, n_k, stats);
-  }
-  return 0;
+#define E(NN) skewer_smem_bytes_##NN(threads, n_z, n_k, stats)
+  MK_SWITCH(E, 0)
+#undef E
 }
 
-// Calls fn with the kernel instance for (N, layout, box size).
-template <typename F>
-static cudaError_t with_skewer_kernel(int n_fft, int layout, bool big, F &&fn) {
-#define MK_SK_CASE(NN)                                                                            \
-  case NN:                                                                                        \
-    if (layout == MK_BOX_INTERLEAVED)                                                             \
-      return big ? fn(k_skewer<NN, MK_BOX_INTERLEAVED, true>) : fn(k_skewer<NN, MK_BOX_INTERLEAVED, false>); \
-    return big ? fn(k_skewer<NN, MK_BOX_PLANAR, true>) : fn(k_skewer<NN, MK_BOX_PLANAR, false>);
-  switch (n_fft) {
-    MK_SK_CASE(256)
-    MK_SK_CASE(512)
-    MK_SK_CASE(1024)
-    MK_SK_CASE(2048)
-  }
-#undef MK_SK_CASE
-  return cudaErrorInvalidValue;
+int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
+#define E(NN) skewer_blocks_per_sm_##NN(layout, lgn, minb, threads, n_z, n_k, stats)
+  MK_SWITCH(E, 1)
+#undef E
 }
 
-template <typename F>
-static cudaError_t with_stats_kernel(int n_fft, F &&fn) {
-  switch (n_fft) {
-    case 256: return fn(k_stats<256>);
-    case 512: return fn(k_stats<512>);
-    case 1024: return fn(k_stats<1024>);
-    case 2048: return fn(k_stats<2048>);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename K>
-static int occupancy(K kern, int threads, size_t smem) {
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  int v = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem) != cudaSuccess || v < 1) return 1;
-  return v;
-}
-
-int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int threads, int n_z, int n_k, bool stats) {
-  const size_t smem = skewer_smem_bytes(n_fft, threads, n_z, n_k, stats);
-  int b = 1;
-  with_skewer_kernel(n_fft, layout, lgn > 10, [&](auto kern) {
-    b = occupancy(kern, threads, smem);
-    return cudaSuccess;
-  });
-  return b;
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int minb, int grid, int threads,
+                          cudaStream_t st) {
+#define E(NN) launch_skewer_##NN(P, layout, minb, grid, threads, st)
+  MK_SWITCH(E, cudaErrorInvalidValue)
+#undef E
 }
 
 int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k) {
-  const size_t smem = skewer_smem_bytes(n_fft, threads, n_z, n_k, true);
-  int b = 1;
-  with_stats_kernel(n_fft, [&](auto kern) {
-    b = occupancy(kern, threads, smem);
-    return cudaSuccess;
-  });
-  return b;
+#define E(NN) stats_blocks_per_sm_##NN(threads, n_z, n_k)
+  MK_SWITCH(E, 1)
+#undef E
 }
 
-cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads, cudaStream_t st) {
-  const size_t smem = skewer_smem_bytes(n_fft, threads, P.n_z, P.n_k, P.do_stats != 0);
-  return with_skewer_kernel(n_fft, layout, P.lgn > 10, [&](auto kern) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    kern<<<grid, threads, smem, st>>>(P);
-    return cudaGetLastError();
-  });
+cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st) {
+#define E(NN) launch_stats_##NN(P, grid, threads, st)
+  MK_SWITCH(E, cudaErrorInvalidValue)
+#undef E
 }
+#undef MK_SWITCH
 
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st) {
   if (P.n_sk == 0) return cudaSuccess;
@@ -711,16 +434,6 @@ cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st) {
   if (grid > sms * 16) grid = sms * 16;
   k_flux<<<grid, 256, 0, st>>>(P);
   return cudaGetLastError();
-}
-
-cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st) {
-  const size_t smem = skewer_smem_bytes(n_fft, threads, P.n_z, P.n_k, true);
-  return with_stats_kernel(n_fft, [&](auto kern) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    kern<<<grid, threads, smem, st>>>(P);
-    return cudaGetLastError();
-  });
 }
 
 cudaError_t launch_finalize(const double *partials, int nparts, int n_z, int n_k, int n_fft, mk_stats_out *out,

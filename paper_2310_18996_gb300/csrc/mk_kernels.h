@@ -21,10 +21,12 @@ cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, d
 cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);
 cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st);
-int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int threads, int n_z, int n_k, bool stats);
+int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
 int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k);
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
-cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int grid, int threads,
+// minb: occupancy target of the instance (1: compiler's choice, 4: four
+// 256-thread CTAs per SM)
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int minb, int grid, int threads,
                           cudaStream_t st);
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st);

@@ -1,0 +1,264 @@
+// Templates of the fused skewer kernel and the statistics kernel; each FFT
+// length is instantiated in its own translation unit (mk_skewer_<N>.cu).
+#pragma once
+
+#include "mk_device.cuh"
+
+namespace mk {
+
+// =================================================================== shared-memory plan
+// Per CTA: per-warp statistic accumulators (when statistics are on), then one
+// FFT buffer of N/2 + 2 complex values per team.
+template <int N>
+struct TeamSmem {
+  static constexpr int T = N / 8;
+  static constexpr int BUF = N / 2 + 2;
+  static size_t bytes(int threads, int n_z, int n_k, bool stats) {
+    return (stats ? static_cast<size_t>(threads / 32) * WarpAcc::bytes(n_z, n_k) : 0) +
+           static_cast<size_t>(threads / T) * BUF * sizeof(float2);
+  }
+};
+
+// largest i with a[i] <= v over a[0..n] (a non-decreasing)
+__device__ __forceinline__ int64_t upper_index(const int64_t *a, int64_t n, int64_t v) {
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void zero_warp_acc(unsigned char *base, size_t wbytes) {
+  float *f = reinterpret_cast<float *>(base);
+  for (size_t i = threadIdx.x & 31; i < wbytes / sizeof(float); i += 32) f[i] = 0.f;
+  __syncwarp();
+}
+
+// Sum the warps' compensated FP32 accumulators in FP64 and write this CTA's
+// partials in the StatLayout order.
+__device__ __forceinline__ void flush_warp_partials(unsigned char *smem, int nwarps, size_t wbytes, int n_z, int n_k,
+                                    double *partials) {
+  __syncthreads();
+  const StatLayout L{n_z, n_k};
+  const int ns = n_z * MK_NSUM, np = n_z * n_k;
+  for (int idx = threadIdx.x; idx < L.size(); idx += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nwarps; ++w) {
+      const WarpAcc A = WarpAcc::at(smem + w * wbytes, n_z, n_k);
+      if (idx < ns) {
+        const float2 v = A.sums[idx];
+        s += static_cast<double>(v.x) - static_cast<double>(v.y);
+      } else if (idx < ns + np) {
+        const float2 v = A.p1d[idx - ns];
+        s += static_cast<double>(v.x) - static_cast<double>(v.y);
+      } else {
+        s += static_cast<double>(A.nseg[idx - ns - np]);
+      }
+    }
+    partials[static_cast<size_t>(blockIdx.x) * L.size() + idx] = s;
+  }
+}
+
+// =================================================================== fused skewer kernel
+// One team per segment of N pixels: small-scale modes -> inverse real FFT ->
+// per pixel gather, growth, FGPA, stores and pixel sums -> forward FFT of the
+// flux -> P1D.  Teams take contiguous ranges of segments (all segments cost
+// the same); statistics go to per-warp compensated accumulators.
+template <int N, int LAYOUT, bool BIG, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
+  constexpr int T = N / 8;
+  constexpr int BUF = TeamSmem<N>::BUF;
+  const int teams = blockDim.x / T;
+  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t wbytes = P.do_stats ? WarpAcc::bytes(P.n_z, P.n_k) : 0;
+  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
+  float *fb = reinterpret_cast<float *>(buf);
+  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
+  if (P.do_stats) zero_warp_acc(smem + warp * wbytes, wbytes);
+
+  Twiddles<N> tw;
+  load_twiddles<N>(tw, P.tw, t);
+
+  const int64_t nunits = P.segoff[P.n_sk];
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
+  int64_t u = g * nunits / G;
+  const int64_t uend = (g + 1) * nunits / G;
+  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
+  team_sync<T>(team);
+
+  for (; u < uend; ++u) {
+    while (P.segoff[i + 1] <= u) ++i;
+    const int s = static_cast<int>(u - P.segoff[i]);
+    const mk_skewer sk = P.sk[i];
+    const int64_t j0 = static_cast<int64_t>(s) * N;
+    const int npx = static_cast<int>(min(static_cast<int64_t>(N), sk.n - j0));
+    if ((P.delta_out || P.flux_out) && sk.offset + sk.n > P.capacity) {
+      if (t == 0) raise_error(P.err, ERR_CAPACITY);
+      continue;
+    }
+    // ---- small-scale field of this segment
+    small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
+    team_sync<T>(team);
+    inverse_real_fft<N>(buf, tw, t, team);
+
+    // ---- per pixel: gather, growth, FGPA, stores, pixel sums
+    const int jb = sk.j_lo + static_cast<int>(j0);
+    int zf = 0, zl = 0;
+    if (P.do_stats) {
+      zf = __ldg(P.zbin + jb);
+      zl = __ldg(P.zbin + jb + npx - 1);
+    }
+    float a0[MK_NSUM], a1[MK_NSUM];
+#pragma unroll
+    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
+    int64_t px = sk.p0[0] + (j0 + t) * sk.step[0];
+    int64_t py = sk.p0[1] + (j0 + t) * sk.step[1];
+    int64_t pz = sk.p0[2] + (j0 + t) * sk.step[2];
+    const int64_t sx = T * sk.step[0], sy = T * sk.step[1], sz = T * sk.step[2];
+    const int64_t out0 = sk.offset + j0;
+#pragma unroll 2
+    for (int k = 0; k < 8; ++k) {
+      const int p = t + T * k;
+      float f = 0.f;
+      if (p < npx) {
+        const float2 de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
+        const float4 tb = __ldg(P.pixtab + jb + p);
+        const float dt = fmaf(tb.x, de.x, fb[swf(p)]);
+        const float eg = tb.x * de.y;
+        f = fgpa(tb, dt, eg);
+        if (P.delta_out) {
+          P.delta_out[out0 + p] = dt;
+          P.eta_out[out0 + p] = eg;
+        }
+        if (P.flux_out) P.flux_out[out0 + p] = f;
+        if (P.do_stats) {
+          const int zb = __ldg(P.zbin + jb + p);
+          if (zb == zf) add_pixel(a0, f, dt, eg);
+          else if (zb == zf + 1) add_pixel(a1, f, dt, eg);
+          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dt, eg);
+        }
+      }
+      fb[swf(p)] = f;
+      px += sx;
+      py += sy;
+      pz += sz;
+    }
+
+    // ---- statistics
+    if (P.do_stats) {
+      flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
+      if (npx == N) {
+        const int zs = __ldg(P.segzbin + jb);
+        if (zs >= 0 && zs < P.n_z) {
+          forward_packed_fft<N>(buf, tw, t, team);
+          float pk[4];
+          power_of_modes<N>(buf, P.tw, t, pk);
+          accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
+          if (t == 0) W.nseg[zs] += 1u;
+        }
+      }
+    }
+    team_sync<T>(team);
+  }
+  if (P.do_stats) flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
+}
+
+// =================================================================== statistics kernel
+template <int N>
+__global__ void __launch_bounds__(256) k_stats(StatParams P) {
+  constexpr int T = N / 8;
+  constexpr int BUF = TeamSmem<N>::BUF;
+  const int teams = blockDim.x / T;
+  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
+  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
+  float *fb = reinterpret_cast<float *>(buf);
+  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
+  zero_warp_acc(smem + warp * wbytes, wbytes);
+  Twiddles<N> tw;
+  load_twiddles<N>(tw, P.tw, t);
+
+  const int64_t nunits = P.segoff[P.n_sk];
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
+  int64_t u = g * nunits / G;
+  const int64_t uend = (g + 1) * nunits / G;
+  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
+  const int R = P.rebin;
+  team_sync<T>(team);
+
+  for (; u < uend; ++u) {
+    while (P.segoff[i + 1] <= u) ++i;
+    const int s = static_cast<int>(u - P.segoff[i]);
+    const mk_skewer sk = P.sk[i];
+    const int64_t o = P.off_out[i];
+    const int64_t nout = P.off_out[i + 1] - o;
+    const int64_t k0 = static_cast<int64_t>(s) * N;
+    const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
+    auto zbin_of = [&](int64_t kk) -> int {
+      const int64_t J = sk.j_lo + kk * R;
+      if (R == 1) return __ldg(P.zbin + J);
+      const double fz = floor(((P.cumz[J + R] - P.cumz[J]) / R - P.z_lo) / P.dz);
+      return fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
+    };
+    const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
+    float a0[MK_NSUM], a1[MK_NSUM];
+#pragma unroll
+    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
+#pragma unroll 2
+    for (int q = 0; q < 8; ++q) {
+      const int p = t + T * q;
+      float f = 0.f;
+      if (p < npx) {
+        const int64_t kk = k0 + p;
+        f = P.flux[o + kk];
+        float ds = 0.f, es = 0.f;
+        if (P.delta) {
+          for (int r = 0; r < R; ++r) {
+            ds += P.delta[sk.offset + kk * R + r];
+            es += P.eta[sk.offset + kk * R + r];
+          }
+          if (R > 1) {
+            ds /= static_cast<float>(R);
+            es /= static_cast<float>(R);
+          }
+        }
+        const int zb = zbin_of(kk);
+        if (zb == zf) add_pixel(a0, f, ds, es);
+        else if (zb == zf + 1) add_pixel(a1, f, ds, es);
+        else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, ds, es);
+      }
+      fb[swf(p)] = f;
+    }
+    flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
+    if (npx == N) {
+      int zs;
+      if (R == 1) {
+        zs = __ldg(P.segzbin + sk.j_lo + k0);
+      } else {
+        const int64_t J0 = sk.j_lo + k0 * R;
+        const double zm =
+            (P.cumz[J0 + static_cast<int64_t>(N) * R] - P.cumz[J0]) / (static_cast<double>(N) * R);
+        const double fz = floor((zm - P.z_lo) / P.dz);
+        zs = fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
+      }
+      if (zs >= 0 && zs < P.n_z) {
+        forward_packed_fft<N>(buf, tw, t, team);
+        float pk[4];
+        power_of_modes<N>(buf, P.tw, t, pk);
+        accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
+        if (t == 0) W.nseg[zs] += 1u;
+      }
+    }
+    team_sync<T>(team);
+  }
+  flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
+}
+
+}  // namespace mk

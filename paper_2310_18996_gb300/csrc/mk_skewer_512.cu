@@ -1,0 +1,68 @@
+// Instances of the fused skewer kernel and the statistics kernel for one
+// FFT length, with their launch and occupancy helpers.
+#include "mk_kernels.h"
+#include "mk_skewer.cuh"
+
+namespace mk {
+
+namespace {
+constexpr int NN = 512;
+
+// Calls fn with the kernel instance for (layout, box size, occupancy target).
+template <typename F>
+cudaError_t with_skewer_kernel(int layout, bool big, int minb, F &&fn) {
+  const bool il = layout == MK_BOX_INTERLEAVED;
+  if (minb >= 4) {
+    if (il) return big ? fn(k_skewer<NN, MK_BOX_INTERLEAVED, true, 4>) : fn(k_skewer<NN, MK_BOX_INTERLEAVED, false, 4>);
+    return big ? fn(k_skewer<NN, MK_BOX_PLANAR, true, 4>) : fn(k_skewer<NN, MK_BOX_PLANAR, false, 4>);
+  }
+  if (il) return big ? fn(k_skewer<NN, MK_BOX_INTERLEAVED, true, 1>) : fn(k_skewer<NN, MK_BOX_INTERLEAVED, false, 1>);
+  return big ? fn(k_skewer<NN, MK_BOX_PLANAR, true, 1>) : fn(k_skewer<NN, MK_BOX_PLANAR, false, 1>);
+}
+
+template <typename K>
+int occupancy(K kern, int threads, size_t smem) {
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, threads, smem) != cudaSuccess || v < 1) return 1;
+  return v;
+}
+}  // namespace
+
+size_t skewer_smem_bytes_512(int threads, int n_z, int n_k, bool stats) {
+  return TeamSmem<NN>::bytes(threads, n_z, n_k, stats);
+}
+
+int skewer_blocks_per_sm_512(int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
+  const size_t smem = TeamSmem<NN>::bytes(threads, n_z, n_k, stats);
+  int b = 1;
+  with_skewer_kernel(layout, lgn > 10, minb, [&](auto kern) {
+    b = occupancy(kern, threads, smem);
+    return cudaSuccess;
+  });
+  return b;
+}
+
+cudaError_t launch_skewer_512(const SkewerParams &P, int layout, int minb, int grid, int threads, cudaStream_t st) {
+  const size_t smem = TeamSmem<NN>::bytes(threads, P.n_z, P.n_k, P.do_stats != 0);
+  return with_skewer_kernel(layout, P.lgn > 10, minb, [&](auto kern) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, threads, smem, st>>>(P);
+    return cudaGetLastError();
+  });
+}
+
+int stats_blocks_per_sm_512(int threads, int n_z, int n_k) {
+  return occupancy(k_stats<NN>, threads, TeamSmem<NN>::bytes(threads, n_z, n_k, true));
+}
+
+cudaError_t launch_stats_512(const StatParams &P, int grid, int threads, cudaStream_t st) {
+  const size_t smem = TeamSmem<NN>::bytes(threads, P.n_z, P.n_k, true);
+  cudaError_t e = cudaFuncSetAttribute(k_stats<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  k_stats<NN><<<grid, threads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+}  // namespace mk

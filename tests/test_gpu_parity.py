@@ -159,6 +159,48 @@ def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
             assert abs(X[0]) < 1e-5 * rms
 
 
+def test_graph_replay_and_autotune_match_direct_launch(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, ctx.pack_box(dv["d"], dv["e"]), None)
+    n = len(tiny["ids"])
+    flags = mk.STATS | mk.STORE_FLUX
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        st_tuned, o = ctx.run(box, dv["qso"], n, w, flags=flags | mk.AUTOTUNE, capacity=tiny["orc"]["offsets"][-1])
+        threads, occ, tuned = ctx.launch_config(w["n_fft"], flags=flags)
+        assert tuned and threads in (128, 256) and occ in (1, 4)
+        st_direct, _ = ctx.run(box, dv["qso"], n, w, flags=flags, outputs=o, capacity=o["flux"].numel())
+        f_direct = o["flux"].clone()
+        o["flux"].zero_()
+        st_g1, _ = ctx.run(box, dv["qso"], n, w, flags=flags | mk.GRAPH, outputs=o, capacity=o["flux"].numel())
+        st_g2, _ = ctx.run(box, dv["qso"], n, w, flags=flags | mk.GRAPH, outputs=o, capacity=o["flux"].numel())
+        # a changed argument (the FGPA nodes) must re-capture, not replay
+        w2 = dict(w)
+        w2["node_b"] = [1.5] * len(w["node_z"])
+        st_g3, _ = ctx.run(box, dv["qso"], n, w2, flags=flags | mk.GRAPH, outputs=o, capacity=o["flux"].numel())
+        st_d3, _ = ctx.run(box, dv["qso"], n, w2, flags=flags, outputs=o, capacity=o["flux"].numel())
+    torch.cuda.synchronize()
+    for st in (st_g1, st_g2):
+        for k in ("sums", "p1d_sum", "n_seg"):
+            np.testing.assert_array_equal(st[k], st_direct[k])
+    for k in ("sums", "p1d_sum", "n_seg"):
+        np.testing.assert_array_equal(st_g3[k], st_d3[k])
+    assert not np.array_equal(st_g3["mean_flux"], st_g1["mean_flux"])
+    assert_stats_close(st_tuned, tiny["st"], check_fields=False)
+    assert_stats_close(st_direct, tiny["st"], check_fields=False)
+    tot = tiny["orc"]["offsets"][-1]
+    assert_flux_close(f_direct[:tot].cpu().numpy(), tiny["orc"]["flux"])
+
+
+def test_graph_needs_a_non_default_stream(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    with torch.cuda.stream(torch.cuda.default_stream()):
+        with pytest.raises(mk.MkError) as ei:
+            ctx.run(box, dv["qso"], 10, w, flags=mk.STATS | mk.GRAPH)
+    assert ei.value.code == mk.MK_EINVAL
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_catalogue_and_zero_length_skewers(ctx, tiny):
     w, dv = tiny["w"], tiny["dev"]
@@ -244,8 +286,10 @@ def _full_size_check(ctx, w, n_sample, seed, lognormal=False):
     tot = int(off[-1])
     st2 = ctx.stats(w, g["sk"], len(ids), g["offsets"], g["flux"], delta=g["delta"], eta=g["eta"])
     np.testing.assert_array_equal(st2["sums"][:, 0], st["sums"][:, 0])
-    np.testing.assert_allclose(st2["sums"], st["sums"], rtol=1e-9, atol=1e-9)
-    np.testing.assert_allclose(st2["p1d_sum"], st["p1d_sum"], rtol=1e-9)
+    # both passes add FP32 partial sums with compensation in different orders:
+    # agreement to 1e-8 of the pixel count (pixel values are O(1)) or 1e-6 relative
+    assert np.all(np.abs(st2["sums"] - st["sums"]) <= 1e-6 * np.abs(st["sums"]) + 1e-8 * st["sums"][:, :1])
+    np.testing.assert_allclose(st2["p1d_sum"], st["p1d_sum"], rtol=1e-6)
     jl = torch.from_numpy(rec["j_lo"].astype(np.int64)).cuda()
     nn = torch.from_numpy(rec["n"].astype(np.int64)).cuda()
     owner = torch.repeat_interleave(torch.arange(len(ids), device="cuda"), nn)
