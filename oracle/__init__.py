@@ -114,6 +114,9 @@ def lib():
                 "orc_stats_accumulate": (C.c_int, [P(Cfg), P(Bins), i32, P(i32), P(i64),
                                                    P(i64), i64, P(d), P(d), P(d), P(Stats)]),
                 "orc_stats_finalize": (None, [P(Bins), P(Stats)]),
+                "orc_mlp_forward": (None, [P(d), P(d), i64, P(d)]),
+                "orc_mlp_loss_grad": (d, [P(d), P(d), P(d), i64, P(d)]),
+                "orc_gelu": (d, [d]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -337,3 +340,32 @@ def stats(w, j_lo, offsets_fine, offsets_out, flux_out, delta=None, eta=None, re
         sigma_f=arr(st.sigma_f)[:nz].copy(), p1d_f=arr(st.p1d_f)[:nz, :nk].copy(),
         p1d_df=arr(st.p1d_df)[:nz, :nk].copy(), b_f=arr(st.b_f)[:nz].copy(),
         beta_f=arr(st.beta_f)[:nz].copy())
+
+
+# ---------------------------------------------------------------- surrogate MLP
+MLP_DIMS = (4, 128, 128, 128, 35)
+MLP_NPARAM = 38179
+
+
+def gelu(x):
+    return lib().orc_gelu(float(x))
+
+
+def mlp_forward(params, x):
+    """FP64 forward of the 4-128-128-128-35 GELU MLP; x (n, 4) -> (n, 35)."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    y = np.zeros((x.shape[0], 35))
+    lib().orc_mlp_forward(_p(p, C.c_double), _p(x, C.c_double), x.shape[0], _p(y, C.c_double))
+    return y
+
+
+def mlp_loss_grad(params, x, t):
+    """Mean squared error and its gradient (FP64) at params."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
+    t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1, 35)
+    g = np.zeros(MLP_NPARAM)
+    loss = lib().orc_mlp_loss_grad(_p(p, C.c_double), _p(x, C.c_double), _p(t, C.c_double),
+                                   x.shape[0], _p(g, C.c_double))
+    return loss, g

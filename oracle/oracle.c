@@ -570,3 +570,87 @@ void orc_stats_finalize(const orc_bins *bins, orc_stats *st) {
     }
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Surrogate MLP (no counterpart in the paper): 4 -> 128 -> 128 -> 128 -> 35, */
+/* GELU(x) = x Phi(x) on the hidden layers, linear output, mean squared      */
+/* error; backward pass by the chain rule written out layer by layer.        */
+/* ------------------------------------------------------------------------ */
+static const int mlp_dims[5] = {4, 128, 128, 128, 35};
+
+/* Phi(x) = erfc(-x/sqrt 2)/2 keeps full relative accuracy in the negative tail */
+double orc_gelu(double x) { return 0.5 * x * erfc(-x / sqrt(2.0)); }
+
+static double gelu_deriv(double x) {
+  return 0.5 * erfc(-x / sqrt(2.0)) + x * exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+}
+
+static void mlp_offsets(int64_t w_off[4], int64_t b_off[4]) {
+  int64_t o = 0;
+  for (int l = 0; l < 4; ++l) {
+    w_off[l] = o;
+    o += (int64_t)mlp_dims[l + 1] * mlp_dims[l];
+    b_off[l] = o;
+    o += mlp_dims[l + 1];
+  }
+}
+
+/* forward of one sample; z[l], h[l] hold layer l's pre- and post-activation */
+static void mlp_sample(const double *p, const double *x, double z[4][128], double h[4][128],
+                       double *y) {
+  int64_t wo[4], bo[4];
+  mlp_offsets(wo, bo);
+  const double *in = x;
+  for (int l = 0; l < 4; ++l) {
+    int ni = mlp_dims[l], no = mlp_dims[l + 1];
+    for (int j = 0; j < no; ++j) {
+      double s = p[bo[l] + j];
+      for (int k = 0; k < ni; ++k) s += p[wo[l] + (int64_t)j * ni + k] * in[k];
+      z[l][j] = s;
+      h[l][j] = (l < 3) ? orc_gelu(s) : s;
+    }
+    in = h[l];
+  }
+  for (int j = 0; j < mlp_dims[4]; ++j) y[j] = h[3][j];
+}
+
+void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y) {
+  double z[4][128], h[4][128];
+  for (int64_t s = 0; s < n; ++s) mlp_sample(params, x + 4 * s, z, h, y + 35 * s);
+}
+
+double orc_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n,
+                         double *grad) {
+  int64_t wo[4], bo[4];
+  mlp_offsets(wo, bo);
+  if (grad) memset(grad, 0, sizeof(double) * ORC_MLP_NPARAM);
+  double z[4][128], h[4][128], y[35], dz[128], dh[128];
+  double loss = 0.0;
+  const double scale = 1.0 / ((double)n * 35.0);
+  for (int64_t s = 0; s < n; ++s) {
+    const double *xs = x + 4 * s;
+    mlp_sample(params, xs, z, h, y);
+    for (int j = 0; j < 35; ++j) {
+      double r = y[j] - t[35 * s + j];
+      loss += r * r * scale;
+      dz[j] = 2.0 * r * scale; /* d loss / d y (output layer is linear) */
+    }
+    if (!grad) continue;
+    for (int l = 3; l >= 0; --l) {
+      int ni = mlp_dims[l], no = mlp_dims[l + 1];
+      const double *in = (l > 0) ? h[l - 1] : xs;
+      for (int j = 0; j < no; ++j) {
+        grad[bo[l] + j] += dz[j];
+        for (int k = 0; k < ni; ++k) grad[wo[l] + (int64_t)j * ni + k] += dz[j] * in[k];
+      }
+      if (l == 0) break;
+      for (int k = 0; k < ni; ++k) {
+        double a = 0.0;
+        for (int j = 0; j < no; ++j) a += params[wo[l] + (int64_t)j * ni + k] * dz[j];
+        dh[k] = a;
+      }
+      for (int k = 0; k < ni; ++k) dz[k] = dh[k] * gelu_deriv(z[l - 1][k]);
+    }
+  }
+  return loss;
+}

@@ -134,6 +134,16 @@ int orc_stats_accumulate(const orc_cfg *cfg, const orc_bins *bins, int32_t rebin
                          const double *delta_fine, const double *eta_fine, orc_stats *st);
 void orc_stats_finalize(const orc_bins *bins, orc_stats *st);
 
+/* ---- surrogate MLP 4 -> 128 -> 128 -> 128 -> 35 with GELU hidden units ----
+   Parameters in order W0 [128x4], b0, W1 [128x128], b1, W2 [128x128], b2,
+   W3 [35x128], b3, each W row-major [out][in]; 38179 values. */
+#define ORC_MLP_NPARAM 38179
+void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y);
+/* mean squared error over n samples and 35 outputs, and its gradient */
+double orc_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n,
+                         double *grad);
+double orc_gelu(double x);
+
 #ifdef __cplusplus
 }
 #endif

@@ -392,3 +392,63 @@ def test_table3_target_rows():
         de = abs(targets.b_eff_target(z + 5e-4) - targets.b_eff_target(z - 5e-4)) / 2
         assert abs(targets.beta_target(z) - beta) <= 5e-4 + db
         assert abs(targets.b_eff_target(z) - beff) <= 5e-5 + de
+
+
+# ------------------------------------------------------------ surrogate MLP
+def test_gelu_is_x_times_normal_cdf():
+    from scipy.special import ndtr
+    for x in [-6.0, -1.3, -0.2, 0.0, 0.5, 1.0, 2.7, 8.0]:
+        assert oracle.gelu(x) == pytest.approx(x * ndtr(x), rel=1e-13, abs=1e-300)
+
+
+def _mlp_params(seed, scale=0.2):
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(oracle.MLP_NPARAM) * scale
+
+
+def test_mlp_zero_hidden_weights_give_the_output_bias():
+    p = np.zeros(oracle.MLP_NPARAM)
+    b3 = np.arange(35) * 0.1 - 1.0
+    p[-35:] = b3
+    y = oracle.mlp_forward(p, np.random.default_rng(1).standard_normal((7, 4)))
+    np.testing.assert_allclose(y, np.tile(b3, (7, 1)), atol=0)
+
+
+def test_mlp_single_path_closed_form():
+    # one live path x0 -> h1[0] -> h2[0] -> h3[0] -> y[j]: y_j = v_j G(w3 G(w2 G(w1 x0)))
+    dims = oracle.MLP_DIMS
+    p = np.zeros(oracle.MLP_NPARAM)
+    offs, o = [], 0
+    for l in range(4):
+        offs.append(o)
+        o += dims[l + 1] * dims[l] + dims[l + 1]
+    w1, w2, w3 = 0.7, -1.3, 0.9
+    p[offs[0] + 0] = w1                      # W0[0][0]
+    p[offs[1] + 0] = w2                      # W1[0][0]
+    p[offs[2] + 0] = w3                      # W2[0][0]
+    v = np.linspace(-1, 1, 35)
+    p[offs[3]:offs[3] + 35 * 128].reshape(35, 128)[:, 0] = v   # W3[:, 0]
+    from scipy.special import ndtr
+    G = lambda z: z * ndtr(z)
+    for x0 in [-1.5, 0.3, 2.0]:
+        y = oracle.mlp_forward(p, np.array([[x0, 5.0, -2.0, 1.0]]))[0]
+        np.testing.assert_allclose(y, v * G(w3 * G(w2 * G(w1 * x0))), rtol=1e-12, atol=1e-15)
+
+
+def test_mlp_gradient_matches_central_differences():
+    p = _mlp_params(3)
+    rng = np.random.default_rng(4)
+    x = rng.standard_normal((6, 4))
+    t = rng.standard_normal((6, 35))
+    loss, g = oracle.mlp_loss_grad(p, x, t)
+    y = oracle.mlp_forward(p, x)
+    assert loss == pytest.approx(np.mean((y - t) ** 2), rel=1e-13)
+    idx = np.concatenate([rng.choice(oracle.MLP_NPARAM, 60, replace=False),
+                          [0, 511, 512, 639, 640, 17151, 17152, 33663, 33664, 38178]])
+    h = 1e-4  # truncation ~h^2, round-off ~1e-16/h: both well below the tolerance
+    for i in idx:
+        pp, pm = p.copy(), p.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd = (oracle.mlp_loss_grad(pp, x, t)[0] - oracle.mlp_loss_grad(pm, x, t)[0]) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=2e-6, abs=1e-9), i
