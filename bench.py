@@ -174,6 +174,54 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------- tuning A/B
+def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs):
+    """Plain vs surrogate tuning of ln a, b, c at the 12 z nodes on the stored
+    skewers of the benchmark catalogue; the surrogate is trained on
+    constant-parameter passes over a 512^3 box with 100k quasars."""
+    import torch
+    from paper_2310_18996_gb300 import tuning
+
+    r = ctx.make_skewers(box, qso, n_q, w)  # stored pre-FGPA skewers (untimed)
+    target, _ = tuning.make_target(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], seed=7)
+    nd0 = tuning.start_nodes(w)
+    nd_p, rep_p = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
+                          method=mk.TUNE_PLAIN, max_passes=200)
+    # surrogate training set: 512^3 box, 100k quasars, same recipe and binning
+    ws = si.shrink(w, n=512, n_q=100_000)
+    ws["seed_box"], ws["seed_cat"] = w["seed_box"] + 1, w["seed_cat"] + 1
+    d, e = si.gaussian_box(ws["n"], ws["cell"], ws["seed_box"], backend="torch", device=dev)
+    pos, ids = si.catalogue(ws)
+    bs = ctx.load_box(ws, ctx.pack_box(d, e), None)
+    del d, e
+    rs = ctx.make_skewers(bs, mk.catalogue_tensor(pos, ids, dev), len(ids), ws)
+    t0 = time.perf_counter()
+    hx, ht = mk.surrogate_labels(ctx, ws, rs["sk"], len(ids), rs["offsets"], rs["delta"], rs["eta"],
+                                 n_draws=draws, seed=11)
+    t_lab = time.perf_counter() - t0
+    mlp = mk.Mlp(ctx, max_batch=1024, seed=3)
+    t0 = time.perf_counter()
+    norm, losses = mlp.fit(hx, ht, batch=256, epochs=epochs, lr=2e-3, seed=5)
+    t_fit = time.perf_counter() - t0
+    nd_s, rep_s = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
+                          method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm, max_passes=60)
+    mlp.close()
+    del r, rs
+    torch.cuda.empty_cache()
+
+    def rep(x):
+        return {"converged": bool(x.converged), "passes": x.passes, "gpu_ms": x.gpu_ms, "wall_ms": x.wall_ms,
+                "max_abs_dfbar": x.max_abs_dfbar, "max_rel_p1d": x.max_rel_p1d, "max_rel_beta": x.max_rel_beta}
+
+    return {"workload": "stored skewers of the benchmark catalogue (1024^3, 1M quasars), 12 z nodes, target "
+                        "Fbar = exp(-0.0025 (1+z)^3.7) +- 1e-3, P1D and beta_F of seeded hidden power laws +- 2%",
+            "plain": rep(rep_p), "surrogate": rep(rep_s),
+            "gpu_time_ratio_plain_over_surrogate": rep_p.gpu_ms / max(rep_s.gpu_ms, 1e-9),
+            "surrogate_training": {"box": "512^3", "quasars": 100_000, "draws": draws, "samples": int(hx.shape[0]),
+                                   "label_s": t_lab, "fit_s": t_fit, "epochs": epochs,
+                                   "final_loss": float(losses[-1]) if len(losses) else None}}
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gb300(args, rank, world, local_rank):
     import torch
@@ -275,6 +323,9 @@ def run_gb300(args, rank, world, local_rank):
     peak, peak_kind = measured_peaks()
     alg = algorithmic_bytes(pos, npix, w)
     achieved = alg / (kms / 1000.0) / 1e9
+    tune = None
+    if rank == 0 and world == 1 and not args.no_tuning:
+        tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs)
     cpu = None
     if want_cpu:
         rate, px, n, dt = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds, os.cpu_count() or 1)
@@ -306,6 +357,8 @@ def run_gb300(args, rank, world, local_rank):
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if tune:
+            line["tuning"] = tune
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -321,6 +374,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tuning", action="store_true")
+    ap.add_argument("--surrogate-draws", type=int, default=4000)
+    ap.add_argument("--surrogate-epochs", type=int, default=200)
     ap.add_argument("--box-n", type=int, default=None, help="smaller box (profiling runs)")
     ap.add_argument("--n-q", type=int, default=None, help="fewer quasars (profiling runs)")
     args = ap.parse_args()

@@ -232,6 +232,15 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
              const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
              mk_stats_out *h_out);
 
+/* Tuning pass over stored pre-FGPA skewers (the paper's post-production,
+   Sec. 3, re-run for new FGPA parameters, Sec. 2.6): the FGPA of d_delta /
+   d_eta with `nodes` (Eq. FGPA) and the statistics of that flux at full
+   resolution (as mk_stats with rebin 1), without storing the flux.
+   d_offsets are the skewer offsets (n_sk + 1).  Synchronous. */
+int mk_flux_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+                  const int64_t *d_offsets, const float *d_delta, const float *d_eta,
+                  const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, mk_stats_out *h_out);
+
 /* The whole path in one pass (rebin 1): geometry, gather, growth, delta_S,
    FGPA and statistics in one persistent kernel, skipping the stores that
    `flags` does not ask for.  P1D segments coincide with delta_S segments
@@ -293,6 +302,123 @@ int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer
                     const int64_t *d_offsets_out, const float *d_flux, int32_t rebin,
                     const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
                     mk_stats_out *h_out);
+
+/* ---------------------------------------------------------------- surrogate MLP */
+
+/* The paper has no counterpart to the surrogate: a learned map from FGPA
+   parameters to the statistics the tuning of Sec. 2.6 matches, used to cut
+   the number of full passes the tuning needs.  A multilayer perceptron
+   4 -> 128 -> 128 -> 128 -> 35 with GELU hidden units (GELU(x) = x Phi(x)) and
+   a linear output.  Parameters: MK_MLP_NPARAM floats in the order W0 [128x4],
+   b0, W1 [128x128], b1, W2 [128x128], b2, W3 [35x128], b3, each W row-major
+   [out][in].  The kernels use the weights in BF16, rounded from an FP32 master
+   copy that Adam updates; biases, activations and all accumulation are FP32.
+   Device arrays are row-major: x n x 4, outputs n x 35. */
+#define MK_MLP_NPARAM 38179
+#define MK_MLP_IN 4
+#define MK_MLP_OUT 35
+typedef struct mk_mlp mk_mlp; /* opaque, library-owned, bound to one context */
+
+/* He-initialised weights (normal, variance 2/fan_in, seeded), zero biases.
+   max_batch bounds the samples of one gradient evaluation (scratch size). */
+int mk_mlp_create(mk_ctx *ctx, mk_mlp **out, int64_t max_batch, uint64_t seed);
+void mk_mlp_destroy(mk_mlp *mlp);
+/* Set the FP32 master parameters (the BF16 copy follows; Adam state resets). */
+int mk_mlp_set_params(mk_mlp *mlp, const float *h_params);
+/* FP32 master parameters and/or the BF16 copy the kernels use (either NULL). */
+int mk_mlp_get_params(mk_mlp *mlp, float *h_params, uint16_t *h_bf16);
+/* Inference: d_y = MLP(d_x) for n samples.  Asynchronous. */
+int mk_mlp_forward(mk_mlp *mlp, const float *d_x, int64_t n, float *d_y);
+/* Mean squared error over n x 35 outputs against d_t and its gradient with
+   respect to every parameter (h_grad: MK_MLP_NPARAM floats), at the current
+   weights, without an update.  n <= max_batch.  Synchronous. */
+int mk_mlp_loss_grad(mk_mlp *mlp, const float *d_x, const float *d_t, int64_t n, double *h_loss,
+                     float *h_grad);
+/* Adam (beta 0.9, 0.999, eps 1e-8) on shuffled minibatches of `batch` (<=
+   max_batch) samples for `epochs` epochs, learning rate lr decayed on a cosine
+   to lr/20; h_epoch_loss (epochs values) receives each epoch's mean training
+   loss, or NULL.  Synchronous. */
+int mk_mlp_train(mk_mlp *mlp, const float *d_x, const float *d_t, int64_t n, int32_t batch,
+                 int32_t epochs, float lr, uint64_t seed, double *h_epoch_loss);
+
+/* ---------------------------------------------------------------- tuning of a, b, c */
+
+/* Box of constant FGPA parameters from which surrogate training draws come. */
+typedef struct mk_surrogate_space {
+  double ln_a_min, ln_a_max, b_min, b_max, c_min, c_max;
+} mk_surrogate_space;
+
+/* Affine normalisation between physical surrogate inputs/outputs and the
+   MLP's: x_mlp = (x - x_mean)/x_std, t = t_mlp t_std + t_mean.  Inputs are
+   (z, ln a, b, c); outputs (Fbar, b_F, beta_F, ln P1D_dF of 32 k bins). */
+typedef struct mk_surrogate_norm {
+  double x_mean[MK_MLP_IN], x_std[MK_MLP_IN];
+  double t_mean[MK_MLP_OUT], t_std[MK_MLP_OUT];
+} mk_surrogate_norm;
+
+/* Training set of the surrogate: n_draws parameter sets drawn uniformly in
+   `space` (seeded), each applied at every z node (constant in z) in one
+   tuning pass (mk_flux_stats) over the stored skewers; every z bin with
+   pixel and P1D data and Fbar > 1e-3 gives one raw sample into h_x (4
+   values) and h_t (35 values; bins->n_k must be 32).  *h_count receives the
+   number of samples (at most n_draws * bins->n_z).  Synchronous. */
+int mk_surrogate_labels(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
+                        int64_t n_sk, const int64_t *d_offsets, const float *d_delta,
+                        const float *d_eta, const mk_stat_bins *bins,
+                        const mk_surrogate_space *space, int32_t n_draws, uint64_t seed,
+                        double *h_x, double *h_t, int64_t *h_count);
+
+/* Fit the surrogate on n raw samples: computes *norm (means and standard
+   deviations of the samples), uploads the normalised samples and runs
+   mk_mlp_train.  Synchronous. */
+int mk_surrogate_fit(mk_mlp *mlp, const double *h_x, const double *h_t, int64_t n, int32_t batch,
+                     int32_t epochs, float lr, uint64_t seed, mk_surrogate_norm *norm,
+                     double *h_epoch_loss);
+
+#define MK_TUNE_PLAIN 0
+#define MK_TUNE_SURROGATE 1
+
+/* Tuning target (Sec. 2.6): mean flux, P1D_dF and optionally beta_F per z
+   bin, with the tolerances that define convergence in every active bin:
+   |Fbar - target| <= tol_mean_flux, |P1D/target - 1| <= tol_p1d in every k bin
+   of [k_lo, k_hi), and |beta_F/target - 1| <= tol_beta when use_beta. */
+typedef struct mk_tune_target {
+  double mean_flux[MK_MAX_ZBINS];
+  double p1d[MK_MAX_ZBINS][MK_MAX_KBINS];
+  double beta[MK_MAX_ZBINS];
+  int32_t use_beta;
+  int32_t k_lo, k_hi;
+  uint32_t active; /* bit i: tune z bin i */
+  double tol_mean_flux, tol_p1d, tol_beta;
+} mk_tune_target;
+
+typedef struct mk_tune_report {
+  int32_t converged;  /* 1 when every active bin met the tolerances on a full pass */
+  int32_t passes;     /* full tuning passes over the skewers */
+  int32_t iterations; /* parameter updates */
+  double gpu_ms;      /* GPU time of the passes and of the surrogate inference */
+  double wall_ms;
+  double max_abs_dfbar, max_rel_p1d, max_rel_beta; /* of the last full pass */
+} mk_tune_report;
+
+/* Solve for ln a, b, c at the z nodes in *inout (count = bins->n_z, nodes at
+   the bin centres) so that the statistics of the stored skewers meet the
+   target (Sec. 2.6 tunes a, b sigma_g and P_S by Minuit fits and ratio
+   iterations; here a Levenberg-Marquardt step per node on
+   r = [(Fbar - F*)/tol_F, ln(P1D/P*)/tol_P, (beta - b*)/(tol_b |b*|)]).
+   MK_TUNE_PLAIN: each iteration is one pass at the current parameters plus
+   three passes with ln a, b, c shifted (finite-difference Jacobian).
+   MK_TUNE_SURROGATE: the parameters are first fitted to the target on the
+   surrogate alone; every later iteration is one verifying pass, after which
+   the fit is redone on the surrogate shifted by that pass's discrepancy
+   (true minus predicted residual).  Nodes of inactive
+   bins follow the nearest active node (ties: the lower one).  Stops when a
+   pass meets the tolerances or after max_passes passes.  Synchronous. */
+int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+            const int64_t *d_offsets, const float *d_delta, const float *d_eta,
+            const mk_stat_bins *bins, const mk_tune_target *target, int32_t method,
+            mk_mlp *surrogate, const mk_surrogate_norm *norm, int32_t max_passes,
+            mk_fgpa_nodes *inout, mk_tune_report *report);
 
 /* ---------------------------------------------------------------- timing */
 

@@ -26,7 +26,9 @@ STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
            "mk_free_box", "mk_pack_box", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
-           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config"]
+           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
+           "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
+           "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune"]
 
 
 class MkError(RuntimeError):
@@ -75,6 +77,32 @@ class StatsOut(C.Structure):
     ]
 
 
+class SurrogateSpace(C.Structure):
+    _fields_ = [("ln_a_min", C.c_double), ("ln_a_max", C.c_double), ("b_min", C.c_double),
+                ("b_max", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double)]
+
+
+class SurrogateNorm(C.Structure):
+    _fields_ = [("x_mean", C.c_double * 4), ("x_std", C.c_double * 4),
+                ("t_mean", C.c_double * 35), ("t_std", C.c_double * 35)]
+
+
+class TuneTarget(C.Structure):
+    _fields_ = [("mean_flux", C.c_double * MAX_ZBINS),
+                ("p1d", (C.c_double * MAX_KBINS) * MAX_ZBINS),
+                ("beta", C.c_double * MAX_ZBINS), ("use_beta", C.c_int32),
+                ("k_lo", C.c_int32), ("k_hi", C.c_int32), ("active", C.c_uint32),
+                ("tol_mean_flux", C.c_double), ("tol_p1d", C.c_double), ("tol_beta", C.c_double)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("converged", C.c_int32), ("passes", C.c_int32), ("iterations", C.c_int32),
+                ("gpu_ms", C.c_double), ("wall_ms", C.c_double), ("max_abs_dfbar", C.c_double),
+                ("max_rel_p1d", C.c_double), ("max_rel_beta", C.c_double)]
+
+
+MLP_NPARAM = 38179
+TUNE_PLAIN, TUNE_SURROGATE = 0, 1
 SKEWER_BYTES = 72  # sizeof(mk_skewer)
 QSO_DTYPE = np.dtype([("pos", np.float64, 3), ("id", np.uint64)])  # mk_qso, 32 bytes
 
@@ -111,6 +139,25 @@ def lib():
                 "mk_stats_static": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, i32, vp, vp,
                                               P(StatBins), P(StatsOut)]),
                 "mk_launch_config": (C.c_int, [vp, i32, i32, i32, u32, P(i32), P(i32)]),
+                "mk_flux_stats": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, vp, P(FgpaNodes),
+                                            P(StatBins), P(StatsOut)]),
+                "mk_mlp_create": (C.c_int, [vp, P(vp), i64, C.c_uint64]),
+                "mk_mlp_destroy": (None, [vp]),
+                "mk_mlp_set_params": (C.c_int, [vp, P(C.c_float)]),
+                "mk_mlp_get_params": (C.c_int, [vp, P(C.c_float), P(C.c_uint16)]),
+                "mk_mlp_forward": (C.c_int, [vp, vp, i64, vp]),
+                "mk_mlp_loss_grad": (C.c_int, [vp, vp, vp, i64, P(C.c_double), P(C.c_float)]),
+                "mk_mlp_train": (C.c_int, [vp, vp, vp, i64, i32, i32, C.c_float, C.c_uint64,
+                                           P(C.c_double)]),
+                "mk_surrogate_labels": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, vp, P(StatBins),
+                                                  P(SurrogateSpace), i32, C.c_uint64, P(C.c_double),
+                                                  P(C.c_double), P(i64)]),
+                "mk_surrogate_fit": (C.c_int, [vp, P(C.c_double), P(C.c_double), i64, i32, i32,
+                                               C.c_float, C.c_uint64, P(SurrogateNorm),
+                                               P(C.c_double)]),
+                "mk_tune": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, vp, P(StatBins),
+                                      P(TuneTarget), i32, vp, P(SurrogateNorm), i32, P(FgpaNodes),
+                                      P(TuneReport)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -305,6 +352,17 @@ class Context:
                                    rebin, _ptr(delta), _ptr(eta), C.byref(b), C.byref(st)))
         return stats_dict(st, b.n_z, b.n_k)
 
+    def flux_stats(self, w, sk, n_sk, offsets, delta, eta, nodes=None):
+        """Tuning pass: FGPA of stored fields and their statistics (no flux stored)."""
+        p = skewer_params(w)
+        nd = fgpa_nodes(w) if nodes is None else nodes
+        b = stat_bins(w)
+        st = StatsOut()
+        self._stream()
+        self._check(lib().mk_flux_stats(self.h, C.byref(p), _ptr(sk), n_sk, _ptr(offsets), _ptr(delta),
+                                        _ptr(eta), C.byref(nd), C.byref(b), C.byref(st)))
+        return stats_dict(st, b.n_z, b.n_k)
+
     def run(self, box, qso, n_qso, w, flags=STATS, capacity=0, outputs=None, nodes=None):
         """The fused path; returns (stats dict or None, dict of device tensors)."""
         torch = self._torch
@@ -337,3 +395,110 @@ def skewer_records(sk, n):
                    ("p0", np.int64, 3), ("step", np.int64, 3), ("id", np.uint64)])
     assert dt.itemsize == SKEWER_BYTES
     return sk[: n * SKEWER_BYTES].cpu().numpy().view(dt)
+
+
+# ------------------------------------------------------------------ surrogate and tuning
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Mlp:
+    """The surrogate MLP (4-128-128-128-35, GELU) bound to a Context."""
+
+    def __init__(self, ctx, max_batch=4096, seed=0):
+        self.ctx = ctx
+        h = C.c_void_p()
+        ctx._stream()
+        ctx._check(lib().mk_mlp_create(ctx.h, C.byref(h), max_batch, seed))
+        self.h = h
+        self.max_batch = max_batch
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.mk_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == MLP_NPARAM
+        self.ctx._stream()
+        self.ctx._check(lib().mk_mlp_set_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def get_params(self):
+        p = np.zeros(MLP_NPARAM, np.float32)
+        b = np.zeros(MLP_NPARAM, np.uint16)
+        self.ctx._stream()
+        self.ctx._check(lib().mk_mlp_get_params(self.h, p.ctypes.data_as(C.POINTER(C.c_float)),
+                                                b.ctypes.data_as(C.POINTER(C.c_uint16))))
+        return p, b
+
+    def forward(self, x):
+        torch = self.ctx._torch
+        y = torch.empty((x.shape[0], 35), dtype=torch.float32, device=x.device)
+        self.ctx._stream()
+        self.ctx._check(lib().mk_mlp_forward(self.h, _ptr(x), x.shape[0], _ptr(y)))
+        return y
+
+    def loss_grad(self, x, t):
+        g = np.zeros(MLP_NPARAM, np.float32)
+        loss = C.c_double()
+        self.ctx._stream()
+        self.ctx._check(lib().mk_mlp_loss_grad(self.h, _ptr(x), _ptr(t), x.shape[0], C.byref(loss),
+                                               g.ctypes.data_as(C.POINTER(C.c_float))))
+        return loss.value, g
+
+    def train(self, x, t, batch=2048, epochs=10, lr=2e-3, seed=0):
+        losses = np.zeros(max(epochs, 1))
+        self.ctx._stream()
+        self.ctx._check(lib().mk_mlp_train(self.h, _ptr(x), _ptr(t), x.shape[0], batch, epochs, lr, seed,
+                                           _dp(losses)))
+        return losses[:epochs]
+
+    def fit(self, hx, ht, batch=2048, epochs=10, lr=2e-3, seed=0):
+        """Normalise raw samples, train; returns (SurrogateNorm, per-epoch loss)."""
+        hx = np.ascontiguousarray(hx, dtype=np.float64)
+        ht = np.ascontiguousarray(ht, dtype=np.float64)
+        norm = SurrogateNorm()
+        losses = np.zeros(max(epochs, 1))
+        self.ctx._stream()
+        self.ctx._check(lib().mk_surrogate_fit(self.h, _dp(hx), _dp(ht), hx.shape[0], batch, epochs, lr, seed,
+                                               C.byref(norm), _dp(losses)))
+        return norm, losses[:epochs]
+
+
+def surrogate_labels(ctx, w, sk, n_sk, offsets, delta, eta, n_draws, seed=0, space=None):
+    """Raw surrogate training samples x (n, 4) and t (n, 35) from tuning passes."""
+    sp = space or SurrogateSpace(ln_a_min=math.log(1e-3), ln_a_max=math.log(3.0), b_min=1.0, b_max=2.2,
+                                 c_min=0.5, c_max=1.5)
+    p = skewer_params(w)
+    b = stat_bins(w)
+    hx = np.zeros((n_draws * b.n_z, 4))
+    ht = np.zeros((n_draws * b.n_z, 35))
+    cnt = C.c_int64()
+    ctx._stream()
+    ctx._check(lib().mk_surrogate_labels(ctx.h, C.byref(p), _ptr(sk), n_sk, _ptr(offsets), _ptr(delta),
+                                         _ptr(eta), C.byref(b), C.byref(sp), n_draws, seed, _dp(hx), _dp(ht),
+                                         C.byref(cnt)))
+    return hx[:cnt.value], ht[:cnt.value]
+
+
+def tune(ctx, w, sk, n_sk, offsets, delta, eta, target, nodes, method=TUNE_PLAIN, mlp=None, norm=None,
+         max_passes=60):
+    """Run mk_tune; returns (FgpaNodes, TuneReport)."""
+    p = skewer_params(w)
+    b = stat_bins(w)
+    rep = TuneReport()
+    nd = FgpaNodes()
+    C.pointer(nd)[0] = nodes
+    ctx._stream()
+    ctx._check(lib().mk_tune(ctx.h, C.byref(p), _ptr(sk), n_sk, _ptr(offsets), _ptr(delta), _ptr(eta),
+                             C.byref(b), C.byref(target), method, mlp.h if mlp else None,
+                             C.byref(norm) if norm is not None else None, max_passes, C.byref(nd),
+                             C.byref(rep)))
+    return nd, rep

@@ -666,20 +666,25 @@ int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, 
   return MK_OK;
 }
 
-int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
-             const int64_t *d_offsets_out, const float *d_flux, int32_t rebin, const float *d_delta,
-             const float *d_eta, const mk_stat_bins *bins, mk_stats_out *h_out) {
+namespace {
+// Statistics pass shared by mk_stats (stored flux) and mk_flux_stats (flux
+// computed from stored fields with the FGPA table of `nodes`).
+int stats_pass(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+               const int64_t *d_offsets_out, const float *d_flux, int32_t rebin, const float *d_delta,
+               const float *d_eta, const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, mk_stats_out *h_out) {
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, false);
   if (rc || (rc = check_bins(ctx, bins))) return rc;
   if (rebin < 1 || rebin > 4096) return fail(ctx, MK_EINVAL, "rebin must be in [1, 4096]");
-  if (!h_out || n_sk < 0 || (n_sk > 0 && (!d_sk || !d_offsets_out || !d_flux)))
+  if (!h_out || n_sk < 0 || (n_sk > 0 && (!d_sk || !d_offsets_out || (!d_flux && !nodes))))
     return fail(ctx, MK_EINVAL, "bad stats arguments");
+  if (nodes && (rebin != 1 || !d_delta)) return fail(ctx, MK_EINVAL, "the tuning pass needs rebin 1 and the fields");
   if ((d_delta == nullptr) != (d_eta == nullptr)) return fail(ctx, MK_EINVAL, "d_delta and d_eta go together");
   CK(cudaSetDevice(ctx->device));
   if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_sk)) ||
       (rc = ensure_twiddles(ctx, bins->n_fft)) || (rc = ensure_zbin(ctx, bins)))
     return rc;
+  if (nodes && (rc = ensure_pixtab(ctx, nodes))) return rc;
   const int threads = 256;
   const StatLayout L{bins->n_z, bins->n_k};
   const int grid = stats_grid(ctx, bins, threads);
@@ -693,7 +698,8 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
   P.off_out = d_offsets_out;
   P.segoff = ctx->d_segoff;
   P.n_sk = n_sk;
-  P.flux = d_flux;
+  P.flux = nodes ? nullptr : d_flux;
+  P.pixtab = nodes ? ctx->d_pixtab : nullptr;
   P.delta = d_delta;
   P.eta = d_eta;
   P.rebin = rebin;
@@ -714,6 +720,25 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
   CK(launch_stats(P, bins->n_fft, grid, threads, ctx->stream));
   if ((rc = time_end(ctx))) return rc;
   return finish_stats(ctx, grid, bins, h_out);
+}
+}  // namespace
+
+int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+             const int64_t *d_offsets_out, const float *d_flux, int32_t rebin, const float *d_delta,
+             const float *d_eta, const mk_stat_bins *bins, mk_stats_out *h_out) {
+  if (!ctx) return MK_EINVAL;
+  if (n_sk > 0 && !d_flux) return fail(ctx, MK_EINVAL, "d_flux is NULL");
+  return stats_pass(ctx, params, d_sk, n_sk, d_offsets_out, d_flux, rebin, d_delta, d_eta, nullptr, bins, h_out);
+}
+
+int mk_flux_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+                  const int64_t *d_offsets, const float *d_delta, const float *d_eta, const mk_fgpa_nodes *nodes,
+                  const mk_stat_bins *bins, mk_stats_out *h_out) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_nodes(ctx, nodes);
+  if (rc) return rc;
+  if (n_sk > 0 && (!d_delta || !d_eta)) return fail(ctx, MK_EINVAL, "the tuning pass needs d_delta and d_eta");
+  return stats_pass(ctx, params, d_sk, n_sk, d_offsets, nullptr, 1, d_delta, d_eta, nodes, bins, h_out);
 }
 
 int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, const mk_skewer_params *params,
@@ -1021,3 +1046,11 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
   std::memcpy(h_out, ctx->h_stats, sizeof(mk_stats_out));
   return MK_OK;
 }
+
+// ====================================================================== internal accessors
+// for the surrogate and tuner translation unit (mk_tune.cu)
+namespace mkhost {
+cudaStream_t ctx_stream(mk_ctx *c) { return c->stream; }
+int ctx_device(mk_ctx *c) { return c->device; }
+int ctx_fail(mk_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
+}  // namespace mkhost

@@ -77,8 +77,9 @@ struct StatParams {
   const int64_t *off_out;  // output offsets, n_sk + 1
   const int64_t *segoff;   // prefix of ceil(n_out / N) per skewer
   int64_t n_sk;
-  const float *flux;
+  const float *flux;         // stored flux, or NULL with pixtab set
   const float *delta, *eta;  // fine fields or NULL
+  const float4 *pixtab;      // tuning pass: FGPA table; the flux is computed from delta, eta
   int32_t rebin;
   const int16_t *zbin;
   const int16_t *segzbin;

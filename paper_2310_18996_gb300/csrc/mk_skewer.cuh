@@ -217,7 +217,6 @@ __global__ void __launch_bounds__(256) k_stats(StatParams P) {
       float f = 0.f;
       if (p < npx) {
         const int64_t kk = k0 + p;
-        f = P.flux[o + kk];
         float ds = 0.f, es = 0.f;
         if (P.delta) {
           for (int r = 0; r < R; ++r) {
@@ -229,6 +228,8 @@ __global__ void __launch_bounds__(256) k_stats(StatParams P) {
             es /= static_cast<float>(R);
           }
         }
+        // flux: stored, or (tuning pass, rebin 1) the FGPA of the stored fields
+        f = P.pixtab ? fgpa(__ldg(P.pixtab + sk.j_lo + kk), ds, es) : P.flux[o + kk];
         const int zb = zbin_of(kk);
         if (zb == zf) add_pixel(a0, f, ds, es);
         else if (zb == zf + 1) add_pixel(a1, f, ds, es);

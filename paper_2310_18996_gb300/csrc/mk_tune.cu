@@ -1,0 +1,658 @@
+// Surrogate MLP objects, surrogate training data and the tuning of a, b, c.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "../../include/mockskewer.h"
+#include "mk_host.h"
+#include "mk_mlp.h"
+
+using namespace mk;
+
+struct mk_mlp {
+  mk_ctx *ctx = nullptr;
+  int device = 0;  // kept so that destruction does not depend on the context
+  int64_t cap = 0;
+  float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+  void *wbf = nullptr;
+  float *y = nullptr, *dy = nullptr, *acts = nullptr, *dzs = nullptr;
+  double *loss_part = nullptr, *h_loss_part = nullptr;
+  int64_t step = 0;
+};
+
+namespace {
+
+int mfail(mk_ctx *ctx, int code, const char *msg) { return mkhost::ctx_fail(ctx, code, msg); }
+
+#define CKM(ctx, call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      char b_[256];                                                                        \
+      snprintf(b_, sizeof(b_), "%s: %s", #call, cudaGetErrorString(e_));                    \
+      return mfail(ctx, MK_ECUDA, b_);                                                     \
+    }                                                                                      \
+  } while (0)
+
+void mlp_free(mk_mlp *p) {
+  cudaFree(p->master);
+  cudaFree(p->m);
+  cudaFree(p->v);
+  cudaFree(p->grad);
+  cudaFree(p->wbf);
+  cudaFree(p->y);
+  cudaFree(p->dy);
+  cudaFree(p->acts);
+  cudaFree(p->dzs);
+  cudaFree(p->loss_part);
+  cudaFreeHost(p->h_loss_part);
+}
+
+// Mean squared error from the per-CTA partials of the last gradient evaluation.
+int read_loss(mk_mlp *p, double *loss) {
+  cudaStream_t st = mkhost::ctx_stream(p->ctx);
+  CKM(p->ctx, cudaMemcpyAsync(p->h_loss_part, p->loss_part, sizeof(double) * kLossParts, cudaMemcpyDeviceToHost, st));
+  CKM(p->ctx, cudaStreamSynchronize(st));
+  double s = 0.0;
+  for (int i = 0; i < kLossParts; ++i) s += p->h_loss_part[i];
+  *loss = s;
+  return MK_OK;
+}
+
+}  // namespace
+
+// ====================================================================== MLP
+extern "C" int mk_mlp_create(mk_ctx *ctx, mk_mlp **out, int64_t max_batch, uint64_t seed) {
+  if (!ctx || !out) return MK_EINVAL;
+  *out = nullptr;
+  if (max_batch < 1 || max_batch > (1 << 24)) return mfail(ctx, MK_EINVAL, "max_batch must be in [1, 2^24]");
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  mk_mlp *p = new mk_mlp();
+  p->ctx = ctx;
+  p->device = mkhost::ctx_device(ctx);
+  p->cap = max_batch;
+  const size_t np = sizeof(float) * kMlpParams;
+  const size_t nh = sizeof(float) * static_cast<size_t>(max_batch) * kMlpHidden;
+  if (cudaMalloc(&p->master, np) != cudaSuccess || cudaMalloc(&p->m, np) != cudaSuccess ||
+      cudaMalloc(&p->v, np) != cudaSuccess || cudaMalloc(&p->grad, np) != cudaSuccess ||
+      cudaMalloc(&p->wbf, sizeof(uint16_t) * kMlpParams) != cudaSuccess ||
+      cudaMalloc(&p->y, sizeof(float) * max_batch * kMlpOut) != cudaSuccess ||
+      cudaMalloc(&p->dy, sizeof(float) * max_batch * kMlpOut) != cudaSuccess ||
+      cudaMalloc(&p->acts, 6 * nh) != cudaSuccess || cudaMalloc(&p->dzs, 3 * nh) != cudaSuccess ||
+      cudaMalloc(&p->loss_part, sizeof(double) * kLossParts) != cudaSuccess ||
+      cudaMallocHost(&p->h_loss_part, sizeof(double) * kLossParts) != cudaSuccess) {
+    mlp_free(p);
+    delete p;
+    return mfail(ctx, MK_ENOMEM, "surrogate MLP allocation");
+  }
+  // He initialisation: W ~ N(0, 2 / fan_in), b = 0
+  std::vector<float> h(kMlpParams, 0.f);
+  std::mt19937_64 rng(seed);
+  const int dims[5] = {kMlpIn, kMlpHidden, kMlpHidden, kMlpHidden, kMlpOut};
+  size_t o = 0;
+  for (int l = 0; l < 4; ++l) {
+    std::normal_distribution<double> nd(0.0, std::sqrt(2.0 / dims[l]));
+    for (int i = 0; i < dims[l + 1] * dims[l]; ++i) h[o++] = static_cast<float>(nd(rng));
+    o += dims[l + 1];
+  }
+  *out = p;
+  return mk_mlp_set_params(p, h.data());
+}
+
+extern "C" void mk_mlp_destroy(mk_mlp *mlp) {
+  if (!mlp) return;
+  cudaSetDevice(mlp->device);
+  cudaDeviceSynchronize();
+  mlp_free(mlp);
+  delete mlp;
+}
+
+extern "C" int mk_mlp_set_params(mk_mlp *p, const float *h_params) {
+  if (!p || !h_params) return MK_EINVAL;
+  mk_ctx *ctx = p->ctx;
+  cudaStream_t st = mkhost::ctx_stream(ctx);
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  CKM(ctx, cudaMemcpyAsync(p->master, h_params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st));
+  CKM(ctx, cudaMemsetAsync(p->m, 0, sizeof(float) * kMlpParams, st));
+  CKM(ctx, cudaMemsetAsync(p->v, 0, sizeof(float) * kMlpParams, st));
+  CKM(ctx, mlp_to_bf16(p->master, p->wbf, st));
+  CKM(ctx, cudaStreamSynchronize(st));
+  p->step = 0;
+  return MK_OK;
+}
+
+extern "C" int mk_mlp_get_params(mk_mlp *p, float *h_params, uint16_t *h_bf16) {
+  if (!p) return MK_EINVAL;
+  mk_ctx *ctx = p->ctx;
+  cudaStream_t st = mkhost::ctx_stream(ctx);
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  if (h_params)
+    CKM(ctx, cudaMemcpyAsync(h_params, p->master, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st));
+  if (h_bf16) CKM(ctx, cudaMemcpyAsync(h_bf16, p->wbf, sizeof(uint16_t) * kMlpParams, cudaMemcpyDeviceToHost, st));
+  CKM(ctx, cudaStreamSynchronize(st));
+  return MK_OK;
+}
+
+extern "C" int mk_mlp_forward(mk_mlp *p, const float *d_x, int64_t n, float *d_y) {
+  if (!p) return MK_EINVAL;
+  if (n < 0 || (n > 0 && (!d_x || !d_y))) return mfail(p->ctx, MK_EINVAL, "bad forward arguments");
+  CKM(p->ctx, cudaSetDevice(mkhost::ctx_device(p->ctx)));
+  CKM(p->ctx, mlp_forward(p->wbf, p->master, d_x, nullptr, n, d_y, nullptr, mkhost::ctx_stream(p->ctx)));
+  return MK_OK;
+}
+
+extern "C" int mk_mlp_loss_grad(mk_mlp *p, const float *d_x, const float *d_t, int64_t n, double *h_loss,
+                                float *h_grad) {
+  if (!p) return MK_EINVAL;
+  if (n < 1 || n > p->cap || !d_x || !d_t) return mfail(p->ctx, MK_EINVAL, "n must be in [1, max_batch]");
+  mk_ctx *ctx = p->ctx;
+  cudaStream_t st = mkhost::ctx_stream(ctx);
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  CKM(ctx, mlp_gradient(p->wbf, p->master, d_x, d_t, nullptr, n, 1.0 / (static_cast<double>(n) * kMlpOut), p->y,
+                        p->dy, p->acts, p->dzs, p->grad, p->loss_part, st));
+  if (h_grad)
+    CKM(ctx, cudaMemcpyAsync(h_grad, p->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st));
+  double loss = 0.0;
+  int rc = read_loss(p, &loss);  // synchronises
+  if (rc) return rc;
+  if (h_loss) *h_loss = loss;
+  return MK_OK;
+}
+
+extern "C" int mk_mlp_train(mk_mlp *p, const float *d_x, const float *d_t, int64_t n, int32_t batch,
+                            int32_t epochs, float lr, uint64_t seed, double *h_epoch_loss) {
+  if (!p) return MK_EINVAL;
+  mk_ctx *ctx = p->ctx;
+  if (n < 1 || !d_x || !d_t || batch < 1 || batch > p->cap || epochs < 0 || !(lr > 0.f))
+    return mfail(ctx, MK_EINVAL, "bad training arguments (n >= 1, 1 <= batch <= max_batch, lr > 0)");
+  if (n > INT32_MAX) return mfail(ctx, MK_EINVAL, "too many samples");
+  cudaStream_t st = mkhost::ctx_stream(ctx);
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  int32_t *d_rows = nullptr;
+  if (cudaMalloc(&d_rows, sizeof(int32_t) * n) != cudaSuccess) return mfail(ctx, MK_ENOMEM, "training index array");
+  std::vector<int32_t> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::mt19937_64 rng(seed);
+  int rc = MK_OK;
+  for (int e = 0; e < epochs && rc == MK_OK; ++e) {
+    std::shuffle(perm.begin(), perm.end(), rng);
+    if (cudaMemcpyAsync(d_rows, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      rc = mfail(ctx, MK_ECUDA, "training index upload");
+      break;
+    }
+    const double lr_e = lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * e / std::max(1, epochs))));
+    double esum = 0.0;
+    for (int64_t b0 = 0; b0 < n && rc == MK_OK; b0 += batch) {
+      const int64_t nb = std::min<int64_t>(batch, n - b0);
+      cudaError_t ce = mlp_gradient(p->wbf, p->master, d_x, d_t, d_rows + b0, nb,
+                                    1.0 / (static_cast<double>(nb) * kMlpOut), p->y, p->dy, p->acts, p->dzs, p->grad,
+                                    p->loss_part, st);
+      if (ce == cudaSuccess)
+        ce = mlp_adam(p->master, p->wbf, p->grad, p->m, p->v, static_cast<float>(lr_e), 0.9f, 0.999f, 1e-8f,
+                      ++p->step, st);
+      if (ce != cudaSuccess) {
+        rc = mfail(ctx, MK_ECUDA, cudaGetErrorString(ce));
+        break;
+      }
+      if (h_epoch_loss) {
+        double l = 0.0;
+        if ((rc = read_loss(p, &l))) break;
+        esum += l * nb;
+      }
+    }
+    if (h_epoch_loss) h_epoch_loss[e] = esum / n;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(d_rows);
+  return rc;
+}
+
+// ====================================================================== surrogate data
+namespace {
+
+bool valid_stat_sample(const mk_stats_out &st, int zb, int n_k) {
+  if (st.sums[zb][0] <= 0.0 || st.n_seg[zb] <= 0.0 || !(st.mean_flux[zb] > 1e-3)) return false;
+  if (!std::isfinite(st.b_f[zb]) || !std::isfinite(st.beta_f[zb])) return false;
+  for (int k = 0; k < n_k; ++k)
+    if (!(st.p1d_df[zb][k] > 0.0) || !std::isfinite(std::log(st.p1d_df[zb][k]))) return false;
+  return true;
+}
+
+void stat_vector(const mk_stats_out &st, int zb, double *t) {
+  t[0] = st.mean_flux[zb];
+  t[1] = st.b_f[zb];
+  t[2] = st.beta_f[zb];
+  for (int k = 0; k < 32; ++k) t[3 + k] = std::log(st.p1d_df[zb][k]);
+}
+
+mk_fgpa_nodes constant_nodes(const mk_stat_bins *b, double ln_a, double bb, double c) {
+  mk_fgpa_nodes nd;
+  std::memset(&nd, 0, sizeof(nd));
+  nd.count = b->n_z;
+  for (int i = 0; i < b->n_z; ++i) {
+    nd.z[i] = b->z_lo + (i + 0.5) * b->dz;
+    nd.ln_a[i] = ln_a;
+    nd.b[i] = bb;
+    nd.c[i] = c;
+  }
+  return nd;
+}
+
+}  // namespace
+
+extern "C" int mk_surrogate_labels(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+                                   const int64_t *d_offsets, const float *d_delta, const float *d_eta,
+                                   const mk_stat_bins *bins, const mk_surrogate_space *space, int32_t n_draws,
+                                   uint64_t seed, double *h_x, double *h_t, int64_t *h_count) {
+  if (!ctx) return MK_EINVAL;
+  if (!bins || bins->n_k != 32 || !space || n_draws < 0 || !h_x || !h_t || !h_count)
+    return mfail(ctx, MK_EINVAL, "surrogate labels need 32 k bins, a parameter space and host outputs");
+  std::mt19937_64 rng(seed);
+  std::uniform_real_distribution<double> ua(space->ln_a_min, space->ln_a_max), ub(space->b_min, space->b_max),
+      uc(space->c_min, space->c_max);
+  int64_t cnt = 0;
+  mk_stats_out st;
+  for (int d = 0; d < n_draws; ++d) {
+    const double la = ua(rng), b = ub(rng), c = uc(rng);
+    const mk_fgpa_nodes nd = constant_nodes(bins, la, b, c);
+    const int rc = mk_flux_stats(ctx, params, d_sk, n_sk, d_offsets, d_delta, d_eta, &nd, bins, &st);
+    if (rc) return rc;
+    for (int zb = 0; zb < bins->n_z; ++zb) {
+      if (!valid_stat_sample(st, zb, 32)) continue;
+      double *x = h_x + 4 * cnt;
+      x[0] = nd.z[zb];
+      x[1] = la;
+      x[2] = b;
+      x[3] = c;
+      stat_vector(st, zb, h_t + kMlpOut * cnt);
+      ++cnt;
+    }
+  }
+  *h_count = cnt;
+  return MK_OK;
+}
+
+extern "C" int mk_surrogate_fit(mk_mlp *p, const double *h_x, const double *h_t, int64_t n, int32_t batch,
+                                int32_t epochs, float lr, uint64_t seed, mk_surrogate_norm *norm,
+                                double *h_epoch_loss) {
+  if (!p) return MK_EINVAL;
+  mk_ctx *ctx = p->ctx;
+  if (n < 2 || !h_x || !h_t || !norm) return mfail(ctx, MK_EINVAL, "surrogate fit needs >= 2 samples and a norm");
+  std::memset(norm, 0, sizeof(*norm));
+  auto moments = [&](const double *a, int stride, int col, double &mean, double &sd) {
+    double s = 0.0, s2 = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += a[i * stride + col];
+    mean = s / n;
+    for (int64_t i = 0; i < n; ++i) {
+      const double d = a[i * stride + col] - mean;
+      s2 += d * d;
+    }
+    sd = std::sqrt(s2 / n);
+    if (!(sd > 1e-12)) sd = 1.0;
+  };
+  for (int c = 0; c < kMlpIn; ++c) moments(h_x, kMlpIn, c, norm->x_mean[c], norm->x_std[c]);
+  for (int c = 0; c < kMlpOut; ++c) moments(h_t, kMlpOut, c, norm->t_mean[c], norm->t_std[c]);
+  std::vector<float> xs(n * kMlpIn), ts(n * kMlpOut);
+  for (int64_t i = 0; i < n; ++i) {
+    for (int c = 0; c < kMlpIn; ++c)
+      xs[i * kMlpIn + c] = static_cast<float>((h_x[i * kMlpIn + c] - norm->x_mean[c]) / norm->x_std[c]);
+    for (int c = 0; c < kMlpOut; ++c)
+      ts[i * kMlpOut + c] = static_cast<float>((h_t[i * kMlpOut + c] - norm->t_mean[c]) / norm->t_std[c]);
+  }
+  cudaStream_t st = mkhost::ctx_stream(ctx);
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  float *dx = nullptr, *dt = nullptr;
+  if (cudaMalloc(&dx, sizeof(float) * xs.size()) != cudaSuccess ||
+      cudaMalloc(&dt, sizeof(float) * ts.size()) != cudaSuccess) {
+    cudaFree(dx);
+    return mfail(ctx, MK_ENOMEM, "surrogate training set");
+  }
+  int rc = MK_OK;
+  if (cudaMemcpyAsync(dx, xs.data(), sizeof(float) * xs.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dt, ts.data(), sizeof(float) * ts.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    rc = mfail(ctx, MK_ECUDA, "surrogate training set upload");
+  if (!rc) rc = mk_mlp_train(p, dx, dt, n, batch, epochs, lr, seed, h_epoch_loss);
+  cudaStreamSynchronize(st);
+  cudaFree(dx);
+  cudaFree(dt);
+  return rc;
+}
+
+// ====================================================================== tuning
+namespace {
+
+struct Residuals {
+  std::vector<double> r;  // per node, concatenated
+  int m = 0;              // residuals per node
+};
+
+struct TuneState {
+  mk_ctx *ctx;
+  const mk_skewer_params *params;
+  const mk_skewer *d_sk;
+  int64_t n_sk;
+  const int64_t *d_offsets;
+  const float *d_delta, *d_eta;
+  const mk_stat_bins *bins;
+  const mk_tune_target *tg;
+  mk_tune_report *rep;
+  cudaEvent_t e0, e1;
+  int nk() const { return tg->k_hi - tg->k_lo; }
+  int m() const { return 1 + nk() + (tg->use_beta ? 1 : 0); }
+  bool active(int zb) const { return (tg->active >> zb) & 1u; }
+};
+
+// Residual vector of one bin from statistic values (Fbar, beta, ln P1D).
+void residual(const TuneState &S, int zb, double fbar, double beta, const double *lnp, double *r) {
+  const mk_tune_target *t = S.tg;
+  r[0] = (fbar - t->mean_flux[zb]) / t->tol_mean_flux;
+  for (int k = t->k_lo; k < t->k_hi; ++k) r[1 + k - t->k_lo] = (lnp[k] - std::log(t->p1d[zb][k])) / t->tol_p1d;
+  if (t->use_beta) r[1 + S.nk()] = (beta - t->beta[zb]) / (t->tol_beta * std::fabs(t->beta[zb]));
+}
+
+// One full tuning pass at `nodes`; residuals of every bin, GPU time added.
+int full_pass(TuneState &S, const mk_fgpa_nodes &nodes, mk_stats_out &st, std::vector<double> &r) {
+  cudaStream_t stream = mkhost::ctx_stream(S.ctx);
+  cudaEventRecord(S.e0, stream);
+  const int rc = mk_flux_stats(S.ctx, S.params, S.d_sk, S.n_sk, S.d_offsets, S.d_delta, S.d_eta, &nodes, S.bins, &st);
+  if (rc) return rc;
+  cudaEventRecord(S.e1, stream);
+  cudaEventSynchronize(S.e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, S.e0, S.e1);
+  S.rep->gpu_ms += ms;
+  S.rep->passes += 1;
+  const int m = S.m();
+  r.assign(static_cast<size_t>(S.bins->n_z) * m, 0.0);
+  double lnp[MK_MAX_KBINS];
+  for (int zb = 0; zb < S.bins->n_z; ++zb) {
+    if (!S.active(zb)) continue;
+    for (int k = 0; k < S.bins->n_k; ++k) lnp[k] = std::log(std::max(st.p1d_df[zb][k], 1e-300));
+    residual(S, zb, st.mean_flux[zb], st.beta_f[zb], lnp, &r[static_cast<size_t>(zb) * m]);
+  }
+  return MK_OK;
+}
+
+// Convergence check of a full pass; also fills the report's error measures.
+bool converged(TuneState &S, const mk_stats_out &st) {
+  const mk_tune_target *t = S.tg;
+  double df = 0.0, dp = 0.0, db = 0.0;
+  for (int zb = 0; zb < S.bins->n_z; ++zb) {
+    if (!S.active(zb)) continue;
+    df = std::max(df, std::fabs(st.mean_flux[zb] - t->mean_flux[zb]));
+    for (int k = t->k_lo; k < t->k_hi; ++k) dp = std::max(dp, std::fabs(st.p1d_df[zb][k] / t->p1d[zb][k] - 1.0));
+    if (t->use_beta) db = std::max(db, std::fabs(st.beta_f[zb] / t->beta[zb] - 1.0));
+  }
+  S.rep->max_abs_dfbar = df;
+  S.rep->max_rel_p1d = dp;
+  S.rep->max_rel_beta = db;
+  return df <= t->tol_mean_flux && dp <= t->tol_p1d && (!t->use_beta || db <= t->tol_beta);
+}
+
+// Levenberg-Marquardt step for 3 parameters: (J^T J + lam diag) d = -J^T r.
+void lm_step(const double *J, const double *r, int m, double lam, double *d) {
+  double A[3][3] = {{0}}, g[3] = {0, 0, 0};
+  for (int i = 0; i < m; ++i)
+    for (int p = 0; p < 3; ++p) {
+      g[p] += J[i * 3 + p] * r[i];
+      for (int q = 0; q < 3; ++q) A[p][q] += J[i * 3 + p] * J[i * 3 + q];
+    }
+  for (int p = 0; p < 3; ++p) A[p][p] += lam * A[p][p] + 1e-12;
+  // Gaussian elimination with partial pivoting on [A | -g]
+  double M[3][4];
+  for (int p = 0; p < 3; ++p) {
+    for (int q = 0; q < 3; ++q) M[p][q] = A[p][q];
+    M[p][3] = -g[p];
+  }
+  for (int c = 0; c < 3; ++c) {
+    int piv = c;
+    for (int rr = c + 1; rr < 3; ++rr)
+      if (std::fabs(M[rr][c]) > std::fabs(M[piv][c])) piv = rr;
+    for (int q = 0; q < 4; ++q) std::swap(M[c][q], M[piv][q]);
+    for (int rr = c + 1; rr < 3; ++rr) {
+      const double f = M[rr][c] / M[c][c];
+      for (int q = c; q < 4; ++q) M[rr][q] -= f * M[c][q];
+    }
+  }
+  for (int c = 2; c >= 0; --c) {
+    double s = M[c][3];
+    for (int q = c + 1; q < 3; ++q) s -= M[c][q] * d[q];
+    d[c] = s / M[c][c];
+  }
+}
+
+// Applies a clamped step; returns its largest component.
+double apply_step(mk_fgpa_nodes &nd, int zb, const double *d) {
+  const double lim[3] = {1.0, 0.4, 0.4};
+  double s = 1.0;
+  for (int p = 0; p < 3; ++p)
+    if (std::fabs(d[p]) > lim[p]) s = std::min(s, lim[p] / std::fabs(d[p]));
+  nd.ln_a[zb] += s * d[0];
+  nd.b[zb] += s * d[1];
+  nd.c[zb] += s * d[2];
+  return s * std::max(std::fabs(d[0]), std::max(std::fabs(d[1]), std::fabs(d[2])));
+}
+
+constexpr double kSurrogateStop = 1e-4;  // surrogate-only fits stop below this step
+
+// Nodes of bins without data follow the nearest tuned node (ties: the lower).
+void fill_inactive(mk_fgpa_nodes &nd, const TuneState &S) {
+  const int nz = S.bins->n_z;
+  for (int i = 0; i < nz; ++i) {
+    if (S.active(i)) continue;
+    int best = -1;
+    for (int j = 0; j < nz; ++j)
+      if (S.active(j) && (best < 0 || std::abs(j - i) < std::abs(best - i))) best = j;
+    if (best < 0) return;
+    nd.ln_a[i] = nd.ln_a[best];
+    nd.b[i] = nd.b[best];
+    nd.c[i] = nd.c[best];
+  }
+}
+
+void shift(mk_fgpa_nodes &nd, int p, double h) {
+  for (int i = 0; i < nd.count; ++i) {
+    if (p == 0) nd.ln_a[i] += h;
+    if (p == 1) nd.b[i] += h;
+    if (p == 2) nd.c[i] += h;
+  }
+}
+
+// Surrogate predictions at `rows` inputs (z, ln a, b, c): host in, host out.
+struct Surrogate {
+  mk_mlp *mlp;
+  const mk_surrogate_norm *norm;
+  float *dx = nullptr, *dy = nullptr;
+  int cap = 0;
+  int eval(TuneState &S, const std::vector<double> &x, std::vector<double> &t) {
+    const int n = static_cast<int>(x.size() / 4);
+    cudaStream_t st = mkhost::ctx_stream(S.ctx);
+    if (n > cap) {
+      cudaFree(dx);
+      cudaFree(dy);
+      dx = dy = nullptr;
+      if (cudaMalloc(&dx, sizeof(float) * 4 * n) != cudaSuccess || cudaMalloc(&dy, sizeof(float) * 35 * n) != cudaSuccess)
+        return mfail(S.ctx, MK_ENOMEM, "surrogate inference buffers");
+      cap = n;
+    }
+    std::vector<float> xs(4 * n), ys(35 * n);
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 4; ++c) xs[4 * i + c] = static_cast<float>((x[4 * i + c] - norm->x_mean[c]) / norm->x_std[c]);
+    cudaEventRecord(S.e0, st);
+    CKM(S.ctx, cudaMemcpyAsync(dx, xs.data(), sizeof(float) * xs.size(), cudaMemcpyHostToDevice, st));
+    int rc = mk_mlp_forward(mlp, dx, n, dy);
+    if (rc) return rc;
+    CKM(S.ctx, cudaMemcpyAsync(ys.data(), dy, sizeof(float) * ys.size(), cudaMemcpyDeviceToHost, st));
+    cudaEventRecord(S.e1, st);
+    CKM(S.ctx, cudaEventSynchronize(S.e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, S.e0, S.e1);
+    S.rep->gpu_ms += ms;
+    t.resize(35 * static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i)
+      for (int c = 0; c < 35; ++c) t[35 * i + c] = ys[35 * i + c] * norm->t_std[c] + norm->t_mean[c];
+    return MK_OK;
+  }
+  // residuals and finite-difference Jacobians of all active nodes at nd
+  int model(TuneState &S, const mk_fgpa_nodes &nd, std::vector<double> &r, std::vector<double> &J) {
+    const double h[3] = {0.02, 0.02, 0.02};
+    const int nz = S.bins->n_z, m = S.m();
+    std::vector<double> x(static_cast<size_t>(nz) * 4 * 4), t;
+    for (int zb = 0; zb < nz; ++zb)
+      for (int v = 0; v < 4; ++v) {
+        double *xi = &x[(static_cast<size_t>(zb) * 4 + v) * 4];
+        xi[0] = nd.z[zb];
+        xi[1] = nd.ln_a[zb] + (v == 1 ? h[0] : 0.0);
+        xi[2] = nd.b[zb] + (v == 2 ? h[1] : 0.0);
+        xi[3] = nd.c[zb] + (v == 3 ? h[2] : 0.0);
+      }
+    int rc = eval(S, x, t);
+    if (rc) return rc;
+    r.assign(static_cast<size_t>(nz) * m, 0.0);
+    J.assign(static_cast<size_t>(nz) * m * 3, 0.0);
+    std::vector<double> rv(m);
+    for (int zb = 0; zb < nz; ++zb) {
+      if (!S.active(zb)) continue;
+      for (int v = 0; v < 4; ++v) {
+        const double *ti = &t[(static_cast<size_t>(zb) * 4 + v) * 35];
+        double *dst = (v == 0) ? &r[static_cast<size_t>(zb) * m] : rv.data();
+        residual(S, zb, ti[0], ti[2], ti + 3, dst);  // ti[3 + k] = ln P1D of k bin k
+        if (v > 0)
+          for (int i = 0; i < m; ++i)
+            J[(static_cast<size_t>(zb) * m + i) * 3 + (v - 1)] = (rv[i] - r[static_cast<size_t>(zb) * m + i]) / h[v - 1];
+      }
+    }
+    return MK_OK;
+  }
+  ~Surrogate() {
+    cudaFree(dx);
+    cudaFree(dy);
+  }
+};
+
+}  // namespace
+
+extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+                       const int64_t *d_offsets, const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
+                       const mk_tune_target *target, int32_t method, mk_mlp *surrogate,
+                       const mk_surrogate_norm *norm, int32_t max_passes, mk_fgpa_nodes *inout,
+                       mk_tune_report *report) {
+  if (!ctx) return MK_EINVAL;
+  if (!bins || !target || !inout || !report || max_passes < 1)
+    return mfail(ctx, MK_EINVAL, "mk_tune needs bins, a target, nodes, a report and max_passes >= 1");
+  if (inout->count != bins->n_z) return mfail(ctx, MK_EINVAL, "one node per z bin is required");
+  for (int i = 0; i < bins->n_z; ++i)
+    if (std::fabs(inout->z[i] - (bins->z_lo + (i + 0.5) * bins->dz)) > 1e-9)
+      return mfail(ctx, MK_EINVAL, "nodes must sit at the z bin centres");
+  if (target->k_lo < 0 || target->k_hi > bins->n_k || target->k_hi <= target->k_lo)
+    return mfail(ctx, MK_EINVAL, "bad k range");
+  if (!(target->tol_mean_flux > 0) || !(target->tol_p1d > 0) || (target->use_beta && !(target->tol_beta > 0)))
+    return mfail(ctx, MK_EINVAL, "tolerances must be > 0");
+  for (int zb = 0; zb < bins->n_z; ++zb) {
+    if (!((target->active >> zb) & 1u)) continue;
+    for (int k = target->k_lo; k < target->k_hi; ++k)
+      if (!(target->p1d[zb][k] > 0)) return mfail(ctx, MK_EINVAL, "P1D targets must be > 0");
+  }
+  if (method == MK_TUNE_SURROGATE && (!surrogate || !norm || bins->n_k != 32))
+    return mfail(ctx, MK_EINVAL, "surrogate tuning needs a fitted surrogate, its norm and 32 k bins");
+  if (method != MK_TUNE_PLAIN && method != MK_TUNE_SURROGATE) return mfail(ctx, MK_EINVAL, "unknown method");
+  std::memset(report, 0, sizeof(*report));
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  TuneState S{ctx, params, d_sk, n_sk, d_offsets, d_delta, d_eta, bins, target, report, nullptr, nullptr};
+  CKM(ctx, cudaEventCreate(&S.e0));
+  CKM(ctx, cudaEventCreate(&S.e1));
+  const auto t0 = std::chrono::steady_clock::now();
+  const int m = S.m(), nz = bins->n_z;
+  mk_fgpa_nodes nd = *inout;
+  fill_inactive(nd, S);
+  mk_stats_out st;
+  std::vector<double> r, J, rp;
+  int rc = MK_OK;
+  if (method == MK_TUNE_PLAIN) {
+    const double h[3] = {0.05, 0.05, 0.05};
+    while (rc == MK_OK && report->passes < max_passes) {
+      if ((rc = full_pass(S, nd, st, r))) break;
+      if (converged(S, st)) {
+        report->converged = 1;
+        break;
+      }
+      if (report->passes + 4 > max_passes) break;
+      J.assign(static_cast<size_t>(nz) * m * 3, 0.0);
+      for (int p = 0; p < 3 && rc == MK_OK; ++p) {
+        mk_fgpa_nodes q = nd;
+        shift(q, p, h[p]);
+        mk_stats_out sq;
+        if ((rc = full_pass(S, q, sq, rp))) break;
+        for (int zb = 0; zb < nz; ++zb)
+          for (int i = 0; i < m; ++i)
+            J[(static_cast<size_t>(zb) * m + i) * 3 + p] = (rp[static_cast<size_t>(zb) * m + i] - r[static_cast<size_t>(zb) * m + i]) / h[p];
+      }
+      if (rc) break;
+      for (int zb = 0; zb < nz; ++zb) {
+        if (!S.active(zb)) continue;
+        double d[3];
+        lm_step(&J[static_cast<size_t>(zb) * m * 3], &r[static_cast<size_t>(zb) * m], m, 1e-3, d);
+        (void)apply_step(nd, zb, d);
+      }
+      fill_inactive(nd, S);
+      report->iterations += 1;
+    }
+  } else {
+    Surrogate sg{surrogate, norm};
+    // fit the target on the surrogate alone
+    for (int it = 0; it < 25 && rc == MK_OK; ++it) {
+      if ((rc = sg.model(S, nd, r, J))) break;
+      double big = 0.0;
+      for (int zb = 0; zb < nz; ++zb) {
+        if (!S.active(zb)) continue;
+        double d[3];
+        lm_step(&J[static_cast<size_t>(zb) * m * 3], &r[static_cast<size_t>(zb) * m], m, 1e-2, d);
+        big = std::max(big, apply_step(nd, zb, d));
+      }
+      fill_inactive(nd, S);
+      if (big < kSurrogateStop) break;
+    }
+    // verify on full passes; between passes re-solve on the surrogate with the
+    // last pass's discrepancy (true minus predicted residual) as an offset
+    while (rc == MK_OK && report->passes < max_passes) {
+      std::vector<double> rt;
+      if ((rc = full_pass(S, nd, st, rt))) break;
+      if (converged(S, st)) {
+        report->converged = 1;
+        break;
+      }
+      if (report->passes >= max_passes) break;
+      std::vector<double> rs, off;
+      if ((rc = sg.model(S, nd, rs, J))) break;
+      off.resize(rs.size());
+      for (size_t i = 0; i < rs.size(); ++i) off[i] = rt[i] - rs[i];
+      for (int it = 0; it < 12 && rc == MK_OK; ++it) {
+        if (it > 0 && (rc = sg.model(S, nd, rs, J))) break;
+        double big = 0.0;
+        for (int zb = 0; zb < nz; ++zb) {
+          if (!S.active(zb)) continue;
+          std::vector<double> rr(m);
+          for (int i = 0; i < m; ++i) rr[i] = rs[static_cast<size_t>(zb) * m + i] + off[static_cast<size_t>(zb) * m + i];
+          double d[3];
+          lm_step(&J[static_cast<size_t>(zb) * m * 3], rr.data(), m, 1e-2, d);
+          big = std::max(big, apply_step(nd, zb, d));
+        }
+        fill_inactive(nd, S);
+        if (big < kSurrogateStop) break;
+      }
+      report->iterations += 1;
+    }
+  }
+  report->wall_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  cudaEventDestroy(S.e0);
+  cudaEventDestroy(S.e1);
+  if (rc) return rc;
+  *inout = nd;
+  return MK_OK;
+}

@@ -103,6 +103,27 @@ def test_split_statistics_match_oracle(ctx, tiny):
     np.testing.assert_array_equal(st2["p1d_sum"], st["p1d_sum"])
 
 
+def test_tuning_pass_matches_oracle_and_split_path(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    st = ctx.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+    assert_stats_close(st, tiny["st"])
+    f, off = ctx.flux(w, r["sk"], n, r["delta"], r["eta"])
+    st2 = ctx.stats(w, r["sk"], n, off, f, delta=r["delta"], eta=r["eta"])
+    for k in ("sums", "p1d_sum", "n_seg"):
+        np.testing.assert_array_equal(st[k], st2[k])
+    # other FGPA parameters on the same stored fields
+    w2 = dict(w)
+    w2["node_b"] = [1.2 + 0.05 * i for i in range(len(w["node_z"]))]
+    w2["node_c"] = [0.7] * len(w["node_z"])
+    o2 = oracle.run_skewers(w2, tiny["d"], tiny["e"], tiny["pos"], tiny["ids"], n_threads=16)
+    so2 = oracle.stats(w2, o2["j_lo"], o2["offsets"], o2["offsets_out"], o2["flux"], o2["delta"], o2["eta"])
+    st3 = ctx.flux_stats(w2, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+    assert_stats_close(st3, so2)
+
+
 def test_fused_path_matches_split_path_and_oracle(ctx, tiny):
     w, dv = tiny["w"], tiny["dev"]
     box = ctx.load_box(w, dv["d"], dv["e"])
