@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
 
 // =================================================================== statistics kernel
 template <int N>
-__global__ void __launch_bounds__(256) k_stats(StatParams P) {
+__global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
   constexpr int T = N / 8;
   constexpr int BUF = TeamSmem<N>::BUF;
   const int teams = blockDim.x / T;
@@ -211,31 +211,61 @@ __global__ void __launch_bounds__(256) k_stats(StatParams P) {
     float a0[MK_NSUM], a1[MK_NSUM];
 #pragma unroll
     for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
+    if (R == 1) {
+      // streaming case: issue every load of the thread's 8 pixels before any use
+      float dv[8], ev[8], fv[8];
+      float4 tb[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int p = t + T * q;
+        const bool ok = p < npx;
+        const int64_t kk = k0 + (ok ? p : 0);
+        dv[q] = (ok && P.delta) ? __ldg(P.delta + sk.offset + kk) : 0.f;
+        ev[q] = (ok && P.delta) ? __ldg(P.eta + sk.offset + kk) : 0.f;
+        if (P.pixtab) {
+          tb[q] = __ldg(P.pixtab + sk.j_lo + kk);
+          fv[q] = 0.f;
+        } else {
+          fv[q] = ok ? __ldg(P.flux + o + kk) : 0.f;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int p = t + T * q;
+        float f = 0.f;
+        if (p < npx) {
+          f = P.pixtab ? fgpa(tb[q], dv[q], ev[q]) : fv[q];
+          const int zb = (zf == zl) ? zf : __ldg(P.zbin + sk.j_lo + k0 + p);
+          if (zb == zf) add_pixel(a0, f, dv[q], ev[q]);
+          else if (zb == zf + 1) add_pixel(a1, f, dv[q], ev[q]);
+          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dv[q], ev[q]);
+        }
+        fb[swf(p)] = f;
+      }
+    } else {
 #pragma unroll 2
-    for (int q = 0; q < 8; ++q) {
-      const int p = t + T * q;
-      float f = 0.f;
-      if (p < npx) {
-        const int64_t kk = k0 + p;
-        float ds = 0.f, es = 0.f;
-        if (P.delta) {
-          for (int r = 0; r < R; ++r) {
-            ds += P.delta[sk.offset + kk * R + r];
-            es += P.eta[sk.offset + kk * R + r];
-          }
-          if (R > 1) {
+      for (int q = 0; q < 8; ++q) {
+        const int p = t + T * q;
+        float f = 0.f;
+        if (p < npx) {
+          const int64_t kk = k0 + p;
+          float ds = 0.f, es = 0.f;
+          if (P.delta) {
+            for (int r = 0; r < R; ++r) {
+              ds += P.delta[sk.offset + kk * R + r];
+              es += P.eta[sk.offset + kk * R + r];
+            }
             ds /= static_cast<float>(R);
             es /= static_cast<float>(R);
           }
+          f = P.flux[o + kk];
+          const int zb = zbin_of(kk);
+          if (zb == zf) add_pixel(a0, f, ds, es);
+          else if (zb == zf + 1) add_pixel(a1, f, ds, es);
+          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, ds, es);
         }
-        // flux: stored, or (tuning pass, rebin 1) the FGPA of the stored fields
-        f = P.pixtab ? fgpa(__ldg(P.pixtab + sk.j_lo + kk), ds, es) : P.flux[o + kk];
-        const int zb = zbin_of(kk);
-        if (zb == zf) add_pixel(a0, f, ds, es);
-        else if (zb == zf + 1) add_pixel(a1, f, ds, es);
-        else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, ds, es);
+        fb[swf(p)] = f;
       }
-      fb[swf(p)] = f;
     }
     flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
     if (npx == N) {
