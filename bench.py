@@ -175,10 +175,11 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- tuning A/B
-def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs):
+def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source):
     """Plain vs surrogate tuning of ln a, b, c at the 12 z nodes on the stored
     skewers of the benchmark catalogue; the surrogate is trained on
-    constant-parameter passes over a 512^3 box with 100k quasars."""
+    constant-parameter passes over 100k quasars: the first 100k of the same
+    catalogue ("subset") or a separate 512^3 box ("box512")."""
     import torch
     from paper_2310_18996_gb300 import tuning
 
@@ -187,16 +188,21 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs):
     nd0 = tuning.start_nodes(w)
     nd_p, rep_p = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
                           method=mk.TUNE_PLAIN, max_passes=200)
-    # surrogate training set: 512^3 box, 100k quasars, same recipe and binning
-    ws = si.shrink(w, n=512, n_q=100_000)
-    ws["seed_box"], ws["seed_cat"] = w["seed_box"] + 1, w["seed_cat"] + 1
-    d, e = si.gaussian_box(ws["n"], ws["cell"], ws["seed_box"], backend="torch", device=dev)
-    pos, ids = si.catalogue(ws)
-    bs = ctx.load_box(ws, ctx.pack_box(d, e), None)
-    del d, e
-    rs = ctx.make_skewers(bs, mk.catalogue_tensor(pos, ids, dev), len(ids), ws)
+    # surrogate training set: constant-parameter passes over 100k quasars
+    if source == "subset":   # the first 100k stored skewers of the same box
+        ws, n_lab = w, 100_000
+        rs = {"sk": r["sk"], "offsets": r["offsets"], "delta": r["delta"], "eta": r["eta"]}
+    else:                    # a separate 512^3 box, same recipe and binning
+        ws = si.shrink(w, n=512, n_q=100_000)
+        ws["seed_box"], ws["seed_cat"] = w["seed_box"] + 1, w["seed_cat"] + 1
+        d, e = si.gaussian_box(ws["n"], ws["cell"], ws["seed_box"], backend="torch", device=dev)
+        pos, ids = si.catalogue(ws)
+        bs = ctx.load_box(ws, ctx.pack_box(d, e), None)
+        del d, e
+        rs = ctx.make_skewers(bs, mk.catalogue_tensor(pos, ids, dev), len(ids), ws)
+        n_lab = len(ids)
     t0 = time.perf_counter()
-    hx, ht = mk.surrogate_labels(ctx, ws, rs["sk"], len(ids), rs["offsets"], rs["delta"], rs["eta"],
+    hx, ht = mk.surrogate_labels(ctx, ws, rs["sk"], n_lab, rs["offsets"], rs["delta"], rs["eta"],
                                  n_draws=draws, seed=11)
     t_lab = time.perf_counter() - t0
     mlp = mk.Mlp(ctx, max_batch=1024, seed=3)
@@ -217,7 +223,8 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs):
                         "Fbar = exp(-0.0025 (1+z)^3.7) +- 1e-3, P1D and beta_F of seeded hidden power laws +- 2%",
             "plain": rep(rep_p), "surrogate": rep(rep_s),
             "gpu_time_ratio_plain_over_surrogate": rep_p.gpu_ms / max(rep_s.gpu_ms, 1e-9),
-            "surrogate_training": {"box": "512^3", "quasars": 100_000, "draws": draws, "samples": int(hx.shape[0]),
+            "surrogate_training": {"source": source, "box": "1024^3" if source == "subset" else "512^3",
+                                   "quasars": 100_000, "draws": draws, "samples": int(hx.shape[0]),
                                    "label_s": t_lab, "fit_s": t_fit, "epochs": epochs,
                                    "final_loss": float(losses[-1]) if len(losses) else None}}
 
@@ -325,7 +332,8 @@ def run_gb300(args, rank, world, local_rank):
     achieved = alg / (kms / 1000.0) / 1e9
     tune = None
     if rank == 0 and world == 1 and not args.no_tuning:
-        tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs)
+        tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs,
+                         args.surrogate_source)
     cpu = None
     if want_cpu:
         rate, px, n, dt = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds, os.cpu_count() or 1)
@@ -377,6 +385,7 @@ def main():
     ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--surrogate-draws", type=int, default=4000)
     ap.add_argument("--surrogate-epochs", type=int, default=200)
+    ap.add_argument("--surrogate-source", default="subset", choices=["subset", "box512"])
     ap.add_argument("--box-n", type=int, default=None, help="smaller box (profiling runs)")
     ap.add_argument("--n-q", type=int, default=None, help="fewer quasars (profiling runs)")
     args = ap.parse_args()

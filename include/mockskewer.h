@@ -411,7 +411,8 @@ typedef struct mk_tune_report {
    MK_TUNE_SURROGATE: the parameters are first fitted to the target on the
    surrogate alone; every later iteration is one verifying pass, after which
    the fit is redone on the surrogate shifted by that pass's discrepancy
-   (true minus predicted residual).  Nodes of inactive
+   (true minus predicted residual) plus a linear term in the parameter change
+   whose slope is Broyden-updated from successive passes.  Nodes of inactive
    bins follow the nearest active node (ties: the lower one).  Stops when a
    pass meets the tolerances or after max_passes passes.  Synchronous. */
 int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,

@@ -619,7 +619,10 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       if (big < kSurrogateStop) break;
     }
     // verify on full passes; between passes re-solve on the surrogate with the
-    // last pass's discrepancy (true minus predicted residual) as an offset
+    // last pass's discrepancy (true minus predicted residual) as an offset,
+    // plus a per-node linear term E (theta - theta_i) for how the discrepancy
+    // changes with the parameters (Broyden updates from successive passes)
+    std::vector<double> E(static_cast<size_t>(nz) * m * 3, 0.0), prev_off, prev_theta;
     while (rc == MK_OK && report->passes < max_passes) {
       std::vector<double> rt;
       if ((rc = full_pass(S, nd, st, rt))) break;
@@ -632,15 +635,50 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       if ((rc = sg.model(S, nd, rs, J))) break;
       off.resize(rs.size());
       for (size_t i = 0; i < rs.size(); ++i) off[i] = rt[i] - rs[i];
+      std::vector<double> theta(static_cast<size_t>(nz) * 3);
+      for (int zb = 0; zb < nz; ++zb) {
+        theta[3 * zb] = nd.ln_a[zb];
+        theta[3 * zb + 1] = nd.b[zb];
+        theta[3 * zb + 2] = nd.c[zb];
+      }
+      if (!prev_off.empty()) {
+        for (int zb = 0; zb < nz; ++zb) {
+          if (!S.active(zb)) continue;
+          double dth[3], nn = 0.0;
+          for (int p = 0; p < 3; ++p) {
+            dth[p] = theta[3 * zb + p] - prev_theta[3 * zb + p];
+            nn += dth[p] * dth[p];
+          }
+          if (nn < 1e-14) continue;
+          for (int i = 0; i < m; ++i) {
+            const size_t row = static_cast<size_t>(zb) * m + i;
+            double pred = 0.0;
+            for (int p = 0; p < 3; ++p) pred += E[row * 3 + p] * dth[p];
+            const double u = (off[row] - prev_off[row]) - pred;
+            for (int p = 0; p < 3; ++p) E[row * 3 + p] += u * dth[p] / nn;
+          }
+        }
+      }
+      prev_off = off;
+      prev_theta = theta;
       for (int it = 0; it < 12 && rc == MK_OK; ++it) {
         if (it > 0 && (rc = sg.model(S, nd, rs, J))) break;
         double big = 0.0;
         for (int zb = 0; zb < nz; ++zb) {
           if (!S.active(zb)) continue;
-          std::vector<double> rr(m);
-          for (int i = 0; i < m; ++i) rr[i] = rs[static_cast<size_t>(zb) * m + i] + off[static_cast<size_t>(zb) * m + i];
+          std::vector<double> rr(m), JJ(static_cast<size_t>(m) * 3);
+          const double cur[3] = {nd.ln_a[zb], nd.b[zb], nd.c[zb]};
+          for (int i = 0; i < m; ++i) {
+            const size_t row = static_cast<size_t>(zb) * m + i;
+            double lin = 0.0;
+            for (int p = 0; p < 3; ++p) {
+              lin += E[row * 3 + p] * (cur[p] - theta[3 * zb + p]);
+              JJ[i * 3 + p] = J[row * 3 + p] + E[row * 3 + p];
+            }
+            rr[i] = rs[row] + off[row] + lin;
+          }
           double d[3];
-          lm_step(&J[static_cast<size_t>(zb) * m * 3], rr.data(), m, 1e-2, d);
+          lm_step(JJ.data(), rr.data(), m, 1e-2, d);
           big = std::max(big, apply_step(nd, zb, d));
         }
         fill_inactive(nd, S);
