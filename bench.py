@@ -100,6 +100,25 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def profiled_traffic(total_px):
+    """DRAM bytes per fused-kernel launch from the committed ncu record, scaled
+    by pixels, or None when the kernel sources changed since it was taken."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "k_skewer_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    if h.hexdigest() != rec["sha256"]:
+        return None
+    return rec["dram_bytes_per_pixel"] * total_px
+
+
 def algorithmic_bytes(pos, npix, w):
     """Bytes a launch must move: each skewer's distinct trilinear voxels (8 B,
     interleaved), its flux (4 B/pixel), catalogue and record traffic."""
@@ -129,14 +148,31 @@ def oracle_rate(w, dh, eh, pos, ids, target_s, threads):
     return px / dt, px, n, dt
 
 
-def make_inputs(w, rank, device, box_n=None, n_q=None):
+def rank_catalogue(w, rank):
+    """Rank `rank`'s own quasars: a catalogue seed of its own and ids offset by
+    rank * n_q, so that ranks synthesise disjoint sets of skewers (weak scaling)
+    on identical box replicas."""
+    w = dict(w)
+    w["seed_cat"] = w["seed_cat"] + 7919 * rank
+    pos, ids = si.catalogue(w)
+    return w, pos, ids + np.uint64(rank * w["n_q"])
+
+
+def max_over_ranks(values, dist, device):
+    """Elementwise maximum of per-rank timings (identity without a process group)."""
+    if dist is None:
+        return list(values)
     import torch
 
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def make_inputs(w, rank, device, box_n=None, n_q=None):
     w = si.shrink(w, n=box_n, n_q=n_q)
-    w["seed_cat"] = w["seed_cat"] + 7919 * rank
+    w, pos, ids = rank_catalogue(w, rank)
     d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"], backend="torch", device=device)
-    pos, ids = si.catalogue(w)
-    ids = ids + np.uint64(rank * w["n_q"])
     return w, d, e, pos, ids
 
 
@@ -299,10 +335,7 @@ def run_gb300(args, rank, world, local_rank):
     if dist:
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    if dist:
-        t = torch.tensor([ms, kms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, kms = t.tolist()
+    ms, kms = max_over_ranks([ms, kms], dist, dev)
     value = world * total / (ms / 1000.0)
 
     # end to end through the public API with host buffers: catalogue H2D from
@@ -322,10 +355,7 @@ def run_gb300(args, rank, world, local_rank):
         host_flux.copy_(flux, non_blocking=True)
         torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1000.0 / e2e_steps if e2e_steps else float("nan")
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    (e2e_ms,) = max_over_ranks([e2e_ms], dist, dev)
 
     peak, peak_kind = measured_peaks()
     alg = algorithmic_bytes(pos, npix, w)
@@ -351,7 +381,7 @@ def run_gb300(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (8.6 GB box)",
                        "outputs": "flux stored + FP64 statistics"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": profiled_traffic(total), "peak_kind": peak_kind,
                          "kernel": f"k_skewer<256,interleaved> {threads} threads/CTA, occupancy "
                                    f"target {occ}{' (autotuned)' if tuned else ''}", "kernel_ms": kms,
                          "algorithmic_bytes": alg},
