@@ -121,7 +121,7 @@ def profiled_traffic(total_px):
 
 def algorithmic_bytes(pos, npix, w):
     """Bytes a launch must move: each skewer's distinct trilinear voxels (8 B,
-    interleaved), its flux (4 B/pixel), catalogue and record traffic."""
+    a (delta, eta) pair), its flux (4 B/pixel), catalogue and record traffic."""
     u = np.abs(pos / np.linalg.norm(pos, axis=1, keepdims=True))
     vox = 4.0 * w["dr"] * u.sum(axis=1) / w["cell"] * npix + 8.0 * (npix > 0)
     per_skewer = 32 + 72 + 72 + 16  # catalogue read, record write + read, offsets
@@ -233,7 +233,7 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source):
         ws["seed_box"], ws["seed_cat"] = w["seed_box"] + 1, w["seed_cat"] + 1
         d, e = si.gaussian_box(ws["n"], ws["cell"], ws["seed_box"], backend="torch", device=dev)
         pos, ids = si.catalogue(ws)
-        bs = ctx.load_box(ws, ctx.pack_box(d, e), None)
+        bs = ctx.load_box(ws, ctx.pack_box(d, e, padded=True), None, layout=mk.BOX_PADDED)
         del d, e
         rs = ctx.make_skewers(bs, mk.catalogue_tensor(pos, ids, dev), len(ids), ws)
         n_lab = len(ids)
@@ -284,11 +284,11 @@ def run_gb300(args, rank, world, local_rank):
     if want_cpu:
         dh, eh = d.cpu().numpy(), e.cpu().numpy()
     ctx = mk.Context(local_rank)
-    packed = ctx.pack_box(d, e)
+    packed = ctx.pack_box(d, e, padded=True)
     torch.cuda.synchronize()
     del d, e
     torch.cuda.empty_cache()
-    box = ctx.load_box(w, packed, None)
+    box = ctx.load_box(w, packed, None, layout=mk.BOX_PADDED)
     n_q = len(ids)
     rec_np = np.zeros(n_q, dtype=mk.QSO_DTYPE)
     rec_np["pos"] = pos
@@ -310,7 +310,7 @@ def run_gb300(args, rank, world, local_rank):
     step(mk.AUTOTUNE)
     for _ in range(args.warmup):
         step()
-    threads, occ, tuned = ctx.launch_config(w["n_fft"], flags=flags)
+    threads, occ, tuned = ctx.launch_config(w["n_fft"], flags=flags, layout=mk.BOX_PADDED)
     # kernel-only time of the fused kernel (direct launches, CUDA events on the stream)
     ctx.set_timing(True)
     kern = []
@@ -375,14 +375,14 @@ def run_gb300(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{w['n']}^3 box (delta+eta FP32, interleaved), {n_q} quasars "
+            "config": {"workload": f"{w['n']}^3 box (delta+eta FP32 pairs, periodic ghost layer), {n_q} quasars "
                                    "z 2.04-4.0, 200-1500 px skewers, N_fft 256, fused persistent launch",
                        "pixels_per_step_per_gpu": int(total), "skewers_per_gpu": n_q,
                        "l2": "inputs larger than L2 (8.6 GB box)",
                        "outputs": "flux stored + FP64 statistics"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(total), "peak_kind": peak_kind,
-                         "kernel": f"k_skewer<256,interleaved> {threads} threads/CTA, occupancy "
+                         "kernel": f"k_skewer<256,padded> {threads} threads/CTA, occupancy "
                                    f"target {occ}{' (autotuned)' if tuned else ''}", "kernel_ms": kms,
                          "algorithmic_bytes": alg},
             "e2e": {"value": world * total / (e2e_ms / 1000.0), "unit": UNIT,

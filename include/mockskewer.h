@@ -65,6 +65,8 @@ extern "C" {
 
 #define MK_BOX_PLANAR 0      /* two FP32 arrays, delta and eta, index x + n (y + n z) */
 #define MK_BOX_INTERLEAVED 1 /* one FP32 array of (delta, eta) pairs, same index order */
+#define MK_BOX_PADDED 2      /* (delta, eta) pairs on (n+1)^3 points, index x + (n+1) (y + (n+1) z);
+                                plane, row and column n repeat index 0 (periodic ghost layer) */
 
 /* mk_run flags */
 #define MK_STORE_FIELDS 1u /* write delta_tot and eta (pre-FGPA skewers) */
@@ -87,7 +89,7 @@ typedef struct mk_cosmo {
 /* Box of n^3 cubic cells (n a power of two, 2..2048), periodic. */
 typedef struct mk_box_desc {
   int32_t n;
-  int32_t layout;   /* MK_BOX_PLANAR or MK_BOX_INTERLEAVED */
+  int32_t layout;   /* MK_BOX_PLANAR, MK_BOX_INTERLEAVED or MK_BOX_PADDED */
   double cell;      /* cell side [Mpc/h] */
   double origin[3]; /* corner of the box in the observer frame [Mpc/h] */
 } mk_box_desc;
@@ -192,6 +194,14 @@ void mk_free_box(mk_box *box);
 /* Interleave two planar boxes into d_out (2 n_voxels floats, caller-owned). */
 int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float *d_eta,
                 float *d_out);
+
+/* Pack two planar n^3 boxes into the MK_BOX_PADDED layout: d_out (caller-owned,
+   8-byte aligned) receives 2 (n+1)^3 floats.  The paper stores plain periodic
+   boxes (Sec. 2.1); the ghost layer is a storage choice of this library, so
+   that the fused kernel reads the 8 corners of a cell at fixed offsets.
+   Asynchronous on the context stream.  MK_EINVAL for n outside [2, 2048] or
+   not a power of two, or NULL pointers. */
+int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out);
 
 /* ---------------------------------------------------------------- skewers */
 

@@ -21,11 +21,11 @@ from . import build as _build
 MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
 MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
 STATIC_MAX_SKEWERS = 131072
-BOX_PLANAR, BOX_INTERLEAVED = 0, 1
+BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED = 0, 1, 2
 STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
-           "mk_free_box", "mk_pack_box", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
+           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune"]
@@ -128,6 +128,7 @@ def lib():
                 "mk_load_box": (C.c_int, [vp, P(vp), P(BoxDesc), vp, vp]),
                 "mk_free_box": (None, [vp]),
                 "mk_pack_box": (C.c_int, [vp, i64, vp, vp, vp]),
+                "mk_pack_box_padded": (C.c_int, [vp, i32, vp, vp, vp]),
                 "mk_make_skewers": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), vp, vp, vp, vp,
                                               i64, P(i64)]),
                 "mk_flux": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, P(FgpaNodes), i32, vp,
@@ -299,9 +300,17 @@ class Context:
         self._check(lib().mk_load_box(self.h, C.byref(h), C.byref(desc), _ptr(delta), _ptr(eta)))
         return Box(self, h, desc, (delta, eta))
 
-    def pack_box(self, delta, eta):
-        out = self._torch.empty(delta.numel() * 2, dtype=self._torch.float32, device=delta.device)
+    def pack_box(self, delta, eta, padded=False):
+        """Interleaved (delta, eta) pairs; padded=True: the MK_BOX_PADDED layout
+        ((n+1)^3 pairs with a periodic ghost layer), for load_box(..., layout=BOX_PADDED)."""
+        torch = self._torch
         self._stream()
+        if padded:
+            n = round(delta.numel() ** (1.0 / 3.0))
+            out = torch.empty(2 * (n + 1) ** 3, dtype=torch.float32, device=delta.device)
+            self._check(lib().mk_pack_box_padded(self.h, n, _ptr(delta), _ptr(eta), _ptr(out)))
+            return out
+        out = torch.empty(delta.numel() * 2, dtype=torch.float32, device=delta.device)
         self._check(lib().mk_pack_box(self.h, delta.numel(), _ptr(delta), _ptr(eta), _ptr(out)))
         return out
 

@@ -155,6 +155,7 @@ struct mk_ctx {
   float *d_gpix = nullptr;
   float4 *d_pixtab = nullptr;
   int16_t *d_zbin = nullptr, *d_segzbin = nullptr;
+  int32_t *d_bin_end = nullptr;  // MK_MAX_ZBINS + 2 entries
   bool pixtab_valid = false;
   mk_fgpa_nodes nodes_key{};
   bool zbin_valid = false;
@@ -355,8 +356,13 @@ int ensure_pixtab(mk_ctx *ctx, const mk_fgpa_nodes *nd) {
 
 int ensure_zbin(mk_ctx *ctx, const mk_stat_bins *b) {
   if (ctx->zbin_valid && std::memcmp(&ctx->bins_key, b, sizeof(*b)) == 0) return MK_OK;
+  if (!ctx->d_bin_end) {
+    ++ctx->generation;
+    CK(cudaMalloc(&ctx->d_bin_end, sizeof(int32_t) * (MK_MAX_ZBINS + 2)));
+  }
   CK(launch_zbin(ctx->d_zpix, ctx->d_cumz, ctx->j_max, b->z_lo, b->dz, b->n_z, b->n_fft, ctx->d_zbin,
                  ctx->d_segzbin, ctx->stream));
+  CK(launch_bin_end(ctx->d_zbin, ctx->j_max, b->n_z, ctx->d_bin_end, ctx->stream));
   ctx->bins_key = *b;
   ctx->zbin_valid = true;
   return MK_OK;
@@ -460,6 +466,7 @@ SkewerParams skewer_params(mk_ctx *ctx, const mk_box *box, const mk_skewer *d_sk
   S.seed = p->seed;
   S.j_max = ctx->j_max;
   S.segzbin = ctx->d_segzbin;
+  S.bin_end = ctx->d_bin_end;
   S.err = ctx->d_err;
   S.dr = p->dr;
   S.p1d_scale = static_cast<float>(p->dr / p->n_fft);
@@ -533,6 +540,7 @@ void mk_destroy(mk_ctx *ctx) {
   cudaFree(ctx->d_pixtab);
   cudaFree(ctx->d_zbin);
   cudaFree(ctx->d_segzbin);
+  cudaFree(ctx->d_bin_end);
   cudaFree(ctx->d_amp);
   for (auto *p : ctx->d_tw) cudaFree(p);
   cudaFree(ctx->d_cnt_px);
@@ -571,9 +579,9 @@ int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float 
   if (!(desc->cell > 0.0)) return fail(ctx, MK_EINVAL, "cell must be > 0");
   if (desc->layout == MK_BOX_PLANAR) {
     if (!d_delta || !d_eta) return fail(ctx, MK_EINVAL, "planar box needs d_delta and d_eta");
-  } else if (desc->layout == MK_BOX_INTERLEAVED) {
-    if (!d_delta || d_eta) return fail(ctx, MK_EINVAL, "interleaved box: d_delta holds pairs, d_eta must be NULL");
-    if (reinterpret_cast<uintptr_t>(d_delta) % 8) return fail(ctx, MK_EINVAL, "interleaved box must be 8-byte aligned");
+  } else if (desc->layout == MK_BOX_INTERLEAVED || desc->layout == MK_BOX_PADDED) {
+    if (!d_delta || d_eta) return fail(ctx, MK_EINVAL, "paired box: d_delta holds pairs, d_eta must be NULL");
+    if (reinterpret_cast<uintptr_t>(d_delta) % 8) return fail(ctx, MK_EINVAL, "paired box must be 8-byte aligned");
   } else {
     return fail(ctx, MK_EINVAL, "unknown layout %d", desc->layout);
   }
@@ -594,6 +602,18 @@ int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float
   if (n_voxels < 0 || !d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
   CK(cudaSetDevice(ctx->device));
   CK(launch_pack(d_delta, d_eta, n_voxels, d_out, ctx->sms, ctx->stream));
+  return MK_OK;
+}
+
+int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out) {
+  if (!ctx) return MK_EINVAL;
+  if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
+  if (!d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
+  if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(ctx, MK_EINVAL, "d_out must be 8-byte aligned");
+  int lgn = 0;
+  while ((1 << lgn) < n) ++lgn;
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_pack_padded(d_delta, d_eta, lgn, d_out, ctx->sms, ctx->stream));
   return MK_OK;
 }
 

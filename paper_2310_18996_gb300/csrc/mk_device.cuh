@@ -91,6 +91,39 @@ __device__ __forceinline__ float2 cmul_i(float2 a) {  // times +i (SIGN > 0) or 
   return SIGN > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// sm_100 and later execute add, sub, mul and fma on the two FP32 halves of a
+// 64-bit register pair in one instruction; each half rounds exactly as the
+// scalar instruction (round to nearest even, no flush to zero).
+#define MK_F2_BINOP(name, op)                                                                  \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                                 \
+    float2 r;                                                                                  \
+    asm("{.reg .b64 a, b, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\t" op        \
+        " d, a, b;\n\tmov.b64 {%0, %1}, d;}"                                                  \
+        : "=f"(r.x), "=f"(r.y)                                                                 \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                             \
+    return r;                                                                                  \
+  }
+MK_F2_BINOP(f2add, "add.rn.f32x2")
+MK_F2_BINOP(f2sub, "sub.rn.f32x2")
+MK_F2_BINOP(f2mul, "mul.rn.f32x2")
+#undef MK_F2_BINOP
+
+// a * b + c per half, one rounding
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{.reg .b64 a, b, c, d;\n\tmov.b64 a, {%2, %3};\n\tmov.b64 b, {%4, %5};\n\tmov.b64 c, {%6, %7};\n\t"
+      "fma.rn.f32x2 d, a, b, c;\n\tmov.b64 {%0, %1}, d;}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+
+// a + t (b - a) per half, t the same for both: the scalar lerp's rounding
+__device__ __forceinline__ float2 f2lerp(float2 a, float2 b, float t) {
+  return f2fma(make_float2(t, t), f2sub(b, a), a);
+}
+
 // ------------------------------------------------------------------ team barrier
 template <int T>
 __device__ __forceinline__ void team_sync(int team) {
@@ -120,50 +153,62 @@ __device__ __forceinline__ int sw(int i) { return i ^ (5 * ((i >> 4) & 3)); }
 // float view: real value p of the packed sequence z_n = x_2n + i x_2n+1
 __device__ __forceinline__ int swf(int p) { return 2 * sw(p >> 1) + (p & 1); }
 
-// Per-thread twiddles, fixed for the kernel's lifetime.  Stored for the
-// forward sign e^{-i...}; the inverse uses conjugates.
+// Per-thread twiddles, one shared-memory table per CTA (its teams share it):
+// slot s of team thread t at tws[s T + t], so a warp's reads of one slot are
+// conflict-free.  Stored for the forward sign e^{-i...}; the inverse uses
+// conjugates.
+//   slots 3 (p - 1) + r - 1, p = 1 .. P4 - 1, r = 1 .. 3: radix-4 pass p
+//     (pass 0 has unit twiddles), e^{-2 pi i r (t mod 4^p) / 4^(p+1)}
+//   slots R2 + q, q = 0, 1: radix-2 pass, butterflies t and t + T
+//   slots U + r, r = 0 .. 3: e^{-2 pi i k/N}, k = t + r T (real-FFT untangle)
 template <int N>
-struct Twiddles {
-  float2 w4[Fft<N>::P4][3];  // radix-4 pass p, r = 1..3
-  float2 w2[2];              // radix-2 pass, butterflies t and t + T
-  float2 wu[4];              // e^{-2 pi i k/N}, k = t + r T (real-FFT untangle)
+struct TwTab {
+  static constexpr int T = Fft<N>::T;
+  static constexpr int R2 = 3 * (Fft<N>::P4 - 1);
+  static constexpr int U = R2 + 2;
+  static constexpr int SLOTS = U + 4;
+  static constexpr size_t BYTES = sizeof(float2) * SLOTS * T;
 };
 
-// tab[k] = e^{-2 pi i k/N}, k < N (FP64-rounded table in global memory)
+// tab[k] = e^{-2 pi i k/N}, k < N (FP64-rounded table in global memory).
+// Called by every thread of the CTA; ends with a CTA barrier.
 template <int N>
-__device__ __forceinline__ void load_twiddles(Twiddles<N> &tw, const float2 *__restrict__ tab, int t) {
+__device__ __forceinline__ void fill_twiddles(float2 *tws, const float2 *__restrict__ tab) {
   constexpr int T = Fft<N>::T;
-  int ns = 1;
-#pragma unroll
-  for (int p = 0; p < Fft<N>::P4; ++p) {
-    const int jm = t % ns;
-#pragma unroll
-    for (int r = 1; r < 4; ++r) tw.w4[p][r - 1] = tab[(r * jm * (N / (4 * ns))) % N];
-    ns *= 4;
+  for (int i = threadIdx.x; i < TwTab<N>::SLOTS * T; i += blockDim.x) {
+    const int s = i / T, t = i % T;
+    int k;
+    if (s < TwTab<N>::R2) {
+      const int p = s / 3 + 1, r = s % 3 + 1, ns = 1 << (2 * p);
+      k = (r * (t % ns) * (N / (4 * ns))) % N;
+    } else if (s < TwTab<N>::U) {
+      const int ns = 1 << (2 * Fft<N>::P4);
+      k = (2 * ((t + (s - TwTab<N>::R2) * T) % ns)) % N;
+    } else {
+      k = t + (s - TwTab<N>::U) * T;
+    }
+    tws[i] = tab[k];
   }
-  if constexpr (Fft<N>::R2) {
-    tw.w2[0] = tab[(2 * (t % ns)) % N];
-    tw.w2[1] = tab[(2 * ((t + T) % ns)) % N];
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) tw.wu[r] = tab[t + r * T];
+  __syncthreads();
 }
 
+// 4-point DFT in place (SIGN = -1 forward, +1 inverse); the sums run on
+// packed pairs, the rotated difference b +- i^SIGN e on scalars.
 template <int SIGN>
 __device__ __forceinline__ void dft4(float2 &v0, float2 &v1, float2 &v2, float2 &v3) {
-  const float2 a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = cmul_i<SIGN>(csub(v1, v3));
-  v0 = cadd(a, c);
-  v2 = csub(a, c);
-  v1 = cadd(b, d);
-  v3 = csub(b, d);
+  const float2 a = f2add(v0, v2), b = f2sub(v0, v2), c = f2add(v1, v3), e = f2sub(v1, v3);
+  v0 = f2add(a, c);
+  v2 = f2sub(a, c);
+  const float2 d = cmul_i<SIGN>(e);
+  v1 = make_float2(b.x + d.x, b.y + d.y);
+  v3 = make_float2(b.x - d.x, b.y - d.y);
 }
 
 // Stockham passes after pass 0 (whose butterfly j = t outputs are in v[]).
 // SIGN = -1 forward, +1 inverse.  On return buf holds the transform in
 // natural order (through the swizzle).
 template <int N, int SIGN>
-__device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const Twiddles<N> &tw, int t,
-                                           int team) {
+__device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const float2 *tws, int t, int team) {
   constexpr int T = Fft<N>::T;
   constexpr int M = Fft<N>::M;
   team_sync<T>(team);
@@ -176,7 +221,10 @@ __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const Tw
 #pragma unroll
     for (int r = 0; r < 4; ++r) v[r] = buf[sw(t + r * T)];
 #pragma unroll
-    for (int r = 1; r < 4; ++r) v[r] = cmul(v[r], SIGN < 0 ? tw.w4[p][r - 1] : cconj(tw.w4[p][r - 1]));
+    for (int r = 1; r < 4; ++r) {
+      const float2 w = tws[(3 * (p - 1) + r - 1) * T + t];
+      v[r] = cmul(v[r], SIGN < 0 ? w : cconj(w));
+    }
     dft4<SIGN>(v[0], v[1], v[2], v[3]);
     const int base = (t / ns) * ns * 4 + t % ns;
     team_sync<T>(team);
@@ -187,13 +235,14 @@ __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const Tw
   if constexpr (Fft<N>::R2) {
     team_sync<T>(team);
     float2 a0 = buf[sw(t)], b0 = buf[sw(t + M / 2)], a1 = buf[sw(t + T)], b1 = buf[sw(t + T + M / 2)];
-    b0 = cmul(b0, SIGN < 0 ? tw.w2[0] : cconj(tw.w2[0]));
-    b1 = cmul(b1, SIGN < 0 ? tw.w2[1] : cconj(tw.w2[1]));
+    const float2 w0 = tws[TwTab<N>::R2 * T + t], w1 = tws[(TwTab<N>::R2 + 1) * T + t];
+    b0 = cmul(b0, SIGN < 0 ? w0 : cconj(w0));
+    b1 = cmul(b1, SIGN < 0 ? w1 : cconj(w1));
     team_sync<T>(team);
-    buf[sw(t)] = cadd(a0, b0);
-    buf[sw(t + M / 2)] = csub(a0, b0);
-    buf[sw(t + T)] = cadd(a1, b1);
-    buf[sw(t + T + M / 2)] = csub(a1, b1);
+    buf[sw(t)] = f2add(a0, b0);
+    buf[sw(t + M / 2)] = f2sub(a0, b0);
+    buf[sw(t + T)] = f2add(a1, b1);
+    buf[sw(t + T + M / 2)] = f2sub(a1, b1);
   }
   team_sync<T>(team);
 }
@@ -202,7 +251,7 @@ __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const Tw
 // scaled by 1/N); on return the float view holds the N real outputs
 // (pixel p at swf(p)).
 template <int N>
-__device__ __forceinline__ void inverse_real_fft(float2 *buf, const Twiddles<N> &tw, int t, int team) {
+__device__ __forceinline__ void inverse_real_fft(float2 *buf, const float2 *tws, int t, int team) {
   constexpr int T = Fft<N>::T;
   constexpr int M = Fft<N>::M;
   float2 v[4];
@@ -212,23 +261,23 @@ __device__ __forceinline__ void inverse_real_fft(float2 *buf, const Twiddles<N> 
     const float2 yk = buf[sw(k)];
     const float2 ym = cconj(buf[sw(M - k)]);
     // Z_k = (Y_k + conj Y_{M-k}) + i (Y_k - conj Y_{M-k}) e^{+2 pi i k/N}
-    v[r] = cadd(cadd(yk, ym), cmul_i<1>(cmul(csub(yk, ym), cconj(tw.wu[r]))));
+    v[r] = cadd(cadd(yk, ym), cmul_i<1>(cmul(csub(yk, ym), cconj(tws[(TwTab<N>::U + r) * T + t]))));
   }
   dft4<1>(v[0], v[1], v[2], v[3]);
-  fft_finish<N, 1>(buf, v, tw, t, team);
+  fft_finish<N, 1>(buf, v, tws, t, team);
 }
 
 // Forward complex FFT of the N reals in the float view of buf; on return buf
 // holds Z_0..Z_{M-1}.
 template <int N>
-__device__ __forceinline__ void forward_packed_fft(float2 *buf, const Twiddles<N> &tw, int t, int team) {
+__device__ __forceinline__ void forward_packed_fft(float2 *buf, const float2 *tws, int t, int team) {
   constexpr int T = Fft<N>::T;
   float2 v[4];
   team_sync<T>(team);
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = buf[sw(t + r * T)];
   dft4<-1>(v[0], v[1], v[2], v[3]);
-  fft_finish<N, -1>(buf, v, tw, t, team);
+  fft_finish<N, -1>(buf, v, tws, t, team);
 }
 
 // |X_k|^2 of the real input for k = 4t+1 .. 4t+4 after forward_packed_fft:
@@ -279,55 +328,68 @@ __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__re
 }
 
 // ------------------------------------------------------------------ fixed-point gather
-// Q20.44 cell coordinate (minus 1/2) -> base cell index and weight in [0, 1].
-__device__ __forceinline__ void split_coord(int64_t p, int mask, int &i0, int &i1, float &t) {
-  const int base = static_cast<int>(p >> 44);
-  i0 = base & mask;
-  i1 = (base + 1) & mask;
-  t = __uint2float_rn(static_cast<uint32_t>(static_cast<uint64_t>(p) >> 12)) * 0x1p-32f;
+// Positions are Q20.44 cell coordinates (minus 1/2, so that integer values
+// fall on cell centres).  The kernels add kRoundQ to a skewer's start so that
+// the weight below, the top 23 fraction bits, is the fraction rounded to
+// nearest; a fraction that rounds up to 1 moves to the next cell with weight 0.
+constexpr int64_t kRoundQ = int64_t(1) << 20;
+
+// base cell index (periodic, n = mask + 1)
+__device__ __forceinline__ int cell_of(int64_t p, int mask) { return static_cast<int>(p >> 44) & mask; }
+
+// weight in [0, 1): 1.m - 1 with m the fraction bits 43..21 (exact)
+__device__ __forceinline__ float weight_of(int64_t p) {
+  const uint32_t m = static_cast<uint32_t>(static_cast<uint64_t>(p) >> 21) & 0x7FFFFFu;
+  return __uint_as_float(0x3F800000u | m) - 1.0f;
 }
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
 // Trilinear (delta, eta) at fixed-point coordinate (px, py, pz).  BIG: box
 // with more than 2^30 cells (64-bit indices).
+//   MK_BOX_PLANAR / MK_BOX_INTERLEAVED: n^3 cells, periodic indices.
+//   MK_BOX_PADDED: (delta, eta) pairs on (n+1)^3 points whose last plane,
+//   row and column repeat index 0, so the 8 corners sit at fixed offsets
+//   from the base corner and no index wraps.
 template <int LAYOUT, bool BIG>
 __device__ __forceinline__ float2 gather(const float *__restrict__ d, const float *__restrict__ e, int lgn,
                                          int64_t px, int64_t py, int64_t pz) {
   const int mask = (1 << lgn) - 1;
-  int x0, x1, y0, y1, z0, z1;
-  float tx, ty, tz;
-  split_coord(px, mask, x0, x1, tx);
-  split_coord(py, mask, y0, y1, ty);
-  split_coord(pz, mask, z0, z1, tz);
-  using I = typename std::conditional<BIG, size_t, uint32_t>::type;
-  const I zz0 = static_cast<I>(z0) << (2 * lgn), zz1 = static_cast<I>(z1) << (2 * lgn);
-  const I yy0 = static_cast<I>(y0) << lgn, yy1 = static_cast<I>(y1) << lgn;
-  const I r00 = zz0 | yy0, r10 = zz0 | yy1, r01 = zz1 | yy0, r11 = zz1 | yy1;
+  const int x0 = cell_of(px, mask), y0 = cell_of(py, mask), z0 = cell_of(pz, mask);
+  const float tx = weight_of(px), ty = weight_of(py), tz = weight_of(pz);
+  using I = typename std::conditional<BIG, int64_t, int32_t>::type;
   float2 v[8];
-  if constexpr (LAYOUT == MK_BOX_INTERLEAVED) {
-    const float2 *b = reinterpret_cast<const float2 *>(d);
-    v[0] = __ldg(b + (r00 | x0)); v[1] = __ldg(b + (r00 | x1));
-    v[2] = __ldg(b + (r10 | x0)); v[3] = __ldg(b + (r10 | x1));
-    v[4] = __ldg(b + (r01 | x0)); v[5] = __ldg(b + (r01 | x1));
-    v[6] = __ldg(b + (r11 | x0)); v[7] = __ldg(b + (r11 | x1));
+  if constexpr (LAYOUT == MK_BOX_PADDED) {
+    const I n1 = mask + 2;
+    const float2 *a00 = reinterpret_cast<const float2 *>(d) + ((static_cast<I>(z0) * n1 + y0) * n1 + x0);
+    const float2 *a01 = a00 + n1, *a10 = a00 + n1 * n1;
+    const float2 *a11 = a10 + n1;
+    v[0] = __ldg(a00); v[1] = __ldg(a00 + 1);
+    v[2] = __ldg(a01); v[3] = __ldg(a01 + 1);
+    v[4] = __ldg(a10); v[5] = __ldg(a10 + 1);
+    v[6] = __ldg(a11); v[7] = __ldg(a11 + 1);
   } else {
-    const I idx[8] = {r00 | x0, r00 | x1, r10 | x0, r10 | x1, r01 | x0, r01 | x1, r11 | x0, r11 | x1};
+    const int x1 = (x0 + 1) & mask, y1 = (y0 + 1) & mask, z1 = (z0 + 1) & mask;
+    using U = typename std::conditional<BIG, size_t, uint32_t>::type;
+    const U zz0 = static_cast<U>(z0) << (2 * lgn), zz1 = static_cast<U>(z1) << (2 * lgn);
+    const U yy0 = static_cast<U>(y0) << lgn, yy1 = static_cast<U>(y1) << lgn;
+    const U r00 = zz0 | yy0, r10 = zz0 | yy1, r01 = zz1 | yy0, r11 = zz1 | yy1;
+    if constexpr (LAYOUT == MK_BOX_INTERLEAVED) {
+      const float2 *b = reinterpret_cast<const float2 *>(d);
+      v[0] = __ldg(b + (r00 | x0)); v[1] = __ldg(b + (r00 | x1));
+      v[2] = __ldg(b + (r10 | x0)); v[3] = __ldg(b + (r10 | x1));
+      v[4] = __ldg(b + (r01 | x0)); v[5] = __ldg(b + (r01 | x1));
+      v[6] = __ldg(b + (r11 | x0)); v[7] = __ldg(b + (r11 | x1));
+    } else {
+      const U idx[8] = {r00 | x0, r00 | x1, r10 | x0, r10 | x1, r01 | x0, r01 | x1, r11 | x0, r11 | x1};
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = make_float2(__ldg(d + idx[k]), __ldg(e + idx[k]));
+      for (int k = 0; k < 8; ++k) v[k] = make_float2(__ldg(d + idx[k]), __ldg(e + idx[k]));
+    }
   }
-  float2 out;
-  {
-    const float a = lerpf(v[0].x, v[1].x, tx), b = lerpf(v[2].x, v[3].x, tx);
-    const float c = lerpf(v[4].x, v[5].x, tx), dd = lerpf(v[6].x, v[7].x, tx);
-    out.x = lerpf(lerpf(a, b, ty), lerpf(c, dd, ty), tz);
-  }
-  {
-    const float a = lerpf(v[0].y, v[1].y, tx), b = lerpf(v[2].y, v[3].y, tx);
-    const float c = lerpf(v[4].y, v[5].y, tx), dd = lerpf(v[6].y, v[7].y, tx);
-    out.y = lerpf(lerpf(a, b, ty), lerpf(c, dd, ty), tz);
-  }
-  return out;
+  // x, then y, then z; delta and eta as one packed pair
+  const float2 c0 = f2lerp(v[0], v[1], tx), c1 = f2lerp(v[2], v[3], tx);
+  const float2 c2 = f2lerp(v[4], v[5], tx), c3 = f2lerp(v[6], v[7], tx);
+  return f2lerp(f2lerp(c0, c1, ty), f2lerp(c2, c3, ty), tz);
 }
 
 // ------------------------------------------------------------------ FGPA
@@ -412,6 +474,35 @@ __device__ __forceinline__ void add_pixel(float *a, float f, float d, float e) {
   a[7] = fmaf(d, e, a[7]);
   a[8] = fmaf(f, d, a[8]);
   a[9] = fmaf(f, e, a[9]);
+}
+
+// Pixel sums of one thread for one z bin, in the StatLayout order
+// n, F, F^2, d, e, d^2, e^2, d e, F d, F e; the (d, e) pairs run packed.
+struct PixelSums {
+  float n, f, ff, de;
+  float2 m1, m2, fm;  // (d, e), (d^2, e^2), (F d, F e)
+  __device__ __forceinline__ void zero() {
+    n = f = ff = de = 0.f;
+    m1 = m2 = fm = make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ void add(float F, float2 x) {
+    n += 1.f;
+    f += F;
+    ff = fmaf(F, F, ff);
+    de = fmaf(x.x, x.y, de);
+    m1 = f2add(m1, x);
+    m2 = f2fma(x, x, m2);
+    fm = f2fma(make_float2(F, F), x, fm);
+  }
+};
+
+// Add the warp's PixelSums of bin zb to the warp accumulators (warp-uniform
+// call; bins outside [0, n_z) are dropped).
+__device__ __forceinline__ void flush_bin_sums(const WarpAcc &W, int n_z, int zb, const PixelSums &a, int lane) {
+  float v[16] = {a.n, a.f, a.ff, a.m1.x, a.m1.y, a.m2.x, a.m2.y, a.de, a.fm.x, a.fm.y,
+                 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const float s = reduce_scatter16(v, lane);
+  if (lane < MK_NSUM && zb >= 0 && zb < n_z) kahan_add(W.sums[zb * MK_NSUM + lane], s);
 }
 
 // Flush the thread sums of bins zf (a0) and zf + 1 (a1) into the warp

@@ -225,6 +225,29 @@ __global__ void k_zbin(const double *__restrict__ zpix, const double *__restrict
                                     : static_cast<int16_t>(n_z);
 }
 
+// bin_end[k + 1] for k = -1 .. n_z: the first J whose z bin exceeds k (zbin is
+// non-decreasing in J); kBinEndNever where no tabulated pixel does.  One CTA.
+__global__ void k_bin_end(const int16_t *__restrict__ zbin, int32_t j_max, int n_z, int32_t *bin_end) {
+  for (int k = threadIdx.x; k <= n_z + 1; k += blockDim.x) bin_end[k] = kBinEndNever;
+  __syncthreads();
+  for (int j = threadIdx.x; j < j_max; j += blockDim.x) {
+    const int z = zbin[j];
+    const int zp = j ? max(static_cast<int>(zbin[j - 1]), -1) : -1;
+    for (int k = zp; k < z; ++k) bin_end[k + 1] = j;
+  }
+}
+
+// (n+1)^3 padded pairs from planar n^3 boxes (periodic ghost layer).
+__global__ void k_pack_padded(const float *__restrict__ d, const float *__restrict__ e, int lgn, float2 *out) {
+  const int64_t n = int64_t(1) << lgn, n1 = n + 1, total = n1 * n1 * n1;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t x = i % n1, y = (i / n1) % n1, z = i / (n1 * n1);
+    const int64_t src = ((z & (n - 1)) << (2 * lgn)) | ((y & (n - 1)) << lgn) | (x & (n - 1));
+    out[i] = make_float2(d[src], e[src]);
+  }
+}
+
 __global__ void k_pack(const float *__restrict__ d, const float *__restrict__ e, int64_t n, float2 *out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -352,6 +375,16 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
 cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st) {
   k_zbin<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, cumz, j_max, z_lo, dz, n_z, n_seg, zbin, segzbin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t *bin_end, cudaStream_t st) {
+  k_bin_end<<<1, 256, 0, st>>>(zbin, j_max, n_z, bin_end);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st) {
+  k_pack_padded<<<sms * 8, 256, 0, st>>>(d, e, lgn, reinterpret_cast<float2 *>(out));
   return cudaGetLastError();
 }
 

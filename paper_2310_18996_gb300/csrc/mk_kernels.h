@@ -19,6 +19,8 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
 cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st);
 cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
+cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
+cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t *bin_end, cudaStream_t st);
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);
 cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st);
 int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats);

@@ -10,6 +10,9 @@ namespace mk {
 // error bits of the device error word
 enum : int { ERR_RANGE = 1, ERR_CAPACITY = 2, ERR_TIMEOUT = 4 };
 
+// bin_end entry of a z bin that no tabulated pixel leaves
+constexpr int32_t kBinEndNever = 1 << 30;
+
 // Cubic-Hermite table of D_C(z) on z_i = i h: values and slopes c/(H0 E(z_i)).
 struct DcTable {
   const double2 *dc;  // {D_C(z_i), dD_C/dz(z_i)}
@@ -47,13 +50,14 @@ struct SkewerParams {
   const int64_t *segoff;  // exclusive prefix of segments per skewer, n_sk + 1
   int64_t n_sk;
   // box
-  const float *box_d;  // planar delta, or interleaved (delta, eta)
+  const float *box_d;  // planar delta, or (delta, eta) pairs (interleaved, padded)
   const float *box_e;  // planar eta or NULL
   int32_t lgn;
   // tables
   const float4 *pixtab;  // per global pixel J: {G, a log2e, b log2e, c}
   const int16_t *zbin;     // per J: z bin, -1 below, n_z above
   const int16_t *segzbin;  // per J: z bin of the mean z of pixels J .. J+N-1
+  const int32_t *bin_end;  // [k + 1], k = -1 .. n_z: first J with zbin > k (large beyond the tables)
   const double *cumz;      // per J: sum_{J' < J} z_J'
   const float *amp;        // A_m / N, m = 0..N/2
   const float2 *tw;      // e^{-2 pi i k/N}, k < N

@@ -7,14 +7,17 @@
 namespace mk {
 
 // =================================================================== shared-memory plan
-// Per CTA: per-warp statistic accumulators (when statistics are on), then one
-// FFT buffer of N/2 + 2 complex values per team.
+// Per CTA: per-warp statistic accumulators (when statistics are on), the
+// twiddle table, then one FFT buffer of N/2 + 2 complex values per team.
 template <int N>
 struct TeamSmem {
   static constexpr int T = N / 8;
   static constexpr int BUF = N / 2 + 2;
+  static size_t acc_bytes(int threads, int n_z, int n_k, bool stats) {
+    return stats ? static_cast<size_t>(threads / 32) * WarpAcc::bytes(n_z, n_k) : 0;
+  }
   static size_t bytes(int threads, int n_z, int n_k, bool stats) {
-    return (stats ? static_cast<size_t>(threads / 32) * WarpAcc::bytes(n_z, n_k) : 0) +
+    return acc_bytes(threads, n_z, n_k, stats) + TwTab<N>::BYTES +
            static_cast<size_t>(threads / T) * BUF * sizeof(float2);
   }
 };
@@ -64,23 +67,26 @@ __device__ __forceinline__ void flush_warp_partials(unsigned char *smem, int nwa
 // One team per segment of N pixels: small-scale modes -> inverse real FFT ->
 // per pixel gather, growth, FGPA, stores and pixel sums -> forward FFT of the
 // flux -> P1D.  Teams take contiguous ranges of segments (all segments cost
-// the same); statistics go to per-warp compensated accumulators.
+// the same).  Pixel sums stay in registers, across segments, for as long as
+// the warp's pixels stay in one z bin: the warp flushes them to its shared
+// accumulators when its pixels reach the end of the bin (bin_end) or a
+// segment starts in another bin.
 template <int N, int LAYOUT, bool BIG, int MINB>
 __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
   constexpr int T = N / 8;
   constexpr int BUF = TeamSmem<N>::BUF;
   const int teams = blockDim.x / T;
   const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wlo0 = t & ~31;  // first team pixel of this warp
   const int nwarps = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t wbytes = P.do_stats ? WarpAcc::bytes(P.n_z, P.n_k) : 0;
-  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
+  float2 *tws = reinterpret_cast<float2 *>(smem + nwarps * wbytes);
+  float2 *buf = tws + TwTab<N>::SLOTS * T + team * BUF;
   float *fb = reinterpret_cast<float *>(buf);
   const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
   if (P.do_stats) zero_warp_acc(smem + warp * wbytes, wbytes);
-
-  Twiddles<N> tw;
-  load_twiddles<N>(tw, P.tw, t);
+  fill_twiddles<N>(tws, P.tw);
 
   const int64_t nunits = P.segoff[P.n_sk];
   const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
@@ -88,7 +94,10 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
   int64_t u = g * nunits / G;
   const int64_t uend = (g + 1) * nunits / G;
   int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
-  team_sync<T>(team);
+
+  PixelSums acc;
+  acc.zero();
+  int zc = -2;  // z bin of acc (warp-uniform), -2 before the first segment
 
   for (; u < uend; ++u) {
     while (P.segoff[i + 1] <= u) ++i;
@@ -103,44 +112,56 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
     // ---- small-scale field of this segment
     small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
     team_sync<T>(team);
-    inverse_real_fft<N>(buf, tw, t, team);
+    inverse_real_fft<N>(buf, tws, t, team);
 
     // ---- per pixel: gather, growth, FGPA, stores, pixel sums
     const int jb = sk.j_lo + static_cast<int>(j0);
-    int zf = 0, zl = 0;
+    int pend = 0;  // segment pixel where bin zc ends
     if (P.do_stats) {
-      zf = __ldg(P.zbin + jb);
-      zl = __ldg(P.zbin + jb + npx - 1);
+      const int zs = __ldg(P.zbin + jb);
+      if (zs != zc) {
+        if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
+        acc.zero();
+        zc = zs;
+      }
+      pend = __ldg(P.bin_end + zc + 1) - jb;
     }
-    float a0[MK_NSUM], a1[MK_NSUM];
-#pragma unroll
-    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
-    int64_t px = sk.p0[0] + (j0 + t) * sk.step[0];
-    int64_t py = sk.p0[1] + (j0 + t) * sk.step[1];
-    int64_t pz = sk.p0[2] + (j0 + t) * sk.step[2];
+    int64_t px = sk.p0[0] + kRoundQ + (j0 + t) * sk.step[0];
+    int64_t py = sk.p0[1] + kRoundQ + (j0 + t) * sk.step[1];
+    int64_t pz = sk.p0[2] + kRoundQ + (j0 + t) * sk.step[2];
     const int64_t sx = T * sk.step[0], sy = T * sk.step[1], sz = T * sk.step[2];
     const int64_t out0 = sk.offset + j0;
 #pragma unroll 2
     for (int k = 0; k < 8; ++k) {
       const int p = t + T * k;
       float f = 0.f;
+      float2 x = make_float2(0.f, 0.f);
       if (p < npx) {
         const float2 de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
         const float4 tb = __ldg(P.pixtab + jb + p);
-        const float dt = fmaf(tb.x, de.x, fb[swf(p)]);
-        const float eg = tb.x * de.y;
-        f = fgpa(tb, dt, eg);
+        x = make_float2(fmaf(tb.x, de.x, fb[swf(p)]), tb.x * de.y);
+        f = fgpa(tb, x.x, x.y);
         if (P.delta_out) {
-          P.delta_out[out0 + p] = dt;
-          P.eta_out[out0 + p] = eg;
+          P.delta_out[out0 + p] = x.x;
+          P.eta_out[out0 + p] = x.y;
         }
         if (P.flux_out) P.flux_out[out0 + p] = f;
-        if (P.do_stats) {
-          const int zb = __ldg(P.zbin + jb + p);
-          if (zb == zf) add_pixel(a0, f, dt, eg);
-          else if (zb == zf + 1) add_pixel(a1, f, dt, eg);
-          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dt, eg);
+      }
+      if (P.do_stats) {
+        // this warp's pixels at k: T k + wlo0 + lane; flush while they pass pend
+        const int hi = min(T * k + wlo0 + 32, npx);
+        bool todo = p < npx;
+        while (hi > pend) {
+          if (todo && p < pend) {
+            acc.add(f, x);
+            todo = false;
+          }
+          flush_bin_sums(W, P.n_z, zc, acc, lane);
+          acc.zero();
+          ++zc;
+          pend = __ldg(P.bin_end + zc + 1) - jb;
         }
+        if (todo) acc.add(f, x);
       }
       fb[swf(p)] = f;
       px += sx;
@@ -148,23 +169,23 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
       pz += sz;
     }
 
-    // ---- statistics
-    if (P.do_stats) {
-      flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
-      if (npx == N) {
-        const int zs = __ldg(P.segzbin + jb);
-        if (zs >= 0 && zs < P.n_z) {
-          forward_packed_fft<N>(buf, tw, t, team);
-          float pk[4];
-          power_of_modes<N>(buf, P.tw, t, pk);
-          accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
-          if (t == 0) W.nseg[zs] += 1u;
-        }
+    // ---- P1D of the segment
+    if (P.do_stats && npx == N) {
+      const int zs = __ldg(P.segzbin + jb);
+      if (zs >= 0 && zs < P.n_z) {
+        forward_packed_fft<N>(buf, tws, t, team);
+        float pk[4];
+        power_of_modes<N>(buf, P.tw, t, pk);
+        accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
+        if (t == 0) W.nseg[zs] += 1u;
       }
     }
     team_sync<T>(team);
   }
-  if (P.do_stats) flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
+  if (P.do_stats) {
+    if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
+    flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
+  }
 }
 
 // =================================================================== statistics kernel
@@ -177,12 +198,12 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
   const int nwarps = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
-  float2 *buf = reinterpret_cast<float2 *>(smem + nwarps * wbytes) + team * BUF;
+  float2 *tws = reinterpret_cast<float2 *>(smem + nwarps * wbytes);
+  float2 *buf = tws + TwTab<N>::SLOTS * T + team * BUF;
   float *fb = reinterpret_cast<float *>(buf);
   const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
   zero_warp_acc(smem + warp * wbytes, wbytes);
-  Twiddles<N> tw;
-  load_twiddles<N>(tw, P.tw, t);
+  fill_twiddles<N>(tws, P.tw);
 
   const int64_t nunits = P.segoff[P.n_sk];
   const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
@@ -280,7 +301,7 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
         zs = fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
       }
       if (zs >= 0 && zs < P.n_z) {
-        forward_packed_fft<N>(buf, tw, t, team);
+        forward_packed_fft<N>(buf, tws, t, team);
         float pk[4];
         power_of_modes<N>(buf, P.tw, t, pk);
         accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);

@@ -9,15 +9,17 @@ namespace {
 constexpr int NN = 256;
 
 // Calls fn with the kernel instance for (layout, box size, occupancy target).
+template <int L, typename F>
+cudaError_t with_layout(bool big, int minb, F &&fn) {
+  if (minb >= 4) return big ? fn(k_skewer<NN, L, true, 4>) : fn(k_skewer<NN, L, false, 4>);
+  return big ? fn(k_skewer<NN, L, true, 1>) : fn(k_skewer<NN, L, false, 1>);
+}
+
 template <typename F>
 cudaError_t with_skewer_kernel(int layout, bool big, int minb, F &&fn) {
-  const bool il = layout == MK_BOX_INTERLEAVED;
-  if (minb >= 4) {
-    if (il) return big ? fn(k_skewer<NN, MK_BOX_INTERLEAVED, true, 4>) : fn(k_skewer<NN, MK_BOX_INTERLEAVED, false, 4>);
-    return big ? fn(k_skewer<NN, MK_BOX_PLANAR, true, 4>) : fn(k_skewer<NN, MK_BOX_PLANAR, false, 4>);
-  }
-  if (il) return big ? fn(k_skewer<NN, MK_BOX_INTERLEAVED, true, 1>) : fn(k_skewer<NN, MK_BOX_INTERLEAVED, false, 1>);
-  return big ? fn(k_skewer<NN, MK_BOX_PLANAR, true, 1>) : fn(k_skewer<NN, MK_BOX_PLANAR, false, 1>);
+  if (layout == MK_BOX_PADDED) return with_layout<MK_BOX_PADDED>(big, minb, fn);
+  if (layout == MK_BOX_INTERLEAVED) return with_layout<MK_BOX_INTERLEAVED>(big, minb, fn);
+  return with_layout<MK_BOX_PLANAR>(big, minb, fn);
 }
 
 template <typename K>

@@ -58,13 +58,29 @@ def test_geometry_matches_oracle_exactly(ctx, tiny):
     assert total == o["offsets"][-1]
 
 
-@pytest.mark.parametrize("layout", ["planar", "interleaved"])
+def load(ctx, w, d, e, layout):
+    if layout == "planar":
+        return ctx.load_box(w, d, e)
+    if layout == "interleaved":
+        return ctx.load_box(w, ctx.pack_box(d, e), None)
+    return ctx.load_box(w, ctx.pack_box(d, e, padded=True), None, layout=mk.BOX_PADDED)
+
+
+def test_padded_pack_repeats_the_periodic_box(ctx, tiny):
+    d, e = tiny["dev"]["d"], tiny["dev"]["e"]
+    n = tiny["w"]["n"]
+    p = ctx.pack_box(d, e, padded=True).view(n + 1, n + 1, n + 1, 2)
+    torch.cuda.synchronize()
+    idx = torch.arange(n + 1, device="cuda") % n
+    ref_d = d.view(n, n, n)[idx][:, idx][:, :, idx]
+    ref_e = e.view(n, n, n)[idx][:, idx][:, :, idx]
+    assert torch.equal(p[..., 0], ref_d) and torch.equal(p[..., 1], ref_e)
+
+
+@pytest.mark.parametrize("layout", ["planar", "interleaved", "padded"])
 def test_pre_fgpa_fields_match_oracle(ctx, tiny, layout):
     w, o, dv = tiny["w"], tiny["orc"], tiny["dev"]
-    if layout == "planar":
-        box = ctx.load_box(w, dv["d"], dv["e"])
-    else:
-        box = ctx.load_box(w, ctx.pack_box(dv["d"], dv["e"]), None)
+    box = load(ctx, w, dv["d"], dv["e"], layout)
     r = ctx.make_skewers(box, dv["qso"], len(tiny["ids"]), w)
     ctx.sync()
     assert_field_close(r["delta"].cpu().numpy(), o["delta"], "delta_tot")
@@ -124,9 +140,10 @@ def test_tuning_pass_matches_oracle_and_split_path(ctx, tiny):
     assert_stats_close(st3, so2)
 
 
-def test_fused_path_matches_split_path_and_oracle(ctx, tiny):
+@pytest.mark.parametrize("layout", ["planar", "padded"])
+def test_fused_path_matches_split_path_and_oracle(ctx, tiny, layout):
     w, dv = tiny["w"], tiny["dev"]
-    box = ctx.load_box(w, dv["d"], dv["e"])
+    box = load(ctx, w, dv["d"], dv["e"], layout)
     n = len(tiny["ids"])
     st, o = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
     r = ctx.make_skewers(box, dv["qso"], n, w)
@@ -140,14 +157,15 @@ def test_fused_path_matches_split_path_and_oracle(ctx, tiny):
         np.testing.assert_array_equal(st_fast[k], st[k])
 
 
+@pytest.mark.parametrize("layout", ["planar", "padded"])
 @pytest.mark.parametrize("n_fft", [512, 1024, 2048])
-def test_other_fft_lengths(ctx, tiny, n_fft):
+def test_other_fft_lengths(ctx, tiny, n_fft, layout):
     w = si.shrink(tiny["w"], n_fft=n_fft)
     idx = np.arange(0, 500, 7)
     pos, ids = tiny["pos"][idx], tiny["ids"][idx]
     o = oracle.run_skewers(w, tiny["d"], tiny["e"], pos, ids, n_threads=16)
     so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
-    box = ctx.load_box(w, tiny["dev"]["d"], tiny["dev"]["e"])
+    box = load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], layout)
     st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w,
                     flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
     tot = o["offsets"][-1]
@@ -155,6 +173,22 @@ def test_other_fft_lengths(ctx, tiny, n_fft):
     assert_field_close(g["eta"][:tot].cpu().numpy(), o["eta"], "eta")
     assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
     assert_stats_close(st, so, check_fields=False)
+
+
+@pytest.mark.parametrize("n_fft", [256, 2048])
+def test_segments_crossing_many_z_bins(ctx, tiny, n_fft):
+    # narrow z bins: a segment of N pixels crosses several bin edges (up to ~10
+    # at N = 2048), inside one warp's pixels and between the warps of a team
+    w = si.shrink(tiny["w"], n_fft=n_fft, n_zbins=32, z_bin_lo=1.8, dz_bin=0.05, n_kbins=8)
+    idx = np.arange(0, 500, 3)
+    pos, ids = tiny["pos"][idx], tiny["ids"][idx]
+    o = oracle.run_skewers(w, tiny["d"], tiny["e"], pos, ids, n_threads=16)
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    assert np.count_nonzero(so["sums"][:, 0]) >= 10
+    box = load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], "padded")
+    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w, flags=mk.STATS | mk.STORE_FLUX)
+    assert_flux_close(g["flux"][:o["offsets"][-1]].cpu().numpy(), o["flux"])
+    assert_stats_close(st, so)
 
 
 def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
@@ -182,13 +216,13 @@ def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
 
 def test_graph_replay_and_autotune_match_direct_launch(ctx, tiny):
     w, dv = tiny["w"], tiny["dev"]
-    box = ctx.load_box(w, ctx.pack_box(dv["d"], dv["e"]), None)
+    box = load(ctx, w, dv["d"], dv["e"], "padded")
     n = len(tiny["ids"])
     flags = mk.STATS | mk.STORE_FLUX
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         st_tuned, o = ctx.run(box, dv["qso"], n, w, flags=flags | mk.AUTOTUNE, capacity=tiny["orc"]["offsets"][-1])
-        threads, occ, tuned = ctx.launch_config(w["n_fft"], flags=flags)
+        threads, occ, tuned = ctx.launch_config(w["n_fft"], flags=flags, layout=mk.BOX_PADDED)
         assert tuned and threads in (128, 256) and occ in (1, 4)
         st_direct, _ = ctx.run(box, dv["qso"], n, w, flags=flags, outputs=o, capacity=o["flux"].numel())
         f_direct = o["flux"].clone()
@@ -285,8 +319,8 @@ def _full_size_check(ctx, w, n_sample, seed, lognormal=False):
     dh = d.cpu().numpy()
     pos, ids = si.catalogue(w, delta=dh if lognormal else None)
     qso = mk.catalogue_tensor(pos, ids)
-    box = ctx.load_box(w, ctx.pack_box(d, e), None)
     eh = e.cpu().numpy()
+    box = ctx.load_box(w, ctx.pack_box(d, e, padded=True), None, layout=mk.BOX_PADDED)
     del d, e
     st, g = ctx.run(box, qso, len(ids), w, flags=mk.STATS | mk.STORE_FLUX | mk.STORE_FIELDS)
     rec = records(g["sk"], len(ids))
