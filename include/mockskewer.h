@@ -259,7 +259,7 @@ int mk_flux_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *
    synchronises and fills *h_out; otherwise it is asynchronous.
    MK_AUTOTUNE: the first call of a kernel variant (FFT length, box layout
    and size, store/statistics flags) times each admissible launch shape
-   (CTA of 128 or 256 threads, compiler or four-CTA-per-SM occupancy) on its
+   (CTA of 128 or 256 threads; register budget of 2, 3 or 4 256-thread CTAs per SM) on its
    own inputs and keeps the fastest for later calls.  MK_GRAPH: the step is
    captured into a CUDA graph on the context stream (which must not be the
    legacy default stream) and replayed while the arguments, tables and
@@ -272,9 +272,9 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
            mk_stats_out *h_out);
 
 /* Launch shape the context uses for a fused-kernel variant: *threads per CTA
-   and *occupancy target (1: compiler's register choice, 4: four CTAs per
-   SM).  MK_OK when the autotuner chose it, MK_ERANGE when it is the default
-   (still written). */
+   and *occupancy target, the register budget of that many 256-thread CTAs
+   per SM (2, 3 or 4).  MK_OK when the autotuner chose it, MK_ERANGE when it
+   is the default (still written). */
 int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box, uint32_t flags,
                      int32_t *threads, int32_t *occupancy);
 

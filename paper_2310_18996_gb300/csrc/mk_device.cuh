@@ -150,8 +150,6 @@ struct Fft {
 // base + r Ns for Ns = 1, 4, 16, ..., the mode and power reads) then hits 16
 // distinct 8-byte slots per half warp.
 __device__ __forceinline__ int sw(int i) { return i ^ (5 * ((i >> 4) & 3)); }
-// float view: real value p of the packed sequence z_n = x_2n + i x_2n+1
-__device__ __forceinline__ int swf(int p) { return 2 * sw(p >> 1) + (p & 1); }
 
 // Per-thread twiddles, one shared-memory table per CTA (its teams share it):
 // slot s of team thread t at tws[s T + t], so a warp's reads of one slot are
@@ -206,8 +204,11 @@ __device__ __forceinline__ void dft4(float2 &v0, float2 &v1, float2 &v2, float2 
 
 // Stockham passes after pass 0 (whose butterfly j = t outputs are in v[]).
 // SIGN = -1 forward, +1 inverse.  On return buf holds the transform in
-// natural order (through the swizzle).
-template <int N, int SIGN>
+// natural order, through the swizzle, or with PLAIN at plain indices: the
+// last pass writes t + r T (radix-4 ending: base t, stride T; radix-2
+// ending: t, t + T, t + 2T, t + 3T), consecutive per lane, so the plain
+// layout is conflict-free there.
+template <int N, int SIGN, bool PLAIN = false>
 __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const float2 *tws, int t, int team) {
   constexpr int T = Fft<N>::T;
   constexpr int M = Fft<N>::M;
@@ -227,9 +228,10 @@ __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const fl
     }
     dft4<SIGN>(v[0], v[1], v[2], v[3]);
     const int base = (t / ns) * ns * 4 + t % ns;
+    const bool plain = PLAIN && !Fft<N>::R2 && p == Fft<N>::P4 - 1;
     team_sync<T>(team);
 #pragma unroll
-    for (int r = 0; r < 4; ++r) buf[sw(base + r * ns)] = v[r];
+    for (int r = 0; r < 4; ++r) buf[plain ? base + r * ns : sw(base + r * ns)] = v[r];
     ns *= 4;
   }
   if constexpr (Fft<N>::R2) {
@@ -239,17 +241,17 @@ __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const fl
     b0 = cmul(b0, SIGN < 0 ? w0 : cconj(w0));
     b1 = cmul(b1, SIGN < 0 ? w1 : cconj(w1));
     team_sync<T>(team);
-    buf[sw(t)] = f2add(a0, b0);
-    buf[sw(t + M / 2)] = f2sub(a0, b0);
-    buf[sw(t + T)] = f2add(a1, b1);
-    buf[sw(t + T + M / 2)] = f2sub(a1, b1);
+    buf[PLAIN ? t : sw(t)] = f2add(a0, b0);
+    buf[PLAIN ? t + M / 2 : sw(t + M / 2)] = f2sub(a0, b0);
+    buf[PLAIN ? t + T : sw(t + T)] = f2add(a1, b1);
+    buf[PLAIN ? t + T + M / 2 : sw(t + T + M / 2)] = f2sub(a1, b1);
   }
   team_sync<T>(team);
 }
 
 // Inverse real FFT of the Hermitian modes Y_0..Y_M held in buf (already
-// scaled by 1/N); on return the float view holds the N real outputs
-// (pixel p at swf(p)).
+// scaled by 1/N); on return the float view holds the N real outputs at plain
+// indices (pixel p at float p).
 template <int N>
 __device__ __forceinline__ void inverse_real_fft(float2 *buf, const float2 *tws, int t, int team) {
   constexpr int T = Fft<N>::T;
@@ -264,18 +266,19 @@ __device__ __forceinline__ void inverse_real_fft(float2 *buf, const float2 *tws,
     v[r] = cadd(cadd(yk, ym), cmul_i<1>(cmul(csub(yk, ym), cconj(tws[(TwTab<N>::U + r) * T + t]))));
   }
   dft4<1>(v[0], v[1], v[2], v[3]);
-  fft_finish<N, 1>(buf, v, tws, t, team);
+  fft_finish<N, 1, true>(buf, v, tws, t, team);
 }
 
-// Forward complex FFT of the N reals in the float view of buf; on return buf
-// holds Z_0..Z_{M-1}.
+// Forward complex FFT of the N reals in the float view of buf (plain
+// indices, pixel p at float p); on return buf holds Z_0..Z_{M-1} through the
+// swizzle.
 template <int N>
 __device__ __forceinline__ void forward_packed_fft(float2 *buf, const float2 *tws, int t, int team) {
   constexpr int T = Fft<N>::T;
   float2 v[4];
   team_sync<T>(team);
 #pragma unroll
-  for (int r = 0; r < 4; ++r) v[r] = buf[sw(t + r * T)];
+  for (int r = 0; r < 4; ++r) v[r] = buf[t + r * T];
   dft4<-1>(v[0], v[1], v[2], v[3]);
   fft_finish<N, -1>(buf, v, tws, t, team);
 }

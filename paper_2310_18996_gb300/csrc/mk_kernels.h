@@ -26,8 +26,8 @@ cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t 
 int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
 int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k);
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
-// minb: occupancy target of the instance (1: compiler's choice, 4: four
-// 256-thread CTAs per SM)
+// minb: register budget of the instance, that of minb 256-thread CTAs per SM
+// (2, 3 or 4)
 cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int minb, int grid, int threads,
                           cudaStream_t st);
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);

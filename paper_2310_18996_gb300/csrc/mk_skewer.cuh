@@ -131,6 +131,8 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
     int64_t pz = sk.p0[2] + kRoundQ + (j0 + t) * sk.step[2];
     const int64_t sx = T * sk.step[0], sy = T * sk.step[1], sz = T * sk.step[2];
     const int64_t out0 = sk.offset + j0;
+    // warp-uniform: this warp's pixels of the segment all lie before pend
+    const bool one_bin = min(T * 7 + wlo0 + 32, npx) <= pend;
 #pragma unroll 2
     for (int k = 0; k < 8; ++k) {
       const int p = t + T * k;
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
       if (p < npx) {
         const float2 de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
         const float4 tb = __ldg(P.pixtab + jb + p);
-        x = make_float2(fmaf(tb.x, de.x, fb[swf(p)]), tb.x * de.y);
+        x = make_float2(fmaf(tb.x, de.x, fb[p]), tb.x * de.y);
         f = fgpa(tb, x.x, x.y);
         if (P.delta_out) {
           P.delta_out[out0 + p] = x.x;
@@ -147,7 +149,9 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
         }
         if (P.flux_out) P.flux_out[out0 + p] = f;
       }
-      if (P.do_stats) {
+      if (P.do_stats && one_bin) {
+        if (p < npx) acc.add(f, x);
+      } else if (P.do_stats) {
         // this warp's pixels at k: T k + wlo0 + lane; flush while they pass pend
         const int hi = min(T * k + wlo0 + 32, npx);
         bool todo = p < npx;
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
         }
         if (todo) acc.add(f, x);
       }
-      fb[swf(p)] = f;
+      fb[p] = f;
       px += sx;
       py += sy;
       pz += sz;
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
           else if (zb == zf + 1) add_pixel(a1, f, dv[q], ev[q]);
           else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dv[q], ev[q]);
         }
-        fb[swf(p)] = f;
+        fb[p] = f;
       }
     } else {
 #pragma unroll 2
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
           else if (zb == zf + 1) add_pixel(a1, f, ds, es);
           else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, ds, es);
         }
-        fb[swf(p)] = f;
+        fb[p] = f;
       }
     }
     flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);

@@ -9,10 +9,12 @@ namespace {
 constexpr int NN = 256;
 
 // Calls fn with the kernel instance for (layout, box size, occupancy target).
+// minb: register budget of the instance, that of minb 256-thread CTAs per SM
 template <int L, typename F>
 cudaError_t with_layout(bool big, int minb, F &&fn) {
   if (minb >= 4) return big ? fn(k_skewer<NN, L, true, 4>) : fn(k_skewer<NN, L, false, 4>);
-  return big ? fn(k_skewer<NN, L, true, 1>) : fn(k_skewer<NN, L, false, 1>);
+  if (minb == 3) return big ? fn(k_skewer<NN, L, true, 3>) : fn(k_skewer<NN, L, false, 3>);
+  return big ? fn(k_skewer<NN, L, true, 2>) : fn(k_skewer<NN, L, false, 2>);
 }
 
 template <typename F>

@@ -223,7 +223,7 @@ def test_graph_replay_and_autotune_match_direct_launch(ctx, tiny):
     with torch.cuda.stream(s):
         st_tuned, o = ctx.run(box, dv["qso"], n, w, flags=flags | mk.AUTOTUNE, capacity=tiny["orc"]["offsets"][-1])
         threads, occ, tuned = ctx.launch_config(w["n_fft"], flags=flags, layout=mk.BOX_PADDED)
-        assert tuned and threads in (128, 256) and occ in (1, 4)
+        assert tuned and threads in (128, 256) and occ in (2, 3, 4)
         st_direct, _ = ctx.run(box, dv["qso"], n, w, flags=flags, outputs=o, capacity=o["flux"].numel())
         f_direct = o["flux"].clone()
         o["flux"].zero_()
