@@ -61,6 +61,8 @@ extern "C" {
 #define MK_MAX_NODES 32
 #define MK_MAX_ZBINS 32
 #define MK_MAX_KBINS 64
+#define MK_MAX_CHUNKS 64   /* slices of mk_run_host */
+#define MK_HOST_COPY_STREAMS 2
 #define MK_NSUM 10
 
 #define MK_BOX_PLANAR 0      /* two FP32 arrays, delta and eta, index x + n (y + n z) */
@@ -255,7 +257,9 @@ int mk_flux_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *
    FGPA and statistics in one persistent kernel, skipping the stores that
    `flags` does not ask for.  P1D segments coincide with delta_S segments
    (bins->n_fft must equal params->n_fft).  d_delta_out / d_eta_out /
-   d_flux_out may be NULL when not stored.  With MK_STATS the call
+   d_flux_out may be NULL when not stored; they may also point to page-locked
+   host memory (cudaHostAlloc; unified addressing makes it device-accessible),
+   which the kernel then writes over the host link while it computes.  With MK_STATS the call
    synchronises and fills *h_out; otherwise it is asynchronous.
    MK_AUTOTUNE: the first call of a kernel variant (FFT length, box layout
    and size, store/statistics flags) times each admissible launch shape
@@ -270,6 +274,29 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
            const mk_stat_bins *bins, uint32_t flags, mk_skewer *d_sk, int64_t *d_offsets,
            float *d_delta_out, float *d_eta_out, float *d_flux_out, int64_t capacity_px,
            mk_stats_out *h_out);
+
+/* The fused pass (as mk_run with MK_STORE_FLUX, plus MK_STATS if asked) with
+   the catalogue and the flux in host memory, pipelined.  No counterpart in
+   the paper (which writes skewers to disk after the run, Sec. 3): this is the
+   library's way to bring a large flux array to the host at link speed.
+   Steps: h_qso (n_qso records) is copied to the device; the geometry of all
+   quasars runs once; the skewers are then processed in n_chunks consecutive
+   slices of n_qso / n_chunks quasars, each slice's flux going to one of two
+   device staging buffers and from there to h_flux_out (split over
+   MK_HOST_COPY_STREAMS copy streams) while the next slice computes.
+   h_qso and h_flux_out should be page-locked (cudaHostAlloc) so that the
+   copies run asynchronously.  h_flux_out receives the flux at the skewer
+   offsets of mk_make_skewers (n_qso + 1 offsets are not returned; *h_total_px
+   receives their last value).  Statistics are those of mk_run over the whole
+   catalogue (the slices' partial sums are reduced together once).
+   flags: 0 or MK_STATS.  n_chunks in [1, MK_MAX_CHUNKS].  MK_ERANGE if the
+   flux exceeds capacity_px floats (nothing is written to h_flux_out then).
+   Uses the launch shape mk_run tuned for (MK_STORE_FLUX | flags).  The
+   context's workspaces are reused by later calls.  Synchronous. */
+int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_qso,
+                const mk_skewer_params *params, const mk_fgpa_nodes *nodes,
+                const mk_stat_bins *bins, uint32_t flags, int32_t n_chunks, float *h_flux_out,
+                int64_t capacity_px, int64_t *h_total_px, mk_stats_out *h_out);
 
 /* Launch shape the context uses for a fused-kernel variant: *threads per CTA
    and *occupancy target, the register budget of that many 256-thread CTAs

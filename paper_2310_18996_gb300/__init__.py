@@ -25,7 +25,7 @@ BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED = 0, 1, 2
 STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
-           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_make_skewers", "mk_flux", "mk_stats", "mk_run",
+           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune"]
@@ -129,6 +129,8 @@ def lib():
                 "mk_free_box": (None, [vp]),
                 "mk_pack_box": (C.c_int, [vp, i64, vp, vp, vp]),
                 "mk_pack_box_padded": (C.c_int, [vp, i32, vp, vp, vp]),
+                "mk_run_host": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(FgpaNodes), P(StatBins), u32,
+                                          i32, vp, i64, P(i64), P(StatsOut)]),
                 "mk_make_skewers": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), vp, vp, vp, vp,
                                               i64, P(i64)]),
                 "mk_flux": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, P(FgpaNodes), i32, vp,
@@ -396,6 +398,22 @@ class Context:
                                  _ptr(o.get("delta")), _ptr(o.get("eta")), _ptr(o.get("flux")),
                                  capacity, C.byref(st)))
         return (stats_dict(st, b.n_z, b.n_k) if flags & STATS else None), o
+
+    def run_host(self, box, host_qso, n_qso, w, host_flux, n_chunks=8, stats=True, nodes=None):
+        """The fused pass from a host catalogue to a host flux array, pipelined in
+        n_chunks slices (mk_run_host).  host_qso: catalogue_tensor bytes in
+        page-locked host memory; host_flux: page-locked float32 tensor of at
+        least the total pixel count.  Returns (stats dict or None, total pixels)."""
+        p = skewer_params(w)
+        nd = fgpa_nodes(w) if nodes is None else nodes
+        b = stat_bins(w)
+        st = StatsOut()
+        total = C.c_int64()
+        self._stream()
+        self._check(lib().mk_run_host(self.h, box.handle, _ptr(host_qso), n_qso, C.byref(p), C.byref(nd),
+                                      C.byref(b), STATS if stats else 0, n_chunks, _ptr(host_flux),
+                                      host_flux.numel(), C.byref(total), C.byref(st)))
+        return (stats_dict(st, b.n_z, b.n_k) if stats else None), total.value
 
 
 def skewer_records(sk, n):

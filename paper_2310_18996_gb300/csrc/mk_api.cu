@@ -1,6 +1,7 @@
 // C-ABI of the skewer-synthesis library: context, tables, entry points.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -20,6 +21,7 @@ namespace {
 constexpr double kCH = 2997.92458;  // c/H0 [Mpc/h]
 constexpr double kZMax = 12.0;      // redshift range of the tables
 constexpr double kDcStep = 1.0 / 512.0;
+constexpr double kZrStep = 1.0;  // Mpc/h, spacing of the z(r) starting table
 
 // ------------------------------------------------------------------ host cosmology
 // Flat LCDM, Omega_L = 1 - Omega_M (Table 1).  D_C is tabulated on a uniform
@@ -146,6 +148,8 @@ struct mk_ctx {
   HostCosmo cos;
   double2 *d_dc = nullptr;
   int n_dc = 0;
+  double *d_zr = nullptr;  // z(r) on r_i = i kZrStep
+  int n_zr = 0;
   int *d_err = nullptr;
   int *h_err = nullptr;  // pinned
   // pixel tables (per dr)
@@ -183,6 +187,17 @@ struct mk_ctx {
   bool timing = false;
   bool timed = false;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // mk_run_host: device copies of the catalogue and records, two staging
+  // buffers, slice boundaries, copy streams and their events
+  void *d_hq = nullptr, *d_hsk = nullptr, *d_hoff = nullptr;
+  size_t hq_cap = 0, hsk_cap = 0, hoff_cap = 0;
+  void *d_stage[2] = {nullptr, nullptr};
+  size_t stage_cap[2] = {0, 0};
+  int64_t *d_pick = nullptr, *h_pick = nullptr;  // MK_MAX_CHUNKS + 1
+  cudaStream_t copy_st[MK_HOST_COPY_STREAMS] = {};
+  cudaEvent_t ev_done[MK_MAX_CHUNKS] = {};
+  cudaEvent_t ev_copy[MK_HOST_COPY_STREAMS][MK_MAX_CHUNKS] = {};
+  bool host_ready = false;
 };
 
 namespace {
@@ -420,7 +435,7 @@ int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads) {
 GeomParams geom_params(mk_ctx *ctx, const mk_box *box, const mk_skewer_params *p) {
   GeomParams G;
   std::memset(&G, 0, sizeof(G));
-  G.tab = DcTable{ctx->d_dc, ctx->n_dc, kDcStep, ctx->cosmo.omega_m};
+  G.tab = DcTable{ctx->d_dc, ctx->n_dc, kDcStep, ctx->cosmo.omega_m, ctx->d_zr, ctx->n_zr, 1.0 / kZrStep};
   G.lambda_lya = ctx->cosmo.lambda_lya;
   G.dr = p->dr;
   G.lrf_min = p->lrf_min;
@@ -507,8 +522,13 @@ int mk_create(mk_ctx **out, int device, void *cuda_stream, const mk_cosmo *cosmo
     ctx->n_dc = static_cast<int>(ctx->cos.dc.size());
     std::vector<double2> tab(ctx->n_dc);
     for (int i = 0; i < ctx->n_dc; ++i) tab[i] = make_double2(ctx->cos.dc[i], ctx->cos.slope[i]);
+    ctx->n_zr = static_cast<int>(ctx->cos.dc.back() / kZrStep) + 2;
+    std::vector<double> zr(ctx->n_zr);
+    for (int i = 0; i < ctx->n_zr; ++i) zr[i] = ctx->cos.z_of(i * kZrStep);
     if (cudaMalloc(&ctx->d_dc, sizeof(double2) * ctx->n_dc) != cudaSuccess ||
         cudaMemcpy(ctx->d_dc, tab.data(), sizeof(double2) * ctx->n_dc, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&ctx->d_zr, sizeof(double) * ctx->n_zr) != cudaSuccess ||
+        cudaMemcpy(ctx->d_zr, zr.data(), sizeof(double) * ctx->n_zr, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMalloc(&ctx->d_err, sizeof(int)) != cudaSuccess || cudaMemset(ctx->d_err, 0, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_err, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&ctx->h_total, sizeof(int64_t)) != cudaSuccess ||
@@ -531,6 +551,7 @@ void mk_destroy(mk_ctx *ctx) {
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->d_dc);
+  cudaFree(ctx->d_zr);
   cudaFree(ctx->d_err);
   cudaFreeHost(ctx->h_err);
   cudaFreeHost(ctx->h_total);
@@ -553,6 +574,20 @@ void mk_destroy(mk_ctx *ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  cudaFree(ctx->d_hq);
+  cudaFree(ctx->d_hsk);
+  cudaFree(ctx->d_hoff);
+  cudaFree(ctx->d_stage[0]);
+  cudaFree(ctx->d_stage[1]);
+  cudaFree(ctx->d_pick);
+  if (ctx->h_pick) cudaFreeHost(ctx->h_pick);
+  if (ctx->host_ready) {
+    for (int c = 0; c < MK_HOST_COPY_STREAMS; ++c) {
+      cudaStreamDestroy(ctx->copy_st[c]);
+      for (int k = 0; k < MK_MAX_CHUNKS; ++k) cudaEventDestroy(ctx->ev_copy[c][k]);
+    }
+    for (int k = 0; k < MK_MAX_CHUNKS; ++k) cudaEventDestroy(ctx->ev_done[k]);
+  }
   delete ctx;
 }
 
@@ -914,6 +949,130 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
   const int e = *ctx->h_err;
   if (e) return read_error_word(ctx);
   std::memcpy(h_out, ctx->h_stats, sizeof(mk_stats_out));
+  return MK_OK;
+}
+
+namespace {
+int ensure_host_path(mk_ctx *ctx) {
+  if (ctx->host_ready) return MK_OK;
+  CK(cudaMalloc(&ctx->d_pick, sizeof(int64_t) * (MK_MAX_CHUNKS + 1)));
+  CK(cudaMallocHost(&ctx->h_pick, sizeof(int64_t) * (MK_MAX_CHUNKS + 1)));
+  for (int c = 0; c < MK_HOST_COPY_STREAMS; ++c) {
+    CK(cudaStreamCreateWithFlags(&ctx->copy_st[c], cudaStreamNonBlocking));
+    for (int k = 0; k < MK_MAX_CHUNKS; ++k) CK(cudaEventCreateWithFlags(&ctx->ev_copy[c][k], cudaEventDisableTiming));
+  }
+  for (int k = 0; k < MK_MAX_CHUNKS; ++k) CK(cudaEventCreateWithFlags(&ctx->ev_done[k], cudaEventDisableTiming));
+  ctx->host_ready = true;
+  return MK_OK;
+}
+}  // namespace
+
+int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_qso, const mk_skewer_params *params,
+                const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, uint32_t flags, int32_t n_chunks,
+                float *h_flux_out, int64_t capacity_px, int64_t *h_total_px, mk_stats_out *h_out) {
+  if (!ctx) return MK_EINVAL;
+  int rc = check_params(ctx, params, true);
+  if (rc || (rc = check_nodes(ctx, nodes))) return rc;
+  if (flags & ~MK_STATS) return fail(ctx, MK_EINVAL, "mk_run_host: flags may hold MK_STATS only");
+  const bool stats = flags & MK_STATS;
+  if (stats) {
+    if ((rc = check_bins(ctx, bins))) return rc;
+    if (bins->n_fft != params->n_fft) return fail(ctx, MK_EINVAL, "fused statistics need bins n_fft == n_fft");
+    if (!h_out) return fail(ctx, MK_EINVAL, "h_out is NULL");
+  }
+  if (!box || n_qso < 0 || (n_qso > 0 && !h_qso) || !h_flux_out || !h_total_px)
+    return fail(ctx, MK_EINVAL, "bad box, catalogue or output arguments");
+  if (n_chunks < 1 || n_chunks > MK_MAX_CHUNKS) return fail(ctx, MK_EINVAL, "n_chunks must be in [1, %d]", MK_MAX_CHUNKS);
+  CK(cudaSetDevice(ctx->device));
+  if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_qso)) ||
+      (rc = ensure_twiddles(ctx, params->n_fft)) || (rc = ensure_amp(ctx, params)) ||
+      (rc = ensure_pixtab(ctx, nodes)) || (rc = ensure_host_path(ctx)))
+    return rc;
+  if (stats && (rc = ensure_zbin(ctx, bins))) return rc;
+  const size_t nq = static_cast<size_t>(n_qso);
+  if ((rc = grow(ctx, &ctx->d_hq, &ctx->hq_cap, sizeof(mk_qso) * (nq ? nq : 1))) ||
+      (rc = grow(ctx, &ctx->d_hsk, &ctx->hsk_cap, sizeof(mk_skewer) * (nq ? nq : 1))) ||
+      (rc = grow(ctx, &ctx->d_hoff, &ctx->hoff_cap, sizeof(int64_t) * (nq + 1))))
+    return rc;
+  mk_skewer *d_sk = static_cast<mk_skewer *>(ctx->d_hsk);
+  int64_t *d_off = static_cast<int64_t *>(ctx->d_hoff);
+  cudaStream_t s0 = ctx->stream;
+
+  // catalogue in, geometry of every quasar, slice boundaries out
+  if (n_qso > 0) CK(cudaMemcpyAsync(ctx->d_hq, h_qso, sizeof(mk_qso) * nq, cudaMemcpyHostToDevice, s0));
+  const GeomParams G = geom_params(ctx, box, params);
+  if ((rc = enqueue_geometry(ctx, G, static_cast<const mk_qso *>(ctx->d_hq), n_qso, d_sk, d_off))) return rc;
+  const int K = n_chunks;
+  CK(launch_pick(d_off, n_qso, K, ctx->d_pick, s0));
+  CK(cudaMemcpyAsync(ctx->h_pick, ctx->d_pick, sizeof(int64_t) * (K + 1), cudaMemcpyDeviceToHost, s0));
+  if ((rc = read_error_word(ctx))) return rc;  // synchronises s0
+  const int64_t *pk = ctx->h_pick;
+  const int64_t total = pk[K];
+  *h_total_px = total;
+  if (total > capacity_px) return fail(ctx, MK_ERANGE, "flux of %lld pixels exceeds capacity %lld",
+                                      static_cast<long long>(total), static_cast<long long>(capacity_px));
+  int64_t maxc = 1;
+  for (int k = 0; k < K; ++k) maxc = std::max<int64_t>(maxc, pk[k + 1] - pk[k]);
+  for (int b = 0; b < 2; ++b)
+    if ((rc = grow(ctx, &ctx->d_stage[b], &ctx->stage_cap[b], sizeof(float) * static_cast<size_t>(maxc)))) return rc;
+
+  const uint32_t kflags = MK_STORE_FLUX | (stats ? MK_STATS : 0u);
+  LaunchCfg cfg = default_cfg(params->n_fft);
+  auto it = ctx->tuned.find(tune_key(params->n_fft, box, kflags));
+  if (it != ctx->tuned.end()) cfg = it->second;
+  const int grid = skewer_grid(ctx, params->n_fft, box, cfg, stats ? bins : nullptr);
+  const StatLayout L{stats ? bins->n_z : 0, stats ? bins->n_k : 0};
+  if (stats && (rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
+                          sizeof(double) * static_cast<size_t>(grid) * K * L.size())))
+    return rc;
+  SkewerParams S = skewer_params(ctx, box, d_sk, n_qso, params);
+  S.do_stats = stats ? 1 : 0;
+  if (stats) {
+    S.n_z = bins->n_z;
+    S.n_k = bins->n_k;
+    S.z_lo = bins->z_lo;
+    S.dz = bins->dz;
+  }
+
+  // slices: compute on s0 into staging buffer k % 2, copy out on the copy
+  // streams once the slice is done; slice k + 2 reuses the buffer after them
+  for (int k = 0; k < K; ++k) {
+    const int64_t q0 = static_cast<int64_t>(k) * n_qso / K, q1 = static_cast<int64_t>(k + 1) * n_qso / K;
+    const int64_t p0 = pk[k], p1 = pk[k + 1];
+    if (k >= 2)
+      for (int c = 0; c < MK_HOST_COPY_STREAMS; ++c) CK(cudaStreamWaitEvent(s0, ctx->ev_copy[c][k - 2], 0));
+    float *stage = static_cast<float *>(ctx->d_stage[k & 1]);
+    if (q1 > q0) {
+      S.sk = d_sk + q0;
+      S.segoff = ctx->d_segoff + q0;
+      S.n_sk = q1 - q0;
+      // records hold absolute offsets: shift the base so that pixel p0 lands at stage[0]
+      S.flux_out = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(stage) - sizeof(float) * p0);
+      S.capacity = p1;
+      S.partials = stats ? ctx->d_partials + static_cast<size_t>(k) * grid * L.size() : nullptr;
+      CK(launch_skewer(S, params->n_fft, box->desc.layout, cfg.minb, grid, cfg.threads, s0));
+    } else if (stats) {
+      CK(cudaMemsetAsync(ctx->d_partials + static_cast<size_t>(k) * grid * L.size(), 0,
+                         sizeof(double) * static_cast<size_t>(grid) * L.size(), s0));
+    }
+    CK(cudaEventRecord(ctx->ev_done[k], s0));
+    const int64_t n = p1 - p0;
+    for (int c = 0; c < MK_HOST_COPY_STREAMS; ++c) {
+      const int64_t a = n * c / MK_HOST_COPY_STREAMS, b = n * (c + 1) / MK_HOST_COPY_STREAMS;
+      CK(cudaStreamWaitEvent(ctx->copy_st[c], ctx->ev_done[k], 0));
+      if (b > a)
+        CK(cudaMemcpyAsync(h_flux_out + p0 + a, stage + a, sizeof(float) * (b - a), cudaMemcpyDeviceToHost,
+                           ctx->copy_st[c]));
+      CK(cudaEventRecord(ctx->ev_copy[c][k], ctx->copy_st[c]));
+    }
+  }
+  if (stats) {
+    CK(launch_finalize(ctx->d_partials, grid * K, bins->n_z, bins->n_k, bins->n_fft, ctx->d_stats, s0));
+    CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, sizeof(mk_stats_out), cudaMemcpyDeviceToHost, s0));
+  }
+  for (int c = 0; c < MK_HOST_COPY_STREAMS; ++c) CK(cudaStreamWaitEvent(s0, ctx->ev_copy[c][K - 1], 0));
+  if ((rc = read_error_word(ctx))) return rc;  // synchronises s0, after every copy
+  if (stats) std::memcpy(h_out, ctx->h_stats, sizeof(mk_stats_out));
   return MK_OK;
 }
 

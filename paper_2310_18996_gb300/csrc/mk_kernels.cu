@@ -22,21 +22,18 @@ __device__ __forceinline__ double dc_eval(const DcTable &T, double z) {
          (-2.0 * t3 + 3.0 * t2) * b.x + (t3 - t2) * T.h * b.y;
 }
 
-__device__ __forceinline__ double dc_slope(const DcTable &T, double z) {
-  const double zp = 1.0 + z;
-  return 2997.92458 / sqrt(T.omega_m * zp * zp * zp + (1.0 - T.omega_m));
-}
-
-// z(r): bracket by bisection on the tabulated values, then Newton.
+// z(r): linear interpolation in the z(r) table (error ~1e-7), then two
+// Newton steps on the Hermite D_C, dz = (D_C(z) - r) E(z) H0/c.
 __device__ double z_of_dc(const DcTable &T, double r) {
-  int lo = 0, hi = T.n - 1;
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (T.dc[mid].x <= r) lo = mid; else hi = mid;
+  const double s = r * T.inv_hr;
+  const int i = max(0, min(static_cast<int>(s), T.n_r - 2));
+  const double z0 = T.zr[i], z1 = T.zr[i + 1];
+  double z = fma(s - i, z1 - z0, z0);
+  for (int it = 0; it < 2; ++it) {
+    const double zp = 1.0 + z;
+    const double e = sqrt(fma(T.omega_m * zp, zp * zp, 1.0 - T.omega_m));
+    z -= (dc_eval(T, z) - r) * e * (1.0 / 2997.92458);
   }
-  const double2 a = T.dc[lo], b = T.dc[hi];
-  double z = (lo + (r - a.x) / (b.x - a.x)) * T.h;
-  for (int it = 0; it < 4; ++it) z -= (dc_eval(T, z) - r) / dc_slope(T, z);
   return z;
 }
 
@@ -81,12 +78,15 @@ __global__ void k_geometry(const mk_qso *__restrict__ q, int64_t nq, GeomParams 
     }
     s.n = static_cast<int32_t>(n);
     s.j_lo = static_cast<int32_t>(jl);
+    // Q20.44 cell coordinates of the first pixel and the step (rounding at
+    // 2^-44 cells; the pixel decisions above use the exact divisions)
     const double rc = (static_cast<double>(jl) + 0.5) * P.dr;
+    const double inv_r = 1.0 / r, inv_cell = 1.0 / P.cell;
     for (int d = 0; d < 3; ++d) {
-      const double u = Q.pos[d] / r;
-      const double c0 = (rc * u - P.origin[d]) / P.cell - 0.5;
+      const double u = Q.pos[d] * inv_r;
+      const double c0 = fma(rc * u - P.origin[d], inv_cell, -0.5);
       s.p0[d] = llrint(c0 * 0x1p44);
-      s.step[d] = llrint(P.dr * u / P.cell * 0x1p44);
+      s.step[d] = llrint(P.dr * u * inv_cell * 0x1p44);
     }
   }
   sk[i] = s;
@@ -237,6 +237,12 @@ __global__ void k_bin_end(const int16_t *__restrict__ zbin, int32_t j_max, int n
   }
 }
 
+// out[i] = off[i n / k], i = 0..k: the offsets at the slice boundaries.
+__global__ void k_pick(const int64_t *__restrict__ off, int64_t n, int k, int64_t *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= k) out[i] = off[static_cast<int64_t>(i) * n / k];
+}
+
 // (n+1)^3 padded pairs from planar n^3 boxes (periodic ghost layer).
 __global__ void k_pack_padded(const float *__restrict__ d, const float *__restrict__ e, int lgn, float2 *out) {
   const int64_t n = int64_t(1) << lgn, n1 = n + 1, total = n1 * n1 * n1;
@@ -375,6 +381,11 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
 cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st) {
   k_zbin<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, cumz, j_max, z_lo, dz, n_z, n_seg, zbin, segzbin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pick(const int64_t *off, int64_t n, int k, int64_t *out, cudaStream_t st) {
+  k_pick<<<blocks_for(k + 1, 64), 64, 0, st>>>(off, n, k, out);
   return cudaGetLastError();
 }
 

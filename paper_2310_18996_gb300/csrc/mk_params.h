@@ -19,6 +19,9 @@ struct DcTable {
   int n;              // entries
   double h;           // z spacing
   double omega_m;     // for E(z) in the Newton inversion
+  const double *zr;   // z(r_i) on r_i = i hr: the starting point of the inversion
+  int n_r;            // entries
+  double inv_hr;      // 1 / hr
 };
 
 struct GeomParams {

@@ -88,11 +88,13 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
   if (P.do_stats) zero_warp_acc(smem + warp * wbytes, wbytes);
   fill_twiddles<N>(tws, P.tw);
 
-  const int64_t nunits = P.segoff[P.n_sk];
+  // segments segoff[0] .. segoff[n_sk] (a slice of a larger catalogue may
+  // start at segoff[0] > 0)
+  const int64_t u0 = P.segoff[0], nunits = P.segoff[P.n_sk] - u0;
   const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
   const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
-  int64_t u = g * nunits / G;
-  const int64_t uend = (g + 1) * nunits / G;
+  int64_t u = u0 + g * nunits / G;
+  const int64_t uend = u0 + (g + 1) * nunits / G;
   int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
 
   PixelSums acc;

@@ -247,6 +247,51 @@ def test_graph_replay_and_autotune_match_direct_launch(ctx, tiny):
     assert_flux_close(f_direct[:tot].cpu().numpy(), tiny["orc"]["flux"])
 
 
+def test_flux_stored_into_pinned_host_memory(ctx, tiny):
+    w, dv = tiny["w"], tiny["dev"]
+    box = load(ctx, w, dv["d"], dv["e"], "padded")
+    n = len(tiny["ids"])
+    tot = int(tiny["orc"]["offsets"][-1])
+    host = torch.full((tot,), float("nan"), dtype=torch.float32).pin_memory()
+    st_h, _ = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FLUX, capacity=tot, outputs={"flux": host})
+    st_d, o = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FLUX, capacity=tot)
+    torch.cuda.synchronize()
+    assert torch.equal(host, o["flux"][:tot].cpu())
+    for k in ("sums", "p1d_sum", "n_seg"):
+        np.testing.assert_array_equal(st_h[k], st_d[k])
+
+
+@pytest.mark.parametrize("n_chunks", [1, 5])
+def test_host_pipelined_run_matches_device_run(ctx, tiny, n_chunks):
+    w, dv = tiny["w"], tiny["dev"]
+    box = load(ctx, w, dv["d"], dv["e"], "padded")
+    n = len(tiny["ids"])
+    off = tiny["orc"]["offsets"]
+    tot = int(off[-1])
+    hq = mk.catalogue_tensor(tiny["pos"], tiny["ids"], device="cpu").pin_memory()
+    hf = torch.full((tot + 7,), float("nan"), dtype=torch.float32).pin_memory()
+    st_h, total = ctx.run_host(box, hq, n, w, hf, n_chunks=n_chunks)
+    assert total == tot
+    st_d, o = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FLUX, capacity=tot)
+    torch.cuda.synchronize()
+    assert torch.equal(hf[:tot], o["flux"][:tot].cpu())
+    assert torch.isnan(hf[tot:]).all()
+    np.testing.assert_array_equal(st_h["sums"][:, 0], st_d["sums"][:, 0])
+    np.testing.assert_array_equal(st_h["n_seg"], st_d["n_seg"])
+    assert_stats_close(st_h, tiny["st"])
+    # more slices than quasars (empty slices), no statistics
+    rb = mk.QSO_DTYPE.itemsize
+    hf.fill_(float("nan"))
+    st3, t3 = ctx.run_host(box, hq[: 3 * rb], 3, w, hf, n_chunks=n_chunks + 4, stats=False)
+    assert st3 is None and t3 == off[3]
+    assert torch.equal(hf[:t3], o["flux"][:t3].cpu())
+    # a flux array too small is refused before anything is written
+    hf.fill_(float("nan"))
+    with pytest.raises(mk.MkError) as e:
+        ctx.run_host(box, hq, n, w, hf[: tot - 1], n_chunks=n_chunks)
+    assert e.value.code == mk.MK_ERANGE and torch.isnan(hf).all()
+
+
 def test_graph_needs_a_non_default_stream(ctx, tiny):
     w, dv = tiny["w"], tiny["dev"]
     box = ctx.load_box(w, dv["d"], dv["e"])
