@@ -133,13 +133,14 @@ def oracle_rate(w, dh, eh, pos, ids, target_s, threads):
     """Oracle pixels/s on a bounded sample (skewers taken in catalogue order)."""
     import oracle
 
-    n0 = 16
+    # calibrate the time per skewer (fields, flux and statistics) on a few
+    # skewers, then time a sample sized to take about target_s
+    n0 = 64
     t = time.perf_counter()
     o = oracle.run_skewers(w, dh, eh, pos[:n0], ids[:n0], n_threads=threads)
-    dt = time.perf_counter() - t
-    px0 = int(o["offsets"][-1])
-    per_px = dt / max(px0, 1)
-    n = int(min(len(ids), max(n0, target_s / max(per_px * 900.0, 1e-9))))
+    oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    per_sk = (time.perf_counter() - t) / n0
+    n = int(min(len(ids) - n0, max(n0, target_s / max(per_sk, 1e-9))))
     t = time.perf_counter()
     o = oracle.run_skewers(w, dh, eh, pos[n0:n0 + n], ids[n0:n0 + n], n_threads=threads)
     st = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])

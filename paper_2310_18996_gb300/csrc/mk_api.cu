@@ -1232,4 +1232,39 @@ namespace mkhost {
 cudaStream_t ctx_stream(mk_ctx *c) { return c->stream; }
 int ctx_device(mk_ctx *c) { return c->device; }
 int ctx_fail(mk_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
+
+int ctx_pixel_histogram(mk_ctx *ctx, double dr, const mk_skewer *d_sk, int64_t n_sk, std::vector<double> &z,
+                        std::vector<int64_t> &count, double *ms) {
+  int rc = ensure_pixel_tables(ctx, dr);
+  if (rc) return rc;
+  const int32_t jm = ctx->j_max;
+  int32_t *d_diff = nullptr;
+  CK(cudaMalloc(&d_diff, sizeof(int32_t) * (jm + 1)));
+  cudaEvent_t a = nullptr, b = nullptr;
+  std::vector<int32_t> diff(jm + 1);
+  z.resize(jm);
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) e = cudaEventRecord(a, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_diff, 0, sizeof(int32_t) * (jm + 1), ctx->stream);
+  if (e == cudaSuccess) e = launch_jcount(d_sk, n_sk, jm, d_diff, ctx->sms, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(diff.data(), d_diff, sizeof(int32_t) * (jm + 1), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(z.data(), ctx->d_zpix, sizeof(double) * jm, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(b, ctx->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(b);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  cudaFree(d_diff);
+  if (e != cudaSuccess) return fail(ctx, MK_ECUDA, "pixel histogram: %s", cudaGetErrorString(e));
+  if (ms) *ms += t;
+  count.assign(jm, 0);
+  int64_t run = 0;
+  for (int32_t j = 0; j < jm; ++j) {
+    run += diff[j];
+    count[j] = run;
+  }
+  return MK_OK;
+}
 }  // namespace mkhost

@@ -237,6 +237,18 @@ __global__ void k_bin_end(const int16_t *__restrict__ zbin, int32_t j_max, int n
   }
 }
 
+// Difference array of the pixel count per global pixel J: +1 at j_lo, -1 at
+// j_lo + n of every skewer (diff has j_max + 1 entries, zeroed by the caller).
+__global__ void k_jcount(const mk_skewer *__restrict__ sk, int64_t n_sk, int32_t j_max, int32_t *diff) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_sk;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int32_t a = sk[i].j_lo, n = sk[i].n;
+    if (n <= 0 || a < 0 || a + n > j_max) continue;
+    atomicAdd(diff + a, 1);
+    atomicAdd(diff + a + n, -1);
+  }
+}
+
 // out[i] = off[i n / k], i = 0..k: the offsets at the slice boundaries.
 __global__ void k_pick(const int64_t *__restrict__ off, int64_t n, int k, int64_t *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -381,6 +393,12 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
 cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st) {
   k_zbin<<<blocks_for(j_max, 256), 256, 0, st>>>(zpix, cumz, j_max, z_lo, dz, n_z, n_seg, zbin, segzbin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jcount(const mk_skewer *sk, int64_t n_sk, int32_t j_max, int32_t *diff, int sms, cudaStream_t st) {
+  if (n_sk == 0) return cudaSuccess;
+  k_jcount<<<sms * 4, 256, 0, st>>>(sk, n_sk, j_max, diff);
   return cudaGetLastError();
 }
 

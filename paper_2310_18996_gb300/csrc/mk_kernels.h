@@ -20,6 +20,7 @@ cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, d
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st);
 cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
 cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
+cudaError_t launch_jcount(const mk_skewer *sk, int64_t n_sk, int32_t j_max, int32_t *diff, int sms, cudaStream_t st);
 cudaError_t launch_pick(const int64_t *off, int64_t n, int k, int64_t *out, cudaStream_t st);
 cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t *bin_end, cudaStream_t st);
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);

@@ -348,11 +348,16 @@ struct TuneState {
   bool active(int zb) const { return (tg->active >> zb) & 1u; }
 };
 
-// Residual vector of one bin from statistic values (Fbar, beta, ln P1D).
+// Residual vector of one bin from statistic values (Fbar, beta, ln P1D), in
+// units of the tolerances; the P1D block is scaled by 1/sqrt(k bins) so that it
+// weighs in the least-squares steps like one statistic (F and beta are single
+// numbers), and model noise spread over many k bins cannot outvote beta.
 void residual(const TuneState &S, int zb, double fbar, double beta, const double *lnp, double *r) {
   const mk_tune_target *t = S.tg;
   r[0] = (fbar - t->mean_flux[zb]) / t->tol_mean_flux;
-  for (int k = t->k_lo; k < t->k_hi; ++k) r[1 + k - t->k_lo] = (lnp[k] - std::log(t->p1d[zb][k])) / t->tol_p1d;
+  const double wp = 1.0 / std::sqrt(static_cast<double>(S.nk()));
+  for (int k = t->k_lo; k < t->k_hi; ++k)
+    r[1 + k - t->k_lo] = wp * (lnp[k] - std::log(t->p1d[zb][k])) / t->tol_p1d;
   if (t->use_beta) r[1 + S.nk()] = (beta - t->beta[zb]) / (t->tol_beta * std::fabs(t->beta[zb]));
 }
 
@@ -427,18 +432,6 @@ void lm_step(const double *J, const double *r, int m, double lam, double *d) {
   }
 }
 
-// Applies a clamped step; returns its largest component.
-double apply_step(mk_fgpa_nodes &nd, int zb, const double *d) {
-  const double lim[3] = {1.0, 0.4, 0.4};
-  double s = 1.0;
-  for (int p = 0; p < 3; ++p)
-    if (std::fabs(d[p]) > lim[p]) s = std::min(s, lim[p] / std::fabs(d[p]));
-  nd.ln_a[zb] += s * d[0];
-  nd.b[zb] += s * d[1];
-  nd.c[zb] += s * d[2];
-  return s * std::max(std::fabs(d[0]), std::max(std::fabs(d[1]), std::fabs(d[2])));
-}
-
 constexpr double kSurrogateStop = 1e-4;  // surrogate-only fits stop below this step
 
 // Nodes of bins without data follow the nearest tuned node (ties: the lower).
@@ -454,6 +447,134 @@ void fill_inactive(mk_fgpa_nodes &nd, const TuneState &S) {
     nd.b[i] = nd.b[best];
     nd.c[i] = nd.c[best];
   }
+}
+
+// Effective parameters of a z bin: the FGPA parameters ln a, b, c are linear
+// in z between nodes (clamped at the ends), so the pixels of bin i see a blend
+// of nodes i - 1, i, i + 1.  To first order a bin's statistics are those at
+// constant parameters equal to the pixel-weighted mean of the interpolated
+// parameters, theta_eff = W theta, with W[i][j] the mean interpolation weight
+// of node j over the pixels of bin i (inactive nodes folded into the nearest
+// active node they follow).  Tuning solves each bin for theta_eff and maps
+// back to the nodes through W.
+struct EffMap {
+  int nz = 0;
+  std::vector<int> act;   // active bins (= active nodes), ascending
+  std::vector<double> W;  // nz x nz
+  bool identity = true;
+
+  int build(TuneState &S, const mk_fgpa_nodes &nd) {
+    nz = S.bins->n_z;
+    act.clear();
+    for (int i = 0; i < nz; ++i)
+      if (S.active(i)) act.push_back(i);
+    W.assign(static_cast<size_t>(nz) * nz, 0.0);
+    for (int i = 0; i < nz; ++i) W[static_cast<size_t>(i) * nz + i] = 1.0;
+    identity = true;
+    std::vector<double> zj;
+    std::vector<int64_t> cnt;
+    int rc = mkhost::ctx_pixel_histogram(S.ctx, S.params->dr, S.d_sk, S.n_sk, zj, cnt, &S.rep->gpu_ms);
+    if (rc) return rc;
+    std::vector<double> acc(static_cast<size_t>(nz) * nz, 0.0), tot(nz, 0.0);
+    const int k = nd.count;
+    for (size_t j = 0; j < zj.size(); ++j) {
+      if (cnt[j] <= 0) continue;
+      const double z = zj[j];
+      const double f = std::floor((z - S.bins->z_lo) / S.bins->dz);
+      if (f < 0.0 || f >= nz) continue;
+      const int zb = static_cast<int>(f);
+      const double c = static_cast<double>(cnt[j]);
+      tot[zb] += c;
+      // the node interpolation of the pixel table
+      if (z <= nd.z[0]) {
+        acc[static_cast<size_t>(zb) * nz] += c;
+      } else if (z >= nd.z[k - 1]) {
+        acc[static_cast<size_t>(zb) * nz + k - 1] += c;
+      } else {
+        int i = 0;
+        while (i + 2 < k && z >= nd.z[i + 1]) ++i;
+        const double w = (z - nd.z[i]) / (nd.z[i + 1] - nd.z[i]);
+        acc[static_cast<size_t>(zb) * nz + i] += c * (1.0 - w);
+        acc[static_cast<size_t>(zb) * nz + i + 1] += c * w;
+      }
+    }
+    // fold inactive nodes into the active node they follow
+    std::vector<int> follow(nz, -1);
+    for (int i = 0; i < nz; ++i) {
+      if (S.active(i)) {
+        follow[i] = i;
+        continue;
+      }
+      for (int j : act)
+        if (follow[i] < 0 || std::abs(j - i) < std::abs(follow[i] - i)) follow[i] = j;
+    }
+    for (int zb : act) {
+      if (!(tot[zb] > 0.0)) continue;
+      for (int j = 0; j < nz; ++j) W[static_cast<size_t>(zb) * nz + j] = 0.0;
+      for (int j = 0; j < nz; ++j)
+        if (follow[j] >= 0) W[static_cast<size_t>(zb) * nz + follow[j]] += acc[static_cast<size_t>(zb) * nz + j] / tot[zb];
+    }
+    identity = false;
+    return MK_OK;
+  }
+
+  // theta_eff of the active bins, tb[3 zb + p]
+  void eff(const mk_fgpa_nodes &nd, std::vector<double> &tb) const {
+    tb.assign(static_cast<size_t>(nz) * 3, 0.0);
+    for (int zb : act)
+      for (int j : act) {
+        const double w = W[static_cast<size_t>(zb) * nz + j];
+        tb[3 * zb] += w * nd.ln_a[j];
+        tb[3 * zb + 1] += w * nd.b[j];
+        tb[3 * zb + 2] += w * nd.c[j];
+      }
+  }
+
+  // nodes whose theta_eff is tb (W restricted to the active bins and nodes,
+  // Gaussian elimination with partial pivoting); inactive nodes then follow
+  void nodes(const std::vector<double> &tb, mk_fgpa_nodes &nd, const TuneState &S) const {
+    const int n = static_cast<int>(act.size());
+    std::vector<double> M(static_cast<size_t>(n) * (n + 3));
+    for (int r = 0; r < n; ++r) {
+      for (int c = 0; c < n; ++c) M[static_cast<size_t>(r) * (n + 3) + c] = W[static_cast<size_t>(act[r]) * nz + act[c]];
+      for (int p = 0; p < 3; ++p) M[static_cast<size_t>(r) * (n + 3) + n + p] = tb[3 * act[r] + p];
+    }
+    bool ok = true;
+    for (int c = 0; c < n && ok; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < n; ++r)
+        if (std::fabs(M[static_cast<size_t>(r) * (n + 3) + c]) > std::fabs(M[static_cast<size_t>(piv) * (n + 3) + c])) piv = r;
+      if (std::fabs(M[static_cast<size_t>(piv) * (n + 3) + c]) < 1e-9) {
+        ok = false;
+        break;
+      }
+      for (int q = 0; q < n + 3; ++q) std::swap(M[static_cast<size_t>(c) * (n + 3) + q], M[static_cast<size_t>(piv) * (n + 3) + q]);
+      for (int r = 0; r < n; ++r) {
+        if (r == c) continue;
+        const double f = M[static_cast<size_t>(r) * (n + 3) + c] / M[static_cast<size_t>(c) * (n + 3) + c];
+        for (int q = c; q < n + 3; ++q) M[static_cast<size_t>(r) * (n + 3) + q] -= f * M[static_cast<size_t>(c) * (n + 3) + q];
+      }
+    }
+    for (int r = 0; r < n; ++r) {
+      const int j = act[r];
+      for (int p = 0; p < 3; ++p) {
+        const double v = ok ? M[static_cast<size_t>(r) * (n + 3) + n + p] / M[static_cast<size_t>(r) * (n + 3) + r]
+                            : tb[3 * j + p];  // singular map: nodes take the bin values
+        (p == 0 ? nd.ln_a : p == 1 ? nd.b : nd.c)[j] = v;
+      }
+    }
+    fill_inactive(nd, S);
+  }
+};
+
+// Clamped LM step on the effective parameters of bin zb; returns its largest component.
+double apply_step_eff(std::vector<double> &tb, int zb, const double *d) {
+  const double lim[3] = {1.0, 0.4, 0.4};
+  double s = 1.0;
+  for (int p = 0; p < 3; ++p)
+    if (std::fabs(d[p]) > lim[p]) s = std::min(s, lim[p] / std::fabs(d[p]));
+  for (int p = 0; p < 3; ++p) tb[3 * zb + p] += s * d[p];
+  return s * std::max(std::fabs(d[0]), std::max(std::fabs(d[1]), std::fabs(d[2])));
 }
 
 void shift(mk_fgpa_nodes &nd, int p, double h) {
@@ -499,18 +620,20 @@ struct Surrogate {
       for (int c = 0; c < 35; ++c) t[35 * i + c] = ys[35 * i + c] * norm->t_std[c] + norm->t_mean[c];
     return MK_OK;
   }
-  // residuals and finite-difference Jacobians of all active nodes at nd
-  int model(TuneState &S, const mk_fgpa_nodes &nd, std::vector<double> &r, std::vector<double> &J) {
+  // residuals and finite-difference Jacobians of all active bins at the
+  // effective parameters tb (3 per bin) and bin centres zc
+  int model(TuneState &S, const double *zc, const std::vector<double> &tb, std::vector<double> &r,
+            std::vector<double> &J) {
     const double h[3] = {0.02, 0.02, 0.02};
     const int nz = S.bins->n_z, m = S.m();
     std::vector<double> x(static_cast<size_t>(nz) * 4 * 4), t;
     for (int zb = 0; zb < nz; ++zb)
       for (int v = 0; v < 4; ++v) {
         double *xi = &x[(static_cast<size_t>(zb) * 4 + v) * 4];
-        xi[0] = nd.z[zb];
-        xi[1] = nd.ln_a[zb] + (v == 1 ? h[0] : 0.0);
-        xi[2] = nd.b[zb] + (v == 2 ? h[1] : 0.0);
-        xi[3] = nd.c[zb] + (v == 3 ? h[2] : 0.0);
+        xi[0] = zc[zb];
+        xi[1] = tb[3 * zb] + (v == 1 ? h[0] : 0.0);
+        xi[2] = tb[3 * zb + 1] + (v == 2 ? h[1] : 0.0);
+        xi[3] = tb[3 * zb + 2] + (v == 3 ? h[2] : 0.0);
       }
     int rc = eval(S, x, t);
     if (rc) return rc;
@@ -572,9 +695,17 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
   mk_fgpa_nodes nd = *inout;
   fill_inactive(nd, S);
   mk_stats_out st;
-  std::vector<double> r, J, rp;
+  std::vector<double> r, J, rp, tb;
   int rc = MK_OK;
+  EffMap E;
+  if ((rc = E.build(S, nd))) {
+    cudaEventDestroy(S.e0);
+    cudaEventDestroy(S.e1);
+    return rc;
+  }
   if (method == MK_TUNE_PLAIN) {
+    // a uniform shift of every node shifts every theta_eff by the same amount,
+    // so the three shifted passes give d r / d theta_eff of every bin
     const double h[3] = {0.05, 0.05, 0.05};
     while (rc == MK_OK && report->passes < max_passes) {
       if ((rc = full_pass(S, nd, st, r))) break;
@@ -594,35 +725,38 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
             J[(static_cast<size_t>(zb) * m + i) * 3 + p] = (rp[static_cast<size_t>(zb) * m + i] - r[static_cast<size_t>(zb) * m + i]) / h[p];
       }
       if (rc) break;
+      E.eff(nd, tb);
       for (int zb = 0; zb < nz; ++zb) {
         if (!S.active(zb)) continue;
         double d[3];
         lm_step(&J[static_cast<size_t>(zb) * m * 3], &r[static_cast<size_t>(zb) * m], m, 1e-3, d);
-        (void)apply_step(nd, zb, d);
+        (void)apply_step_eff(tb, zb, d);
       }
-      fill_inactive(nd, S);
+      E.nodes(tb, nd, S);
       report->iterations += 1;
     }
   } else {
     Surrogate sg{surrogate, norm};
+    const double *zc = nd.z;
+    E.eff(nd, tb);
     // fit the target on the surrogate alone
     for (int it = 0; it < 25 && rc == MK_OK; ++it) {
-      if ((rc = sg.model(S, nd, r, J))) break;
+      if ((rc = sg.model(S, zc, tb, r, J))) break;
       double big = 0.0;
       for (int zb = 0; zb < nz; ++zb) {
         if (!S.active(zb)) continue;
         double d[3];
         lm_step(&J[static_cast<size_t>(zb) * m * 3], &r[static_cast<size_t>(zb) * m], m, 1e-2, d);
-        big = std::max(big, apply_step(nd, zb, d));
+        big = std::max(big, apply_step_eff(tb, zb, d));
       }
-      fill_inactive(nd, S);
       if (big < kSurrogateStop) break;
     }
+    E.nodes(tb, nd, S);
     // verify on full passes; between passes re-solve on the surrogate with the
     // last pass's discrepancy (true minus predicted residual) as an offset,
-    // plus a per-node linear term E (theta - theta_i) for how the discrepancy
-    // changes with the parameters (Broyden updates from successive passes)
-    std::vector<double> E(static_cast<size_t>(nz) * m * 3, 0.0), prev_off, prev_theta;
+    // plus a per-bin linear term B (theta_eff - theta_eff,i) for how the
+    // discrepancy changes with the parameters (Broyden updates from successive passes)
+    std::vector<double> B(static_cast<size_t>(nz) * m * 3, 0.0), prev_off, prev_theta;
     while (rc == MK_OK && report->passes < max_passes) {
       std::vector<double> rt;
       if ((rc = full_pass(S, nd, st, rt))) break;
@@ -632,15 +766,11 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       }
       if (report->passes >= max_passes) break;
       std::vector<double> rs, off;
-      if ((rc = sg.model(S, nd, rs, J))) break;
+      E.eff(nd, tb);
+      if ((rc = sg.model(S, zc, tb, rs, J))) break;
       off.resize(rs.size());
       for (size_t i = 0; i < rs.size(); ++i) off[i] = rt[i] - rs[i];
-      std::vector<double> theta(static_cast<size_t>(nz) * 3);
-      for (int zb = 0; zb < nz; ++zb) {
-        theta[3 * zb] = nd.ln_a[zb];
-        theta[3 * zb + 1] = nd.b[zb];
-        theta[3 * zb + 2] = nd.c[zb];
-      }
+      const std::vector<double> theta = tb;
       if (!prev_off.empty()) {
         for (int zb = 0; zb < nz; ++zb) {
           if (!S.active(zb)) continue;
@@ -653,37 +783,36 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
           for (int i = 0; i < m; ++i) {
             const size_t row = static_cast<size_t>(zb) * m + i;
             double pred = 0.0;
-            for (int p = 0; p < 3; ++p) pred += E[row * 3 + p] * dth[p];
+            for (int p = 0; p < 3; ++p) pred += B[row * 3 + p] * dth[p];
             const double u = (off[row] - prev_off[row]) - pred;
-            for (int p = 0; p < 3; ++p) E[row * 3 + p] += u * dth[p] / nn;
+            for (int p = 0; p < 3; ++p) B[row * 3 + p] += u * dth[p] / nn;
           }
         }
       }
       prev_off = off;
       prev_theta = theta;
       for (int it = 0; it < 12 && rc == MK_OK; ++it) {
-        if (it > 0 && (rc = sg.model(S, nd, rs, J))) break;
+        if (it > 0 && (rc = sg.model(S, zc, tb, rs, J))) break;
         double big = 0.0;
         for (int zb = 0; zb < nz; ++zb) {
           if (!S.active(zb)) continue;
           std::vector<double> rr(m), JJ(static_cast<size_t>(m) * 3);
-          const double cur[3] = {nd.ln_a[zb], nd.b[zb], nd.c[zb]};
           for (int i = 0; i < m; ++i) {
             const size_t row = static_cast<size_t>(zb) * m + i;
             double lin = 0.0;
             for (int p = 0; p < 3; ++p) {
-              lin += E[row * 3 + p] * (cur[p] - theta[3 * zb + p]);
-              JJ[i * 3 + p] = J[row * 3 + p] + E[row * 3 + p];
+              lin += B[row * 3 + p] * (tb[3 * zb + p] - theta[3 * zb + p]);
+              JJ[i * 3 + p] = J[row * 3 + p] + B[row * 3 + p];
             }
             rr[i] = rs[row] + off[row] + lin;
           }
           double d[3];
           lm_step(JJ.data(), rr.data(), m, 1e-2, d);
-          big = std::max(big, apply_step(nd, zb, d));
+          big = std::max(big, apply_step_eff(tb, zb, d));
         }
-        fill_inactive(nd, S);
         if (big < kSurrogateStop) break;
       }
+      E.nodes(tb, nd, S);
       report->iterations += 1;
     }
   }
