@@ -395,6 +395,36 @@ __device__ __forceinline__ float2 gather(const float *__restrict__ d, const floa
   return f2lerp(f2lerp(c0, c1, ty), f2lerp(c2, c3, ty), tz);
 }
 
+// Prefetch into L2 the four voxel rows (y0|y1, z0|z1) that the trilinear
+// stencil at (px, py, pz) reads, for the paired layouts (each row's two
+// corners x0, x0 + 1 are adjacent).
+template <int LAYOUT, bool BIG>
+__device__ __forceinline__ void prefetch_stencil(const float *__restrict__ d, int lgn, int64_t px, int64_t py,
+                                                 int64_t pz) {
+  if constexpr (LAYOUT == MK_BOX_PLANAR) return;
+  const int mask = (1 << lgn) - 1;
+  const int x0 = cell_of(px, mask), y0 = cell_of(py, mask), z0 = cell_of(pz, mask);
+  using I = typename std::conditional<BIG, int64_t, int32_t>::type;
+  const float2 *b = reinterpret_cast<const float2 *>(d);
+  const float2 *a[4];
+  if constexpr (LAYOUT == MK_BOX_PADDED) {
+    const I n1 = mask + 2;
+    a[0] = b + ((static_cast<I>(z0) * n1 + y0) * n1 + x0);
+    a[1] = a[0] + n1;
+    a[2] = a[0] + n1 * n1;
+    a[3] = a[2] + n1;
+  } else {
+    const int y1 = (y0 + 1) & mask, z1 = (z0 + 1) & mask;
+    using U = typename std::conditional<BIG, size_t, uint32_t>::type;
+    a[0] = b + ((static_cast<U>(z0) << (2 * lgn)) | (static_cast<U>(y0) << lgn) | x0);
+    a[1] = b + ((static_cast<U>(z0) << (2 * lgn)) | (static_cast<U>(y1) << lgn) | x0);
+    a[2] = b + ((static_cast<U>(z1) << (2 * lgn)) | (static_cast<U>(y0) << lgn) | x0);
+    a[3] = b + ((static_cast<U>(z1) << (2 * lgn)) | (static_cast<U>(y1) << lgn) | x0);
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) asm volatile("prefetch.global.L2 [%0];" ::"l"(a[r]));
+}
+
 // ------------------------------------------------------------------ FGPA
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;

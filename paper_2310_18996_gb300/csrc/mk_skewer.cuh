@@ -111,6 +111,14 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
       if (t == 0) raise_error(P.err, ERR_CAPACITY);
       continue;
     }
+    // ---- start the box rows of this segment's stencils on their way to L2:
+    // lane t samples pixel 8t + 4 (the modes and the inverse FFT below hide
+    // the latency)
+    {
+      const int64_t ps = j0 + min(npx - 1, 8 * t + 4);
+      prefetch_stencil<LAYOUT, BIG>(P.box_d, P.lgn, sk.p0[0] + kRoundQ + ps * sk.step[0],
+                                    sk.p0[1] + kRoundQ + ps * sk.step[1], sk.p0[2] + kRoundQ + ps * sk.step[2]);
+    }
     // ---- small-scale field of this segment
     small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
     team_sync<T>(team);
