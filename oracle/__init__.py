@@ -50,6 +50,7 @@ class Cfg(C.Structure):
         ("dr", C.c_double), ("lrf_min", C.c_double), ("lrf_max", C.c_double),
         ("lobs_min", C.c_double), ("n_min", C.c_int32), ("n_max", C.c_int32),
         ("n_fft", C.c_int32), ("p_s", C.POINTER(C.c_double)), ("seed", C.c_uint32),
+        ("interp", C.c_int32),
     ]
 
 
@@ -101,6 +102,7 @@ def lib():
                 "orc_geometry": (C.c_int, [P(Cfg), P(d), P(i32), P(i32), P(d)]),
                 "orc_pixel_z": (d, [P(Cfg), i64]),
                 "orc_trilinear": (d, [P(C.c_float), i32, P(d)]),
+                "orc_gauss7": (d, [P(C.c_float), i32, P(d)]),
                 "orc_small_scale_modes": (None, [P(Cfg), u64, i32, P(d), P(d)]),
                 "orc_small_scale_segment": (None, [P(Cfg), u64, i32, P(d)]),
                 "orc_skewer_fields": (C.c_int, [P(Cfg), P(C.c_float), P(C.c_float), P(d), u64,
@@ -181,6 +183,13 @@ def trilinear(box, c):
     return lib().orc_trilinear(_p(box, C.c_float), box.shape[0], _p(cc, C.c_double))
 
 
+def gauss7(box, c):
+    """Gaussian-kernel average over 7^3 voxels (Sec. 2.3) at cell coordinate c."""
+    box = np.ascontiguousarray(box, dtype=np.float32)
+    cc = np.ascontiguousarray(c, dtype=np.float64)
+    return lib().orc_gauss7(_p(box, C.c_float), box.shape[0], _p(cc, C.c_double))
+
+
 # ---------------------------------------------------------------- structs
 def make_cfg(w):
     """Build the C config from a workload dict (see skewer_inputs.workload)."""
@@ -199,6 +208,7 @@ def make_cfg(w):
     cfg.n_fft = w["n_fft"]
     cfg.p_s = _p(ps, C.c_double)
     cfg.seed = w["seed_noise"] & 0xFFFFFFFF
+    cfg.interp = w.get("interp", 0)
     cfg._keep = ps  # keep the table alive with the struct
     return cfg
 

@@ -305,6 +305,27 @@ double orc_trilinear(const float *box, int32_t n, const double c[3]) {
   return v;
 }
 
+/* Gaussian-kernel average (Sec. 2.3): voxels ic-3..ic+3 per axis around the */
+/* voxel ic = floor(c) containing the point, weight exp(-|d|^2/2) with d the  */
+/* distance to the voxel centre (i + 1/2) in cell units, normalised.          */
+double orc_gauss7(const float *box, int32_t n, const double c[3]) {
+  int64_t ic[3];
+  for (int d = 0; d < 3; ++d) ic[d] = (int64_t)floor(c[d]);
+  double v = 0.0, wsum = 0.0;
+  for (int64_t kz = ic[2] - 3; kz <= ic[2] + 3; ++kz)
+    for (int64_t ky = ic[1] - 3; ky <= ic[1] + 3; ++ky)
+      for (int64_t kx = ic[0] - 3; kx <= ic[0] + 3; ++kx) {
+        double dx = ((double)kx + 0.5) - c[0];
+        double dy = ((double)ky + 0.5) - c[1];
+        double dz = ((double)kz + 0.5) - c[2];
+        double w = exp(-0.5 * (dx * dx + dy * dy + dz * dz));
+        int64_t ix = wrap(kx, n), iy = wrap(ky, n), iz = wrap(kz, n);
+        v += w * (double)box[ix + (int64_t)n * (iy + (int64_t)n * iz)];
+        wsum += w;
+      }
+  return v / wsum;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Small-scale field delta_S (Sec. 2.3): Gaussian modes times sqrt(P_S),     */
 /* inverse Fourier transform.  Mode m of segment `seg` of quasar `id`:       */
@@ -369,8 +390,9 @@ int orc_skewer_fields(const orc_cfg *cfg, const float *dbox, const float *ebox,
     for (int d = 0; d < 3; ++d) c[d] = (r * u[d] - cfg->origin[d]) / cfg->cell;
     double zj = orc_z_of_distance(cfg->omega_m, r);
     double g = orc_growth(cfg->omega_m, zj);
-    if (delta_lg) delta_lg[j] = g * orc_trilinear(dbox, cfg->n, c);
-    if (eta_g) eta_g[j] = g * orc_trilinear(ebox, cfg->n, c);
+    if (delta_lg)
+      delta_lg[j] = g * (cfg->interp ? orc_gauss7(dbox, cfg->n, c) : orc_trilinear(dbox, cfg->n, c));
+    if (eta_g) eta_g[j] = g * (cfg->interp ? orc_gauss7(ebox, cfg->n, c) : orc_trilinear(ebox, cfg->n, c));
     if (delta_s) {
       if (j / nf != cur) {
         cur = j / nf;

@@ -46,6 +46,9 @@ typedef struct orc_cfg {
   int32_t n_fft;
   const double *p_s; /* n_fft/2+1 samples P_S(k_m), k_m = 2 pi m/(n_fft dr) */
   uint32_t seed;
+  /* interpolation of delta_L and eta at a pixel: 0 trilinear between voxel
+     centres, 1 the Gaussian-kernel average over 7^3 voxels of Sec. 2.3 */
+  int32_t interp;
 } orc_cfg;
 
 /* FGPA parameter nodes (Sec. 2.5: tuned at a few z, interpolated between). */
@@ -101,6 +104,12 @@ double orc_pixel_z(const orc_cfg *cfg, int64_t j);
 
 /* ---- trilinear interpolation of a periodic box (c in cell units) ---- */
 double orc_trilinear(const float *box, int32_t n, const double c[3]);
+
+/* ---- Gaussian-kernel average of a periodic box (Sec. 2.3): the 7^3 voxels
+   centred on the voxel containing c, weighted by exp(-d^2 / 2) with d the
+   distance from c to the voxel centre in cell units (sigma = one voxel side),
+   weights normalised to sum 1 ---- */
+double orc_gauss7(const float *box, int32_t n, const double c[3]);
 
 /* ---- small-scale modes and field of one segment ---- */
 void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double *re,

@@ -140,6 +140,94 @@ def test_trilinear_single_voxel_is_tent_product_with_wrap():
             assert oracle.trilinear(box, c) == pytest.approx(expect, abs=1e-13)
 
 
+# ------------------------------------------------------------ Gaussian-kernel average (Sec. 2.3)
+def _theta_window_sum():
+    # sum_{|m|<=3} exp(-m^2/2) from the Jacobi theta identity
+    # sum_{m in Z} exp(-m^2/2) = sqrt(2 pi) (1 + 2 sum_k exp(-2 pi^2 k^2)), minus the tail |m| >= 4
+    full = math.sqrt(2.0 * math.pi) * (1.0 + 2.0 * sum(math.exp(-2.0 * math.pi ** 2 * k * k) for k in (1, 2)))
+    tail = 2.0 * sum(math.exp(-0.5 * m * m) for m in range(4, 40))
+    return full - tail
+
+
+def test_gauss7_constant_field():
+    box = np.full((16, 16, 16), 0.75, np.float32)
+    rng = np.random.default_rng(21)
+    for _ in range(50):
+        c = rng.uniform(-3.0, 19.0, 3)
+        assert oracle.gauss7(box, c) == pytest.approx(0.75, rel=1e-14)
+
+
+def test_gauss7_single_voxel_weights_window_and_wrap():
+    n = 16
+    s0 = _theta_window_sum()
+    assert s0 == pytest.approx(2.50594988, abs=1e-8)
+    box = np.zeros((n, n, n), np.float32)
+    v = (5, 9, 12)
+    box[v[2], v[1], v[0]] = 1.0
+    ctr = np.array(v, float) + 0.5
+    assert oracle.gauss7(box, ctr) == pytest.approx(s0 ** -3, rel=1e-12)
+    # one and two voxels away along different axes
+    assert oracle.gauss7(box, ctr + [1, 0, 0]) == pytest.approx(math.exp(-0.5) / s0 ** 3, rel=1e-12)
+    assert oracle.gauss7(box, ctr + [0, -2, 1]) == pytest.approx(math.exp(-2.5) / s0 ** 3, rel=1e-12)
+    # 3 voxels away is inside the 7^3 window, 4 is outside
+    assert oracle.gauss7(box, ctr + [0, 0, 3]) == pytest.approx(math.exp(-4.5) / s0 ** 3, rel=1e-12)
+    assert oracle.gauss7(box, ctr + [4, 0, 0]) == 0.0
+    assert oracle.gauss7(box, ctr + [0, -4, 2]) == 0.0
+    # periodic wrap: voxel 0 seen from the centre of voxel n - 1
+    box2 = np.zeros((n, n, n), np.float32)
+    box2[0, 0, 0] = 1.0
+    assert oracle.gauss7(box2, [n - 0.5, 0.5, 0.5]) == pytest.approx(math.exp(-0.5) / s0 ** 3, rel=1e-12)
+
+
+def test_gauss7_linear_field_centres_and_face_bias():
+    # f = x on voxel centres (no wrap inside the window): symmetric windows give
+    # the centre value exactly; on a voxel face the window (containing voxel
+    # +-3) reaches 3.5 cells ahead and 2.5 behind, a bias sum(d w)/sum(w) > 0
+    n = 32
+    i = np.arange(n) + 0.5
+    box = np.broadcast_to(i[None, None, :], (n, n, n)).astype(np.float32).copy()
+    for x in (8.5, 11.5, 20.5):
+        assert oracle.gauss7(box, [x, 12.3, 17.9]) == pytest.approx(x, abs=1e-12)
+    ds = [-2.5, -1.5, -0.5, 0.5, 1.5, 2.5, 3.5]
+    wts = [math.exp(-0.5 * d * d) for d in ds]
+    bias = sum(d * w for d, w in zip(ds, wts)) / sum(wts)
+    assert bias == pytest.approx(3.5 * math.exp(-6.125) / sum(wts), rel=1e-3)  # the unmatched far voxel
+    assert oracle.gauss7(box, [14.0, 12.3, 17.9]) == pytest.approx(14.0 + bias, abs=1e-12)
+
+
+def test_gauss7_separable_field_is_product_of_axis_averages():
+    n = 16
+    rng = np.random.default_rng(22)
+    gx, gy, gz = (rng.uniform(0.5, 1.5, n) for _ in range(3))
+    box = (gz[:, None, None] * gy[None, :, None] * gx[None, None, :]).astype(np.float64)
+    box32 = box.astype(np.float32)
+
+    def avg1(g, c):  # 1D normalised Gaussian average over the 7 voxels around floor(c)
+        ic = math.floor(c)
+        ks = range(ic - 3, ic + 4)
+        w = [math.exp(-0.5 * ((k + 0.5) - c) ** 2) for k in ks]
+        return sum(wi * g[k % n] for wi, k in zip(w, ks)) / sum(w)
+
+    for _ in range(40):
+        c = rng.uniform(-2.0, n + 2.0, 3)
+        expect = avg1(gx, c[0]) * avg1(gy, c[1]) * avg1(gz, c[2])
+        # the box holds FP32-rounded products
+        assert oracle.gauss7(box32, c) == pytest.approx(expect, rel=2e-7)
+
+
+def test_skewer_fields_gauss7_constant_box_is_growth_times_constant():
+    w = si.shrink(si.workload("tiny"), interp=1)
+    n = w["n"]
+    d = np.full((n, n, n), 0.5, np.float32)
+    e = np.full((n, n, n), -0.25, np.float32)
+    pos, ids = si.catalogue(w, n_q=3)
+    o = oracle.run_skewers(w, d, e, pos, ids, n_threads=1)
+    zj = np.array([oracle.pixel_z(w, j) for j in range(o["j_lo"][0], o["j_lo"][0] + o["npix"][0])])
+    g = np.array([oracle.growth(w["omega_m"], z) for z in zj])
+    k = o["offsets"][1]
+    np.testing.assert_allclose(o["eta"][:k], -0.25 * g, rtol=1e-12)
+
+
 # ------------------------------------------------------------ geometry
 def test_geometry_forest_window():
     w = si.workload("tiny")
