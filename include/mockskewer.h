@@ -69,6 +69,15 @@ extern "C" {
 #define MK_BOX_INTERLEAVED 1 /* one FP32 array of (delta, eta) pairs, same index order */
 #define MK_BOX_PADDED 2      /* (delta, eta) pairs on (n+1)^3 points, index x + (n+1) (y + (n+1) z);
                                 plane, row and column n repeat index 0 (periodic ghost layer) */
+#define MK_BOX_HALO 3        /* (delta, eta) pairs on (n+6)^3 points for x, y, z in [-3, n+3),
+                                index (x+3) + (n+6) ((y+3) + (n+6) (z+3)), periodic copies
+                                (required by MK_INTERP_GAUSS7, usable by trilinear) */
+
+/* Interpolation of delta_L and eta at a pixel (mk_skewer_params.interp). */
+#define MK_INTERP_TRILINEAR 0 /* between the 8 surrounding voxel centres */
+#define MK_INTERP_GAUSS7 1    /* Sec. 2.3: Gaussian-kernel average over the 7^3 voxels around
+                                 the voxel containing the pixel, sigma = one voxel side,
+                                 weights normalised; needs an MK_BOX_HALO box */
 
 /* mk_run flags */
 #define MK_STORE_FIELDS 1u /* write delta_tot and eta (pre-FGPA skewers) */
@@ -91,7 +100,7 @@ typedef struct mk_cosmo {
 /* Box of n^3 cubic cells (n a power of two, 2..2048), periodic. */
 typedef struct mk_box_desc {
   int32_t n;
-  int32_t layout;   /* MK_BOX_PLANAR, MK_BOX_INTERLEAVED or MK_BOX_PADDED */
+  int32_t layout;   /* MK_BOX_PLANAR, MK_BOX_INTERLEAVED, MK_BOX_PADDED or MK_BOX_HALO */
   double cell;      /* cell side [Mpc/h] */
   double origin[3]; /* corner of the box in the observer frame [Mpc/h] */
 } mk_box_desc;
@@ -122,6 +131,7 @@ typedef struct mk_skewer_params {
   int32_t n_fft;           /* delta_S segment length: power of two, 256..2048 */
   uint32_t seed;           /* small-scale noise seed */
   const double *h_p_s;     /* n_fft/2 + 1 values P_S(k_m), k_m = 2 pi m/(n_fft dr) */
+  int32_t interp;          /* MK_INTERP_TRILINEAR (0) or MK_INTERP_GAUSS7 */
 } mk_skewer_params;
 
 /* FGPA nodes: ln a, b, c at increasing z, linear in z between nodes, clamped
@@ -188,7 +198,8 @@ int mk_sync(mk_ctx *ctx);
    box delta_m and the velocity-gradient box, here the single line-of-sight
    component eta_par).  MK_BOX_PLANAR: d_delta and d_eta each n^3 floats.
    MK_BOX_INTERLEAVED: d_delta holds 2 n^3 floats (delta, eta) per cell and
-   d_eta must be NULL.  The memory must outlive the box.  Synchronous. */
+   d_eta must be NULL.  MK_BOX_PADDED / MK_BOX_HALO: d_delta holds the pairs of
+   that layout (8-byte aligned), d_eta NULL.  The memory must outlive the box.  Synchronous. */
 int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float *d_delta,
                 const float *d_eta);
 void mk_free_box(mk_box *box);
@@ -204,6 +215,13 @@ int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float
    Asynchronous on the context stream.  MK_EINVAL for n outside [2, 2048] or
    not a power of two, or NULL pointers. */
 int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out);
+
+/* Pack two planar n^3 boxes into the MK_BOX_HALO layout: d_out (caller-owned,
+   8-byte aligned) receives 2 (n+6)^3 floats.  The margin of 3 periodic copies
+   lets the 7^3 Gaussian-kernel average of Sec. 2.3 read its 49 x-rows without
+   index wrap.  No counterpart in the paper (a storage choice).  Asynchronous
+   on the context stream.  MK_EINVAL as mk_pack_box_padded. */
+int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out);
 
 /* ---------------------------------------------------------------- skewers */
 
@@ -300,8 +318,9 @@ int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_q
 
 /* Launch shape the context uses for a fused-kernel variant: *threads per CTA
    and *occupancy target, the register budget of that many 256-thread CTAs
-   per SM (2, 3 or 4).  MK_OK when the autotuner chose it, MK_ERANGE when it
-   is the default (still written). */
+   per SM (2, 3 or 4).  layout: the box layout, plus 16 for MK_INTERP_GAUSS7.
+   MK_OK when the autotuner chose it, MK_ERANGE when it is the default
+   (still written). */
 int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box, uint32_t flags,
                      int32_t *threads, int32_t *occupancy);
 

@@ -21,11 +21,13 @@ from . import build as _build
 MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
 MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
 STATIC_MAX_SKEWERS = 131072
-BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED = 0, 1, 2
+BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED, BOX_HALO = 0, 1, 2, 3
+INTERP_TRILINEAR, INTERP_GAUSS7 = 0, 1
+GAUSS7_VARIANT = 16  # mk_launch_config: layout + 16 for the Gaussian-kernel instance
 STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
-           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
+           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_pack_box_halo", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune"]
@@ -49,7 +51,8 @@ class BoxDesc(C.Structure):
 class SkewerParams(C.Structure):
     _fields_ = [("dr", C.c_double), ("lrf_min", C.c_double), ("lrf_max", C.c_double),
                 ("lobs_min", C.c_double), ("n_min", C.c_int32), ("n_max", C.c_int32),
-                ("n_fft", C.c_int32), ("seed", C.c_uint32), ("h_p_s", C.POINTER(C.c_double))]
+                ("n_fft", C.c_int32), ("seed", C.c_uint32), ("h_p_s", C.POINTER(C.c_double)),
+                ("interp", C.c_int32)]
 
 
 class FgpaNodes(C.Structure):
@@ -129,6 +132,7 @@ def lib():
                 "mk_free_box": (None, [vp]),
                 "mk_pack_box": (C.c_int, [vp, i64, vp, vp, vp]),
                 "mk_pack_box_padded": (C.c_int, [vp, i32, vp, vp, vp]),
+                "mk_pack_box_halo": (C.c_int, [vp, i32, vp, vp, vp]),
                 "mk_run_host": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(FgpaNodes), P(StatBins), u32,
                                           i32, vp, i64, P(i64), P(StatsOut)]),
                 "mk_make_skewers": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), vp, vp, vp, vp,
@@ -179,7 +183,7 @@ def skewer_params(w):
                      lobs_min=w.get("lobs_min", 0.0), n_min=w.get("n_min", 0),
                      n_max=w.get("n_max", 0), n_fft=w["n_fft"],
                      seed=w["seed_noise"] & 0xFFFFFFFF,
-                     h_p_s=ps.ctypes.data_as(C.POINTER(C.c_double)))
+                     h_p_s=ps.ctypes.data_as(C.POINTER(C.c_double)), interp=w.get("interp", 0))
     p._keep = ps
     return p
 
@@ -302,15 +306,18 @@ class Context:
         self._check(lib().mk_load_box(self.h, C.byref(h), C.byref(desc), _ptr(delta), _ptr(eta)))
         return Box(self, h, desc, (delta, eta))
 
-    def pack_box(self, delta, eta, padded=False):
+    def pack_box(self, delta, eta, padded=False, halo=False):
         """Interleaved (delta, eta) pairs; padded=True: the MK_BOX_PADDED layout
-        ((n+1)^3 pairs with a periodic ghost layer), for load_box(..., layout=BOX_PADDED)."""
+        ((n+1)^3 pairs with a periodic ghost layer), for load_box(..., layout=BOX_PADDED);
+        halo=True: the MK_BOX_HALO layout ((n+6)^3 pairs, periodic margin of 3)."""
         torch = self._torch
         self._stream()
-        if padded:
+        if padded or halo:
             n = round(delta.numel() ** (1.0 / 3.0))
-            out = torch.empty(2 * (n + 1) ** 3, dtype=torch.float32, device=delta.device)
-            self._check(lib().mk_pack_box_padded(self.h, n, _ptr(delta), _ptr(eta), _ptr(out)))
+            m = n + (6 if halo else 1)
+            out = torch.empty(2 * m ** 3, dtype=torch.float32, device=delta.device)
+            fn = lib().mk_pack_box_halo if halo else lib().mk_pack_box_padded
+            self._check(fn(self.h, n, _ptr(delta), _ptr(eta), _ptr(out)))
             return out
         out = torch.empty(delta.numel() * 2, dtype=torch.float32, device=delta.device)
         self._check(lib().mk_pack_box(self.h, delta.numel(), _ptr(delta), _ptr(eta), _ptr(out)))

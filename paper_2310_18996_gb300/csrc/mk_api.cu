@@ -342,6 +342,8 @@ int check_params(mk_ctx *ctx, const mk_skewer_params *p, bool need_ps) {
   if (p->n_min < 0 || p->n_max < 0) return fail(ctx, MK_EINVAL, "n_min/n_max must be >= 0");
   if (tw_slot(p->n_fft) < 0) return fail(ctx, MK_EINVAL, "n_fft must be 256, 512, 1024 or 2048");
   if (need_ps && !p->h_p_s) return fail(ctx, MK_EINVAL, "h_p_s is NULL");
+  if (p->interp != MK_INTERP_TRILINEAR && p->interp != MK_INTERP_GAUSS7)
+    return fail(ctx, MK_EINVAL, "interp must be MK_INTERP_TRILINEAR or MK_INTERP_GAUSS7");
   return MK_OK;
 }
 
@@ -411,8 +413,8 @@ int time_end(mk_ctx *ctx) {
 }
 
 // persistent grids: as many resident CTAs as the SMs hold
-int skewer_grid(mk_ctx *ctx, int n_fft, const mk_box *box, LaunchCfg cfg, const mk_stat_bins *bins) {
-  return ctx->sms * skewer_blocks_per_sm(n_fft, box->desc.layout, box->lgn, cfg.minb, cfg.threads,
+int skewer_grid(mk_ctx *ctx, int n_fft, int variant, int lgn, LaunchCfg cfg, const mk_stat_bins *bins) {
+  return ctx->sms * skewer_blocks_per_sm(n_fft, variant, lgn, cfg.minb, cfg.threads,
                                          bins ? bins->n_z : 0, bins ? bins->n_k : 0, bins != nullptr);
 }
 
@@ -423,9 +425,20 @@ LaunchCfg default_cfg(int n_fft) {
   return LaunchCfg{256, 3};
 }
 
-uint64_t tune_key(int n_fft, const mk_box *box, uint32_t flags) {
-  return (static_cast<uint64_t>(n_fft) << 32) | (static_cast<uint64_t>(box->desc.layout) << 16) |
-         (static_cast<uint64_t>(box->lgn > 10) << 8) | (flags & (MK_STORE_FIELDS | MK_STORE_FLUX | MK_STATS));
+// kernel variant: the box layout, plus kGauss7Variant for the Gaussian kernel
+int kernel_variant(const mk_box *box, const mk_skewer_params *p) {
+  return box->desc.layout | (p->interp == MK_INTERP_GAUSS7 ? kGauss7Variant : 0);
+}
+
+int check_interp(mk_ctx *ctx, const mk_box *box, const mk_skewer_params *p) {
+  if (p->interp == MK_INTERP_GAUSS7 && box->desc.layout != MK_BOX_HALO)
+    return fail(ctx, MK_EINVAL, "MK_INTERP_GAUSS7 needs an MK_BOX_HALO box");
+  return MK_OK;
+}
+
+uint64_t tune_key(int n_fft, int variant, int lgn, uint32_t flags) {
+  return (static_cast<uint64_t>(n_fft) << 32) | (static_cast<uint64_t>(variant) << 16) |
+         (static_cast<uint64_t>(lgn > 10) << 8) | (flags & (MK_STORE_FIELDS | MK_STORE_FLUX | MK_STATS));
 }
 
 int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads) {
@@ -614,7 +627,7 @@ int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float 
   if (!(desc->cell > 0.0)) return fail(ctx, MK_EINVAL, "cell must be > 0");
   if (desc->layout == MK_BOX_PLANAR) {
     if (!d_delta || !d_eta) return fail(ctx, MK_EINVAL, "planar box needs d_delta and d_eta");
-  } else if (desc->layout == MK_BOX_INTERLEAVED || desc->layout == MK_BOX_PADDED) {
+  } else if (desc->layout == MK_BOX_INTERLEAVED || desc->layout == MK_BOX_PADDED || desc->layout == MK_BOX_HALO) {
     if (!d_delta || d_eta) return fail(ctx, MK_EINVAL, "paired box: d_delta holds pairs, d_eta must be NULL");
     if (reinterpret_cast<uintptr_t>(d_delta) % 8) return fail(ctx, MK_EINVAL, "paired box must be 8-byte aligned");
   } else {
@@ -652,6 +665,18 @@ int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float
   return MK_OK;
 }
 
+int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out) {
+  if (!ctx) return MK_EINVAL;
+  if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
+  if (!d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
+  if (reinterpret_cast<uintptr_t>(d_out) % 8) return fail(ctx, MK_EINVAL, "d_out must be 8-byte aligned");
+  int lgn = 0;
+  while ((1 << lgn) < n) ++lgn;
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_pack_halo(d_delta, d_eta, lgn, d_out, ctx->sms, ctx->stream));
+  return MK_OK;
+}
+
 int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
                     const mk_skewer_params *params, mk_skewer *d_sk, int64_t *d_offsets, float *d_delta_out,
                     float *d_eta_out, int64_t capacity_px, int64_t *h_total_px) {
@@ -660,6 +685,7 @@ int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t
   if (rc) return rc;
   if (!box || n_qso < 0 || (n_qso > 0 && !d_qso) || !d_sk || !d_offsets)
     return fail(ctx, MK_EINVAL, "bad box, catalogue or skewer arguments");
+  if ((rc = check_interp(ctx, box, params))) return rc;
   if ((d_delta_out == nullptr) != (d_eta_out == nullptr))
     return fail(ctx, MK_EINVAL, "d_delta_out and d_eta_out go together");
   CK(cudaSetDevice(ctx->device));
@@ -684,9 +710,10 @@ int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t
   S.capacity = capacity_px;
   S.do_stats = 0;
   const LaunchCfg cfg = default_cfg(params->n_fft);
-  const int grid = skewer_grid(ctx, params->n_fft, box, cfg, nullptr);
+  const int variant = kernel_variant(box, params);
+  const int grid = skewer_grid(ctx, params->n_fft, variant, box->lgn, cfg, nullptr);
   if ((rc = time_begin(ctx))) return rc;
-  CK(launch_skewer(S, params->n_fft, box->desc.layout, cfg.minb, grid, cfg.threads, ctx->stream));
+  CK(launch_skewer(S, params->n_fft, variant, cfg.minb, grid, cfg.threads, ctx->stream));
   return time_end(ctx);
 }
 
@@ -813,6 +840,7 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
   }
   if (!box || n_qso < 0 || (n_qso > 0 && !d_qso) || !d_sk || !d_offsets)
     return fail(ctx, MK_EINVAL, "bad box, catalogue or skewer arguments");
+  if ((rc = check_interp(ctx, box, params))) return rc;
   if ((flags & MK_STORE_FIELDS) && (!d_delta_out || !d_eta_out))
     return fail(ctx, MK_EINVAL, "MK_STORE_FIELDS needs d_delta_out and d_eta_out");
   if ((flags & MK_STORE_FLUX) && !d_flux_out) return fail(ctx, MK_EINVAL, "MK_STORE_FLUX needs d_flux_out");
@@ -827,7 +855,8 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
   const StatLayout L{stats ? bins->n_z : 0, stats ? bins->n_k : 0};
 
   // the launch shape: tuned, or tune now, or the default
-  const uint64_t key = tune_key(params->n_fft, box, flags);
+  const int variant = kernel_variant(box, params);
+  const uint64_t key = tune_key(params->n_fft, variant, box->lgn, flags);
   LaunchCfg cfg = default_cfg(params->n_fft);
   auto it = ctx->tuned.find(key);
   if (it != ctx->tuned.end()) cfg = it->second;
@@ -852,7 +881,7 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
     if (r) return r;
     S.partials = ctx->d_partials;
     if (timed && (r = time_begin(ctx))) return r;
-    CK(launch_skewer(S, params->n_fft, box->desc.layout, c.minb, grid, c.threads, ctx->stream));
+    CK(launch_skewer(S, params->n_fft, variant, c.minb, grid, c.threads, ctx->stream));
     if (timed && (r = time_end(ctx))) return r;
     if (stats) {
       CK(launch_finalize(ctx->d_partials, grid, bins->n_z, bins->n_k, bins->n_fft, ctx->d_stats, ctx->stream));
@@ -877,14 +906,14 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
     float best = 1e30f;
     for (const LaunchCfg &c : cand) {
       if (c.threads < params->n_fft / 8) continue;  // a team must fit in a CTA
-      const int grid = skewer_grid(ctx, params->n_fft, box, c, stats ? bins : nullptr);
+      const int grid = skewer_grid(ctx, params->n_fft, variant, box->lgn, c, stats ? bins : nullptr);
       if ((rc = ensure_partials(grid))) break;
       if ((rc = enqueue_geometry(ctx, G, d_qso, n_qso, d_sk, d_offsets))) break;
       S.partials = ctx->d_partials;
       float ms = 0.f;
       for (int rep = 0; rep < 2 && rc == MK_OK; ++rep) {  // first launch warms caches
         if (cudaEventRecord(a0, ctx->stream) != cudaSuccess ||
-            launch_skewer(S, params->n_fft, box->desc.layout, c.minb, grid, c.threads, ctx->stream) != cudaSuccess ||
+            launch_skewer(S, params->n_fft, variant, c.minb, grid, c.threads, ctx->stream) != cudaSuccess ||
             cudaEventRecord(a1, ctx->stream) != cudaSuccess || cudaEventSynchronize(a1) != cudaSuccess ||
             cudaEventElapsedTime(&ms, a0, a1) != cudaSuccess)
           rc = fail(ctx, MK_ECUDA, "autotune launch failed: %s", cudaGetErrorString(cudaGetLastError()));
@@ -901,7 +930,7 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
     ctx->tuned[key] = cfg;
   }
 
-  const int grid = skewer_grid(ctx, params->n_fft, box, cfg, stats ? bins : nullptr);
+  const int grid = skewer_grid(ctx, params->n_fft, variant, box->lgn, cfg, stats ? bins : nullptr);
   if ((rc = ensure_partials(grid))) return rc;
 
   if (flags & MK_GRAPH) {
@@ -982,6 +1011,7 @@ int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_q
   }
   if (!box || n_qso < 0 || (n_qso > 0 && !h_qso) || !h_flux_out || !h_total_px)
     return fail(ctx, MK_EINVAL, "bad box, catalogue or output arguments");
+  if ((rc = check_interp(ctx, box, params))) return rc;
   if (n_chunks < 1 || n_chunks > MK_MAX_CHUNKS) return fail(ctx, MK_EINVAL, "n_chunks must be in [1, %d]", MK_MAX_CHUNKS);
   CK(cudaSetDevice(ctx->device));
   if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_qso)) ||
@@ -1018,9 +1048,10 @@ int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_q
 
   const uint32_t kflags = MK_STORE_FLUX | (stats ? MK_STATS : 0u);
   LaunchCfg cfg = default_cfg(params->n_fft);
-  auto it = ctx->tuned.find(tune_key(params->n_fft, box, kflags));
+  const int variant = kernel_variant(box, params);
+  auto it = ctx->tuned.find(tune_key(params->n_fft, variant, box->lgn, kflags));
   if (it != ctx->tuned.end()) cfg = it->second;
-  const int grid = skewer_grid(ctx, params->n_fft, box, cfg, stats ? bins : nullptr);
+  const int grid = skewer_grid(ctx, params->n_fft, variant, box->lgn, cfg, stats ? bins : nullptr);
   const StatLayout L{stats ? bins->n_z : 0, stats ? bins->n_k : 0};
   if (stats && (rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
                           sizeof(double) * static_cast<size_t>(grid) * K * L.size())))
@@ -1050,7 +1081,7 @@ int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_q
       S.flux_out = reinterpret_cast<float *>(reinterpret_cast<uintptr_t>(stage) - sizeof(float) * p0);
       S.capacity = p1;
       S.partials = stats ? ctx->d_partials + static_cast<size_t>(k) * grid * L.size() : nullptr;
-      CK(launch_skewer(S, params->n_fft, box->desc.layout, cfg.minb, grid, cfg.threads, s0));
+      CK(launch_skewer(S, params->n_fft, variant, cfg.minb, grid, cfg.threads, s0));
     } else if (stats) {
       CK(cudaMemsetAsync(ctx->d_partials + static_cast<size_t>(k) * grid * L.size(), 0,
                          sizeof(double) * static_cast<size_t>(grid) * L.size(), s0));
@@ -1080,11 +1111,8 @@ int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box
                      int32_t *threads, int32_t *occupancy) {
   if (!ctx || !threads || !occupancy) return MK_EINVAL;
   if (tw_slot(n_fft) < 0) return fail(ctx, MK_EINVAL, "bad n_fft");
-  mk_box b{};
-  b.desc.layout = layout;
-  b.lgn = big_box ? 11 : 10;
   LaunchCfg c = default_cfg(n_fft);
-  auto it = ctx->tuned.find(tune_key(n_fft, &b, flags));
+  auto it = ctx->tuned.find(tune_key(n_fft, layout, big_box ? 11 : 10, flags));
   if (it != ctx->tuned.end()) c = it->second;
   *threads = c.threads;
   *occupancy = c.minb;

@@ -354,6 +354,8 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(
 //   MK_BOX_PADDED: (delta, eta) pairs on (n+1)^3 points whose last plane,
 //   row and column repeat index 0, so the 8 corners sit at fixed offsets
 //   from the base corner and no index wraps.
+//   MK_BOX_HALO: pairs on (n+6)^3 points, a periodic margin of 3 on every
+//   side; the same fixed offsets from base index (x+3, y+3, z+3).
 template <int LAYOUT, bool BIG>
 __device__ __forceinline__ float2 gather(const float *__restrict__ d, const float *__restrict__ e, int lgn,
                                          int64_t px, int64_t py, int64_t pz) {
@@ -362,9 +364,11 @@ __device__ __forceinline__ float2 gather(const float *__restrict__ d, const floa
   const float tx = weight_of(px), ty = weight_of(py), tz = weight_of(pz);
   using I = typename std::conditional<BIG, int64_t, int32_t>::type;
   float2 v[8];
-  if constexpr (LAYOUT == MK_BOX_PADDED) {
-    const I n1 = mask + 2;
-    const float2 *a00 = reinterpret_cast<const float2 *>(d) + ((static_cast<I>(z0) * n1 + y0) * n1 + x0);
+  if constexpr (LAYOUT == MK_BOX_PADDED || LAYOUT == MK_BOX_HALO) {
+    constexpr int h = LAYOUT == MK_BOX_HALO ? 3 : 0;
+    const I n1 = mask + 1 + (LAYOUT == MK_BOX_HALO ? 6 : 1);
+    const float2 *a00 =
+        reinterpret_cast<const float2 *>(d) + ((static_cast<I>(z0 + h) * n1 + (y0 + h)) * n1 + (x0 + h));
     const float2 *a01 = a00 + n1, *a10 = a00 + n1 * n1;
     const float2 *a11 = a10 + n1;
     v[0] = __ldg(a00); v[1] = __ldg(a00 + 1);
@@ -395,6 +399,77 @@ __device__ __forceinline__ float2 gather(const float *__restrict__ d, const floa
   return f2lerp(f2lerp(c0, c1, ty), f2lerp(c2, c3, ty), tz);
 }
 
+// Normalised 1D weights of the Gaussian-kernel average (Sec. 2.3) along one
+// axis: voxels c - 3 .. c + 3 around the voxel c containing the point, whose
+// centre is at distance e = 1/2 - f (f the point's offset inside voxel c, in
+// cells); voxel c + m sits at m + e, w_m ~ exp(-(m + e)^2 / 2).  With
+// q = exp(-e), w_m ~ q^m C_m, C_m = exp(-m^2/2) (the common factor
+// exp(-e^2/2) cancels in the normalisation): two exponentials per axis.
+static __constant__ float kGauss7C[7] = {0.011108996538242306f, 0.13533528323661270f, 0.60653065971263342f, 1.0f,
+                                         0.60653065971263342f, 0.13533528323661270f, 0.011108996538242306f};
+
+// q = exp(-e), qi = 1/q and the reciprocal of sum_m q^m C_m
+__device__ __forceinline__ void gauss7_axis(float f, float &q, float &qi, float &inv) {
+  const float e = 0.5f - f;
+  q = expf(-e);
+  qi = expf(e);
+  const float q2 = q * q, qi2 = qi * qi;
+  const float c1 = kGauss7C[2], c2 = kGauss7C[1], c3 = kGauss7C[0];
+  inv = 1.0f / ((c3 * (qi2 * qi) + c3 * (q2 * q)) + (c2 * qi2 + c2 * q2) + (c1 * qi + c1 * q) + 1.0f);
+}
+
+__device__ __forceinline__ void gauss7_weights(float f, float (&w)[7]) {
+  float q, qi, inv;
+  gauss7_axis(f, q, qi, inv);
+  float pw = qi * qi * qi * inv;  // q^m inv for m = -3
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    w[m] = pw * kGauss7C[m];
+    pw *= q;
+  }
+}
+
+// Gaussian-kernel average of (delta, eta) over 7^3 voxels (Sec. 2.3) from an
+// MK_BOX_HALO box, as three nested 1D contractions (the weights are
+// separable): per z plane, 7 x-rows of 7 pairs contracted with the x weights,
+// then with the y weights; the z weights come as a running product.
+template <bool BIG>
+__device__ __forceinline__ float2 gather_gauss7(const float *__restrict__ d, int lgn, int64_t px, int64_t py,
+                                                int64_t pz) {
+  const int mask = (1 << lgn) - 1;
+  // containing voxel: floor(p + 1/2) of the centre-based coordinate p
+  const int64_t hx = px + (int64_t(1) << 43), hy = py + (int64_t(1) << 43), hz = pz + (int64_t(1) << 43);
+  const int cx = cell_of(hx, mask), cy = cell_of(hy, mask), cz = cell_of(hz, mask);
+  float wx[7], wy[7];
+  gauss7_weights(weight_of(hx), wx);
+  gauss7_weights(weight_of(hy), wy);
+  float qz, qiz, invz;
+  gauss7_axis(weight_of(hz), qz, qiz, invz);
+  float pz_run = qiz * qiz * qiz * invz;
+  using I = typename std::conditional<BIG, int64_t, int32_t>::type;
+  const I n6 = mask + 7;
+  // voxel (c - 3) per axis sits at halo index c
+  const float2 *row = reinterpret_cast<const float2 *>(d) + ((static_cast<I>(cz) * n6 + cy) * n6 + cx);
+  float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 1
+  for (int k = 0; k < 7; ++k) {
+    float2 ay = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      const float2 *r = row + j * n6;
+      float2 ax = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < 7; ++i) ax = f2fma(make_float2(wx[i], wx[i]), __ldg(r + i), ax);
+      ay = f2fma(make_float2(wy[j], wy[j]), ax, ay);
+    }
+    const float wk = pz_run * kGauss7C[k];
+    acc = f2fma(make_float2(wk, wk), ay, acc);
+    pz_run *= qz;
+    row += n6 * n6;
+  }
+  return acc;
+}
+
 // Prefetch into L2 the four voxel rows (y0|y1, z0|z1) that the trilinear
 // stencil at (px, py, pz) reads, for the paired layouts (each row's two
 // corners x0, x0 + 1 are adjacent).
@@ -407,9 +482,10 @@ __device__ __forceinline__ void prefetch_stencil(const float *__restrict__ d, in
   using I = typename std::conditional<BIG, int64_t, int32_t>::type;
   const float2 *b = reinterpret_cast<const float2 *>(d);
   const float2 *a[4];
-  if constexpr (LAYOUT == MK_BOX_PADDED) {
-    const I n1 = mask + 2;
-    a[0] = b + ((static_cast<I>(z0) * n1 + y0) * n1 + x0);
+  if constexpr (LAYOUT == MK_BOX_PADDED || LAYOUT == MK_BOX_HALO) {
+    constexpr int h = LAYOUT == MK_BOX_HALO ? 3 : 0;
+    const I n1 = mask + 1 + (LAYOUT == MK_BOX_HALO ? 6 : 1);
+    a[0] = b + ((static_cast<I>(z0 + h) * n1 + (y0 + h)) * n1 + (x0 + h));
     a[1] = a[0] + n1;
     a[2] = a[0] + n1 * n1;
     a[3] = a[2] + n1;

@@ -266,6 +266,17 @@ __global__ void k_pack_padded(const float *__restrict__ d, const float *__restri
   }
 }
 
+// (n+6)^3 pairs with a periodic margin of 3 from planar n^3 boxes.
+__global__ void k_pack_halo(const float *__restrict__ d, const float *__restrict__ e, int lgn, float2 *out) {
+  const int64_t n = int64_t(1) << lgn, p = n + 6, total = p * p * p;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t x = i % p - 3, y = (i / p) % p - 3, z = i / (p * p) - 3;
+    const int64_t src = ((z & (n - 1)) << (2 * lgn)) | ((y & (n - 1)) << lgn) | (x & (n - 1));
+    out[i] = make_float2(d[src], e[src]);
+  }
+}
+
 __global__ void k_pack(const float *__restrict__ d, const float *__restrict__ e, int64_t n, float2 *out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -412,6 +423,11 @@ cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t 
   return cudaGetLastError();
 }
 
+cudaError_t launch_pack_halo(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st) {
+  k_pack_halo<<<sms * 8, 256, 0, st>>>(d, e, lgn, reinterpret_cast<float2 *>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st) {
   k_pack_padded<<<sms * 8, 256, 0, st>>>(d, e, lgn, reinterpret_cast<float2 *>(out));
   return cudaGetLastError();
@@ -437,8 +453,8 @@ cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t 
 // ------------------------------------------------------------------ dispatch by FFT length
 #define MK_DECL(NN)                                                                                      \
   size_t skewer_smem_bytes_##NN(int threads, int n_z, int n_k, bool stats);                              \
-  int skewer_blocks_per_sm_##NN(int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats); \
-  cudaError_t launch_skewer_##NN(const SkewerParams &P, int layout, int minb, int grid, int threads,      \
+  int skewer_blocks_per_sm_##NN(int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats); \
+  cudaError_t launch_skewer_##NN(const SkewerParams &P, int variant, int minb, int grid, int threads,      \
                                  cudaStream_t st);                                                      \
   int stats_blocks_per_sm_##NN(int threads, int n_z, int n_k);                                          \
   cudaError_t launch_stats_##NN(const StatParams &P, int grid, int threads, cudaStream_t st);
@@ -463,15 +479,15 @@ size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats) {
 #undef E
 }
 
-int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
-#define E(NN) skewer_blocks_per_sm_##NN(layout, lgn, minb, threads, n_z, n_k, stats)
+int skewer_blocks_per_sm(int n_fft, int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
+#define E(NN) skewer_blocks_per_sm_##NN(variant, lgn, minb, threads, n_z, n_k, stats)
   MK_SWITCH(E, 1)
 #undef E
 }
 
-cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int minb, int grid, int threads,
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int variant, int minb, int grid, int threads,
                           cudaStream_t st) {
-#define E(NN) launch_skewer_##NN(P, layout, minb, grid, threads, st)
+#define E(NN) launch_skewer_##NN(P, variant, minb, grid, threads, st)
   MK_SWITCH(E, cudaErrorInvalidValue)
 #undef E
 }

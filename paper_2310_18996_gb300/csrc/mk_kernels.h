@@ -7,6 +7,8 @@
 
 namespace mk {
 
+constexpr int kGauss7Variant = 16;  // kernel variant bit of MK_INTERP_GAUSS7
+
 cudaError_t launch_geometry(const mk_qso *q, int64_t nq, const GeomParams &P, mk_skewer *sk, int64_t *cnt_px,
                             int64_t *cnt_seg, int *err, cudaStream_t st);
 size_t scan_workspace_bytes(int64_t n);
@@ -19,18 +21,20 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
 cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st);
 cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
+cudaError_t launch_pack_halo(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_jcount(const mk_skewer *sk, int64_t n_sk, int32_t j_max, int32_t *diff, int sms, cudaStream_t st);
 cudaError_t launch_pick(const int64_t *off, int64_t n, int k, int64_t *out, cudaStream_t st);
 cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t *bin_end, cudaStream_t st);
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);
 cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st);
-int skewer_blocks_per_sm(int n_fft, int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
+int skewer_blocks_per_sm(int n_fft, int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
 int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k);
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
+// variant: box layout, plus kGauss7Variant for the Gaussian-kernel interpolation;
 // minb: register budget of the instance, that of minb 256-thread CTAs per SM
 // (2, 3 or 4)
-cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int layout, int minb, int grid, int threads,
+cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int variant, int minb, int grid, int threads,
                           cudaStream_t st);
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st);

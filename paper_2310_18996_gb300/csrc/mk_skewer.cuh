@@ -71,7 +71,8 @@ __device__ __forceinline__ void flush_warp_partials(unsigned char *smem, int nwa
 // the warp's pixels stay in one z bin: the warp flushes them to its shared
 // accumulators when its pixels reach the end of the bin (bin_end) or a
 // segment starts in another bin.
-template <int N, int LAYOUT, bool BIG, int MINB>
+// INTERP: MK_INTERP_TRILINEAR, or MK_INTERP_GAUSS7 (LAYOUT must be MK_BOX_HALO).
+template <int N, int LAYOUT, bool BIG, int MINB, int INTERP = MK_INTERP_TRILINEAR>
 __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
   constexpr int T = N / 8;
   constexpr int BUF = TeamSmem<N>::BUF;
@@ -149,7 +150,13 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
       float f = 0.f;
       float2 x = make_float2(0.f, 0.f);
       if (p < npx) {
-        const float2 de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
+        float2 de;
+        if constexpr (INTERP == MK_INTERP_GAUSS7) {
+          static_assert(LAYOUT == MK_BOX_HALO, "the Gaussian kernel reads a halo box");
+          de = gather_gauss7<BIG>(P.box_d, P.lgn, px, py, pz);
+        } else {
+          de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
+        }
         const float4 tb = __ldg(P.pixtab + jb + p);
         x = make_float2(fmaf(tb.x, de.x, fb[p]), tb.x * de.y);
         f = fgpa(tb, x.x, x.y);

@@ -8,20 +8,22 @@ namespace mk {
 namespace {
 constexpr int NN = 256;
 
-// Calls fn with the kernel instance for (layout, box size, occupancy target).
 // minb: register budget of the instance, that of minb 256-thread CTAs per SM
-template <int L, typename F>
+template <int L, int INTERP, typename F>
 cudaError_t with_layout(bool big, int minb, F &&fn) {
-  if (minb >= 4) return big ? fn(k_skewer<NN, L, true, 4>) : fn(k_skewer<NN, L, false, 4>);
-  if (minb == 3) return big ? fn(k_skewer<NN, L, true, 3>) : fn(k_skewer<NN, L, false, 3>);
-  return big ? fn(k_skewer<NN, L, true, 2>) : fn(k_skewer<NN, L, false, 2>);
+  if (minb >= 4) return big ? fn(k_skewer<NN, L, true, 4, INTERP>) : fn(k_skewer<NN, L, false, 4, INTERP>);
+  if (minb == 3) return big ? fn(k_skewer<NN, L, true, 3, INTERP>) : fn(k_skewer<NN, L, false, 3, INTERP>);
+  return big ? fn(k_skewer<NN, L, true, 2, INTERP>) : fn(k_skewer<NN, L, false, 2, INTERP>);
 }
 
+// Calls fn with the kernel instance for (kernel variant, box size, register budget).
 template <typename F>
-cudaError_t with_skewer_kernel(int layout, bool big, int minb, F &&fn) {
-  if (layout == MK_BOX_PADDED) return with_layout<MK_BOX_PADDED>(big, minb, fn);
-  if (layout == MK_BOX_INTERLEAVED) return with_layout<MK_BOX_INTERLEAVED>(big, minb, fn);
-  return with_layout<MK_BOX_PLANAR>(big, minb, fn);
+cudaError_t with_skewer_kernel(int variant, bool big, int minb, F &&fn) {
+  if (variant & kGauss7Variant) return with_layout<MK_BOX_HALO, MK_INTERP_GAUSS7>(big, minb, fn);
+  if (variant == MK_BOX_HALO) return with_layout<MK_BOX_HALO, MK_INTERP_TRILINEAR>(big, minb, fn);
+  if (variant == MK_BOX_PADDED) return with_layout<MK_BOX_PADDED, MK_INTERP_TRILINEAR>(big, minb, fn);
+  if (variant == MK_BOX_INTERLEAVED) return with_layout<MK_BOX_INTERLEAVED, MK_INTERP_TRILINEAR>(big, minb, fn);
+  return with_layout<MK_BOX_PLANAR, MK_INTERP_TRILINEAR>(big, minb, fn);
 }
 
 template <typename K>
@@ -37,19 +39,19 @@ size_t skewer_smem_bytes_256(int threads, int n_z, int n_k, bool stats) {
   return TeamSmem<NN>::bytes(threads, n_z, n_k, stats);
 }
 
-int skewer_blocks_per_sm_256(int layout, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
+int skewer_blocks_per_sm_256(int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
   const size_t smem = TeamSmem<NN>::bytes(threads, n_z, n_k, stats);
   int b = 1;
-  with_skewer_kernel(layout, lgn > 10, minb, [&](auto kern) {
+  with_skewer_kernel(variant, lgn > 10, minb, [&](auto kern) {
     b = occupancy(kern, threads, smem);
     return cudaSuccess;
   });
   return b;
 }
 
-cudaError_t launch_skewer_256(const SkewerParams &P, int layout, int minb, int grid, int threads, cudaStream_t st) {
+cudaError_t launch_skewer_256(const SkewerParams &P, int variant, int minb, int grid, int threads, cudaStream_t st) {
   const size_t smem = TeamSmem<NN>::bytes(threads, P.n_z, P.n_k, P.do_stats != 0);
-  return with_skewer_kernel(layout, P.lgn > 10, minb, [&](auto kern) {
+  return with_skewer_kernel(variant, P.lgn > 10, minb, [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<grid, threads, smem, st>>>(P);

@@ -63,6 +63,8 @@ def load(ctx, w, d, e, layout):
         return ctx.load_box(w, d, e)
     if layout == "interleaved":
         return ctx.load_box(w, ctx.pack_box(d, e), None)
+    if layout == "halo":
+        return ctx.load_box(w, ctx.pack_box(d, e, halo=True), None, layout=mk.BOX_HALO)
     return ctx.load_box(w, ctx.pack_box(d, e, padded=True), None, layout=mk.BOX_PADDED)
 
 
@@ -77,7 +79,18 @@ def test_padded_pack_repeats_the_periodic_box(ctx, tiny):
     assert torch.equal(p[..., 0], ref_d) and torch.equal(p[..., 1], ref_e)
 
 
-@pytest.mark.parametrize("layout", ["planar", "interleaved", "padded"])
+def test_halo_pack_repeats_the_periodic_box(ctx, tiny):
+    d, e = tiny["dev"]["d"], tiny["dev"]["e"]
+    n = tiny["w"]["n"]
+    p = ctx.pack_box(d, e, halo=True).view(n + 6, n + 6, n + 6, 2)
+    torch.cuda.synchronize()
+    idx = (torch.arange(n + 6, device="cuda") - 3) % n
+    ref_d = d.view(n, n, n)[idx][:, idx][:, :, idx]
+    ref_e = e.view(n, n, n)[idx][:, idx][:, :, idx]
+    assert torch.equal(p[..., 0], ref_d) and torch.equal(p[..., 1], ref_e)
+
+
+@pytest.mark.parametrize("layout", ["planar", "interleaved", "padded", "halo"])
 def test_pre_fgpa_fields_match_oracle(ctx, tiny, layout):
     w, o, dv = tiny["w"], tiny["orc"], tiny["dev"]
     box = load(ctx, w, dv["d"], dv["e"], layout)
@@ -189,6 +202,41 @@ def test_segments_crossing_many_z_bins(ctx, tiny, n_fft):
     st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w, flags=mk.STATS | mk.STORE_FLUX)
     assert_flux_close(g["flux"][:o["offsets"][-1]].cpu().numpy(), o["flux"])
     assert_stats_close(st, so)
+
+
+# ------------------------------------------------------------------ Gaussian-kernel interpolation (Sec. 2.3)
+@pytest.mark.parametrize("n_fft,step", [(256, 1), (1024, 5)])
+def test_gauss7_path_matches_oracle(ctx, tiny, n_fft, step):
+    w = si.shrink(tiny["w"], n_fft=n_fft, interp=mk.INTERP_GAUSS7)
+    idx = np.arange(0, 500, step)
+    pos, ids = tiny["pos"][idx], tiny["ids"][idx]
+    o = oracle.run_skewers(w, tiny["d"], tiny["e"], pos, ids, n_threads=16)
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    box = load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], "halo")
+    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w,
+                    flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
+    tot = o["offsets"][-1]
+    assert_field_close(g["delta"][:tot].cpu().numpy(), o["delta"], "delta_tot")
+    assert_field_close(g["eta"][:tot].cpu().numpy(), o["eta"], "eta")
+    assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
+    assert_stats_close(st, so, check_fields=(step == 1))
+    # the Gaussian average smooths: its eta differs from trilinear's
+    w_tri = dict(w)
+    w_tri["interp"] = mk.INTERP_TRILINEAR
+    _, gt = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w_tri, flags=mk.STORE_FIELDS)
+    assert not torch.equal(gt["eta"][:tot], g["eta"][:tot])
+
+
+def test_gauss7_needs_a_halo_box(ctx, tiny):
+    w = si.shrink(tiny["w"], interp=mk.INTERP_GAUSS7)
+    box = load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], "padded")
+    with pytest.raises(mk.MkError) as e:
+        ctx.run(box, tiny["dev"]["qso"], 10, w)
+    assert e.value.code == mk.MK_EINVAL
+    bad = dict(w)
+    bad["interp"] = 2
+    with pytest.raises(mk.MkError):
+        ctx.run(load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], "halo"), tiny["dev"]["qso"], 10, bad)
 
 
 def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
@@ -358,14 +406,14 @@ def test_invalid_arguments(ctx, tiny):
 
 
 # ------------------------------------------------------------------ full-size workloads, sampled
-def _full_size_check(ctx, w, n_sample, seed, lognormal=False):
+def _full_size_check(ctx, w, n_sample, seed, lognormal=False, layout="padded"):
     torch.cuda.empty_cache()
     d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"], backend="torch")
     dh = d.cpu().numpy()
     pos, ids = si.catalogue(w, delta=dh if lognormal else None)
     qso = mk.catalogue_tensor(pos, ids)
     eh = e.cpu().numpy()
-    box = ctx.load_box(w, ctx.pack_box(d, e, padded=True), None, layout=mk.BOX_PADDED)
+    box = load(ctx, w, d, e, layout)
     del d, e
     st, g = ctx.run(box, qso, len(ids), w, flags=mk.STATS | mk.STORE_FLUX | mk.STORE_FIELDS)
     rec = records(g["sk"], len(ids))
@@ -418,3 +466,8 @@ def test_scale_workload_sampled(ctx):
 
 def test_batched_workload_sampled(ctx):
     _full_size_check(ctx, si.workload("batched"), 40, 6)
+
+
+def test_batched_workload_sampled_gauss7(ctx):
+    w = si.shrink(si.workload("batched"), interp=mk.INTERP_GAUSS7)
+    _full_size_check(ctx, w, 24, 7, layout="halo")
