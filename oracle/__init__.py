@@ -50,7 +50,7 @@ class Cfg(C.Structure):
         ("dr", C.c_double), ("lrf_min", C.c_double), ("lrf_max", C.c_double),
         ("lobs_min", C.c_double), ("n_min", C.c_int32), ("n_max", C.c_int32),
         ("n_fft", C.c_int32), ("p_s", C.POINTER(C.c_double)), ("seed", C.c_uint32),
-        ("interp", C.c_int32),
+        ("interp", C.c_int32), ("eta_mode", C.c_int32),
     ]
 
 
@@ -209,6 +209,7 @@ def make_cfg(w):
     cfg.p_s = _p(ps, C.c_double)
     cfg.seed = w["seed_noise"] & 0xFFFFFFFF
     cfg.interp = w.get("interp", 0)
+    cfg.eta_mode = w.get("eta_mode", 0)
     cfg._keep = ps  # keep the table alive with the struct
     return cfg
 

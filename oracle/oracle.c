@@ -392,7 +392,23 @@ int orc_skewer_fields(const orc_cfg *cfg, const float *dbox, const float *ebox,
     double g = orc_growth(cfg->omega_m, zj);
     if (delta_lg)
       delta_lg[j] = g * (cfg->interp ? orc_gauss7(dbox, cfg->n, c) : orc_trilinear(dbox, cfg->n, c));
-    if (eta_g) eta_g[j] = g * (cfg->interp ? orc_gauss7(ebox, cfg->n, c) : orc_trilinear(ebox, cfg->n, c));
+    if (eta_g) {
+      if (cfg->eta_mode) {
+        /* eta_par = u_p u_q eta_pq over the symmetric tensor (Eq. eta) */
+        static const int pq[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+        const int64_t n3 = (int64_t)cfg->n * cfg->n * cfg->n;
+        double e = 0.0;
+        for (int k = 0; k < 6; ++k) {
+          const float *bk = ebox + k * n3;
+          double v = cfg->interp ? orc_gauss7(bk, cfg->n, c) : orc_trilinear(bk, cfg->n, c);
+          double w = u[pq[k][0]] * u[pq[k][1]] * (pq[k][0] == pq[k][1] ? 1.0 : 2.0);
+          e += w * v;
+        }
+        eta_g[j] = g * e;
+      } else {
+        eta_g[j] = g * (cfg->interp ? orc_gauss7(ebox, cfg->n, c) : orc_trilinear(ebox, cfg->n, c));
+      }
+    }
     if (delta_s) {
       if (j / nf != cur) {
         cur = j / nf;

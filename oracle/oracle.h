@@ -49,6 +49,11 @@ typedef struct orc_cfg {
   /* interpolation of delta_L and eta at a pixel: 0 trilinear between voxel
      centres, 1 the Gaussian-kernel average over 7^3 voxels of Sec. 2.3 */
   int32_t interp;
+  /* eta_par at a pixel: 0 the single box ebox taken as the line-of-sight
+     gradient; 1 ebox holds the six boxes eta_pq (xx, yy, zz, xy, xz, yz, each
+     n^3, consecutive) and eta_par = u_p u_q eta_pq with u the unit vector to
+     the quasar (Eq. eta) */
+  int32_t eta_mode;
 } orc_cfg;
 
 /* FGPA parameter nodes (Sec. 2.5: tuned at a few z, interpolated between). */

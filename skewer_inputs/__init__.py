@@ -157,6 +157,77 @@ def _box_torch(n, cell, seed, device):
     return delta.contiguous(), eta.contiguous()
 
 
+ETA_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))  # xx, yy, zz, xy, xz, yz
+
+
+def _tensor_numpy(n, cell, seed):
+    delta, eta_xx = _box_numpy(n, cell, seed)
+    rng = np.random.default_rng(seed)
+    wn = rng.standard_normal((n, n, n))
+    wk = np.fft.rfftn(wn)
+    kx = 2.0 * np.pi * np.fft.rfftfreq(n, d=cell)
+    ky = 2.0 * np.pi * np.fft.fftfreq(n, d=cell)
+    ks = (kx[None, None, :], ky[None, :, None], ky[:, None, None])  # k_x, k_y, k_z
+    k2 = ks[0] ** 2 + ks[1] ** 2 + ks[2] ** 2
+    p = power_shape(np.sqrt(k2))
+    mult = np.full(kx.size, 2.0)
+    mult[0] = 1.0
+    if n % 2 == 0:
+        mult[-1] = 1.0
+    amp = 1.0 / (np.sum(p * mult[None, None, :]) / (n ** 3 * cell ** 3))
+    dk = wk * np.sqrt(amp * p / cell ** 3)
+    eta = np.empty((6, n, n, n), np.float32)
+    eta[0] = eta_xx
+    with np.errstate(divide="ignore", invalid="ignore"):
+        for c, (a, b) in enumerate(ETA_PAIRS[1:], start=1):
+            m = np.where(k2 > 0, ks[a] * ks[b] / k2, 0.0)
+            eta[c] = np.fft.irfftn(-m * dk, s=(n, n, n), axes=(0, 1, 2)).astype(np.float32)
+    return delta, eta
+
+
+def _tensor_torch(n, cell, seed, device):
+    import torch
+
+    delta, eta_xx = _box_torch(n, cell, seed, device)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    wk = torch.fft.rfftn(torch.randn((n, n, n), generator=g, device=device, dtype=torch.float32))
+    kx = (2.0 * math.pi * torch.fft.rfftfreq(n, d=cell, device=device, dtype=torch.float64))
+    ky = (2.0 * math.pi * torch.fft.fftfreq(n, d=cell, device=device, dtype=torch.float64))
+    ks = (kx[None, None, :], ky[None, :, None], ky[:, None, None])
+    k2 = ks[0] ** 2 + ks[1] ** 2 + ks[2] ** 2
+    k = torch.sqrt(k2)
+    p = torch.where(k > 0, k.pow(0.96) * torch.exp(-(k / 1.5) ** 2)
+                    * (1.0 + 0.05 * torch.sin(150.0 * k)), torch.zeros_like(k))
+    del k
+    mult = torch.full((kx.numel(),), 2.0, device=device, dtype=torch.float64)
+    mult[0] = 1.0
+    mult[-1] = 1.0
+    amp = 1.0 / (torch.sum(p * mult[None, None, :]).item() / (n ** 3 * cell ** 3))
+    wk.mul_(torch.sqrt(amp * p / cell ** 3).to(torch.float32))
+    del p
+    safe = torch.where(k2 > 0, k2, torch.ones_like(k2))
+    eta = torch.empty((6, n, n, n), device=device, dtype=torch.float32)
+    eta[0] = eta_xx
+    del eta_xx
+    for c, (a, b) in enumerate(ETA_PAIRS[1:], start=1):
+        m = torch.where(k2 > 0, ks[a] * ks[b] / safe, torch.zeros_like(k2)).to(torch.float32)
+        eta[c] = torch.fft.irfftn(wk * (-m), s=(n, n, n))
+        del m
+    return delta.contiguous(), eta
+
+
+def gaussian_box_tensor(n, cell=CELL, seed=0, backend="numpy", device="cuda"):
+    """delta and the six velocity-gradient boxes eta_pq = IFFT[-(k_p k_q/k^2) delta_hat]
+    (Eq. eta with the fixtures' sign, f = 1), shape (6, n, n, n) in the order
+    xx, yy, zz, xy, xz, yz.  delta and eta_xx equal gaussian_box's delta and eta."""
+    if backend == "numpy":
+        return _tensor_numpy(n, cell, seed)
+    if backend == "torch":
+        return _tensor_torch(n, cell, seed, device)
+    raise ValueError(backend)
+
+
 def gaussian_box(n, cell=CELL, seed=0, backend="numpy", device="cuda"):
     """(delta, eta) FP32 boxes of shape (n, n, n), index [z][y][x] (x fastest)."""
     if backend == "numpy":

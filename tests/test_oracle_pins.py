@@ -228,6 +228,61 @@ def test_skewer_fields_gauss7_constant_box_is_growth_times_constant():
     np.testing.assert_allclose(o["eta"][:k], -0.25 * g, rtol=1e-12)
 
 
+# ------------------------------------------------------------ radial eta_par from six eta_pq boxes (Eq. eta)
+_PAIRS = ((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))
+
+
+def test_eta_tensor_constant_components_give_u_c_u():
+    w = si.shrink(si.workload("tiny"), eta_mode=1)
+    n = w["n"]
+    cvals = [0.3, -0.2, 0.5, 0.11, -0.07, 0.05]
+    d = np.zeros((n, n, n), np.float32)
+    e6 = np.stack([np.full((n, n, n), v, np.float32) for v in cvals])
+    pos, ids = si.catalogue(w, n_q=4)
+    o = oracle.run_skewers(w, d, e6, pos, ids, n_threads=1)
+    cm = np.zeros((3, 3))
+    for (a, b), v in zip(_PAIRS, np.float32(cvals).astype(np.float64)):
+        cm[a, b] = cm[b, a] = v
+    for q in range(4):
+        u = pos[q] / np.linalg.norm(pos[q])
+        js = range(o["j_lo"][q], o["j_lo"][q] + o["npix"][q])
+        g = np.array([oracle.growth(w["omega_m"], oracle.pixel_z(w, j)) for j in js])
+        np.testing.assert_allclose(o["eta"][o["offsets"][q]:o["offsets"][q + 1]], g * (u @ cm @ u), rtol=1e-12)
+
+
+def test_eta_tensor_isotropic_diagonal_equals_single_box():
+    w1 = si.workload("tiny")
+    w6 = si.shrink(w1, eta_mode=1)
+    d, e = si.gaussian_box(w1["n"], w1["cell"], w1["seed_box"])
+    z = np.zeros_like(e)
+    pos, ids = si.catalogue(w1, n_q=6)
+    o1 = oracle.run_skewers(w1, d, e, pos, ids, n_threads=1)
+    o6 = oracle.run_skewers(w6, d, np.stack([e, e, e, z, z, z]), pos, ids, n_threads=1)
+    np.testing.assert_allclose(o6["eta"], o1["eta"], rtol=1e-12, atol=1e-14)
+    np.testing.assert_array_equal(o6["delta"], o1["delta"])
+
+
+def test_eta_tensor_sightline_along_x_reduces_to_xx():
+    w1 = si.workload("tiny")
+    w6 = si.shrink(w1, eta_mode=1)
+    d, e6 = si.gaussian_box_tensor(w1["n"], w1["cell"], w1["seed_box"])
+    pos = np.array([[3900.0, 0.0, 0.0], [4300.0, 0.0, 0.0]])
+    ids = np.array([7, 8], dtype=np.uint64)
+    o1 = oracle.run_skewers(w1, d, e6[0], pos, ids, n_threads=1)
+    o6 = oracle.run_skewers(w6, d, e6, pos, ids, n_threads=1)
+    assert o6["offsets"][-1] > 1000
+    np.testing.assert_allclose(o6["eta"], o1["eta"], rtol=1e-12, atol=1e-14)
+
+
+def test_eta_tensor_inputs_trace_and_xx():
+    d, e = si.gaussian_box(16, seed=5)
+    d2, e6 = si.gaussian_box_tensor(16, seed=5)
+    np.testing.assert_array_equal(d, d2)
+    np.testing.assert_array_equal(e, e6[0])
+    # sum_p k_p k_p / k^2 = 1: the trace is -delta (the zero mode of both vanishes)
+    np.testing.assert_allclose(e6[0] + e6[1] + e6[2], -d, atol=1e-6)
+
+
 # ------------------------------------------------------------ geometry
 def test_geometry_forest_window():
     w = si.workload("tiny")
