@@ -374,40 +374,58 @@ def run_gb300(args, rank, world, local_rank):
             raise RuntimeError("pipelined host flux differs from the device-resident flux")
     e2e_ms, e2e_copy_ms = max_over_ranks([e2e_ms, e2e_copy_ms], dist, dev)
 
+    def variant_leg(wv, box_v, layout_code):
+        """The same fused step on another box layout / interpolation: autotuned
+        launch, kernel-only time, graph-replayed steps."""
+        def vstep(extra=mk.GRAPH):
+            return ctx.run(box_v, qso, n_q, wv, flags=flags | extra, capacity=total, outputs=outs)
+
+        vstep(mk.AUTOTUNE)
+        for _ in range(args.warmup):
+            vstep()
+        vt, vo, _ = ctx.launch_config(w["n_fft"], layout=layout_code, flags=flags)
+        ctx.set_timing(True)
+        vk = []
+        for _ in range(max(3, args.steps // 2)):
+            vstep(0)
+            vk.append(ctx.last_kernel_ms())
+        ctx.set_timing(False)
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        v0.record(stream)
+        for _ in range(args.steps):
+            vstep()
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vms, vkms = max_over_ranks([v0.elapsed_time(v1) / args.steps, float(np.mean(vk))], dist, dev)
+        return {"value": world * total / (vms / 1000.0), "unit": UNIT, "ms_per_step": vms, "kernel_ms": vkms,
+                "launch": f"{vt} threads/CTA, occupancy target {vo}"}
+
     # the paper's Gaussian-kernel interpolation (7^3 voxels, Sec. 2.3) on the
     # same catalogue: the same fused step with the other gather
     gauss = None
     if halo is not None:
         wg = dict(w)
         wg["interp"] = mk.INTERP_GAUSS7
-        box_g = ctx.load_box(wg, halo, None, layout=mk.BOX_HALO)
-
-        def gstep(extra=mk.GRAPH):
-            return ctx.run(box_g, qso, n_q, wg, flags=flags | extra, capacity=total, outputs=outs)
-
-        gstep(mk.AUTOTUNE)
-        for _ in range(args.warmup):
-            gstep()
-        gt, go, _ = ctx.launch_config(w["n_fft"], layout=mk.BOX_HALO + mk.GAUSS7_VARIANT, flags=flags)
-        ctx.set_timing(True)
-        gk = []
-        for _ in range(max(3, args.steps // 2)):
-            gstep(0)
-            gk.append(ctx.last_kernel_ms())
-        ctx.set_timing(False)
+        gauss = variant_leg(wg, ctx.load_box(wg, halo, None, layout=mk.BOX_HALO), mk.BOX_HALO + mk.GAUSS7_VARIANT)
+        gauss.update({"interp": "Gaussian kernel over 7^3 voxels, sigma = one voxel (Sec. 2.3)",
+                      "box": f"{w['n']}^3 (delta, eta) pairs with a periodic margin of 3"})
+        del halo
+        torch.cuda.empty_cache()
+    # the radial eta_par of Eq. eta from the six velocity-gradient boxes
+    tens = None
+    if not args.no_tensor:
+        wt = dict(w)
+        wt["eta_mode"] = 1
+        td, te6 = si.gaussian_box_tensor(w["n"], w["cell"], w["seed_box"], backend="torch", device=dev)
+        tpacked = ctx.pack_box_tensor(td, te6)
         torch.cuda.synchronize()
-        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
-        for _ in range(args.steps):
-            gstep()
-        g1.record(stream)
-        torch.cuda.synchronize()
-        gms, gkms = max_over_ranks([g0.elapsed_time(g1) / args.steps, float(np.mean(gk))], dist, dev)
-        gauss = {"interp": "Gaussian kernel over 7^3 voxels, sigma = one voxel (Sec. 2.3)",
-                 "value": world * total / (gms / 1000.0), "unit": UNIT, "ms_per_step": gms, "kernel_ms": gkms,
-                 "kernel": f"k_skewer<256,halo,gauss7> {gt} threads/CTA, occupancy target {go}",
-                 "box": f"{w['n']}^3 (delta, eta) pairs with a periodic margin of 3"}
-        del box_g, halo
+        del td, te6
+        torch.cuda.empty_cache()
+        tens = variant_leg(wt, ctx.load_box(wt, tpacked, None, layout=mk.BOX_TENSOR), mk.BOX_TENSOR)
+        tens.update({"eta": "u_p u_q eta_pq from six velocity-gradient boxes (Eq. eta), trilinear",
+                     "box": f"{w['n']}^3 points of (delta, 6 eta_pq), 32 B each"})
+        del tpacked
         torch.cuda.empty_cache()
 
     peak, peak_kind = measured_peaks()
@@ -456,6 +474,8 @@ def run_gb300(args, rank, world, local_rank):
             line["tuning"] = tune
         if gauss:
             line["gauss7"] = gauss
+        if tens:
+            line["eta_tensor"] = tens
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -473,6 +493,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=8)
     ap.add_argument("--no-gauss7", action="store_true")
+    ap.add_argument("--no-tensor", action="store_true")
     ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--surrogate-draws", type=int, default=4000)
     ap.add_argument("--surrogate-epochs", type=int, default=200)

@@ -73,6 +73,11 @@ extern "C" {
                                 index (x+3) + (n+6) ((y+3) + (n+6) (z+3)), periodic copies
                                 (required by MK_INTERP_GAUSS7, usable by trilinear) */
 
+#define MK_BOX_TENSOR 4      /* delta and the six velocity-gradient boxes of Eq. eta, 8 floats
+                                per point {delta, eta_xx, eta_yy, eta_zz, eta_xy, eta_xz, eta_yz, 0}
+                                on (n+1)^3 points as MK_BOX_PADDED, 16-byte aligned; each sight
+                                line takes eta_par = u_p u_q eta_pq (trilinear only) */
+
 /* Interpolation of delta_L and eta at a pixel (mk_skewer_params.interp). */
 #define MK_INTERP_TRILINEAR 0 /* between the 8 surrounding voxel centres */
 #define MK_INTERP_GAUSS7 1    /* Sec. 2.3: Gaussian-kernel average over the 7^3 voxels around
@@ -100,7 +105,7 @@ typedef struct mk_cosmo {
 /* Box of n^3 cubic cells (n a power of two, 2..2048), periodic. */
 typedef struct mk_box_desc {
   int32_t n;
-  int32_t layout;   /* MK_BOX_PLANAR, MK_BOX_INTERLEAVED, MK_BOX_PADDED or MK_BOX_HALO */
+  int32_t layout;   /* MK_BOX_PLANAR, MK_BOX_INTERLEAVED, MK_BOX_PADDED, MK_BOX_HALO or MK_BOX_TENSOR */
   double cell;      /* cell side [Mpc/h] */
   double origin[3]; /* corner of the box in the observer frame [Mpc/h] */
 } mk_box_desc;
@@ -199,7 +204,8 @@ int mk_sync(mk_ctx *ctx);
    component eta_par).  MK_BOX_PLANAR: d_delta and d_eta each n^3 floats.
    MK_BOX_INTERLEAVED: d_delta holds 2 n^3 floats (delta, eta) per cell and
    d_eta must be NULL.  MK_BOX_PADDED / MK_BOX_HALO: d_delta holds the pairs of
-   that layout (8-byte aligned), d_eta NULL.  The memory must outlive the box.  Synchronous. */
+   that layout (8-byte aligned), d_eta NULL.  MK_BOX_TENSOR: d_delta holds
+   8 (n+1)^3 floats (16-byte aligned), d_eta NULL.  The memory must outlive the box.  Synchronous. */
 int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float *d_delta,
                 const float *d_eta);
 void mk_free_box(mk_box *box);
@@ -222,6 +228,14 @@ int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float
    index wrap.  No counterpart in the paper (a storage choice).  Asynchronous
    on the context stream.  MK_EINVAL as mk_pack_box_padded. */
 int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out);
+
+/* Pack delta (n^3 floats) and the six planar boxes eta_pq (6 n^3 floats in
+   the order xx, yy, zz, xy, xz, yz; Eq. eta) into the MK_BOX_TENSOR layout:
+   d_out (caller-owned, 16-byte aligned) receives 8 (n+1)^3 floats.  The paper
+   keeps the six boxes separately (Sec. 2.1); one 32-byte record per point
+   lets a corner be read with two 16-byte loads.  Asynchronous on the context
+   stream.  MK_EINVAL as mk_pack_box_padded, or d_out not 16-byte aligned. */
+int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta6, float *d_out);
 
 /* ---------------------------------------------------------------- skewers */
 

@@ -21,13 +21,13 @@ from . import build as _build
 MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
 MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
 STATIC_MAX_SKEWERS = 131072
-BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED, BOX_HALO = 0, 1, 2, 3
+BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED, BOX_HALO, BOX_TENSOR = 0, 1, 2, 3, 4
 INTERP_TRILINEAR, INTERP_GAUSS7 = 0, 1
 GAUSS7_VARIANT = 16  # mk_launch_config: layout + 16 for the Gaussian-kernel instance
 STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
-           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_pack_box_halo", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
+           "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_pack_box_halo", "mk_pack_box_tensor", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune"]
@@ -133,6 +133,7 @@ def lib():
                 "mk_pack_box": (C.c_int, [vp, i64, vp, vp, vp]),
                 "mk_pack_box_padded": (C.c_int, [vp, i32, vp, vp, vp]),
                 "mk_pack_box_halo": (C.c_int, [vp, i32, vp, vp, vp]),
+                "mk_pack_box_tensor": (C.c_int, [vp, i32, vp, vp, vp]),
                 "mk_run_host": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(FgpaNodes), P(StatBins), u32,
                                           i32, vp, i64, P(i64), P(StatsOut)]),
                 "mk_make_skewers": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), vp, vp, vp, vp,
@@ -321,6 +322,16 @@ class Context:
             return out
         out = torch.empty(delta.numel() * 2, dtype=torch.float32, device=delta.device)
         self._check(lib().mk_pack_box(self.h, delta.numel(), _ptr(delta), _ptr(eta), _ptr(out)))
+        return out
+
+    def pack_box_tensor(self, delta, eta6):
+        """delta (n^3) and the six eta_pq boxes ((6, n, n, n): xx, yy, zz, xy, xz, yz)
+        into the MK_BOX_TENSOR layout, for load_box(..., layout=BOX_TENSOR)."""
+        torch = self._torch
+        n = round(delta.numel() ** (1.0 / 3.0))
+        out = torch.empty(8 * (n + 1) ** 3, dtype=torch.float32, device=delta.device)
+        self._stream()
+        self._check(lib().mk_pack_box_tensor(self.h, n, _ptr(delta), _ptr(eta6), _ptr(out)))
         return out
 
     # skewers

@@ -627,9 +627,12 @@ int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float 
   if (!(desc->cell > 0.0)) return fail(ctx, MK_EINVAL, "cell must be > 0");
   if (desc->layout == MK_BOX_PLANAR) {
     if (!d_delta || !d_eta) return fail(ctx, MK_EINVAL, "planar box needs d_delta and d_eta");
-  } else if (desc->layout == MK_BOX_INTERLEAVED || desc->layout == MK_BOX_PADDED || desc->layout == MK_BOX_HALO) {
-    if (!d_delta || d_eta) return fail(ctx, MK_EINVAL, "paired box: d_delta holds pairs, d_eta must be NULL");
-    if (reinterpret_cast<uintptr_t>(d_delta) % 8) return fail(ctx, MK_EINVAL, "paired box must be 8-byte aligned");
+  } else if (desc->layout == MK_BOX_INTERLEAVED || desc->layout == MK_BOX_PADDED || desc->layout == MK_BOX_HALO ||
+             desc->layout == MK_BOX_TENSOR) {
+    if (!d_delta || d_eta) return fail(ctx, MK_EINVAL, "packed box: d_delta holds the records, d_eta must be NULL");
+    const int align = desc->layout == MK_BOX_TENSOR ? 16 : 8;
+    if (reinterpret_cast<uintptr_t>(d_delta) % align)
+      return fail(ctx, MK_EINVAL, "packed box must be %d-byte aligned", align);
   } else {
     return fail(ctx, MK_EINVAL, "unknown layout %d", desc->layout);
   }
@@ -674,6 +677,18 @@ int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *
   while ((1 << lgn) < n) ++lgn;
   CK(cudaSetDevice(ctx->device));
   CK(launch_pack_halo(d_delta, d_eta, lgn, d_out, ctx->sms, ctx->stream));
+  return MK_OK;
+}
+
+int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta6, float *d_out) {
+  if (!ctx) return MK_EINVAL;
+  if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
+  if (!d_delta || !d_eta6 || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
+  if (reinterpret_cast<uintptr_t>(d_out) % 16) return fail(ctx, MK_EINVAL, "d_out must be 16-byte aligned");
+  int lgn = 0;
+  while ((1 << lgn) < n) ++lgn;
+  CK(cudaSetDevice(ctx->device));
+  CK(launch_pack_tensor(d_delta, d_eta6, lgn, d_out, ctx->sms, ctx->stream));
   return MK_OK;
 }
 

@@ -399,6 +399,43 @@ __device__ __forceinline__ float2 gather(const float *__restrict__ d, const floa
   return f2lerp(f2lerp(c0, c1, ty), f2lerp(c2, c3, ty), tz);
 }
 
+// Trilinear (delta, eta_par) from an MK_BOX_TENSOR box: all seven fields are
+// interpolated (x, then y, then z, on packed pairs) and the velocity-gradient
+// tensor is contracted with the sight line, eta_par = u_p u_q eta_pq (Eq. eta);
+// uu = {ux^2, uy^2, uz^2, 2 ux uy, 2 ux uz, 2 uy uz}.
+struct F7 {
+  float2 a, b, c;  // (delta, xx), (yy, zz), (xy, xz)
+  float d;         // yz
+};
+__device__ __forceinline__ F7 lerp7(const F7 &p, const F7 &q, float t) {
+  return F7{f2lerp(p.a, q.a, t), f2lerp(p.b, q.b, t), f2lerp(p.c, q.c, t), lerpf(p.d, q.d, t)};
+}
+// the two points (x0, x0 + 1) of a row, lerped in x
+__device__ __forceinline__ F7 tensor_row(const float4 *r, float tx) {
+  const float4 a0 = __ldg(r), b0 = __ldg(r + 1), a1 = __ldg(r + 2), b1 = __ldg(r + 3);
+  const F7 p{make_float2(a0.x, a0.y), make_float2(a0.z, a0.w), make_float2(b0.x, b0.y), b0.z};
+  const F7 q{make_float2(a1.x, a1.y), make_float2(a1.z, a1.w), make_float2(b1.x, b1.y), b1.z};
+  return lerp7(p, q, tx);
+}
+
+template <bool BIG>
+__device__ __forceinline__ float2 gather_tensor(const float *__restrict__ d, int lgn, int64_t px, int64_t py,
+                                                int64_t pz, const float (&uu)[6]) {
+  const int mask = (1 << lgn) - 1;
+  const int x0 = cell_of(px, mask), y0 = cell_of(py, mask), z0 = cell_of(pz, mask);
+  const float tx = weight_of(px), ty = weight_of(py), tz = weight_of(pz);
+  using I = typename std::conditional<BIG, int64_t, int32_t>::type;
+  const I n1 = mask + 2;
+  const float4 *b = reinterpret_cast<const float4 *>(d);
+  const I i00 = (static_cast<I>(z0) * n1 + y0) * n1 + x0;
+  const F7 c0 = tensor_row(b + 2 * i00, tx), c1 = tensor_row(b + 2 * (i00 + n1), tx);
+  const F7 c2 = tensor_row(b + 2 * (i00 + n1 * n1), tx), c3 = tensor_row(b + 2 * (i00 + n1 * n1 + n1), tx);
+  const F7 v = lerp7(lerp7(c0, c1, ty), lerp7(c2, c3, ty), tz);
+  const float eta = fmaf(uu[0], v.a.y, fmaf(uu[1], v.b.x, fmaf(uu[2], v.b.y,
+                    fmaf(uu[3], v.c.x, fmaf(uu[4], v.c.y, uu[5] * v.d)))));
+  return make_float2(v.a.x, eta);
+}
+
 // Normalised 1D weights of the Gaussian-kernel average (Sec. 2.3) along one
 // axis: voxels c - 3 .. c + 3 around the voxel c containing the point, whose
 // centre is at distance e = 1/2 - f (f the point's offset inside voxel c, in
@@ -477,6 +514,18 @@ template <int LAYOUT, bool BIG>
 __device__ __forceinline__ void prefetch_stencil(const float *__restrict__ d, int lgn, int64_t px, int64_t py,
                                                  int64_t pz) {
   if constexpr (LAYOUT == MK_BOX_PLANAR) return;
+  if constexpr (LAYOUT == MK_BOX_TENSOR) {
+    const int mask = (1 << lgn) - 1;
+    const int x0 = cell_of(px, mask), y0 = cell_of(py, mask), z0 = cell_of(pz, mask);
+    using I = typename std::conditional<BIG, int64_t, int32_t>::type;
+    const I n1 = mask + 2;
+    const float4 *b = reinterpret_cast<const float4 *>(d);
+    const I i00 = (static_cast<I>(z0) * n1 + y0) * n1 + x0;
+    const I rows[4] = {i00, i00 + n1, i00 + n1 * n1, i00 + n1 * n1 + n1};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) asm volatile("prefetch.global.L2 [%0];" ::"l"(b + 2 * rows[r]));
+    return;
+  }
   const int mask = (1 << lgn) - 1;
   const int x0 = cell_of(px, mask), y0 = cell_of(py, mask), z0 = cell_of(pz, mask);
   using I = typename std::conditional<BIG, int64_t, int32_t>::type;

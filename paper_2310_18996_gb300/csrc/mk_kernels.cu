@@ -277,6 +277,19 @@ __global__ void k_pack_halo(const float *__restrict__ d, const float *__restrict
   }
 }
 
+// (n+1)^3 points of {delta, eta_xx, eta_yy, eta_zz, eta_xy, eta_xz, eta_yz, 0}
+// from planar boxes (e6: six n^3 boxes), periodic ghost layer as k_pack_padded.
+__global__ void k_pack_tensor(const float *__restrict__ d, const float *__restrict__ e6, int lgn, float4 *out) {
+  const int64_t n = int64_t(1) << lgn, n1 = n + 1, total = n1 * n1 * n1, n3 = n * n * n;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t x = i % n1, y = (i / n1) % n1, z = i / (n1 * n1);
+    const int64_t src = ((z & (n - 1)) << (2 * lgn)) | ((y & (n - 1)) << lgn) | (x & (n - 1));
+    out[2 * i] = make_float4(d[src], e6[src], e6[n3 + src], e6[2 * n3 + src]);
+    out[2 * i + 1] = make_float4(e6[3 * n3 + src], e6[4 * n3 + src], e6[5 * n3 + src], 0.f);
+  }
+}
+
 __global__ void k_pack(const float *__restrict__ d, const float *__restrict__ e, int64_t n, float2 *out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -420,6 +433,11 @@ cudaError_t launch_pick(const int64_t *off, int64_t n, int k, int64_t *out, cuda
 
 cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t *bin_end, cudaStream_t st) {
   k_bin_end<<<1, 256, 0, st>>>(zbin, j_max, n_z, bin_end);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_tensor(const float *d, const float *e6, int lgn, float *out, int sms, cudaStream_t st) {
+  k_pack_tensor<<<sms * 8, 256, 0, st>>>(d, e6, lgn, reinterpret_cast<float4 *>(out));
   return cudaGetLastError();
 }
 

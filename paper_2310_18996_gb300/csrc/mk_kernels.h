@@ -21,6 +21,7 @@ cudaError_t launch_pixtab(const double *zpix, const float *gpix, int32_t j_max, 
 cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, double z_lo, double dz, int n_z,
                         int n_seg, int16_t *zbin, int16_t *segzbin, cudaStream_t st);
 cudaError_t launch_pack(const float *d, const float *e, int64_t n, float *out, int sms, cudaStream_t st);
+cudaError_t launch_pack_tensor(const float *d, const float *e6, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_pack_halo(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_jcount(const mk_skewer *sk, int64_t n_sk, int32_t j_max, int32_t *diff, int sms, cudaStream_t st);

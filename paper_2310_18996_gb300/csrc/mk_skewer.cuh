@@ -137,6 +137,20 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
       }
       pend = __ldg(P.bin_end + zc + 1) - jb;
     }
+    // sight-line weights of the velocity-gradient tensor (Eq. eta)
+    float uu[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if constexpr (LAYOUT == MK_BOX_TENSOR) {
+      const float ux = static_cast<float>(sk.step[0]), uy = static_cast<float>(sk.step[1]),
+                  uz = static_cast<float>(sk.step[2]);
+      const float inv = rsqrtf(ux * ux + uy * uy + uz * uz);
+      const float vx = ux * inv, vy = uy * inv, vz = uz * inv;
+      uu[0] = vx * vx;
+      uu[1] = vy * vy;
+      uu[2] = vz * vz;
+      uu[3] = 2.f * vx * vy;
+      uu[4] = 2.f * vx * vz;
+      uu[5] = 2.f * vy * vz;
+    }
     int64_t px = sk.p0[0] + kRoundQ + (j0 + t) * sk.step[0];
     int64_t py = sk.p0[1] + kRoundQ + (j0 + t) * sk.step[1];
     int64_t pz = sk.p0[2] + kRoundQ + (j0 + t) * sk.step[2];
@@ -154,6 +168,8 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
         if constexpr (INTERP == MK_INTERP_GAUSS7) {
           static_assert(LAYOUT == MK_BOX_HALO, "the Gaussian kernel reads a halo box");
           de = gather_gauss7<BIG>(P.box_d, P.lgn, px, py, pz);
+        } else if constexpr (LAYOUT == MK_BOX_TENSOR) {
+          de = gather_tensor<BIG>(P.box_d, P.lgn, px, py, pz, uu);
         } else {
           de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
         }

@@ -21,6 +21,7 @@ template <typename F>
 cudaError_t with_skewer_kernel(int variant, bool big, int minb, F &&fn) {
   if (variant & kGauss7Variant) return with_layout<MK_BOX_HALO, MK_INTERP_GAUSS7>(big, minb, fn);
   if (variant == MK_BOX_HALO) return with_layout<MK_BOX_HALO, MK_INTERP_TRILINEAR>(big, minb, fn);
+  if (variant == MK_BOX_TENSOR) return with_layout<MK_BOX_TENSOR, MK_INTERP_TRILINEAR>(big, minb, fn);
   if (variant == MK_BOX_PADDED) return with_layout<MK_BOX_PADDED, MK_INTERP_TRILINEAR>(big, minb, fn);
   if (variant == MK_BOX_INTERLEAVED) return with_layout<MK_BOX_INTERLEAVED, MK_INTERP_TRILINEAR>(big, minb, fn);
   return with_layout<MK_BOX_PLANAR, MK_INTERP_TRILINEAR>(big, minb, fn);

@@ -239,6 +239,59 @@ def test_gauss7_needs_a_halo_box(ctx, tiny):
         ctx.run(load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], "halo"), tiny["dev"]["qso"], 10, bad)
 
 
+# ------------------------------------------------------------------ radial eta_par from six eta_pq boxes (Eq. eta)
+@pytest.fixture(scope="module")
+def tensor(tiny):
+    w = si.shrink(tiny["w"], eta_mode=1)
+    d, e6 = si.gaussian_box_tensor(w["n"], w["cell"], w["seed_box"])
+    assert np.array_equal(d, tiny["d"])
+    return dict(w=w, d=d, e6=e6, dev_d=torch.from_numpy(d).cuda(), dev_e6=torch.from_numpy(e6).cuda())
+
+
+def test_tensor_pack_layout(ctx, tensor):
+    n = tensor["w"]["n"]
+    p = ctx.pack_box_tensor(tensor["dev_d"], tensor["dev_e6"]).view(n + 1, n + 1, n + 1, 8)
+    torch.cuda.synchronize()
+    idx = torch.arange(n + 1, device="cuda") % n
+    pick = lambda b: b.view(n, n, n)[idx][:, idx][:, :, idx]
+    assert torch.equal(p[..., 0], pick(tensor["dev_d"]))
+    for c in range(6):
+        assert torch.equal(p[..., 1 + c], pick(tensor["dev_e6"][c]))
+    assert torch.count_nonzero(p[..., 7]) == 0
+
+
+def test_tensor_eta_path_matches_oracle(ctx, tiny, tensor):
+    w = tensor["w"]
+    idx = np.arange(0, 500, 2)
+    pos, ids = tiny["pos"][idx], tiny["ids"][idx]
+    o = oracle.run_skewers(w, tensor["d"], tensor["e6"], pos, ids, n_threads=16)
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    box = ctx.load_box(w, ctx.pack_box_tensor(tensor["dev_d"], tensor["dev_e6"]), None, layout=mk.BOX_TENSOR)
+    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w,
+                    flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
+    tot = o["offsets"][-1]
+    assert_field_close(g["delta"][:tot].cpu().numpy(), o["delta"], "delta_tot")
+    assert_field_close(g["eta"][:tot].cpu().numpy(), o["eta"], "eta_par")
+    assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
+    assert_stats_close(st, so, check_fields=False)
+
+
+def test_tensor_isotropic_diagonal_equals_single_box_path(ctx, tiny, tensor):
+    w = tensor["w"]
+    e = tiny["dev"]["e"]
+    z = torch.zeros_like(e)
+    iso = torch.stack([e, e, e, z, z, z])
+    box6 = ctx.load_box(w, ctx.pack_box_tensor(tiny["dev"]["d"], iso), None, layout=mk.BOX_TENSOR)
+    box1 = load(ctx, tiny["w"], tiny["dev"]["d"], e, "padded")
+    n = 100
+    _, g6 = ctx.run(box6, tiny["dev"]["qso"], n, w, flags=mk.STORE_FIELDS)
+    _, g1 = ctx.run(box1, tiny["dev"]["qso"], n, tiny["w"], flags=mk.STORE_FIELDS)
+    tot = int(tiny["orc"]["offsets"][n])
+    assert torch.equal(g6["delta"][:tot], g1["delta"][:tot])
+    # u_x^2 + u_y^2 + u_z^2 = 1 up to FP32 rounding of the weights
+    assert_field_close(g6["eta"][:tot].cpu().numpy(), g1["eta"][:tot].cpu().numpy().astype(np.float64), "eta")
+
+
 def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
     # zero box: delta_tot is delta_S; each segment's DFT over its amplitude gives
     # back the oracle's modes
@@ -466,6 +519,30 @@ def test_scale_workload_sampled(ctx):
 
 def test_batched_workload_sampled(ctx):
     _full_size_check(ctx, si.workload("batched"), 40, 6)
+
+
+def test_scale_workload_sampled_tensor(ctx):
+    w = si.shrink(si.workload("scale"), eta_mode=1)
+    torch.cuda.empty_cache()
+    d, e6 = si.gaussian_box_tensor(w["n"], w["cell"], w["seed_box"], backend="torch")
+    dh, eh = d.cpu().numpy(), e6.cpu().numpy()
+    pos, ids = si.catalogue(w, delta=dh)
+    box = ctx.load_box(w, ctx.pack_box_tensor(d, e6), None, layout=mk.BOX_TENSOR)
+    del d, e6
+    torch.cuda.empty_cache()
+    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w,
+                    flags=mk.STATS | mk.STORE_FLUX | mk.STORE_FIELDS)
+    rec = records(g["sk"], len(ids))
+    idx = np.sort(np.random.default_rng(8).choice(len(ids), 16, replace=False))
+    o = oracle_subset(w, dh, eh, pos, ids, idx)
+    np.testing.assert_array_equal(rec["n"][idx], o["npix"])
+    off = g["offsets"].cpu().numpy()
+    for k, q in enumerate(idx):
+        a, b = off[q], off[q + 1]
+        assert_field_close(g["eta"][a:b].cpu().numpy(), ragged(o["eta"], o["offsets"], k), f"eta_par q{q}")
+        assert_flux_close(g["flux"][a:b].cpu().numpy(), ragged(o["flux"], o["offsets"], k), f"flux q{q}")
+    del g, box
+    torch.cuda.empty_cache()
 
 
 def test_batched_workload_sampled_gauss7(ctx):
