@@ -416,6 +416,11 @@ int mk_mlp_train(mk_mlp *mlp, const float *d_x, const float *d_t, int64_t n, int
 /* Box of constant FGPA parameters from which surrogate training draws come. */
 typedef struct mk_surrogate_space {
   double ln_a_min, ln_a_max, b_min, b_max, c_min, c_max;
+  /* > 0: each draw is a linear profile in z through a point of the box above
+     (at the middle of the z bins), slopes uniform in +-these maxima per unit z;
+     every bin is then labelled with its effective parameters (the
+     pixel-weighted mean of the node values over its pixels).  0: constant. */
+  double dln_a_dz_max, db_dz_max, dc_dz_max;
 } mk_surrogate_space;
 
 /* Affine normalisation between physical surrogate inputs/outputs and the
@@ -427,7 +432,8 @@ typedef struct mk_surrogate_norm {
 } mk_surrogate_norm;
 
 /* Training set of the surrogate: n_draws parameter sets drawn uniformly in
-   `space` (seeded), each applied at every z node (constant in z) in one
+   `space` (seeded), each applied at the z nodes (constant in z, or a linear
+   profile when the space has slopes) in one
    tuning pass (mk_flux_stats) over the stored skewers; every z bin with
    pixel and P1D data and Fbar > 1e-3 gives one raw sample into h_x (4
    values) and h_t (35 values; bins->n_k must be 32).  *h_count receives the

@@ -82,7 +82,8 @@ class StatsOut(C.Structure):
 
 class SurrogateSpace(C.Structure):
     _fields_ = [("ln_a_min", C.c_double), ("ln_a_max", C.c_double), ("b_min", C.c_double),
-                ("b_max", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double)]
+                ("b_max", C.c_double), ("c_min", C.c_double), ("c_max", C.c_double),
+                ("dln_a_dz_max", C.c_double), ("db_dz_max", C.c_double), ("dc_dz_max", C.c_double)]
 
 
 class SurrogateNorm(C.Structure):
@@ -517,10 +518,13 @@ class Mlp:
         return norm, losses[:epochs]
 
 
-def surrogate_labels(ctx, w, sk, n_sk, offsets, delta, eta, n_draws, seed=0, space=None):
-    """Raw surrogate training samples x (n, 4) and t (n, 35) from tuning passes."""
+def surrogate_labels(ctx, w, sk, n_sk, offsets, delta, eta, n_draws, seed=0, space=None, slopes=None):
+    """Raw surrogate training samples x (n, 4) and t (n, 35) from tuning passes.
+    slopes: (d ln a/dz, db/dz, dc/dz) maxima for linear-in-z draws (None: constant)."""
     sp = space or SurrogateSpace(ln_a_min=math.log(1e-3), ln_a_max=math.log(3.0), b_min=1.0, b_max=2.2,
                                  c_min=0.5, c_max=1.5)
+    if slopes is not None:
+        sp.dln_a_dz_max, sp.db_dz_max, sp.dc_dz_max = slopes
     p = skewer_params(w)
     b = stat_bins(w)
     hx = np.zeros((n_draws * b.n_z, 4))

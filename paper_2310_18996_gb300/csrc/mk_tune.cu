@@ -216,6 +216,126 @@ extern "C" int mk_mlp_train(mk_mlp *p, const float *d_x, const float *d_t, int64
 // ====================================================================== surrogate data
 namespace {
 
+// Effective parameters of a z bin: the FGPA parameters ln a, b, c are linear
+// in z between nodes (clamped at the ends), so the pixels of bin i see a blend
+// of nodes i - 1, i, i + 1.  To first order a bin's statistics are those at
+// constant parameters equal to the pixel-weighted mean of the interpolated
+// parameters, theta_eff = W theta, with W[i][j] the mean interpolation weight
+// of node j over the pixels of bin i (inactive nodes folded into the nearest
+// active node they follow).  Tuning solves each bin for theta_eff and maps
+// back to the nodes through W.
+struct EffMap {
+  int nz = 0;
+  std::vector<int> act;   // active bins (= active nodes), ascending
+  std::vector<double> W;  // nz x nz
+  bool identity = true;
+
+  int build(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
+            const mk_stat_bins *bins, uint32_t active, const mk_fgpa_nodes &nd, double *gpu_ms) {
+    nz = bins->n_z;
+    act.clear();
+    for (int i = 0; i < nz; ++i)
+      if ((active >> i) & 1u) act.push_back(i);
+    W.assign(static_cast<size_t>(nz) * nz, 0.0);
+    for (int i = 0; i < nz; ++i) W[static_cast<size_t>(i) * nz + i] = 1.0;
+    identity = true;
+    std::vector<double> zj;
+    std::vector<int64_t> cnt;
+    int rc = mkhost::ctx_pixel_histogram(ctx, params->dr, d_sk, n_sk, zj, cnt, gpu_ms);
+    if (rc) return rc;
+    std::vector<double> acc(static_cast<size_t>(nz) * nz, 0.0), tot(nz, 0.0);
+    const int k = nd.count;
+    for (size_t j = 0; j < zj.size(); ++j) {
+      if (cnt[j] <= 0) continue;
+      const double z = zj[j];
+      const double f = std::floor((z - bins->z_lo) / bins->dz);
+      if (f < 0.0 || f >= nz) continue;
+      const int zb = static_cast<int>(f);
+      const double c = static_cast<double>(cnt[j]);
+      tot[zb] += c;
+      // the node interpolation of the pixel table
+      if (z <= nd.z[0]) {
+        acc[static_cast<size_t>(zb) * nz] += c;
+      } else if (z >= nd.z[k - 1]) {
+        acc[static_cast<size_t>(zb) * nz + k - 1] += c;
+      } else {
+        int i = 0;
+        while (i + 2 < k && z >= nd.z[i + 1]) ++i;
+        const double w = (z - nd.z[i]) / (nd.z[i + 1] - nd.z[i]);
+        acc[static_cast<size_t>(zb) * nz + i] += c * (1.0 - w);
+        acc[static_cast<size_t>(zb) * nz + i + 1] += c * w;
+      }
+    }
+    // fold inactive nodes into the active node they follow
+    std::vector<int> follow(nz, -1);
+    for (int i = 0; i < nz; ++i) {
+      if ((active >> i) & 1u) {
+        follow[i] = i;
+        continue;
+      }
+      for (int j : act)
+        if (follow[i] < 0 || std::abs(j - i) < std::abs(follow[i] - i)) follow[i] = j;
+    }
+    for (int zb : act) {
+      if (!(tot[zb] > 0.0)) continue;
+      for (int j = 0; j < nz; ++j) W[static_cast<size_t>(zb) * nz + j] = 0.0;
+      for (int j = 0; j < nz; ++j)
+        if (follow[j] >= 0) W[static_cast<size_t>(zb) * nz + follow[j]] += acc[static_cast<size_t>(zb) * nz + j] / tot[zb];
+    }
+    identity = false;
+    return MK_OK;
+  }
+
+  // theta_eff of the active bins, tb[3 zb + p]
+  void eff(const mk_fgpa_nodes &nd, std::vector<double> &tb) const {
+    tb.assign(static_cast<size_t>(nz) * 3, 0.0);
+    for (int zb : act)
+      for (int j : act) {
+        const double w = W[static_cast<size_t>(zb) * nz + j];
+        tb[3 * zb] += w * nd.ln_a[j];
+        tb[3 * zb + 1] += w * nd.b[j];
+        tb[3 * zb + 2] += w * nd.c[j];
+      }
+  }
+
+  // active nodes whose theta_eff is tb (W restricted to the active bins and
+  // nodes, Gaussian elimination with partial pivoting); the caller sets the
+  // inactive nodes
+  void nodes(const std::vector<double> &tb, mk_fgpa_nodes &nd) const {
+    const int n = static_cast<int>(act.size());
+    std::vector<double> M(static_cast<size_t>(n) * (n + 3));
+    for (int r = 0; r < n; ++r) {
+      for (int c = 0; c < n; ++c) M[static_cast<size_t>(r) * (n + 3) + c] = W[static_cast<size_t>(act[r]) * nz + act[c]];
+      for (int p = 0; p < 3; ++p) M[static_cast<size_t>(r) * (n + 3) + n + p] = tb[3 * act[r] + p];
+    }
+    bool ok = true;
+    for (int c = 0; c < n && ok; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < n; ++r)
+        if (std::fabs(M[static_cast<size_t>(r) * (n + 3) + c]) > std::fabs(M[static_cast<size_t>(piv) * (n + 3) + c])) piv = r;
+      if (std::fabs(M[static_cast<size_t>(piv) * (n + 3) + c]) < 1e-9) {
+        ok = false;
+        break;
+      }
+      for (int q = 0; q < n + 3; ++q) std::swap(M[static_cast<size_t>(c) * (n + 3) + q], M[static_cast<size_t>(piv) * (n + 3) + q]);
+      for (int r = 0; r < n; ++r) {
+        if (r == c) continue;
+        const double f = M[static_cast<size_t>(r) * (n + 3) + c] / M[static_cast<size_t>(c) * (n + 3) + c];
+        for (int q = c; q < n + 3; ++q) M[static_cast<size_t>(r) * (n + 3) + q] -= f * M[static_cast<size_t>(c) * (n + 3) + q];
+      }
+    }
+    for (int r = 0; r < n; ++r) {
+      const int j = act[r];
+      for (int p = 0; p < 3; ++p) {
+        const double v = ok ? M[static_cast<size_t>(r) * (n + 3) + n + p] / M[static_cast<size_t>(r) * (n + 3) + r]
+                            : tb[3 * j + p];  // singular map: nodes take the bin values
+        (p == 0 ? nd.ln_a : p == 1 ? nd.b : nd.c)[j] = v;
+      }
+    }
+  }
+};
+
+
 bool valid_stat_sample(const mk_stats_out &st, int zb, int n_k) {
   if (st.sums[zb][0] <= 0.0 || st.n_seg[zb] <= 0.0 || !(st.mean_flux[zb] > 1e-3)) return false;
   if (!std::isfinite(st.b_f[zb]) || !std::isfinite(st.beta_f[zb])) return false;
@@ -255,21 +375,42 @@ extern "C" int mk_surrogate_labels(mk_ctx *ctx, const mk_skewer_params *params, 
     return mfail(ctx, MK_EINVAL, "surrogate labels need 32 k bins, a parameter space and host outputs");
   std::mt19937_64 rng(seed);
   std::uniform_real_distribution<double> ua(space->ln_a_min, space->ln_a_max), ub(space->b_min, space->b_max),
-      uc(space->c_min, space->c_max);
+      uc(space->c_min, space->c_max), unit(-1.0, 1.0);
+  const bool sloped = space->dln_a_dz_max > 0.0 || space->db_dz_max > 0.0 || space->dc_dz_max > 0.0;
+  EffMap E;
+  if (sloped) {
+    // every bin counts as active: each node has its own value
+    const mk_fgpa_nodes probe = constant_nodes(bins, 0.0, 0.0, 0.0);
+    const uint32_t all = bins->n_z >= 32 ? 0xffffffffu : ((1u << bins->n_z) - 1u);
+    const int rc = E.build(ctx, params, d_sk, n_sk, bins, all, probe, nullptr);
+    if (rc) return rc;
+  }
+  const double zmid = bins->z_lo + 0.5 * bins->n_z * bins->dz;
   int64_t cnt = 0;
   mk_stats_out st;
+  std::vector<double> tb;
   for (int d = 0; d < n_draws; ++d) {
     const double la = ua(rng), b = ub(rng), c = uc(rng);
-    const mk_fgpa_nodes nd = constant_nodes(bins, la, b, c);
+    mk_fgpa_nodes nd = constant_nodes(bins, la, b, c);
+    if (sloped) {
+      const double sa = space->dln_a_dz_max * unit(rng), sb = space->db_dz_max * unit(rng),
+                   sc = space->dc_dz_max * unit(rng);
+      for (int i = 0; i < nd.count; ++i) {
+        nd.ln_a[i] += sa * (nd.z[i] - zmid);
+        nd.b[i] += sb * (nd.z[i] - zmid);
+        nd.c[i] += sc * (nd.z[i] - zmid);
+      }
+      E.eff(nd, tb);
+    }
     const int rc = mk_flux_stats(ctx, params, d_sk, n_sk, d_offsets, d_delta, d_eta, &nd, bins, &st);
     if (rc) return rc;
     for (int zb = 0; zb < bins->n_z; ++zb) {
       if (!valid_stat_sample(st, zb, 32)) continue;
       double *x = h_x + 4 * cnt;
       x[0] = nd.z[zb];
-      x[1] = la;
-      x[2] = b;
-      x[3] = c;
+      x[1] = sloped ? tb[3 * zb] : la;
+      x[2] = sloped ? tb[3 * zb + 1] : b;
+      x[3] = sloped ? tb[3 * zb + 2] : c;
       stat_vector(st, zb, h_t + kMlpOut * cnt);
       ++cnt;
     }
@@ -449,124 +590,6 @@ void fill_inactive(mk_fgpa_nodes &nd, const TuneState &S) {
   }
 }
 
-// Effective parameters of a z bin: the FGPA parameters ln a, b, c are linear
-// in z between nodes (clamped at the ends), so the pixels of bin i see a blend
-// of nodes i - 1, i, i + 1.  To first order a bin's statistics are those at
-// constant parameters equal to the pixel-weighted mean of the interpolated
-// parameters, theta_eff = W theta, with W[i][j] the mean interpolation weight
-// of node j over the pixels of bin i (inactive nodes folded into the nearest
-// active node they follow).  Tuning solves each bin for theta_eff and maps
-// back to the nodes through W.
-struct EffMap {
-  int nz = 0;
-  std::vector<int> act;   // active bins (= active nodes), ascending
-  std::vector<double> W;  // nz x nz
-  bool identity = true;
-
-  int build(TuneState &S, const mk_fgpa_nodes &nd) {
-    nz = S.bins->n_z;
-    act.clear();
-    for (int i = 0; i < nz; ++i)
-      if (S.active(i)) act.push_back(i);
-    W.assign(static_cast<size_t>(nz) * nz, 0.0);
-    for (int i = 0; i < nz; ++i) W[static_cast<size_t>(i) * nz + i] = 1.0;
-    identity = true;
-    std::vector<double> zj;
-    std::vector<int64_t> cnt;
-    int rc = mkhost::ctx_pixel_histogram(S.ctx, S.params->dr, S.d_sk, S.n_sk, zj, cnt, &S.rep->gpu_ms);
-    if (rc) return rc;
-    std::vector<double> acc(static_cast<size_t>(nz) * nz, 0.0), tot(nz, 0.0);
-    const int k = nd.count;
-    for (size_t j = 0; j < zj.size(); ++j) {
-      if (cnt[j] <= 0) continue;
-      const double z = zj[j];
-      const double f = std::floor((z - S.bins->z_lo) / S.bins->dz);
-      if (f < 0.0 || f >= nz) continue;
-      const int zb = static_cast<int>(f);
-      const double c = static_cast<double>(cnt[j]);
-      tot[zb] += c;
-      // the node interpolation of the pixel table
-      if (z <= nd.z[0]) {
-        acc[static_cast<size_t>(zb) * nz] += c;
-      } else if (z >= nd.z[k - 1]) {
-        acc[static_cast<size_t>(zb) * nz + k - 1] += c;
-      } else {
-        int i = 0;
-        while (i + 2 < k && z >= nd.z[i + 1]) ++i;
-        const double w = (z - nd.z[i]) / (nd.z[i + 1] - nd.z[i]);
-        acc[static_cast<size_t>(zb) * nz + i] += c * (1.0 - w);
-        acc[static_cast<size_t>(zb) * nz + i + 1] += c * w;
-      }
-    }
-    // fold inactive nodes into the active node they follow
-    std::vector<int> follow(nz, -1);
-    for (int i = 0; i < nz; ++i) {
-      if (S.active(i)) {
-        follow[i] = i;
-        continue;
-      }
-      for (int j : act)
-        if (follow[i] < 0 || std::abs(j - i) < std::abs(follow[i] - i)) follow[i] = j;
-    }
-    for (int zb : act) {
-      if (!(tot[zb] > 0.0)) continue;
-      for (int j = 0; j < nz; ++j) W[static_cast<size_t>(zb) * nz + j] = 0.0;
-      for (int j = 0; j < nz; ++j)
-        if (follow[j] >= 0) W[static_cast<size_t>(zb) * nz + follow[j]] += acc[static_cast<size_t>(zb) * nz + j] / tot[zb];
-    }
-    identity = false;
-    return MK_OK;
-  }
-
-  // theta_eff of the active bins, tb[3 zb + p]
-  void eff(const mk_fgpa_nodes &nd, std::vector<double> &tb) const {
-    tb.assign(static_cast<size_t>(nz) * 3, 0.0);
-    for (int zb : act)
-      for (int j : act) {
-        const double w = W[static_cast<size_t>(zb) * nz + j];
-        tb[3 * zb] += w * nd.ln_a[j];
-        tb[3 * zb + 1] += w * nd.b[j];
-        tb[3 * zb + 2] += w * nd.c[j];
-      }
-  }
-
-  // nodes whose theta_eff is tb (W restricted to the active bins and nodes,
-  // Gaussian elimination with partial pivoting); inactive nodes then follow
-  void nodes(const std::vector<double> &tb, mk_fgpa_nodes &nd, const TuneState &S) const {
-    const int n = static_cast<int>(act.size());
-    std::vector<double> M(static_cast<size_t>(n) * (n + 3));
-    for (int r = 0; r < n; ++r) {
-      for (int c = 0; c < n; ++c) M[static_cast<size_t>(r) * (n + 3) + c] = W[static_cast<size_t>(act[r]) * nz + act[c]];
-      for (int p = 0; p < 3; ++p) M[static_cast<size_t>(r) * (n + 3) + n + p] = tb[3 * act[r] + p];
-    }
-    bool ok = true;
-    for (int c = 0; c < n && ok; ++c) {
-      int piv = c;
-      for (int r = c + 1; r < n; ++r)
-        if (std::fabs(M[static_cast<size_t>(r) * (n + 3) + c]) > std::fabs(M[static_cast<size_t>(piv) * (n + 3) + c])) piv = r;
-      if (std::fabs(M[static_cast<size_t>(piv) * (n + 3) + c]) < 1e-9) {
-        ok = false;
-        break;
-      }
-      for (int q = 0; q < n + 3; ++q) std::swap(M[static_cast<size_t>(c) * (n + 3) + q], M[static_cast<size_t>(piv) * (n + 3) + q]);
-      for (int r = 0; r < n; ++r) {
-        if (r == c) continue;
-        const double f = M[static_cast<size_t>(r) * (n + 3) + c] / M[static_cast<size_t>(c) * (n + 3) + c];
-        for (int q = c; q < n + 3; ++q) M[static_cast<size_t>(r) * (n + 3) + q] -= f * M[static_cast<size_t>(c) * (n + 3) + q];
-      }
-    }
-    for (int r = 0; r < n; ++r) {
-      const int j = act[r];
-      for (int p = 0; p < 3; ++p) {
-        const double v = ok ? M[static_cast<size_t>(r) * (n + 3) + n + p] / M[static_cast<size_t>(r) * (n + 3) + r]
-                            : tb[3 * j + p];  // singular map: nodes take the bin values
-        (p == 0 ? nd.ln_a : p == 1 ? nd.b : nd.c)[j] = v;
-      }
-    }
-    fill_inactive(nd, S);
-  }
-};
-
 // Clamped LM step on the effective parameters of bin zb; returns its largest component.
 double apply_step_eff(std::vector<double> &tb, int zb, const double *d) {
   const double lim[3] = {1.0, 0.4, 0.4};
@@ -698,7 +721,7 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
   std::vector<double> r, J, rp, tb;
   int rc = MK_OK;
   EffMap E;
-  if ((rc = E.build(S, nd))) {
+  if ((rc = E.build(ctx, params, d_sk, n_sk, bins, target->active, nd, &report->gpu_ms))) {
     cudaEventDestroy(S.e0);
     cudaEventDestroy(S.e1);
     return rc;
@@ -732,7 +755,8 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
         lm_step(&J[static_cast<size_t>(zb) * m * 3], &r[static_cast<size_t>(zb) * m], m, 1e-3, d);
         (void)apply_step_eff(tb, zb, d);
       }
-      E.nodes(tb, nd, S);
+      E.nodes(tb, nd);
+      fill_inactive(nd, S);
       report->iterations += 1;
     }
   } else {
@@ -751,7 +775,8 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       }
       if (big < kSurrogateStop) break;
     }
-    E.nodes(tb, nd, S);
+    E.nodes(tb, nd);
+      fill_inactive(nd, S);
     // verify on full passes; between passes re-solve on the surrogate with the
     // last pass's discrepancy (true minus predicted residual) as an offset,
     // plus a per-bin linear term B (theta_eff - theta_eff,i) for how the
@@ -812,7 +837,8 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
         }
         if (big < kSurrogateStop) break;
       }
-      E.nodes(tb, nd, S);
+      E.nodes(tb, nd);
+      fill_inactive(nd, S);
       report->iterations += 1;
     }
   }
