@@ -212,7 +212,7 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- tuning A/B
-def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source):
+def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None):
     """Plain vs surrogate tuning of ln a, b, c at the 12 z nodes on the stored
     skewers of the benchmark catalogue; the surrogate is trained on
     constant-parameter passes over 100k quasars: the first 100k of the same
@@ -240,7 +240,7 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source):
         n_lab = len(ids)
     t0 = time.perf_counter()
     hx, ht = mk.surrogate_labels(ctx, ws, rs["sk"], n_lab, rs["offsets"], rs["delta"], rs["eta"],
-                                 n_draws=draws, seed=11)
+                                 n_draws=draws, seed=11, slopes=slopes)
     t_lab = time.perf_counter() - t0
     mlp = mk.Mlp(ctx, max_batch=1024, seed=3)
     t0 = time.perf_counter()
@@ -260,8 +260,11 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source):
                         "Fbar = exp(-0.0025 (1+z)^3.7) +- 1e-3, P1D and beta_F of seeded hidden power laws +- 2%",
             "plain": rep(rep_p), "surrogate": rep(rep_s),
             "gpu_time_ratio_plain_over_surrogate": rep_p.gpu_ms / max(rep_s.gpu_ms, 1e-9),
+            "wall_time_ratio_including_training": rep_p.wall_ms / (rep_s.wall_ms + 1000.0 * (t_lab + t_fit)),
             "surrogate_training": {"source": source, "box": "1024^3" if source == "subset" else "512^3",
                                    "quasars": 100_000, "draws": draws, "samples": int(hx.shape[0]),
+                                   "profiles": ("linear in z, slopes up to d ln a/dz, db/dz, dc/dz = "
+                                                f"{slopes[0]}, {slopes[1]}, {slopes[2]}" if slopes else "constant"),
                                    "label_s": t_lab, "fit_s": t_fit, "epochs": epochs,
                                    "final_loss": float(losses[-1]) if len(losses) else None}}
 
@@ -433,8 +436,9 @@ def run_gb300(args, rank, world, local_rank):
     achieved = alg / (kms / 1000.0) / 1e9
     tune = None
     if rank == 0 and world == 1 and not args.no_tuning:
+        slopes = None if args.surrogate_slopes == "none" else tuple(float(v) for v in args.surrogate_slopes.split(","))
         tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs,
-                         args.surrogate_source)
+                         args.surrogate_source, slopes)
     cpu = None
     if want_cpu:
         rate, px, n, dt = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds, os.cpu_count() or 1)
@@ -495,8 +499,10 @@ def main():
     ap.add_argument("--no-gauss7", action="store_true")
     ap.add_argument("--no-tensor", action="store_true")
     ap.add_argument("--no-tuning", action="store_true")
-    ap.add_argument("--surrogate-draws", type=int, default=4000)
-    ap.add_argument("--surrogate-epochs", type=int, default=200)
+    ap.add_argument("--surrogate-draws", type=int, default=8000)
+    ap.add_argument("--surrogate-epochs", type=int, default=300)
+    ap.add_argument("--surrogate-slopes", default="1.8,0.45,0.45",
+                    help="maxima of d ln a/dz, db/dz, dc/dz of the training profiles, or 'none'")
     ap.add_argument("--surrogate-source", default="subset", choices=["subset", "box512"])
     ap.add_argument("--box-n", type=int, default=None, help="smaller box (profiling runs)")
     ap.add_argument("--n-q", type=int, default=None, help="fewer quasars (profiling runs)")
