@@ -51,6 +51,7 @@ class Cfg(C.Structure):
         ("lobs_min", C.c_double), ("n_min", C.c_int32), ("n_max", C.c_int32),
         ("n_fft", C.c_int32), ("p_s", C.POINTER(C.c_double)), ("seed", C.c_uint32),
         ("interp", C.c_int32), ("eta_mode", C.c_int32),
+        ("p_s_nodes", C.c_int32), ("p_s_z", C.POINTER(C.c_double)),
     ]
 
 
@@ -103,8 +104,8 @@ def lib():
                 "orc_pixel_z": (d, [P(Cfg), i64]),
                 "orc_trilinear": (d, [P(C.c_float), i32, P(d)]),
                 "orc_gauss7": (d, [P(C.c_float), i32, P(d)]),
-                "orc_small_scale_modes": (None, [P(Cfg), u64, i32, P(d), P(d)]),
-                "orc_small_scale_segment": (None, [P(Cfg), u64, i32, P(d)]),
+                "orc_small_scale_modes": (None, [P(Cfg), u64, i32, i64, P(d), P(d)]),
+                "orc_small_scale_segment": (None, [P(Cfg), u64, i32, i64, P(d)]),
                 "orc_skewer_fields": (C.c_int, [P(Cfg), P(C.c_float), P(C.c_float), P(d), u64,
                                                 i32, i32, P(d), P(d), P(d)]),
                 "orc_fgpa_params": (None, [P(Nodes), d, P(d), P(d), P(d)]),
@@ -210,7 +211,12 @@ def make_cfg(w):
     cfg.seed = w["seed_noise"] & 0xFFFFFFFF
     cfg.interp = w.get("interp", 0)
     cfg.eta_mode = w.get("eta_mode", 0)
-    cfg._keep = ps  # keep the table alive with the struct
+    psz = np.ascontiguousarray(w.get("p_s_z", []), dtype=np.float64)
+    cfg.p_s_nodes = len(psz)
+    if cfg.p_s_nodes >= 2:
+        assert ps.size == cfg.p_s_nodes * (w["n_fft"] // 2 + 1), "p_s needs one table per p_s_z node"
+        cfg.p_s_z = _p(psz, C.c_double)
+    cfg._keep = (ps, psz)  # keep the tables alive with the struct
     return cfg
 
 
@@ -254,20 +260,20 @@ def pixel_z(w, j):
     return lib().orc_pixel_z(C.byref(cfg), int(j))
 
 
-def small_scale_modes(w, qid, seg):
+def small_scale_modes(w, qid, seg, j0=0):
     cfg = make_cfg(w)
     n = w["n_fft"]
     re = np.zeros(n // 2 + 1)
     im = np.zeros(n // 2 + 1)
-    lib().orc_small_scale_modes(C.byref(cfg), int(qid), int(seg), _p(re, C.c_double),
+    lib().orc_small_scale_modes(C.byref(cfg), int(qid), int(seg), int(j0), _p(re, C.c_double),
                                 _p(im, C.c_double))
     return re + 1j * im
 
 
-def small_scale_segment(w, qid, seg):
+def small_scale_segment(w, qid, seg, j0=0):
     cfg = make_cfg(w)
     out = np.zeros(w["n_fft"])
-    lib().orc_small_scale_segment(C.byref(cfg), int(qid), int(seg), _p(out, C.c_double))
+    lib().orc_small_scale_segment(C.byref(cfg), int(qid), int(seg), int(j0), _p(out, C.c_double))
     return out
 
 

@@ -336,7 +336,23 @@ double orc_gauss7(const float *box, int32_t n, const double c[3]) {
 /*   X_m = A_m (e1 + i e2)/sqrt(2) for 0 < m < n/2, X_{n/2} = A e1,          */
 /*   A_m = sqrt(n P_S(k_m) / dr).                                            */
 /* ------------------------------------------------------------------------ */
-void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double *re,
+/* P_S(k_m) of a segment whose window starts at global pixel j0 */
+static double small_scale_power(const orc_cfg *cfg, int32_t m, int64_t j0) {
+  int32_t h = cfg->n_fft / 2 + 1;
+  if (cfg->p_s_nodes <= 1) return cfg->p_s[m];
+  double zs = 0.0;
+  for (int64_t j = j0; j < j0 + cfg->n_fft; ++j) zs += orc_pixel_z(cfg, j);
+  zs /= cfg->n_fft;
+  int32_t k = cfg->p_s_nodes;
+  if (zs <= cfg->p_s_z[0]) return cfg->p_s[m];
+  if (zs >= cfg->p_s_z[k - 1]) return cfg->p_s[(int64_t)(k - 1) * h + m];
+  int32_t i = 0;
+  while (i + 2 < k && zs >= cfg->p_s_z[i + 1]) ++i;
+  double w = (zs - cfg->p_s_z[i]) / (cfg->p_s_z[i + 1] - cfg->p_s_z[i]);
+  return (1.0 - w) * cfg->p_s[(int64_t)i * h + m] + w * cfg->p_s[(int64_t)(i + 1) * h + m];
+}
+
+void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, int64_t j0, double *re,
                            double *im) {
   int32_t n = cfg->n_fft;
   re[0] = 0.0;
@@ -350,7 +366,7 @@ void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double 
     int pair = (m < n / 2 && (m & 1)) ? 2 : 0;
     double e1, e2;
     orc_box_muller(w[pair], w[pair + 1], &e1, &e2);
-    double amp = sqrt((double)n * cfg->p_s[m] / cfg->dr);
+    double amp = sqrt((double)n * small_scale_power(cfg, m, j0) / cfg->dr);
     if (m < n / 2) {
       re[m] = amp * e1 / sqrt(2.0);
       im[m] = amp * e2 / sqrt(2.0);
@@ -361,11 +377,11 @@ void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double 
   }
 }
 
-void orc_small_scale_segment(const orc_cfg *cfg, uint64_t id, int32_t seg, double *out) {
+void orc_small_scale_segment(const orc_cfg *cfg, uint64_t id, int32_t seg, int64_t j0, double *out) {
   int32_t n = cfg->n_fft;
   double *re = (double *)malloc(sizeof(double) * (n / 2 + 1));
   double *im = (double *)malloc(sizeof(double) * (n / 2 + 1));
-  orc_small_scale_modes(cfg, id, seg, re, im);
+  orc_small_scale_modes(cfg, id, seg, j0, re, im);
   orc_dft_inverse_hermitian(re, im, n, out);
   free(re);
   free(im);
@@ -412,7 +428,7 @@ int orc_skewer_fields(const orc_cfg *cfg, const float *dbox, const float *ebox,
     if (delta_s) {
       if (j / nf != cur) {
         cur = j / nf;
-        orc_small_scale_segment(cfg, id, cur, seg);
+        orc_small_scale_segment(cfg, id, cur, (int64_t)j_lo + (int64_t)cur * nf, seg);
       }
       delta_s[j] = seg[j % nf];
     }

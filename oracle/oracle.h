@@ -54,6 +54,12 @@ typedef struct orc_cfg {
      n^3, consecutive) and eta_par = u_p u_q eta_pq with u the unit vector to
      the quasar (Eq. eta) */
   int32_t eta_mode;
+  /* z-dependent small-scale power (Sec. 2.6 tunes P_s per z_t): p_s_nodes >= 2
+     tables at increasing p_s_z, p_s holding p_s_nodes x (n_fft/2+1) values;
+     a segment takes P_s linearly interpolated in z (clamped) at the mean
+     pixel z of its n_fft-pixel window.  p_s_nodes <= 1: one table for all z. */
+  int32_t p_s_nodes;
+  const double *p_s_z;
 } orc_cfg;
 
 /* FGPA parameter nodes (Sec. 2.5: tuned at a few z, interpolated between). */
@@ -117,9 +123,11 @@ double orc_trilinear(const float *box, int32_t n, const double c[3]);
 double orc_gauss7(const float *box, int32_t n, const double c[3]);
 
 /* ---- small-scale modes and field of one segment ---- */
-void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, double *re,
+/* j0: the first global pixel of the segment's window (j_lo + seg n_fft); it
+   only matters with a z-dependent P_s */
+void orc_small_scale_modes(const orc_cfg *cfg, uint64_t id, int32_t seg, int64_t j0, double *re,
                            double *im);
-void orc_small_scale_segment(const orc_cfg *cfg, uint64_t id, int32_t seg, double *out);
+void orc_small_scale_segment(const orc_cfg *cfg, uint64_t id, int32_t seg, int64_t j0, double *out);
 
 /* ---- one skewer: growth-scaled delta_L, eta and delta_S per pixel ---- */
 int orc_skewer_fields(const orc_cfg *cfg, const float *dbox, const float *ebox,

@@ -283,6 +283,34 @@ def test_eta_tensor_inputs_trace_and_xx():
     np.testing.assert_allclose(e6[0] + e6[1] + e6[2], -d, atol=1e-6)
 
 
+# ------------------------------------------------------------ z-dependent small-scale power (Sec. 2.6)
+def test_p_s_nodes_identical_tables_equal_one_table():
+    w1 = si.workload("tiny")
+    w2 = si.shrink(w1, p_s=np.stack([w1["p_s"], w1["p_s"]]), p_s_z=[2.0, 3.0])
+    d, e = si.gaussian_box(w1["n"], w1["cell"], w1["seed_box"])
+    pos, ids = si.catalogue(w1, n_q=5)
+    o1 = oracle.run_skewers(w1, d, e, pos, ids, n_threads=1)
+    o2 = oracle.run_skewers(w2, d, e, pos, ids, n_threads=1)
+    np.testing.assert_allclose(o2["delta"], o1["delta"], rtol=1e-13, atol=1e-15)  # (1-w) P + w P rounds
+
+
+def test_p_s_nodes_interpolate_power_at_window_mean_z():
+    # tables P0 at z = 2.2 and 4 P0 at z = 2.6: every mode of a segment scales by
+    # sqrt((1 - w) + 4 w), w from the mean pixel z of its n_fft window (clamped)
+    w1 = si.workload("tiny")
+    w2 = si.shrink(w1, p_s=np.stack([w1["p_s"], 4.0 * w1["p_s"]]), p_s_z=[2.2, 2.6])
+    n = w1["n_fft"]
+    for qid, j0 in ((7, 17000), (9, 19200), (11, 20000), (3, 22000)):
+        zbar = np.mean([oracle.pixel_z(w1, j) for j in range(j0, j0 + n)])
+        wz = min(max((zbar - 2.2) / 0.4, 0.0), 1.0)
+        ref = oracle.small_scale_modes(w1, qid, 1, j0)
+        got = oracle.small_scale_modes(w2, qid, 1, j0)
+        np.testing.assert_allclose(got, ref * math.sqrt((1.0 - wz) + 4.0 * wz), rtol=1e-12, atol=1e-300)
+    # the four windows cover below, inside and above the node range
+    zs = [np.mean([oracle.pixel_z(w1, j) for j in range(j0, j0 + n)]) for j0 in (17000, 22000)]
+    assert zs[0] < 2.2 and zs[1] > 2.6
+
+
 # ------------------------------------------------------------ geometry
 def test_geometry_forest_window():
     w = si.workload("tiny")
