@@ -137,6 +137,13 @@ typedef struct mk_skewer_params {
   uint32_t seed;           /* small-scale noise seed */
   const double *h_p_s;     /* n_fft/2 + 1 values P_S(k_m), k_m = 2 pi m/(n_fft dr) */
   int32_t interp;          /* MK_INTERP_TRILINEAR (0) or MK_INTERP_GAUSS7 */
+  /* z-dependent small-scale power (Sec. 2.6 tunes P_s at each z_t): with
+     p_s_nodes >= 2, h_p_s holds p_s_nodes tables of n_fft/2 + 1 values at the
+     increasing redshifts h_p_s_z, and a segment takes P_s linearly
+     interpolated in z (clamped) at the mean z of the n_fft pixels of its
+     window (global pixels j_lo + s n_fft onwards).  0 or 1: one table. */
+  int32_t p_s_nodes;       /* 0 .. MK_MAX_NODES */
+  const double *h_p_s_z;
 } mk_skewer_params;
 
 /* FGPA nodes: ln a, b, c at increasing z, linear in z between nodes, clamped

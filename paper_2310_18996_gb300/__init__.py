@@ -52,7 +52,7 @@ class SkewerParams(C.Structure):
     _fields_ = [("dr", C.c_double), ("lrf_min", C.c_double), ("lrf_max", C.c_double),
                 ("lobs_min", C.c_double), ("n_min", C.c_int32), ("n_max", C.c_int32),
                 ("n_fft", C.c_int32), ("seed", C.c_uint32), ("h_p_s", C.POINTER(C.c_double)),
-                ("interp", C.c_int32)]
+                ("interp", C.c_int32), ("p_s_nodes", C.c_int32), ("h_p_s_z", C.POINTER(C.c_double))]
 
 
 class FgpaNodes(C.Structure):
@@ -186,7 +186,13 @@ def skewer_params(w):
                      n_max=w.get("n_max", 0), n_fft=w["n_fft"],
                      seed=w["seed_noise"] & 0xFFFFFFFF,
                      h_p_s=ps.ctypes.data_as(C.POINTER(C.c_double)), interp=w.get("interp", 0))
-    p._keep = ps
+    psz = np.ascontiguousarray(w.get("p_s_z", []), dtype=np.float64)
+    if psz.size >= 2:  # one P_s table per redshift node
+        if ps.size != psz.size * (w["n_fft"] // 2 + 1):
+            raise ValueError("p_s needs one table of n_fft/2 + 1 values per p_s_z node")
+        p.p_s_nodes = psz.size
+        p.h_p_s_z = psz.ctypes.data_as(C.POINTER(C.c_double))
+    p._keep = (ps, psz)
     return p
 
 

@@ -167,6 +167,11 @@ struct mk_ctx {
   // small-scale amplitudes and twiddles
   float *d_amp = nullptr;
   std::vector<double> amp_key;
+  int ps_nodes = 1;  // node tables in d_amp (>= 2: squared amplitudes per node)
+  float ps_z[MK_MAX_NODES] = {};
+  float *d_zwin = nullptr;  // window mean z per J for segments of zwin_n pixels
+  int zwin_n = 0;
+  double zwin_dr = -1.0;
   float2 *d_tw[4] = {nullptr, nullptr, nullptr, nullptr};  // N = 256, 512, 1024, 2048
   // workspaces
   int64_t *d_cnt_px = nullptr, *d_cnt_seg = nullptr, *d_segoff = nullptr;
@@ -267,6 +272,8 @@ int ensure_pixel_tables(mk_ctx *ctx, double dr) {
   cudaFree(ctx->d_pixtab);
   cudaFree(ctx->d_zbin);
   cudaFree(ctx->d_segzbin);
+  cudaFree(ctx->d_zwin);
+  ctx->d_zwin = nullptr;
   ctx->d_zpix = ctx->d_cumz = nullptr;
   ctx->d_gpix = nullptr;
   ctx->d_pixtab = nullptr;
@@ -314,24 +321,43 @@ int ensure_twiddles(mk_ctx *ctx, int n_fft) {
 
 int ensure_amp(mk_ctx *ctx, const mk_skewer_params *p) {
   const int m = p->n_fft / 2;
-  std::vector<double> key(m + 3);
+  const int nodes = p->p_s_nodes >= 2 ? p->p_s_nodes : 1;
+  std::vector<double> key(3 + nodes * (m + 2));
   key[0] = p->n_fft;
   key[1] = p->dr;
-  for (int i = 0; i <= m; ++i) key[i + 2] = p->h_p_s[i];
-  if (key == ctx->amp_key && ctx->d_amp) return MK_OK;
-  std::vector<float> amp(m + 1);
-  for (int i = 0; i <= m; ++i) {
-    const double ps = p->h_p_s[i];
-    if (!(ps >= 0.0)) return fail(ctx, MK_EINVAL, "P_S[%d] must be >= 0", i);
-    amp[i] = static_cast<float>(std::sqrt(p->n_fft * ps / p->dr) / p->n_fft);
+  key[2] = nodes;
+  for (int k = 0; k < nodes; ++k) {
+    key[3 + k] = nodes > 1 ? p->h_p_s_z[k] : 0.0;
+    for (int i = 0; i <= m; ++i) key[3 + nodes + k * (m + 1) + i] = p->h_p_s[k * (m + 1) + i];
   }
-  amp[0] = 0.f;
-  cudaFree(ctx->d_amp);
-  ctx->d_amp = nullptr;
-  ++ctx->generation;
-  CK(cudaMalloc(&ctx->d_amp, sizeof(float) * (m + 1)));
-  CK(cudaMemcpy(ctx->d_amp, amp.data(), sizeof(float) * (m + 1), cudaMemcpyHostToDevice));
-  ctx->amp_key = key;
+  if (!(key == ctx->amp_key && ctx->d_amp)) {
+    std::vector<float> amp(static_cast<size_t>(nodes) * (m + 1));
+    for (int k = 0; k < nodes; ++k)
+      for (int i = 0; i <= m; ++i) {
+        const double ps = p->h_p_s[k * (m + 1) + i];
+        if (!(ps >= 0.0)) return fail(ctx, MK_EINVAL, "P_S[%d][%d] must be >= 0", k, i);
+        const double a2 = p->n_fft * ps / p->dr / (static_cast<double>(p->n_fft) * p->n_fft);
+        // one table: A_m / N; node tables: (A_m / N)^2, interpolated in z then square-rooted
+        amp[k * (m + 1) + i] = static_cast<float>(i == 0 ? 0.0 : (nodes > 1 ? a2 : std::sqrt(a2)));
+      }
+    cudaFree(ctx->d_amp);
+    ctx->d_amp = nullptr;
+    ++ctx->generation;
+    CK(cudaMalloc(&ctx->d_amp, sizeof(float) * amp.size()));
+    CK(cudaMemcpy(ctx->d_amp, amp.data(), sizeof(float) * amp.size(), cudaMemcpyHostToDevice));
+    ctx->amp_key = key;
+    ctx->ps_nodes = nodes;
+    for (int k = 0; k < nodes && nodes > 1; ++k) ctx->ps_z[k] = static_cast<float>(p->h_p_s_z[k]);
+  }
+  if (nodes > 1 && (ctx->zwin_n != p->n_fft || ctx->zwin_dr != ctx->dr || !ctx->d_zwin)) {
+    if (!ctx->d_zwin) {
+      ++ctx->generation;
+      CK(cudaMalloc(&ctx->d_zwin, sizeof(float) * ctx->j_max));
+    }
+    CK(launch_zwin(ctx->d_cumz, ctx->j_max, p->n_fft, ctx->d_zwin, ctx->stream));
+    ctx->zwin_n = p->n_fft;
+    ctx->zwin_dr = ctx->dr;
+  }
   return MK_OK;
 }
 
@@ -342,6 +368,13 @@ int check_params(mk_ctx *ctx, const mk_skewer_params *p, bool need_ps) {
   if (p->n_min < 0 || p->n_max < 0) return fail(ctx, MK_EINVAL, "n_min/n_max must be >= 0");
   if (tw_slot(p->n_fft) < 0) return fail(ctx, MK_EINVAL, "n_fft must be 256, 512, 1024 or 2048");
   if (need_ps && !p->h_p_s) return fail(ctx, MK_EINVAL, "h_p_s is NULL");
+  if (p->p_s_nodes < 0 || p->p_s_nodes > MK_MAX_NODES)
+    return fail(ctx, MK_EINVAL, "p_s_nodes must be in [0, %d]", MK_MAX_NODES);
+  if (p->p_s_nodes >= 2) {
+    if (!p->h_p_s_z) return fail(ctx, MK_EINVAL, "h_p_s_z is NULL");
+    for (int k = 1; k < p->p_s_nodes; ++k)
+      if (!(p->h_p_s_z[k] > p->h_p_s_z[k - 1])) return fail(ctx, MK_EINVAL, "h_p_s_z must increase");
+  }
   if (p->interp != MK_INTERP_TRILINEAR && p->interp != MK_INTERP_GAUSS7)
     return fail(ctx, MK_EINVAL, "interp must be MK_INTERP_TRILINEAR or MK_INTERP_GAUSS7");
   return MK_OK;
@@ -490,6 +523,9 @@ SkewerParams skewer_params(mk_ctx *ctx, const mk_box *box, const mk_skewer *d_sk
   S.zbin = ctx->d_zbin;
   S.cumz = ctx->d_cumz;
   S.amp = ctx->d_amp;
+  S.ps_nodes = ctx->ps_nodes;
+  for (int k = 0; k < MK_MAX_NODES; ++k) S.ps_z[k] = ctx->ps_z[k];
+  S.zwin = ctx->d_zwin;
   S.tw = ctx->d_tw[tw_slot(p->n_fft)];
   S.seed = p->seed;
   S.j_max = ctx->j_max;
@@ -576,6 +612,7 @@ void mk_destroy(mk_ctx *ctx) {
   cudaFree(ctx->d_segzbin);
   cudaFree(ctx->d_bin_end);
   cudaFree(ctx->d_amp);
+  cudaFree(ctx->d_zwin);
   for (auto *p : ctx->d_tw) cudaFree(p);
   cudaFree(ctx->d_cnt_px);
   cudaFree(ctx->d_cnt_seg);

@@ -309,8 +309,11 @@ __device__ __forceinline__ void power_of_modes(const float2 *buf, const float2 *
 // X_m = A_m sqrt(-ln u1) e^{2 pi i u2} (= A (e1 + i e2)/sqrt 2), X_M = A e1.
 // Counter c serves modes 2c (words 0, 1) and 2c + 1 (words 2, 3); the words
 // of counter 0 that mode 0 (X_0 = 0) would use serve the Nyquist mode M.
-template <int N>
-__device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__restrict__ amp, uint32_t seg,
+// ZNODES: amp and amp_hi hold (A_m / N)^2 at two z nodes, mixed with weight
+// w_hi; otherwise amp holds A_m / N and amp_hi is unused.
+template <int N, bool ZNODES>
+__device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__restrict__ amp,
+                                                  const float *__restrict__ amp_hi, float w_hi, uint32_t seg,
                                                   uint64_t id, uint32_t seed, int t) {
   constexpr int T = Fft<N>::T;
   constexpr int M = Fft<N>::M;
@@ -321,9 +324,14 @@ __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__re
     const u32x4 w = philox4x32_10(u32x4{c, seg, id_hi, 0u}, seed, id_lo);
     const bool nyq = (c == 0);
     const int m0 = nyq ? M : 2 * c, m1 = 2 * c + 1;
+    float s0 = __ldg(amp + m0), s1 = __ldg(amp + m1);
+    if (ZNODES) {  // interpolate P_s between the nodes, then the root
+      s0 = sqrtf(fmaf(w_hi, __ldg(amp_hi + m0) - s0, s0));
+      s1 = sqrtf(fmaf(w_hi, __ldg(amp_hi + m1) - s1, s1));
+    }
     const float2 p0 = unit_phase(w.y), p1 = unit_phase(w.w);
-    const float a0 = __ldg(amp + m0) * sqrt_pos((nyq ? 2.0f : 1.0f) * neg_log_uniform(w.x));
-    const float a1 = __ldg(amp + m1) * sqrt_pos(neg_log_uniform(w.z));
+    const float a0 = s0 * sqrt_pos((nyq ? 2.0f : 1.0f) * neg_log_uniform(w.x));
+    const float a1 = s1 * sqrt_pos(neg_log_uniform(w.z));
     buf[sw(m0)] = make_float2(a0 * p0.x, nyq ? 0.f : a0 * p0.y);
     buf[sw(m1)] = make_float2(a1 * p1.x, a1 * p1.y);
   }

@@ -249,6 +249,15 @@ __global__ void k_jcount(const mk_skewer *__restrict__ sk, int64_t n_sk, int32_t
   }
 }
 
+// zwin[J] = mean z of pixels J .. J+n-1 (the window of a delta_S segment
+// starting at J), cut at the end of the tables.
+__global__ void k_zwin(const double *__restrict__ cumz, int32_t j_max, int n, float *zwin) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= j_max) return;
+  const int e = min(j + n, j_max);
+  zwin[j] = static_cast<float>((cumz[e] - cumz[j]) / (e - j));
+}
+
 // out[i] = off[i n / k], i = 0..k: the offsets at the slice boundaries.
 __global__ void k_pick(const int64_t *__restrict__ off, int64_t n, int k, int64_t *out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -423,6 +432,11 @@ cudaError_t launch_zbin(const double *zpix, const double *cumz, int32_t j_max, d
 cudaError_t launch_jcount(const mk_skewer *sk, int64_t n_sk, int32_t j_max, int32_t *diff, int sms, cudaStream_t st) {
   if (n_sk == 0) return cudaSuccess;
   k_jcount<<<sms * 4, 256, 0, st>>>(sk, n_sk, j_max, diff);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zwin(const double *cumz, int32_t j_max, int n, float *zwin, cudaStream_t st) {
+  k_zwin<<<blocks_for(j_max, 256), 256, 0, st>>>(cumz, j_max, n, zwin);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,7 @@ cudaError_t launch_pack_tensor(const float *d, const float *e6, int lgn, float *
 cudaError_t launch_pack_halo(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_pack_padded(const float *d, const float *e, int lgn, float *out, int sms, cudaStream_t st);
 cudaError_t launch_jcount(const mk_skewer *sk, int64_t n_sk, int32_t j_max, int32_t *diff, int sms, cudaStream_t st);
+cudaError_t launch_zwin(const double *cumz, int32_t j_max, int n, float *zwin, cudaStream_t st);
 cudaError_t launch_pick(const int64_t *off, int64_t n, int k, int64_t *out, cudaStream_t st);
 cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t *bin_end, cudaStream_t st);
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);

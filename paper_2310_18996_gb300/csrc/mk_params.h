@@ -62,7 +62,10 @@ struct SkewerParams {
   const int16_t *segzbin;  // per J: z bin of the mean z of pixels J .. J+N-1
   const int32_t *bin_end;  // [k + 1], k = -1 .. n_z: first J with zbin > k (large beyond the tables)
   const double *cumz;      // per J: sum_{J' < J} z_J'
-  const float *amp;        // A_m / N, m = 0..N/2
+  const float *amp;        // A_m / N, m = 0..N/2; with ps_nodes >= 2: (A_m / N)^2 per node, node-major
+  int32_t ps_nodes;        // z-dependent small-scale power: tables at ps_z (>= 2), else one
+  float ps_z[MK_MAX_NODES];
+  const float *zwin;       // per J: mean z of pixels J .. J+N-1 (with ps_nodes >= 2)
   const float2 *tw;      // e^{-2 pi i k/N}, k < N
   uint32_t seed;
   int32_t j_max;

@@ -121,12 +121,22 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
                                     sk.p0[1] + kRoundQ + ps * sk.step[1], sk.p0[2] + kRoundQ + ps * sk.step[2]);
     }
     // ---- small-scale field of this segment
-    small_scale_modes<N>(buf, P.amp, static_cast<uint32_t>(s), sk.id, P.seed, t);
+    const int jb = sk.j_lo + static_cast<int>(j0);
+    if (P.ps_nodes >= 2) {  // P_s at the mean z of the segment's window, linear between nodes
+      const float zw = __ldg(P.zwin + jb);
+      const int k = P.ps_nodes;
+      int n0 = 0;
+      while (n0 + 2 < k && zw >= P.ps_z[n0 + 1]) ++n0;
+      const float w_hi = fminf(fmaxf((zw - P.ps_z[n0]) / (P.ps_z[n0 + 1] - P.ps_z[n0]), 0.f), 1.f);
+      const float *amp = P.amp + n0 * (N / 2 + 1);
+      small_scale_modes<N, true>(buf, amp, amp + (N / 2 + 1), w_hi, static_cast<uint32_t>(s), sk.id, P.seed, t);
+    } else {
+      small_scale_modes<N, false>(buf, P.amp, nullptr, 0.f, static_cast<uint32_t>(s), sk.id, P.seed, t);
+    }
     team_sync<T>(team);
     inverse_real_fft<N>(buf, tws, t, team);
 
     // ---- per pixel: gather, growth, FGPA, stores, pixel sums
-    const int jb = sk.j_lo + static_cast<int>(j0);
     int pend = 0;  // segment pixel where bin zc ends
     if (P.do_stats) {
       const int zs = __ldg(P.zbin + jb);

@@ -27,8 +27,8 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_struct_layouts_match_header_sizes():
-    # 4 doubles, 4 int32, a pointer, interp (int32) and 4 bytes of tail padding
-    assert C.sizeof(mk.SkewerParams) == 8 * 4 + 4 * 4 + 8 + 4 + 4
+    # 4 doubles, 4 int32, a pointer, interp and p_s_nodes (int32), a pointer
+    assert C.sizeof(mk.SkewerParams) == 8 * 4 + 4 * 4 + 8 + 4 + 4 + 8
     assert C.sizeof(mk.FgpaNodes) == 8 + 4 * 8 * mk.MAX_NODES
     assert mk.QSO_DTYPE.itemsize == 32
     assert C.sizeof(mk.StatsOut) == 8 * (32 * 10 + 32 * 64 * 3 + 32 * 5)

@@ -315,6 +315,65 @@ def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
             assert abs(X[0]) < 1e-5 * rms
 
 
+def _p_s_nodes_workload(w):
+    # three redshift nodes with 0.5x, 1x and 2.5x the small-scale power
+    # (Sec. 2.6 tunes P_s at each z_t); segment windows fall on both sides of
+    # the middle node and beyond the outer ones
+    return si.shrink(w, p_s=np.stack([0.5 * w["p_s"], w["p_s"], 2.5 * w["p_s"]]), p_s_z=[2.1, 2.4, 2.8])
+
+
+def test_z_dependent_small_scale_power_matches_oracle(ctx, tiny):
+    w, dv = _p_s_nodes_workload(tiny["w"]), tiny["dev"]
+    n = len(tiny["ids"])
+    o = oracle.run_skewers(w, tiny["d"], tiny["e"], tiny["pos"], tiny["ids"], n_threads=16)
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    box = load(ctx, w, dv["d"], dv["e"], "padded")
+    st, g = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
+    tot = int(o["offsets"][-1])
+    assert_field_close(g["delta"][:tot].cpu().numpy(), o["delta"], "delta_tot")
+    assert_field_close(g["eta"][:tot].cpu().numpy(), o["eta"], "eta")
+    assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
+    assert_stats_close(st, so)
+    # the node tables change the field: it is not the one-table field
+    st1, g1 = ctx.run(box, dv["qso"], n, tiny["w"], flags=mk.STATS | mk.STORE_FIELDS)
+    d0, d1 = g["delta"][:tot].cpu().numpy(), g1["delta"][:tot].cpu().numpy()
+    assert np.abs(d0 - d1).max() > 0.1
+    # back on one table, the cached amplitudes are replaced again
+    st2, g2 = ctx.run(box, dv["qso"], n, tiny["w"], flags=mk.STATS | mk.STORE_FIELDS)
+    assert torch.equal(g2["delta"][:tot], g1["delta"][:tot])
+
+
+def test_z_dependent_small_scale_power_modes(ctx, tiny):
+    # zero box: each segment's DFT gives back the oracle's modes at the
+    # power interpolated to the mean z of its window
+    w = _p_s_nodes_workload(tiny["w"])
+    z = torch.zeros_like(tiny["dev"]["d"])
+    box = ctx.load_box(w, z, z)
+    idx = np.arange(6)
+    r = ctx.make_skewers(box, mk.catalogue_tensor(tiny["pos"][idx], tiny["ids"][idx]), 6, w)
+    ds = r["delta"].cpu().numpy().astype(np.float64)
+    off = r["offsets"].cpu().numpy()
+    rec = records(r["sk"], 6)
+    N = w["n_fft"]
+    for q in range(6):
+        x = ragged(ds, off, q)
+        for s in range(len(x) // N):
+            X = np.fft.rfft(x[s * N:(s + 1) * N])
+            ref = oracle.small_scale_modes(w, int(tiny["ids"][q]), s, j0=int(rec["j_lo"][q]) + s * N)
+            rms = math.sqrt(np.mean(np.abs(ref[1:]) ** 2))
+            np.testing.assert_allclose(X[1:], ref[1:], rtol=0, atol=1e-5 * rms)
+
+
+def test_z_dependent_small_scale_power_rejects_bad_nodes(ctx, tiny):
+    box = ctx.load_box(tiny["w"], tiny["dev"]["d"], tiny["dev"]["e"])
+    w = si.shrink(_p_s_nodes_workload(tiny["w"]), p_s_z=[2.1, 2.1, 2.8])
+    with pytest.raises(mk.MkError) as ei:
+        ctx.run(box, tiny["dev"]["qso"], 10, w)
+    assert ei.value.code == mk.MK_EINVAL
+    with pytest.raises(ValueError):
+        mk.skewer_params(si.shrink(tiny["w"], p_s_z=[2.0, 3.0]))
+
+
 def test_graph_replay_and_autotune_match_direct_launch(ctx, tiny):
     w, dv = tiny["w"], tiny["dev"]
     box = load(ctx, w, dv["d"], dv["e"], "padded")
