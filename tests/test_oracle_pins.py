@@ -311,6 +311,97 @@ def test_p_s_nodes_interpolate_power_at_window_mean_z():
     assert zs[0] < 2.2 and zs[1] > 2.6
 
 
+# ------------------------------------------------------------ tuning of a, b sigma_g and P_s (Sec. 2.6)
+from oracle import ps_tuning  # noqa: E402
+
+
+def test_gauss_moments_without_dispersion():
+    for a in (0.3, 1.2):
+        f, sf = ps_tuning.fgpa_gauss_moments(a, 0.0)
+        assert abs(f - math.exp(-a)) < 1e-14 and sf < 1e-7
+
+
+@pytest.mark.parametrize("a,s", [(0.5, 0.3), (0.2, 0.25), (0.05, 0.35)])
+def test_gauss_moments_lognormal_series(a, s):
+    # E[exp(-t X)] = sum_n (-t)^n E[X^n] / n!, X lognormal with E[X^n] = exp(n^2 s^2 / 2):
+    # t = a gives F-bar, t = 2a gives E[F^2]; the terms are below 1e-14 by n = 30
+    def series(t):
+        return sum((-t) ** n * math.exp(0.5 * n * n * s * s) / math.factorial(n) for n in range(31))
+    f, sf = ps_tuning.fgpa_gauss_moments(a, s)
+    m1, m2 = series(a), series(2.0 * a)
+    assert abs(f - m1) < 1e-12
+    assert abs(sf - math.sqrt(m2 - m1 * m1)) < 1e-10
+
+
+def test_gauss_moments_monte_carlo():
+    rng = np.random.default_rng(2310)
+    a, s = 0.8, 1.5
+    x = rng.standard_normal(4_000_000)
+    f = np.exp(-a * np.exp(s * x))
+    got, gsf = ps_tuning.fgpa_gauss_moments(a, s)
+    se = f.std() / math.sqrt(f.size)
+    assert abs(got - f.mean()) < 5 * se
+    assert abs(gsf - f.std()) < 5 * se * 2
+
+
+@pytest.mark.parametrize("a,s", [(0.3, 0.8), (1.2, 1.6), (0.08, 2.4)])
+def test_fit_a_bsigma_recovers_parameters(a, s):
+    f, sf = ps_tuning.fgpa_gauss_moments(a, s)
+    a2, s2 = ps_tuning.fit_a_bsigma(f, sf)
+    assert abs(a2 / a - 1) < 1e-7 and abs(s2 / s - 1) < 1e-7
+    with pytest.raises(ValueError):
+        ps_tuning.fit_a_bsigma(f, math.sqrt(f * (1 - f)))
+
+
+def test_sigma_f_from_white_p1d():
+    # white noise of variance v: every mode has P = v dr, and the DC-free
+    # variance within a segment is v (N - 1) / N
+    v, dr, n, fbar = 0.04, 0.6, 256, 0.7
+    got = ps_tuning.sigma_f_from_p1d(fbar, np.full(32, v * dr), n, dr)
+    assert abs(got - fbar * math.sqrt(v * (n - 1) / n)) < 1e-15
+
+
+def test_sigma_f_from_p1d_is_the_segment_variance():
+    # Parseval on real segments, binned like the statistics (equal-count k
+    # bins of the P1D modes): the mode sum misses only Nyquist's share
+    rng = np.random.default_rng(5)
+    n, dr, nk = 256, 0.2, 32
+    x = rng.standard_normal((400, n)) * np.exp(-np.arange(n) / 300.0)
+    X = np.fft.rfft(x, axis=1)
+    p = (dr / n) * np.abs(X[:, 1:]) ** 2              # modes 1..N/2
+    pb = p.mean(axis=0).reshape(nk, -1).mean(axis=1)  # k-bin means
+    var = np.mean(np.var(x, axis=1))
+    got = ps_tuning.sigma_f_from_p1d(1.0, pb, n, dr) ** 2
+    nyq_err = abs(p[:, -1].mean() - pb[-1]) / (n * dr)
+    assert abs(got - var) <= nyq_err + 1e-12 * var
+
+
+def test_sigma_g2_from_pixel_sums():
+    # one z bin over every pixel of a tiny run: the bin's sums give the
+    # variance of delta_tot + c eta over those pixels
+    w = si.shrink(si.workload("tiny"), n_zbins=1, z_bin_lo=0.0, dz_bin=11.0)
+    d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"])
+    pos, ids = si.catalogue(w, n_q=20)
+    o = oracle.run_skewers(w, d, e, pos, ids, n_threads=NTHREADS)
+    st = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    for c in (0.0, 0.8, -1.3):
+        ref = np.var(o["delta"] + c * o["eta"])
+        assert abs(ps_tuning.sigma_g2(st["sums"][0], c) / ref - 1) < 1e-10
+
+
+def test_mode_bins():
+    np.testing.assert_array_equal(ps_tuning.mode_bins(256, 256, 1, 32)[1:], (np.arange(1, 129) - 1) // 4)
+    mb = ps_tuning.mode_bins(1024, 256, 1, 32)   # 4 P_s modes per P1D mode
+    assert mb[1] == 0 and mb[512] == 31 and mb[16] == 0 and mb[18] == 1
+    mb = ps_tuning.mode_bins(256, 256, 3, 32)    # rebin 3: k beyond the P1D range -> last bin
+    assert mb[1] == 0 and mb[2] == 1 and np.all(mb[43:] == 31)
+
+
+def test_follow_nearest_tuned_node():
+    np.testing.assert_array_equal(ps_tuning._follow(np.array([0, 1, 1, 0, 0, 1, 0], bool)),
+                                  [1, 1, 2, 2, 5, 5, 5])
+
+
 # ------------------------------------------------------------ geometry
 def test_geometry_forest_window():
     w = si.workload("tiny")
