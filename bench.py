@@ -269,6 +269,31 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
                                    "final_loss": float(losses[-1]) if len(losses) else None}}
 
 
+# ---------------------------------------------------------------- Sec. 2.6 P_S tuning
+def ps_tuning_leg(ctx, mk, box, qso, n_q, w, n_outer, n_inner):
+    """The paper's procedure (mk_tune_ps): a, b sigma_g fitted to F-bar and the
+    P1D integral, c from beta, b from the measured sigma_g, then ratio
+    iterations of P_S(k, z) at the 12 nodes, every pass a fused synthesis of
+    the whole catalogue.  Target: the statistics of the catalogue synthesised
+    at seeded hidden a*, b*, c* and P_S*(k, z)."""
+    import torch
+    from paper_2310_18996_gb300 import tuning
+
+    target, _, _ = tuning.make_ps_target(ctx, box, qso, n_q, w, seed=7)
+    torch.cuda.empty_cache()
+    p0 = tuning.start_small_scale_power(w)
+    nd, ps, rep = mk.tune_ps(ctx, box, qso, n_q, w, target, p0, n_outer=n_outer, n_inner=n_inner)
+    hist = [round(float(rep.max_rel_p1d_pass[i]), 5) for i in range(rep.passes)]
+    return {"workload": f"{w['n']}^3 box, {n_q} quasars, 12 z nodes (bin centres), P_S at each node, every pass "
+                        "a fused synthesis of the catalogue (mk_run, statistics only)",
+            "target": "statistics at seeded hidden a*, b*, c* power laws and P_S*(k, z) = P_S(k) (1 + A (z - 2.6)) "
+                      "(k / k_8)^t; start: the workload's P_S at every node",
+            "outer": n_outer, "inner": n_inner, "passes": rep.passes, "gpu_ms": rep.gpu_ms,
+            "ms_per_pass": rep.gpu_ms / max(rep.passes, 1), "wall_ms": rep.wall_ms,
+            "max_abs_dfbar": rep.max_abs_dfbar, "max_rel_p1d": rep.max_rel_p1d, "max_rel_beta": rep.max_rel_beta,
+            "max_rel_p1d_per_pass": hist}
+
+
 # ---------------------------------------------------------------- GPU arm
 def run_gb300(args, rank, world, local_rank):
     import torch
@@ -439,6 +464,9 @@ def run_gb300(args, rank, world, local_rank):
         slopes = None if args.surrogate_slopes == "none" else tuple(float(v) for v in args.surrogate_slopes.split(","))
         tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs,
                          args.surrogate_source, slopes)
+    pst = None
+    if rank == 0 and world == 1 and not args.no_ps_tuning:
+        pst = ps_tuning_leg(ctx, mk, box, qso, n_q, w, args.ps_outer, args.ps_inner)
     cpu = None
     if want_cpu:
         rate, px, n, dt = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds, os.cpu_count() or 1)
@@ -476,6 +504,8 @@ def run_gb300(args, rank, world, local_rank):
             line["cpu_baseline"] = cpu
         if tune:
             line["tuning"] = tune
+        if pst:
+            line["ps_tuning"] = pst
         if gauss:
             line["gauss7"] = gauss
         if tens:
@@ -499,6 +529,9 @@ def main():
     ap.add_argument("--no-gauss7", action="store_true")
     ap.add_argument("--no-tensor", action="store_true")
     ap.add_argument("--no-tuning", action="store_true")
+    ap.add_argument("--no-ps-tuning", action="store_true")
+    ap.add_argument("--ps-outer", type=int, default=5, help="outer loops of the Sec. 2.6 P_S tuning")
+    ap.add_argument("--ps-inner", type=int, default=10, help="P_S ratio iterations per outer loop")
     ap.add_argument("--surrogate-draws", type=int, default=8000)
     ap.add_argument("--surrogate-epochs", type=int, default=300)
     ap.add_argument("--surrogate-slopes", default="1.8,0.45,0.45",

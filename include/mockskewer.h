@@ -504,6 +504,65 @@ int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, 
             mk_mlp *surrogate, const mk_surrogate_norm *norm, int32_t max_passes,
             mk_fgpa_nodes *inout, mk_tune_report *report);
 
+/* ------------------------------------------- Sec. 2.6 tuning of a, b sigma_g and P_S */
+
+/* Mean and dispersion of the FGPA flux of a Gaussian field (Sec. 2.6: with g
+   Gaussian, F-bar and sigma_F depend only on a and b sigma_g):
+   F = exp(-a exp(s xi)), xi ~ N(0, 1), s = b sigma_g.  Host only (composite
+   8-point Gauss-Legendre over xi in [-10, 10]).  MK_EINVAL for a <= 0, s < 0
+   or a NULL output. */
+int mk_fgpa_gauss_moments(double a, double s, double *fbar, double *sigma_f);
+
+/* The (a, s = b sigma_g) whose moments above are (fbar, sigma_f) (Sec. 2.6
+   fits a and b sigma_g to the target F-bar and sigma_F): Newton iteration in
+   (ln a, ln s).  MK_EINVAL unless 0 < fbar < 1 and
+   0 < sigma_f < sqrt(fbar (1 - fbar)) (no (a, s) reaches it), or if the
+   iteration does not converge. */
+int mk_fit_a_bsigma(double fbar, double sigma_f, double *a, double *s);
+
+#define MK_PS_TUNE_MAX_PASSES 128
+
+typedef struct mk_ps_tune_report {
+  int32_t passes;    /* fused passes run: n_outer (1 + n_inner) + 1 */
+  double gpu_ms;     /* GPU time of the passes */
+  double wall_ms;
+  double sigma_f_target[MK_MAX_ZBINS]; /* from the integral of the target P1D */
+  double bsigma[MK_MAX_ZBINS];         /* fitted b sigma_g per node */
+  double sigma_g[MK_MAX_ZBINS];        /* measured on the last outer loop's first pass */
+  /* of the last pass, over the active bins (P1D over k bins [k_lo, k_hi)) */
+  double max_abs_dfbar, max_rel_p1d, max_rel_beta;
+  double max_rel_p1d_pass[MK_PS_TUNE_MAX_PASSES]; /* the same P1D error after every pass */
+} mk_ps_tune_report;
+
+/* The tuning procedure of Sec. 2.6, each pass a fused synthesis of the whole
+   catalogue (mk_run with MK_STATS; the paper re-generates its spectra for
+   every P_S iteration).  Tuning redshifts are the z-bin centres of `bins`;
+   bins outside target->active are not tuned and copy the nearest tuned node
+   (ties: the lower).
+     1. c = target beta (beta = f c, f = 1);
+     2. per bin, a and s = b sigma_g are fitted (mk_fit_a_bsigma) to the target
+        F-bar and to sigma_F = F-bar sqrt(sum over DFT modes m = 1..N-1 of
+        P1D_dF(k_m) / (N dr)), N = bins->n_fft, the mode sum taken from the
+        target's equal-count k-bin means (the Nyquist mode: the last bin's mean);
+     3. n_outer times: one pass gives sigma_g^2 = var(delta_tot + c eta) over
+        each bin's pixels (sigma_L^2 + sigma_S^2 + c^2 sigma_eta^2 + 2 c cov),
+        then b = s / sigma_g; then n_inner passes, after each of which every
+        P_S mode m of node i is multiplied by target P1D / measured P1D_dF of
+        bin i in the k bin that holds P1D mode round(m bins->n_fft / n_fft)
+        (clamped to 1 .. bins->n_fft/2);
+     4. a last pass measures the result.
+   box, d_qso, n_qso, params: as mk_run (params' own P_S fields are ignored).
+   target: mean_flux in (0, 1), p1d > 0 in every one of the n_k bins and use_beta
+   = 1 in every active bin; k_lo, k_hi and the tolerances only shape the report.
+   d_sk (n_qso records), d_offsets (n_qso + 1): caller-owned device scratch.
+   h_p_s: bins->n_z tables of n_fft/2 + 1 values (host, FP64), in: the start,
+   out: the tuned tables.  out: bins->n_z nodes (z, ln a, b, c).
+   n_outer >= 1, n_inner >= 0, passes <= MK_PS_TUNE_MAX_PASSES.  Synchronous. */
+int mk_tune_ps(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
+               const mk_skewer_params *params, const mk_stat_bins *bins, const mk_tune_target *target,
+               int32_t n_outer, int32_t n_inner, mk_skewer *d_sk, int64_t *d_offsets, double *h_p_s,
+               mk_fgpa_nodes *out, mk_ps_tune_report *report);
+
 /* ---------------------------------------------------------------- timing */
 
 /* When on (non-zero), the library records CUDA events on the context's

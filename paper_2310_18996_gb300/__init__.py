@@ -30,7 +30,8 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_pack_box_halo", "mk_pack_box_tensor", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
-           "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune"]
+           "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
+           "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps"]
 
 
 class MkError(RuntimeError):
@@ -97,6 +98,17 @@ class TuneTarget(C.Structure):
                 ("beta", C.c_double * MAX_ZBINS), ("use_beta", C.c_int32),
                 ("k_lo", C.c_int32), ("k_hi", C.c_int32), ("active", C.c_uint32),
                 ("tol_mean_flux", C.c_double), ("tol_p1d", C.c_double), ("tol_beta", C.c_double)]
+
+
+PS_TUNE_MAX_PASSES = 128
+
+
+class PsTuneReport(C.Structure):
+    _fields_ = [("passes", C.c_int32), ("gpu_ms", C.c_double), ("wall_ms", C.c_double),
+                ("sigma_f_target", C.c_double * MAX_ZBINS), ("bsigma", C.c_double * MAX_ZBINS),
+                ("sigma_g", C.c_double * MAX_ZBINS), ("max_abs_dfbar", C.c_double),
+                ("max_rel_p1d", C.c_double), ("max_rel_beta", C.c_double),
+                ("max_rel_p1d_pass", C.c_double * PS_TUNE_MAX_PASSES)]
 
 
 class TuneReport(C.Structure):
@@ -167,6 +179,10 @@ def lib():
                 "mk_tune": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, vp, P(StatBins),
                                       P(TuneTarget), i32, vp, P(SurrogateNorm), i32, P(FgpaNodes),
                                       P(TuneReport)]),
+                "mk_fgpa_gauss_moments": (C.c_int, [C.c_double, C.c_double, P(C.c_double), P(C.c_double)]),
+                "mk_fit_a_bsigma": (C.c_int, [C.c_double, C.c_double, P(C.c_double), P(C.c_double)]),
+                "mk_tune_ps": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(StatBins), P(TuneTarget), i32,
+                                         i32, vp, vp, P(C.c_double), P(FgpaNodes), P(PsTuneReport)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -557,3 +573,38 @@ def tune(ctx, w, sk, n_sk, offsets, delta, eta, target, nodes, method=TUNE_PLAIN
                              C.byref(norm) if norm is not None else None, max_passes, C.byref(nd),
                              C.byref(rep)))
     return nd, rep
+
+
+def fgpa_gauss_moments(a, s):
+    """(F-bar, sigma_F) of exp(-a exp(s xi)), xi ~ N(0, 1) (Sec. 2.6)."""
+    f, sf = C.c_double(), C.c_double()
+    rc = lib().mk_fgpa_gauss_moments(a, s, C.byref(f), C.byref(sf))
+    if rc != MK_OK:
+        raise MkError(rc, "mk_fgpa_gauss_moments: bad argument")
+    return f.value, sf.value
+
+
+def fit_a_bsigma(fbar, sigma_f):
+    """(a, b sigma_g) reaching (F-bar, sigma_F) for a Gaussian field (Sec. 2.6)."""
+    a, s = C.c_double(), C.c_double()
+    rc = lib().mk_fit_a_bsigma(fbar, sigma_f, C.byref(a), C.byref(s))
+    if rc != MK_OK:
+        raise MkError(rc, "mk_fit_a_bsigma: no (a, b sigma_g) reaches this mean flux and sigma_F")
+    return a.value, s.value
+
+
+def tune_ps(ctx, box, qso, n_qso, w, target, p_s0, n_outer=5, n_inner=10):
+    """Run mk_tune_ps (the Sec. 2.6 procedure); returns (FgpaNodes, P_S tables
+    of shape (n_z, n_fft/2 + 1), PsTuneReport)."""
+    torch = ctx._torch
+    p = skewer_params(w)
+    b = stat_bins(w)
+    ps = np.array(p_s0, dtype=np.float64).reshape(b.n_z, w["n_fft"] // 2 + 1).copy()
+    sk = torch.empty(max(n_qso, 1) * SKEWER_BYTES, dtype=torch.uint8, device=qso.device)
+    off = torch.empty(n_qso + 1, dtype=torch.int64, device=qso.device)
+    nd = FgpaNodes()
+    rep = PsTuneReport()
+    ctx._stream()
+    ctx._check(lib().mk_tune_ps(ctx.h, box.handle, _ptr(qso), n_qso, C.byref(p), C.byref(b), C.byref(target),
+                                n_outer, n_inner, _ptr(sk), _ptr(off), _dp(ps), C.byref(nd), C.byref(rep)))
+    return nd, ps, rep

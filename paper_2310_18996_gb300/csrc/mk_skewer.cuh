@@ -121,9 +121,8 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
                                     sk.p0[1] + kRoundQ + ps * sk.step[1], sk.p0[2] + kRoundQ + ps * sk.step[2]);
     }
     // ---- small-scale field of this segment
-    const int jb = sk.j_lo + static_cast<int>(j0);
     if (P.ps_nodes >= 2) {  // P_s at the mean z of the segment's window, linear between nodes
-      const float zw = __ldg(P.zwin + jb);
+      const float zw = __ldg(P.zwin + sk.j_lo + static_cast<int>(j0));
       const int k = P.ps_nodes;
       int n0 = 0;
       while (n0 + 2 < k && zw >= P.ps_z[n0 + 1]) ++n0;
@@ -137,6 +136,7 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
     inverse_real_fft<N>(buf, tws, t, team);
 
     // ---- per pixel: gather, growth, FGPA, stores, pixel sums
+    const int jb = sk.j_lo + static_cast<int>(j0);
     int pend = 0;  // segment pixel where bin zc ends
     if (P.do_stats) {
       const int zs = __ldg(P.zbin + jb);

@@ -109,3 +109,36 @@ def start_nodes(w, ln_a=math.log(0.2), b=1.6, c=1.0):
     zs = node_z(w)
     n = len(zs)
     return nodes(zs, [ln_a] * n, [b] * n, [c] * n)
+
+
+# ------------------------------------------------------------ small-scale power (Sec. 2.6)
+def hidden_small_scale_power(w, seed):
+    """Seeded P_S*(k, z) = P_S(k) (1 + A (z - 2.6)) (k / k_8)^t at the bin-centre
+    nodes, A in [-0.4, 0.4], t in [-0.3, 0.3], k_8 the mode n_fft/8; P_S(k) is
+    the workload's table.  Shape (n_z, n_fft/2 + 1)."""
+    rng = np.random.default_rng(seed + 1000)
+    amp, tilt = rng.uniform(-0.4, 0.4), rng.uniform(-0.3, 0.3)
+    n = w["n_fft"]
+    p0 = np.asarray(w["p_s"], dtype=np.float64).reshape(-1, n // 2 + 1)[0]
+    m = np.arange(n // 2 + 1, dtype=np.float64)
+    shape = np.where(m > 0, (np.maximum(m, 1.0) / (n // 8)) ** tilt, 1.0)
+    return np.stack([p0 * shape * (1.0 + amp * (z - 2.6)) for z in node_z(w)])
+
+
+def start_small_scale_power(w):
+    """The workload's one P_S table at every bin-centre node: (n_z, n_fft/2 + 1)."""
+    n = w["n_fft"]
+    p0 = np.asarray(w["p_s"], dtype=np.float64).reshape(-1, n // 2 + 1)[0]
+    return np.tile(p0, (len(node_z(w)), 1))
+
+
+def make_ps_target(ctx, box, qso, n_qso, w, seed=5, **kw):
+    """(TuneTarget, hidden FgpaNodes, hidden P_S tables): the statistics of the
+    catalogue synthesised with the seeded hidden P_S*(k, z) and the hidden
+    a*, b*, c* of make_target (on skewers stored at P_S*)."""
+    ps = hidden_small_scale_power(w, seed)
+    ws = dict(w, p_s=ps, p_s_z=node_z(w))
+    r = ctx.make_skewers(box, qso, n_qso, ws)
+    t, nd = make_target(ctx, ws, r["sk"], n_qso, r["offsets"], r["delta"], r["eta"], seed=seed, **kw)
+    del r
+    return t, nd, ps

@@ -59,3 +59,33 @@ def test_context_creation_fails_cleanly_without_gpu():
     assert not h.value
     with pytest.raises(RuntimeError):
         mk.Context()
+
+
+# ------------------------------------------------------------ Sec. 2.6 host logic
+def test_ps_tune_report_layout():
+    assert C.sizeof(mk.PsTuneReport) == 8 + 8 + 8 + 3 * 8 * 32 + 3 * 8 + 8 * mk.PS_TUNE_MAX_PASSES
+
+
+@pytest.mark.parametrize("a,s", [(0.3, 0.8), (1.2, 1.6), (0.08, 2.4), (2.0, 3.0), (0.02, 3.5), (0.7, 0.0)])
+def test_gauss_moments_match_oracle(a, s):
+    from oracle import ps_tuning
+    f, sf = mk.fgpa_gauss_moments(a, s)
+    fo, sfo = ps_tuning.fgpa_gauss_moments(a, s)
+    assert abs(f - fo) < 1e-13 and abs(sf - sfo) < 1e-12
+
+
+@pytest.mark.parametrize("fbar,frac", [(0.95, 0.2), (0.8, 0.5), (0.55, 0.7), (0.3, 0.9), (0.9, 0.05)])
+def test_fit_a_bsigma_matches_oracle(fbar, frac):
+    from oracle import ps_tuning
+    sf = frac * (fbar * (1 - fbar)) ** 0.5
+    a, s = mk.fit_a_bsigma(fbar, sf)
+    ao, so = ps_tuning.fit_a_bsigma(fbar, sf)
+    assert abs(a / ao - 1) < 1e-8 and abs(s / so - 1) < 1e-8
+
+
+def test_fit_a_bsigma_rejects_unreachable_targets():
+    for fbar, sf in ((0.8, 0.4), (1.0, 0.1), (0.5, 0.0), (0.0, 0.1)):
+        with pytest.raises(mk.MkError):
+            mk.fit_a_bsigma(fbar, sf)
+    with pytest.raises(mk.MkError):
+        mk.fgpa_gauss_moments(-1.0, 0.5)
