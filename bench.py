@@ -269,6 +269,52 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
                                    "final_loss": float(losses[-1]) if len(losses) else None}}
 
 
+# ---------------------------------------------------------------- box synthesis (Sec. 2.1)
+def box_synth_leg(ctx, mk, w, dev, peak, reps=3):
+    """mk_synth_box at the benchmark's box size into the padded layout the
+    fused pass reads, against the fixture's torch/cuFFT synthesis plus
+    mk_pack_box_padded; CUDA events on the current stream, one untimed run each."""
+    import torch
+
+    n, cell = w["n"], w["cell"]
+    dk = 2.0 * np.pi * np.sqrt(3.0) / cell / 4000.0
+    tab = si.power_shape(dk * np.arange(4011))
+    work = torch.empty(2 * n ** 3, dtype=torch.float32, device=dev)
+    out = torch.empty(2 * (n + 1) ** 3, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def lib_once(seed):
+        ctx._stream()
+        ctx._check(mk.lib().mk_synth_box(ctx.h, n, cell, seed, mk._dp(tab), tab.size, dk, mk.BOX_PADDED,
+                                         mk._ptr(work), None, mk._ptr(out)))
+
+    def torch_once(seed):
+        d, e = si.gaussian_box(n, cell, seed, backend="torch", device=dev)
+        ctx.pack_box(d, e, padded=True)
+        del d, e
+
+    res = {}
+    for name, fn in (("library", lib_once), ("torch_cufft_fixture", torch_once)):
+        fn(1)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for r in range(reps):
+            fn(2 + r)
+        e1.record(st)
+        e1.synchronize()
+        res[name] = e0.elapsed_time(e1) / reps
+    del work, out
+    torch.cuda.empty_cache()
+    # bytes of the five passes: noise+x (write), y, z (read+write each), inverse y,
+    # inverse x (read, padded write)
+    b = 8.0 * n ** 3 * (1 + 2 + 2 + 2 + 1) + 8.0 * (n + 1) ** 3
+    return {"box": f"{n}^3, cell {cell}, delta + eta_xx into the padded layout",
+            "ms": res["library"], "fixture_ms": res["torch_cufft_fixture"],
+            "pass_bytes": b, "achieved_gbs": b / (res["library"] * 1e6), "frac_of_hbm_peak": b / (res["library"] * 1e6) / peak,
+            "design": "5 passes: Philox noise + FFT x | FFT y | FFT z, filter, inverse z | inverse y | inverse x + layout"}
+
+
 # ---------------------------------------------------------------- Sec. 2.6 P_S tuning
 def ps_tuning_leg(ctx, mk, box, qso, n_q, w, n_outer, n_inner):
     """The paper's procedure (mk_tune_ps): a, b sigma_g fitted to F-bar and the
@@ -464,6 +510,9 @@ def run_gb300(args, rank, world, local_rank):
         slopes = None if args.surrogate_slopes == "none" else tuple(float(v) for v in args.surrogate_slopes.split(","))
         tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs,
                          args.surrogate_source, slopes)
+    boxs = None
+    if rank == 0 and world == 1 and not args.no_box_synth and w["n"] in (128, 256, 512, 1024):
+        boxs = box_synth_leg(ctx, mk, w, dev, peak)
     pst = None
     if rank == 0 and world == 1 and not args.no_ps_tuning:
         pst = ps_tuning_leg(ctx, mk, box, qso, n_q, w, args.ps_outer, args.ps_inner)
@@ -506,6 +555,8 @@ def run_gb300(args, rank, world, local_rank):
             line["tuning"] = tune
         if pst:
             line["ps_tuning"] = pst
+        if boxs:
+            line["box_synth"] = boxs
         if gauss:
             line["gauss7"] = gauss
         if tens:
@@ -530,6 +581,7 @@ def main():
     ap.add_argument("--no-tensor", action="store_true")
     ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--no-ps-tuning", action="store_true")
+    ap.add_argument("--no-box-synth", action="store_true")
     ap.add_argument("--ps-outer", type=int, default=5, help="outer loops of the Sec. 2.6 P_S tuning")
     ap.add_argument("--ps-inner", type=int, default=10, help="P_S ratio iterations per outer loop")
     ap.add_argument("--surrogate-draws", type=int, default=8000)

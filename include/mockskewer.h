@@ -244,6 +244,30 @@ int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *
    stream.  MK_EINVAL as mk_pack_box_padded, or d_out not 16-byte aligned. */
 int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta6, float *d_out);
 
+/* Synthesise the Gaussian boxes of Sec. 2.1 on the device: delta with power
+   spectrum P(k) (Eq. deltaL) and the velocity-gradient boxes
+   eta_pq = -k_p k_q / k^2 delta in Fourier space (Eq. eta with f = 1 and the
+   sign of this library's single-box contract), straight into a box layout.
+     white noise: voxel v = (z n + y) n + x; Philox4x32-10, key (seed low 32
+       bits, seed high 32 bits), counter (v/4 low, v/4 high, 0, 0); words (0, 1)
+       give voxels 4(v/4) and +1, words (2, 3) voxels +2 and +3 (Box-Muller,
+       u = (x + 1/2) 2^-32);
+     modes: DFT(delta)_k = DFT(noise)_k sqrt(P(|k|) / cell^3), with the k = 0
+       mode and every mode with an index n/2 on an axis set to 0; k along an
+       axis at index j is 2 pi (j or j - n) / (n cell);
+     P(k): h_pk[i] at k = i dk, i < n_pk (2 .. 2^24), linear in between, 0 beyond.
+   n: 128, 256, 512 or 1024.  layout and d_out (caller-owned device memory):
+     MK_BOX_INTERLEAVED: (delta, eta_xx) pairs, 2 n^3 floats (d_out may be d_work);
+     MK_BOX_PADDED, MK_BOX_HALO: as mk_pack_box_padded / mk_pack_box_halo;
+     MK_BOX_TENSOR: as mk_pack_box_tensor, and d_spec (2 n^3 floats) keeps the
+       delta modes between the four inverse transforms (NULL otherwise).
+   d_work: 2 n^3 floats of caller-owned scratch, 8-byte aligned, overwritten;
+   it must not overlap d_out (except INTERLEAVED in place) or d_spec.
+   Asynchronous on the context stream (the P(k) upload waits for the
+   stream's earlier work).  MK_EINVAL for a bad size, layout, table or pointer. */
+int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, const double *h_pk, int32_t n_pk, double dk,
+                 int32_t layout, float *d_work, float *d_spec, float *d_out);
+
 /* ---------------------------------------------------------------- skewers */
 
 /* Pre-FGPA skewers (Eq. gfield inputs).  Always computes the geometry of the
@@ -339,7 +363,9 @@ int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_q
 
 /* Launch shape the context uses for a fused-kernel variant: *threads per CTA
    and *occupancy target, the register budget of that many 256-thread CTAs
-   per SM (2, 3 or 4).  layout: the box layout, plus 16 for MK_INTERP_GAUSS7.
+   per SM (2, 3 or 4).  layout: the box layout, plus 16 for MK_INTERP_GAUSS7,
+   plus 32 for P_S tables at several redshifts (p_s_nodes >= 2; that
+   instance has one register budget, 3).
    MK_OK when the autotuner chose it, MK_ERANGE when it is the default
    (still written). */
 int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box, uint32_t flags,

@@ -98,6 +98,7 @@ def lib():
                 "orc_growth": (d, [d, d]),
                 "orc_philox4x32_10": (None, [P(u32), P(u32), P(u32)]),
                 "orc_box_muller": (None, [u32, u32, P(d), P(d)]),
+                "orc_box_noise": (None, [C.c_uint64, i32, P(d)]),
                 "orc_dft_forward_real": (None, [P(d), i32, P(d), P(d)]),
                 "orc_dft_inverse_hermitian": (None, [P(d), P(d), i32, P(d)]),
                 "orc_geometry": (C.c_int, [P(Cfg), P(d), P(i32), P(i32), P(d)]),
@@ -158,6 +159,13 @@ def box_muller(x1, x2):
     e1, e2 = C.c_double(), C.c_double()
     lib().orc_box_muller(int(x1) & 0xFFFFFFFF, int(x2) & 0xFFFFFFFF, C.byref(e1), C.byref(e2))
     return e1.value, e2.value
+
+
+def box_noise(seed, n):
+    """White noise of the synthetic box, shape (n, n, n) as [z][y][x]."""
+    out = np.zeros(n * n * n)
+    lib().orc_box_noise(int(seed) & 0xFFFFFFFFFFFFFFFF, int(n), _p(out, C.c_double))
+    return out.reshape(n, n, n)
 
 
 def dft_forward_real(x):

@@ -195,6 +195,25 @@ void orc_box_muller(uint32_t xu1, uint32_t xu2, double *e1, double *e2) {
   *e2 = rad * sin(2.0 * M_PI * u2);
 }
 
+/* White noise of a synthetic box (Sec. 2.1 draws the Gaussian boxes from    */
+/* white noise): voxel v = (z n + y) n + x; Philox4x32-10 with key (seed low, */
+/* seed high) and counter (g low, g high, 0, 0), g = v / 4; words (0, 1)     */
+/* give voxels 4g, 4g + 1 and words (2, 3) voxels 4g + 2, 4g + 3 through     */
+/* Box-Muller.                                                               */
+void orc_box_noise(uint64_t seed, int32_t n, double *out) {
+  const int64_t nv = (int64_t)n * n * n;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t g = 0; 4 * g < nv; ++g) {
+    const uint32_t ctr[4] = {(uint32_t)g, (uint32_t)((uint64_t)g >> 32), 0u, 0u};
+    uint32_t w[4];
+    orc_philox4x32_10(ctr, key, w);
+    double e[4];
+    orc_box_muller(w[0], w[1], &e[0], &e[1]);
+    orc_box_muller(w[2], w[3], &e[2], &e[3]);
+    for (int q = 0; q < 4 && 4 * g + q < nv; ++q) out[4 * g + q] = e[q];
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Discrete Fourier transforms written as their defining sums.               */
 /* ------------------------------------------------------------------------ */

@@ -103,6 +103,7 @@ double orc_growth(double omega_m, double z);
 /* ---- Philox4x32-10 (Salmon et al. 2011) and Box-Muller ---- */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void orc_box_muller(uint32_t xu1, uint32_t xu2, double *e1, double *e2);
+void orc_box_noise(uint64_t seed, int32_t n, double *out);
 
 /* ---- discrete Fourier transforms, O(N^2) ---- */
 void orc_dft_forward_real(const double *x, int32_t n, double *re, double *im);

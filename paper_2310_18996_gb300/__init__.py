@@ -31,7 +31,7 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
-           "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps"]
+           "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box"]
 
 
 class MkError(RuntimeError):
@@ -147,6 +147,8 @@ def lib():
                 "mk_pack_box_padded": (C.c_int, [vp, i32, vp, vp, vp]),
                 "mk_pack_box_halo": (C.c_int, [vp, i32, vp, vp, vp]),
                 "mk_pack_box_tensor": (C.c_int, [vp, i32, vp, vp, vp]),
+                "mk_synth_box": (C.c_int, [vp, i32, C.c_double, C.c_uint64, P(C.c_double), i32, C.c_double,
+                                           i32, vp, vp, vp]),
                 "mk_run_host": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(FgpaNodes), P(StatBins), u32,
                                           i32, vp, i64, P(i64), P(StatsOut)]),
                 "mk_make_skewers": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), vp, vp, vp, vp,
@@ -355,6 +357,25 @@ class Context:
         out = torch.empty(8 * (n + 1) ** 3, dtype=torch.float32, device=delta.device)
         self._stream()
         self._check(lib().mk_pack_box_tensor(self.h, n, _ptr(delta), _ptr(eta6), _ptr(out)))
+        return out
+
+    def synth_box(self, n, cell, seed, pk, dk, layout=BOX_PADDED, work=None):
+        """Gaussian delta and eta boxes of side n (Sec. 2.1) from the P(k) table
+        pk (at k = i dk) and a seed, in `layout` (BOX_INTERLEAVED, BOX_PADDED,
+        BOX_HALO or BOX_TENSOR), for load_box(..., layout=layout)."""
+        torch = self._torch
+        dev = torch.device("cuda", self.device)
+        pk = np.ascontiguousarray(pk, dtype=np.float64)
+        side, stride = {BOX_INTERLEAVED: (n, 2), BOX_PADDED: (n + 1, 2), BOX_HALO: (n + 6, 2),
+                        BOX_TENSOR: (n + 1, 8)}[layout]
+        if work is None:
+            work = torch.empty(2 * n ** 3, dtype=torch.float32, device=dev)
+        out = work if layout == BOX_INTERLEAVED else torch.empty(stride * side ** 3, dtype=torch.float32,
+                                                                   device=dev)
+        spec = torch.empty(2 * n ** 3, dtype=torch.float32, device=dev) if layout == BOX_TENSOR else None
+        self._stream()
+        self._check(lib().mk_synth_box(self.h, n, cell, int(seed) & 0xFFFFFFFFFFFFFFFF, _dp(pk), pk.size, dk,
+                                       layout, _ptr(work), _ptr(spec), _ptr(out)))
         return out
 
     # skewers

@@ -169,6 +169,8 @@ struct mk_ctx {
   std::vector<double> amp_key;
   int ps_nodes = 1;  // node tables in d_amp (>= 2: squared amplitudes per node)
   float ps_z[MK_MAX_NODES] = {};
+  float *d_pk = nullptr;    // P(k) table of the box synthesis
+  int n_pk_cap = 0;
   float *d_zwin = nullptr;  // window mean z per J for segments of zwin_n pixels
   int zwin_n = 0;
   double zwin_dr = -1.0;
@@ -458,9 +460,11 @@ LaunchCfg default_cfg(int n_fft) {
   return LaunchCfg{256, 3};
 }
 
-// kernel variant: the box layout, plus kGauss7Variant for the Gaussian kernel
+// kernel variant: the box layout, plus kGauss7Variant for the Gaussian kernel,
+// plus kPsNodesVariant for P_s tables at several redshifts
 int kernel_variant(const mk_box *box, const mk_skewer_params *p) {
-  return box->desc.layout | (p->interp == MK_INTERP_GAUSS7 ? kGauss7Variant : 0);
+  return box->desc.layout | (p->interp == MK_INTERP_GAUSS7 ? kGauss7Variant : 0) |
+         (p->p_s_nodes >= 2 ? kPsNodesVariant : 0);
 }
 
 int check_interp(mk_ctx *ctx, const mk_box *box, const mk_skewer_params *p) {
@@ -613,6 +617,7 @@ void mk_destroy(mk_ctx *ctx) {
   cudaFree(ctx->d_bin_end);
   cudaFree(ctx->d_amp);
   cudaFree(ctx->d_zwin);
+  cudaFree(ctx->d_pk);
   for (auto *p : ctx->d_tw) cudaFree(p);
   cudaFree(ctx->d_cnt_px);
   cudaFree(ctx->d_cnt_seg);
@@ -1348,3 +1353,89 @@ int ctx_pixel_histogram(mk_ctx *ctx, double dr, const mk_skewer *d_sk, int64_t n
   return MK_OK;
 }
 }  // namespace mkhost
+
+extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, const double *h_pk, int32_t n_pk,
+                            double dk, int32_t layout, float *d_work, float *d_spec, float *d_out) {
+  if (!ctx) return MK_EINVAL;
+  int lgn = 0;
+  while ((1 << lgn) < n) ++lgn;
+  if (n < 128 || n > 1024 || (1 << lgn) != n) return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512 or 1024");
+  if (!(cell > 0.0) || !(dk > 0.0) || !h_pk || n_pk < 2 || n_pk > (1 << 24))
+    return fail(ctx, MK_EINVAL, "bad cell, dk or P(k) table (2 .. 2^24 entries)");
+  if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 7) || (reinterpret_cast<uintptr_t>(d_out) & 7))
+    return fail(ctx, MK_EINVAL, "d_work and d_out must be 8-byte aligned device pointers");
+  const int64_t nv = static_cast<int64_t>(n) * n * n;
+  int side = n, margin = 0, stride = 2, pairs = 1;
+  switch (layout) {
+    case MK_BOX_INTERLEAVED: break;
+    case MK_BOX_PADDED: side = n + 1; break;
+    case MK_BOX_HALO: side = n + 6; margin = 3; break;
+    case MK_BOX_TENSOR:
+      side = n + 1;
+      stride = 8;
+      pairs = 4;
+      if (!d_spec || (reinterpret_cast<uintptr_t>(d_spec) & 7))
+        return fail(ctx, MK_EINVAL, "MK_BOX_TENSOR needs an 8-byte aligned d_spec of 2 n^3 floats");
+      if ((reinterpret_cast<uintptr_t>(d_out) & 15)) return fail(ctx, MK_EINVAL, "MK_BOX_TENSOR: d_out not 16-byte aligned");
+      break;
+    default: return fail(ctx, MK_EINVAL, "layout must be interleaved, padded, halo or tensor");
+  }
+  auto overlap = [](const float *a, int64_t na, const float *b, int64_t nb) { return a < b + nb && b < a + na; };
+  const int64_t nout = static_cast<int64_t>(side) * side * side * stride;
+  if (!(layout == MK_BOX_INTERLEAVED && d_out == d_work) && overlap(d_work, 2 * nv, d_out, nout))
+    return fail(ctx, MK_EINVAL, "d_work overlaps d_out");
+  if (d_spec && (overlap(d_spec, 2 * nv, d_work, 2 * nv) || overlap(d_spec, 2 * nv, d_out, nout)))
+    return fail(ctx, MK_EINVAL, "d_spec overlaps d_work or d_out");
+  for (int i = 0; i < n_pk; ++i)
+    if (!(h_pk[i] >= 0.0)) return fail(ctx, MK_EINVAL, "P(k) must be >= 0");
+  CK(cudaSetDevice(ctx->device));
+  int rc;
+  if ((rc = ensure_twiddles(ctx, 2 * n))) return rc;
+  std::vector<float> pk(h_pk, h_pk + n_pk);
+  CK(cudaStreamSynchronize(ctx->stream));  // an earlier synthesis may still read the table
+  if (n_pk > ctx->n_pk_cap) {
+    cudaFree(ctx->d_pk);
+    ctx->d_pk = nullptr;
+    ctx->n_pk_cap = 0;
+    CK(cudaMalloc(&ctx->d_pk, sizeof(float) * n_pk));
+    ctx->n_pk_cap = n_pk;
+  }
+  CK(cudaMemcpy(ctx->d_pk, pk.data(), sizeof(float) * n_pk, cudaMemcpyHostToDevice));
+  BoxPassParams P{};
+  P.work = reinterpret_cast<float2 *>(d_work);
+  P.spec = layout == MK_BOX_TENSOR ? reinterpret_cast<float2 *>(d_spec) : nullptr;
+  P.tw = ctx->d_tw[tw_slot(2 * n)];
+  P.pk = ctx->d_pk;
+  P.n_pk = n_pk;
+  P.inv_dk = static_cast<float>(1.0 / dk);
+  P.kf = static_cast<float>(2.0 * M_PI / (n * cell));
+  P.amp = static_cast<float>(1.0 / (std::pow(cell, 1.5) * static_cast<double>(nv)));
+  P.key0 = static_cast<uint32_t>(seed);
+  P.key1 = static_cast<uint32_t>(seed >> 32);
+  P.lgn = lgn;
+  const bool in_place = layout == MK_BOX_INTERLEAVED && d_out == d_work;
+  P.out = in_place ? nullptr : d_out;
+  P.out_side = side;
+  P.out_margin = margin;
+  P.out_stride = stride;
+  for (int p = 0; p < pairs; ++p) {
+    P.pair = p;
+    P.out_slot = 2 * p;
+    if (p == 0) {
+      P.axis = 0;
+      CK(launch_box_pass(P, kBoxNoiseX, ctx->sms, ctx->stream));
+      P.axis = 1;
+      CK(launch_box_pass(P, kBoxFwd, ctx->sms, ctx->stream));
+      P.axis = 2;
+      CK(launch_box_pass(P, kBoxShapeZ, ctx->sms, ctx->stream));
+    } else {
+      P.axis = 2;
+      CK(launch_box_pass(P, kBoxSpecZ, ctx->sms, ctx->stream));
+    }
+    P.axis = 1;
+    CK(launch_box_pass(P, kBoxInv, ctx->sms, ctx->stream));
+    P.axis = 0;
+    CK(launch_box_pass(P, kBoxInvXOut, ctx->sms, ctx->stream));
+  }
+  return MK_OK;
+}

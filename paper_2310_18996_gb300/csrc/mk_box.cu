@@ -1,0 +1,253 @@
+// Gaussian box synthesis (Sec. 2.1, Eq. deltaL, Eq. eta): Philox white noise,
+// a 3D FFT made of batched line FFTs in shared memory, the sqrt(P(k)) filter
+// and the velocity-gradient filters -k_p k_q / k^2, written straight into the
+// library's box layouts.
+//
+// Five passes make one (delta, eta_pq) pair of boxes, each reading and writing
+// the n^3 complex work box once:
+//   noise + FFT x | FFT y | FFT z, filter, inverse FFT z | inverse y | inverse x + layout
+// Two real boxes come out of one complex inverse transform: the modes of
+// delta and eta are Hermitian, so IFFT(D f1 + i D f2) = (delta f1-box) + i (f2-box).
+#include <algorithm>
+
+#include "mk_device.cuh"
+#include "mk_kernels.h"
+
+namespace mk {
+namespace {
+
+constexpr int kLines = 8;     // lines per CTA group
+constexpr int kLinePad = 2;   // complex slots of padding per line buffer
+constexpr int kBoxThreads = 256;
+
+template <int N2>
+struct BoxSmem {
+  static constexpr int M = N2 / 2;  // line length n
+  static constexpr size_t bytes() { return TwTab<N2>::BYTES + sizeof(float2) * kLines * (M + kLinePad); }
+};
+
+__device__ __forceinline__ int wrap_index(int j, int n) { return j < n / 2 ? j : j - n; }
+
+// Filter pair p of the Sec. 2.1 boxes at wave vector k (k2 = |k|^2 > 0):
+// (f1, f2) with eta_pq = -k_p k_q / k^2 delta.
+__device__ __forceinline__ float2 pair_filter(int pair, float kx, float ky, float kz, float inv_k2) {
+  switch (pair) {
+    case 0: return make_float2(1.0f, -kx * kx * inv_k2);
+    case 1: return make_float2(-ky * ky * inv_k2, -kz * kz * inv_k2);
+    case 2: return make_float2(-kx * ky * inv_k2, -kx * kz * inv_k2);
+    default: return make_float2(-ky * kz * inv_k2, 0.0f);
+  }
+}
+
+// Address of element e of line c in group g along `axis` (box side n).
+__device__ __forceinline__ int64_t line_addr(int axis, int64_t g, int c, int e, int n) {
+  const int64_t nn = static_cast<int64_t>(n) * n;
+  if (axis == 0) return (g * kLines + c) * n + e;
+  const int64_t row = g / (n / kLines), x = (g % (n / kLines)) * kLines + c;
+  return axis == 1 ? row * nn + static_cast<int64_t>(e) * n + x : row * n + static_cast<int64_t>(e) * nn + x;
+}
+
+// Flat index i of a group's kLines * n elements to (line c, element e): along
+// x whole lines are contiguous; along y and z the kLines lines of one
+// element are.
+__device__ __forceinline__ void flat_to_ce(int axis, int i, int n, int &c, int &e) {
+  if (axis == 0) {
+    c = i / n;
+    e = i % n;
+  } else {
+    e = i / kLines;
+    c = i % kLines;
+  }
+}
+
+template <int N2, int MODE>
+__global__ void __launch_bounds__(kBoxThreads) k_box_pass(BoxPassParams P) {
+  constexpr int M = N2 / 2;  // box side
+  constexpr int T = Fft<N2>::T;
+  constexpr int TEAMS = kBoxThreads / T;
+  constexpr int LS = M + kLinePad;
+  constexpr int SIGN = (MODE == kBoxNoiseX || MODE == kBoxFwd || MODE == kBoxShapeZ) ? -1 : 1;
+  constexpr int AXIS_FIXED = (MODE == kBoxNoiseX || MODE == kBoxInvXOut) ? 0
+                             : (MODE == kBoxShapeZ || MODE == kBoxSpecZ) ? 2 : -1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tws = reinterpret_cast<float2 *>(smem_raw);
+  float2 *lines = reinterpret_cast<float2 *>(smem_raw + TwTab<N2>::BYTES);
+  fill_twiddles<N2>(tws, P.tw);
+  const int axis = AXIS_FIXED >= 0 ? AXIS_FIXED : P.axis;
+  const int team = threadIdx.x / T, t = threadIdx.x % T;
+  const int64_t groups = static_cast<int64_t>(M) * M / kLines;
+
+  for (int64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+    // ---- load (or draw) the group's lines
+    if constexpr (MODE == kBoxNoiseX) {
+      // 4 voxels per Philox call: (w0, w1) and (w2, w3) through Box-Muller
+      const int64_t v0 = g * kLines * M;
+      for (int i = 4 * threadIdx.x; i < kLines * M; i += 4 * kBoxThreads) {
+        const uint64_t q = static_cast<uint64_t>(v0 + i) >> 2;
+        const u32x4 w = philox4x32_10(u32x4{static_cast<uint32_t>(q), static_cast<uint32_t>(q >> 32), 0u, 0u},
+                                      P.key0, P.key1);
+        const float r0 = sqrt_pos(2.0f * neg_log_uniform(w.x)), r1 = sqrt_pos(2.0f * neg_log_uniform(w.z));
+        const float2 p0 = unit_phase(w.y), p1 = unit_phase(w.w);
+        const int c = i / M, e = i % M;  // 4 | M: the 4 voxels share a line
+        float2 *b = lines + c * LS + e;
+        b[0] = make_float2(r0 * p0.x, 0.f);
+        b[1] = make_float2(r0 * p0.y, 0.f);
+        b[2] = make_float2(r1 * p1.x, 0.f);
+        b[3] = make_float2(r1 * p1.y, 0.f);
+      }
+    } else {
+      const float2 *src = (MODE == kBoxSpecZ) ? P.spec : P.work;
+#pragma unroll 4
+      for (int i = threadIdx.x; i < kLines * M; i += kBoxThreads) {
+        int c, e;
+        flat_to_ce(axis, i, M, c, e);
+        lines[c * LS + e] = src[line_addr(axis, g, c, e, M)];
+      }
+    }
+    __syncthreads();
+
+    // ---- FFT along the line (forward, or inverse for the inverse modes)
+    if constexpr (MODE != kBoxSpecZ) {
+      for (int c = team; c < kLines; c += TEAMS) {
+        float2 *b = lines + c * LS;
+        float2 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = b[t + r * T];
+        dft4<SIGN>(v[0], v[1], v[2], v[3]);
+        fft_finish<N2, SIGN, true>(b, v, tws, t, team);
+      }
+      __syncthreads();
+    }
+
+    // ---- filter in mode space (z lines: element e is k_z)
+    if constexpr (MODE == kBoxShapeZ || MODE == kBoxSpecZ) {
+      const int64_t yrow = g / (M / kLines);
+      const int x0 = static_cast<int>(g % (M / kLines)) * kLines;
+      const int ky_i = static_cast<int>(yrow);
+      for (int i = threadIdx.x; i < kLines * M; i += kBoxThreads) {
+        const int e = i / kLines, c = i % kLines;
+        const int xi = x0 + c;
+        float2 d = lines[c * LS + e];
+        const float kx = P.kf * wrap_index(xi, M), ky = P.kf * wrap_index(ky_i, M), kz = P.kf * wrap_index(e, M);
+        const float k2 = kx * kx + ky * ky + kz * kz;
+        if constexpr (MODE == kBoxShapeZ) {
+          const bool zero = (xi == M / 2) || (ky_i == M / 2) || (e == M / 2) || k2 == 0.0f;
+          float s = 0.0f;
+          if (!zero) {
+            // linear in the table, 0 beyond its last entry (n_pk <= 2^24: the
+            // comparison is exact and j <= n_pk - 2 below)
+            const float u = sqrtf(k2) * P.inv_dk, last = static_cast<float>(P.n_pk - 1);
+            if (u < last) {
+              const int j = static_cast<int>(u);
+              const float f = u - static_cast<float>(j);
+              const float pk = fmaf(f, __ldg(P.pk + j + 1) - __ldg(P.pk + j), __ldg(P.pk + j));
+              s = sqrtf(fmaxf(pk, 0.0f)) * P.amp;
+            } else if (u == last) {
+              s = sqrtf(fmaxf(__ldg(P.pk + P.n_pk - 1), 0.0f)) * P.amp;
+            }
+          }
+          d = make_float2(d.x * s, d.y * s);
+          if (P.spec) P.spec[line_addr(2, g, c, e, M)] = d;
+        }
+        const float2 f = k2 > 0.0f ? pair_filter(P.pair, kx, ky, kz, 1.0f / k2) : make_float2(0.f, 0.f);
+        lines[c * LS + e] = make_float2(d.x * f.x - d.y * f.y, d.y * f.x + d.x * f.y);
+      }
+      __syncthreads();
+      // inverse FFT along z
+      for (int c = team; c < kLines; c += TEAMS) {
+        float2 *b = lines + c * LS;
+        float2 v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) v[r] = b[t + r * T];
+        dft4<1>(v[0], v[1], v[2], v[3]);
+        fft_finish<N2, 1, true>(b, v, tws, t, team);
+      }
+      __syncthreads();
+    }
+
+    // ---- store
+    if constexpr (MODE == kBoxInvXOut) {
+      if (P.out) {
+        // lines l = g kLines + c of x at (y, z) = (l mod n, l / n); each goes to every
+        // periodic copy of its row in the (side)^2 rows of the layout
+        const int S = P.out_side, mg = P.out_margin;
+        for (int c = 0; c < kLines; ++c) {
+          const int64_t l = g * kLines + c;
+          const int y = static_cast<int>(l % M), z = static_cast<int>(l / M);
+          for (int rz = -1; rz <= 1; ++rz) {
+            const int zp = z + mg + rz * M;
+            if (zp < 0 || zp >= S) continue;
+            for (int ry = -1; ry <= 1; ++ry) {
+              const int yp = y + mg + ry * M;
+              if (yp < 0 || yp >= S) continue;
+              float *row = P.out + ((static_cast<int64_t>(zp) * S + yp) * S) * P.out_stride + P.out_slot;
+              for (int xp = threadIdx.x; xp < S; xp += kBoxThreads) {
+                const int x = ((xp - mg) % M + M) % M;
+                const float2 v = lines[c * LS + x];
+                row[static_cast<int64_t>(xp) * P.out_stride] = v.x;
+                row[static_cast<int64_t>(xp) * P.out_stride + 1] = (P.pair == 3) ? 0.0f : v.y;
+              }
+            }
+          }
+        }
+      } else {
+        for (int i = threadIdx.x; i < kLines * M; i += kBoxThreads) {
+          int c, e;
+          flat_to_ce(0, i, M, c, e);
+          P.work[line_addr(0, g, c, e, M)] = lines[c * LS + e];
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int i = threadIdx.x; i < kLines * M; i += kBoxThreads) {
+        int c, e;
+        flat_to_ce(axis, i, M, c, e);
+        P.work[line_addr(axis, g, c, e, M)] = lines[c * LS + e];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int N2, int MODE>
+cudaError_t launch_mode(const BoxPassParams &P, int sms, cudaStream_t st) {
+  const size_t smem = BoxSmem<N2>::bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_box_pass<N2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_box_pass<N2, MODE>, kBoxThreads, smem) !=
+          cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t groups = static_cast<int64_t>(N2 / 2) * (N2 / 2) / kLines;
+  const int grid = static_cast<int>(std::min<int64_t>(groups, static_cast<int64_t>(sms) * per_sm));
+  k_box_pass<N2, MODE><<<grid, kBoxThreads, smem, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <int N2>
+cudaError_t launch_n(const BoxPassParams &P, int mode, int sms, cudaStream_t st) {
+  switch (mode) {
+    case kBoxNoiseX: return launch_mode<N2, kBoxNoiseX>(P, sms, st);
+    case kBoxFwd: return launch_mode<N2, kBoxFwd>(P, sms, st);
+    case kBoxShapeZ: return launch_mode<N2, kBoxShapeZ>(P, sms, st);
+    case kBoxSpecZ: return launch_mode<N2, kBoxSpecZ>(P, sms, st);
+    case kBoxInv: return launch_mode<N2, kBoxInv>(P, sms, st);
+    default: return launch_mode<N2, kBoxInvXOut>(P, sms, st);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_box_pass(const BoxPassParams &P, int mode, int sms, cudaStream_t st) {
+  switch (P.lgn) {
+    case 7: return launch_n<256>(P, mode, sms, st);
+    case 8: return launch_n<512>(P, mode, sms, st);
+    case 9: return launch_n<1024>(P, mode, sms, st);
+    case 10: return launch_n<2048>(P, mode, sms, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace mk

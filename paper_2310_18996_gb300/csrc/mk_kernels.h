@@ -7,7 +7,8 @@
 
 namespace mk {
 
-constexpr int kGauss7Variant = 16;  // kernel variant bit of MK_INTERP_GAUSS7
+constexpr int kGauss7Variant = 16;   // kernel variant bit of MK_INTERP_GAUSS7
+constexpr int kPsNodesVariant = 32;  // kernel variant bit of P_s tables at several redshifts
 
 cudaError_t launch_geometry(const mk_qso *q, int64_t nq, const GeomParams &P, mk_skewer *sk, int64_t *cnt_px,
                             int64_t *cnt_seg, int *err, cudaStream_t st);
@@ -33,13 +34,44 @@ cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t 
 int skewer_blocks_per_sm(int n_fft, int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
 int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k);
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
-// variant: box layout, plus kGauss7Variant for the Gaussian-kernel interpolation;
+// variant: box layout, plus kGauss7Variant for the Gaussian-kernel interpolation,
+// plus kPsNodesVariant for z-dependent P_s (built for register budget 3 only);
 // minb: register budget of the instance, that of minb 256-thread CTAs per SM
 // (2, 3 or 4)
 cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int variant, int minb, int grid, int threads,
                           cudaStream_t st);
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st);
+// One pass of the box synthesis: batched line FFTs of an n^3 complex box
+// ([z][y][x], x fastest) along one axis, with the pass's extra step (noise,
+// mode filter or output layout).
+struct BoxPassParams {
+  float2 *work;          // n^3, transformed in place
+  float2 *spec;          // n^3 delta modes (kept for further filter pairs) or NULL
+  const float2 *tw;      // e^{-2 pi i k / 2n}, k < 2n
+  const float *pk;       // P(k) at k = i dk, i < n_pk
+  int32_t n_pk;
+  float inv_dk;
+  float kf;              // 2 pi / (n cell)
+  float amp;             // 1 / (cell^{3/2} n^3): sqrt(P / cell^3) and the inverse 1/n^3
+  uint32_t key0, key1;   // Philox key of the white noise
+  int32_t pair;          // filter pair 0..3: (1, eta_xx), (eta_yy, eta_zz), (eta_xy, eta_xz), (eta_yz, 0)
+  int32_t axis;          // 0 x, 1 y, 2 z
+  int32_t lgn;
+  float *out;            // output layout (last pass) or NULL
+  int32_t out_side, out_margin, out_stride, out_slot;
+};
+
+// Box synthesis passes (mk_box.cu), modes in the order they run:
+enum BoxPass : int {
+  kBoxNoiseX = 0,  // white noise, forward FFT along x
+  kBoxFwd = 1,     // forward FFT along P.axis
+  kBoxShapeZ = 2,  // forward FFT along z, filter (delta modes to spec if set), inverse along z
+  kBoxSpecZ = 3,   // delta modes from spec, filter, inverse FFT along z
+  kBoxInv = 4,     // inverse FFT along P.axis
+  kBoxInvXOut = 5  // inverse FFT along x, lines written into the output layout (or in place)
+};
+cudaError_t launch_box_pass(const BoxPassParams &P, int mode, int sms, cudaStream_t st);
 cudaError_t launch_finalize(const double *partials, int nparts, int n_z, int n_k, int n_fft, mk_stats_out *out,
                             cudaStream_t st);
 

@@ -72,7 +72,8 @@ __device__ __forceinline__ void flush_warp_partials(unsigned char *smem, int nwa
 // accumulators when its pixels reach the end of the bin (bin_end) or a
 // segment starts in another bin.
 // INTERP: MK_INTERP_TRILINEAR, or MK_INTERP_GAUSS7 (LAYOUT must be MK_BOX_HALO).
-template <int N, int LAYOUT, bool BIG, int MINB, int INTERP = MK_INTERP_TRILINEAR>
+// PSZ: P_s given at several redshifts (P.ps_nodes >= 2), interpolated per segment
+template <int N, int LAYOUT, bool BIG, int MINB, int INTERP = MK_INTERP_TRILINEAR, bool PSZ = false>
 __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
   constexpr int T = N / 8;
   constexpr int BUF = TeamSmem<N>::BUF;
@@ -121,7 +122,7 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
                                     sk.p0[1] + kRoundQ + ps * sk.step[1], sk.p0[2] + kRoundQ + ps * sk.step[2]);
     }
     // ---- small-scale field of this segment
-    if (P.ps_nodes >= 2) {  // P_s at the mean z of the segment's window, linear between nodes
+    if constexpr (PSZ) {  // P_s at the mean z of the segment's window, linear between nodes
       const float zw = __ldg(P.zwin + sk.j_lo + static_cast<int>(j0));
       const int k = P.ps_nodes;
       int n0 = 0;

@@ -8,9 +8,11 @@ namespace mk {
 namespace {
 constexpr int NN = 2048;
 
-// minb: register budget of the instance, that of minb 256-thread CTAs per SM
+// minb: register budget of the instance, that of minb 256-thread CTAs per SM;
+// psz: P_s tables at several redshifts (one instance per layout, budget 3)
 template <int L, int INTERP, typename F>
-cudaError_t with_layout(bool big, int minb, F &&fn) {
+cudaError_t with_layout(bool big, bool psz, int minb, F &&fn) {
+  if (psz) return big ? fn(k_skewer<NN, L, true, 3, INTERP, true>) : fn(k_skewer<NN, L, false, 3, INTERP, true>);
   if (minb >= 4) return big ? fn(k_skewer<NN, L, true, 4, INTERP>) : fn(k_skewer<NN, L, false, 4, INTERP>);
   if (minb == 3) return big ? fn(k_skewer<NN, L, true, 3, INTERP>) : fn(k_skewer<NN, L, false, 3, INTERP>);
   return big ? fn(k_skewer<NN, L, true, 2, INTERP>) : fn(k_skewer<NN, L, false, 2, INTERP>);
@@ -19,12 +21,14 @@ cudaError_t with_layout(bool big, int minb, F &&fn) {
 // Calls fn with the kernel instance for (kernel variant, box size, register budget).
 template <typename F>
 cudaError_t with_skewer_kernel(int variant, bool big, int minb, F &&fn) {
-  if (variant & kGauss7Variant) return with_layout<MK_BOX_HALO, MK_INTERP_GAUSS7>(big, minb, fn);
-  if (variant == MK_BOX_HALO) return with_layout<MK_BOX_HALO, MK_INTERP_TRILINEAR>(big, minb, fn);
-  if (variant == MK_BOX_TENSOR) return with_layout<MK_BOX_TENSOR, MK_INTERP_TRILINEAR>(big, minb, fn);
-  if (variant == MK_BOX_PADDED) return with_layout<MK_BOX_PADDED, MK_INTERP_TRILINEAR>(big, minb, fn);
-  if (variant == MK_BOX_INTERLEAVED) return with_layout<MK_BOX_INTERLEAVED, MK_INTERP_TRILINEAR>(big, minb, fn);
-  return with_layout<MK_BOX_PLANAR, MK_INTERP_TRILINEAR>(big, minb, fn);
+  const bool psz = (variant & kPsNodesVariant) != 0;
+  const int layout = variant & (kGauss7Variant - 1);
+  if (variant & kGauss7Variant) return with_layout<MK_BOX_HALO, MK_INTERP_GAUSS7>(big, psz, minb, fn);
+  if (layout == MK_BOX_HALO) return with_layout<MK_BOX_HALO, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
+  if (layout == MK_BOX_TENSOR) return with_layout<MK_BOX_TENSOR, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
+  if (layout == MK_BOX_PADDED) return with_layout<MK_BOX_PADDED, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
+  if (layout == MK_BOX_INTERLEAVED) return with_layout<MK_BOX_INTERLEAVED, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
+  return with_layout<MK_BOX_PLANAR, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
 }
 
 template <typename K>

@@ -714,3 +714,110 @@ def test_mlp_gradient_matches_central_differences():
         pm[i] -= h
         fd = (oracle.mlp_loss_grad(pp, x, t)[0] - oracle.mlp_loss_grad(pm, x, t)[0]) / (2 * h)
         assert g[i] == pytest.approx(fd, rel=2e-6, abs=1e-9), i
+
+
+# ------------------------------------------------------------ Gaussian box synthesis (Sec. 2.1)
+from oracle import box_synth  # noqa: E402
+
+
+def test_box_noise_is_philox_box_muller_and_normal():
+    n, seed = 32, 0x1234_5678_9ABC
+    r = oracle.box_noise(seed, n).ravel()
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for v in (0, 1, 2, 3, 4, 4097, n ** 3 - 1):
+        g = v // 4
+        w = oracle.philox4x32_10((g & 0xFFFFFFFF, g >> 32, 0, 0), key)
+        e = oracle.box_muller(w[0], w[1]) + oracle.box_muller(w[2], w[3])
+        assert r[v] == e[v % 4]
+    assert sst.kstest(r, "norm").pvalue > 1e-3
+    assert abs(r.mean()) < 5 / math.sqrt(r.size)
+
+
+def _white(n, cell, p0):
+    return 0.5, np.full(int(2 * math.pi * math.sqrt(3) / cell / 0.5) + 3, p0)
+
+
+def test_box_white_spectrum_variance():
+    # P = p0 at every k: var(delta) = p0 / cell^3 times the kept mode fraction
+    # ((n - 1)^3 - 1) / n^3 (no zero mode, no Nyquist planes)
+    n, cell, p0 = 32, 2.0, 3.0
+    dk, tab = _white(n, cell, p0)
+    d, _ = box_synth.synth_box(n, cell, 99, dk, tab)
+    expect = p0 / cell ** 3 * ((n - 1) ** 3 - 1) / n ** 3
+    assert abs(d.var() / expect - 1) < 5 * math.sqrt(2.0 / n ** 3)
+    assert abs(d.mean()) < 1e-12
+
+
+def test_box_shell_power_matches_table():
+    # |DFT(delta)_k|^2 cell^3 / n^3 averages to P(k) in shells (5 sigma)
+    n, cell = 48, 1.5
+    dk = 0.01
+    ks = dk * np.arange(600)
+    tab = (ks + 0.05) ** -1.5
+    D = box_synth.delta_modes(n, cell, 7, dk, tab)
+    kx, ky, kz = box_synth._wavenumbers(n, cell)
+    k = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2).ravel()
+    pw = (np.abs(D) ** 2 * cell ** 3 / n ** 3).ravel()
+    ptab = np.interp(k, ks, tab)
+    keep = pw > 0
+    edges = np.linspace(0.3, 1.8, 7)
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        m = keep & (k >= lo) & (k < hi)
+        ratio = pw[m] / ptab[m]
+        assert abs(ratio.mean() - 1) < 5 / math.sqrt(m.sum())
+
+
+def test_box_eta_trace_is_minus_delta_and_boxes_are_real():
+    n, cell = 32, 1.0
+    dk = 0.02
+    tab = np.exp(-dk * np.arange(400))
+    d, eta = box_synth.synth_box(n, cell, 3, dk, tab, tensor=True)
+    np.testing.assert_allclose(eta[0] + eta[1] + eta[2], -d, atol=1e-12 * np.abs(d).max())
+    D = box_synth.delta_modes(n, cell, 3, dk, tab)
+    z = np.fft.ifftn(D)
+    assert np.abs(z.imag).max() < 1e-12 * np.abs(z.real).max()
+
+
+def test_box_eta_isotropic_moments():
+    # isotropic Gaussian field: <eta_xx^2> = <mu^4> sigma^2 = sigma^2/5,
+    # <eta_xy^2> = sigma^2/15, <delta eta_xx> = -sigma^2/3 (sampling and grid
+    # anisotropy within 3 %)
+    n, cell = 64, 1.0
+    dk = 0.01
+    ks = dk * np.arange(600)
+    tab = np.where((ks > 1.0) & (ks < 2.6), 1.0, 0.0)
+    d, eta = box_synth.synth_box(n, cell, 11, dk, tab, tensor=True)
+    s2 = d.var()
+    for i in range(3):
+        assert abs(np.mean(eta[i] ** 2) / (s2 / 5) - 1) < 0.03
+        assert abs(np.mean(d * eta[i]) / (-s2 / 3) - 1) < 0.03
+    for i in range(3, 6):
+        assert abs(np.mean(eta[i] ** 2) / (s2 / 15) - 1) < 0.03
+
+
+def test_box_eta_axes_by_finite_differences():
+    # d_x^2 eta_yy = d_y^2 eta_xx = d_x d_y eta_xy (all -d_x^2 d_y^2 lap^-1 delta),
+    # checked with central differences on a smooth box; a swapped axis breaks it
+    n, cell = 64, 1.0
+    dk = 0.005
+    ks = dk * np.arange(200)
+    tab = np.exp(-(ks / 0.25) ** 2)
+    _, eta = box_synth.synth_box(n, cell, 5, dk, tab, tensor=True)
+
+    def d2(f, ax):
+        return np.roll(f, -1, ax) - 2 * f + np.roll(f, 1, ax)
+
+    def d1(f, ax):
+        return 0.5 * (np.roll(f, -1, ax) - np.roll(f, 1, ax))
+
+    X, Y, Z = 2, 1, 0
+    a = d2(eta[1], X)
+    b = d2(eta[0], Y)
+    c = d1(d1(eta[3], X), Y)
+    scale = np.abs(a).max()
+    assert np.abs(a - b).max() < 0.05 * scale
+    assert np.abs(a - c).max() < 0.05 * scale
+    # the same identity with z in place of y: d_x^2 eta_zz = d_z^2 eta_xx
+    assert np.abs(d2(eta[2], X) - d2(eta[0], Z)).max() < 0.05 * np.abs(d2(eta[2], X)).max()
+    # and it fails if eta_yy were taken for eta_zz
+    assert np.abs(d2(eta[1], X) - d2(eta[0], Z)).max() > 0.2 * scale
