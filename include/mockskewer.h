@@ -261,7 +261,7 @@ int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float
      MK_BOX_PADDED, MK_BOX_HALO: as mk_pack_box_padded / mk_pack_box_halo;
      MK_BOX_TENSOR: as mk_pack_box_tensor, and d_spec (2 n^3 floats) keeps the
        delta modes between the four inverse transforms (NULL otherwise).
-   d_work: 2 n^3 floats of caller-owned scratch, 8-byte aligned, overwritten;
+   d_work: 2 n^3 floats of caller-owned scratch, 16-byte aligned, overwritten;
    it must not overlap d_out (except INTERLEAVED in place) or d_spec.
    Asynchronous on the context stream (the P(k) upload waits for the
    stream's earlier work).  MK_EINVAL for a bad size, layout, table or pointer. */

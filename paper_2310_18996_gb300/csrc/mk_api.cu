@@ -1362,8 +1362,8 @@ extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, 
   if (n < 128 || n > 1024 || (1 << lgn) != n) return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512 or 1024");
   if (!(cell > 0.0) || !(dk > 0.0) || !h_pk || n_pk < 2 || n_pk > (1 << 24))
     return fail(ctx, MK_EINVAL, "bad cell, dk or P(k) table (2 .. 2^24 entries)");
-  if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 7) || (reinterpret_cast<uintptr_t>(d_out) & 7))
-    return fail(ctx, MK_EINVAL, "d_work and d_out must be 8-byte aligned device pointers");
+  if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 7))
+    return fail(ctx, MK_EINVAL, "d_work must be 16-byte and d_out 8-byte aligned device pointers");
   const int64_t nv = static_cast<int64_t>(n) * n * n;
   int side = n, margin = 0, stride = 2, pairs = 1;
   switch (layout) {

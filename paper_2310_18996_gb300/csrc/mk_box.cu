@@ -18,13 +18,27 @@ namespace {
 
 constexpr int kLines = 8;     // lines per CTA group
 constexpr int kLinePad = 2;   // complex slots of padding per line buffer
-constexpr int kBoxThreads = 256;
+constexpr int kBoxThreads = 512;
 
 template <int N2>
 struct BoxSmem {
   static constexpr int M = N2 / 2;  // line length n
   static constexpr size_t bytes() { return TwTab<N2>::BYTES + sizeof(float2) * kLines * (M + kLinePad); }
 };
+
+// Asynchronous global-to-shared copies (no register round trip, all of a
+// thread's copies in flight at once).
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const uint32_t s = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
 __device__ __forceinline__ int wrap_index(int j, int n) { return j < n / 2 ? j : j - n; }
 
@@ -61,10 +75,11 @@ __device__ __forceinline__ void flat_to_ce(int axis, int i, int n, int &c, int &
 }
 
 template <int N2, int MODE>
-__global__ void __launch_bounds__(kBoxThreads) k_box_pass(BoxPassParams P) {
+__global__ void __launch_bounds__(kBoxThreads, 2) k_box_pass(BoxPassParams P) {
   constexpr int M = N2 / 2;  // box side
   constexpr int T = Fft<N2>::T;
   constexpr int TEAMS = kBoxThreads / T;
+  static_assert(T == 32 || TEAMS <= 15, "teams of more than one warp use named barriers 1..TEAMS");
   constexpr int LS = M + kLinePad;
   constexpr int SIGN = (MODE == kBoxNoiseX || MODE == kBoxFwd || MODE == kBoxShapeZ) ? -1 : 1;
   constexpr int AXIS_FIXED = (MODE == kBoxNoiseX || MODE == kBoxInvXOut) ? 0
@@ -97,12 +112,19 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_pass(BoxPassParams P) {
       }
     } else {
       const float2 *src = (MODE == kBoxSpecZ) ? P.spec : P.work;
-#pragma unroll 4
-      for (int i = threadIdx.x; i < kLines * M; i += kBoxThreads) {
-        int c, e;
-        flat_to_ce(axis, i, M, c, e);
-        lines[c * LS + e] = src[line_addr(axis, g, c, e, M)];
+      if (axis == 0) {  // whole lines: 16-byte copies of element pairs
+        for (int i = 2 * threadIdx.x; i < kLines * M; i += 2 * kBoxThreads) {
+          const int c = i / M, e = i % M;
+          cp_async16(lines + c * LS + e, src + line_addr(0, g, c, e, M));
+        }
+      } else {          // kLines adjacent columns: 8-byte copies, 64 B per row
+        for (int i = threadIdx.x; i < kLines * M; i += kBoxThreads) {
+          int c, e;
+          flat_to_ce(axis, i, M, c, e);
+          cp_async8(lines + c * LS + e, src + line_addr(axis, g, c, e, M));
+        }
       }
+      cp_async_wait_all();
     }
     __syncthreads();
 
@@ -184,8 +206,8 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_pass(BoxPassParams P) {
               for (int xp = threadIdx.x; xp < S; xp += kBoxThreads) {
                 const int x = ((xp - mg) % M + M) % M;
                 const float2 v = lines[c * LS + x];
-                row[static_cast<int64_t>(xp) * P.out_stride] = v.x;
-                row[static_cast<int64_t>(xp) * P.out_stride + 1] = (P.pair == 3) ? 0.0f : v.y;
+                *reinterpret_cast<float2 *>(row + static_cast<int64_t>(xp) * P.out_stride) =
+                    make_float2(v.x, (P.pair == 3) ? 0.0f : v.y);
               }
             }
           }
@@ -196,6 +218,12 @@ __global__ void __launch_bounds__(kBoxThreads) k_box_pass(BoxPassParams P) {
           flat_to_ce(0, i, M, c, e);
           P.work[line_addr(0, g, c, e, M)] = lines[c * LS + e];
         }
+      }
+    } else if (axis == 0) {
+      for (int i = 2 * threadIdx.x; i < kLines * M; i += 2 * kBoxThreads) {
+        const int c = i / M, e = i % M;
+        const float2 a = lines[c * LS + e], b = lines[c * LS + e + 1];
+        *reinterpret_cast<float4 *>(P.work + line_addr(0, g, c, e, M)) = make_float4(a.x, a.y, b.x, b.y);
       }
     } else {
 #pragma unroll 4
