@@ -268,6 +268,63 @@ int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float
 int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, const double *h_pk, int32_t n_pk, double dk,
                  int32_t layout, float *d_work, float *d_spec, float *d_out);
 
+/* ------------------------------------------- quasars from lognormal fields (Sec. 2.2, App. A) */
+
+/* Correlation function of an isotropic power spectrum (host, FP64):
+   xi(r) = (1 / 2 pi^2) int P(k) k^2 j0(k r) dk, the integral taken by the
+   trapezoid rule on the table k_i = i dk, i < n_pk; j0(x) = sin(x)/x.  MK_EINVAL for n_pk < 2,
+   dk <= 0 or NULL pointers. */
+int mk_xi_of_pk(const double *h_pk, int32_t n_pk, double dk, const double *h_r, int32_t n_r, double *h_xi);
+
+/* Power spectrum of the Gaussian field whose exponential has correlation
+   B xi_m(r) (Sec. 2.2: P_q is the Fourier transform of ln[1 + b_q^2 xi_m]; with
+   the growth of App. A, B = b_q^2(z_i) G^2(z_i)):
+     xi_m on r_j = j pi / ((n_pk - 1) dk), j < n_pk (mk_xi_of_pk);
+     h_pq[i] = 4 pi int ln(1 + B xi_m(r)) r^2 j0(k_i r) dr, trapezoid on r_j,
+     set to 0 where the finite sums ring below 0.
+   Host, FP64.  MK_EINVAL for B < 0, NULL pointers, n_pk < 2 or dk <= 0, or if
+   1 + B xi_m <= 0 somewhere. */
+int mk_lognormal_pk(const double *h_pk, int32_t n_pk, double dk, double B, double *h_pq);
+
+/* Parameters of the quasar draw (Sec. 2.2 and App. A). */
+typedef struct mk_qso_draw_params {
+  int32_t n;           /* box side (voxels), box index [z][y][x] */
+  double cell;         /* voxel side, h^-1 Mpc */
+  double origin[3];    /* box corner relative to the observer */
+  double z_box[3];     /* redshifts z_1 < z_2 < z_3 of the three quasar-density boxes */
+  double bias[3];      /* b_q(z) = bias[0] ((1 + z) / (1 + bias[1]))^bias[2] */
+  double xi_m5;        /* xi_m(5 h^-1 Mpc) of the z = 0 matter spectrum */
+  const double *h_nbar; /* mean density, quasars per (h^-1 Mpc)^3, at z = nbar_z0 + j nbar_dz */
+  int32_t n_nbar;      /* 0 outside the table, linear inside */
+  double nbar_z0, nbar_dz;
+  uint64_t seed;
+} mk_qso_draw_params;
+
+/* Draw quasars voxel by voxel from three quasar-density boxes delta_q,i at
+   z_i (App. A).  At the voxel's centre redshift z (cosmological, from its
+   distance to the observer) and growth G:
+     a_i = b_q(z)(1 + z_i) / (b_q(z_i)(1 + z)),   p_i = exp(a_i delta_q,i);
+     p12 interpolates p_1, p_2 linearly in z (t12 = (z - z_1)/(z_2 - z_1)),
+     p23 extrapolates p_2, p_3 (t23 = (z - z_2)/(z_3 - z_2));
+     p = lambda p12 + (1 - lambda) p23, lambda (clamped to [0, 1]) the weight
+     at which the same combination of xi_i = (1 + xi0_i)^(a_i^2) - 1,
+     xi0_i = b_q^2(z_i) G^2(z_i) xi_m5, equals b_q^2(z) G^2(z) xi_m5 (the
+     paper matches them at r = 5 h^-1 Mpc);
+     P = min(1, nbar(z) cell^3 max(p, 0) / E[p]), E[p] = sum of the weights
+     times exp(a_i^2 sigma_i^2 / 2), sigma_i^2 = mean delta_q,i^2 of the box.
+   Voxel v = (z n + y) n + x is drawn by Philox4x32-10, key (seed low, seed
+   high), counter (v low, v high, 0x51534F, 0): accepted when
+   (w0 + 1/2) 2^-32 < P, at origin + (x + u1, y + u2, z + u3) cell with
+   u = (w + 1/2) 2^-32; id = v.  The catalogue lists accepted voxels in
+   increasing v.  The coefficients are tabulated in r (host FP64, 8192
+   points over the box's distance range, linear in between).
+   d_box_q[i]: n^3 floats at stride box_stride (1 planar, 2 for the pairs
+   of mk_synth_box's MK_BOX_INTERLEAVED output, which reads delta).
+   d_qso: capacity records.  *h_count: quasars drawn (also beyond capacity,
+   then MK_ERANGE and only the first capacity are written).  Synchronous. */
+int mk_draw_qso(mk_ctx *ctx, const mk_qso_draw_params *params, const float *const d_box_q[3], int32_t box_stride,
+                mk_qso *d_qso, int64_t capacity, int64_t *h_count);
+
 /* ---------------------------------------------------------------- skewers */
 
 /* Pre-FGPA skewers (Eq. gfield inputs).  Always computes the geometry of the

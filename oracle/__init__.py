@@ -99,6 +99,8 @@ def lib():
                 "orc_philox4x32_10": (None, [P(u32), P(u32), P(u32)]),
                 "orc_box_muller": (None, [u32, u32, P(d), P(d)]),
                 "orc_box_noise": (None, [C.c_uint64, i32, P(d)]),
+                "orc_qso_draw": (i64, [d, P(C.c_float), P(C.c_float), P(C.c_float), i32, i32, d, P(d), P(d),
+                                       P(d), d, P(d), i32, d, d, C.c_uint64, P(d), P(d), P(u64), P(d), i64]),
                 "orc_dft_forward_real": (None, [P(d), i32, P(d), P(d)]),
                 "orc_dft_inverse_hermitian": (None, [P(d), P(d), i32, P(d)]),
                 "orc_geometry": (C.c_int, [P(Cfg), P(d), P(i32), P(i32), P(d)]),
@@ -394,3 +396,28 @@ def mlp_loss_grad(params, x, t):
     loss = lib().orc_mlp_loss_grad(_p(p, C.c_double), _p(x, C.c_double), _p(t, C.c_double),
                                    x.shape[0], _p(g, C.c_double))
     return loss, g
+
+
+def qso_draw(q, boxes, stride=1, capacity=None):
+    """Quasars from three quasar-density boxes (Sec. 2.2, App. A); q holds n,
+    cell, origin, z_box, bias, xi_m5, nbar, nbar_z0, nbar_dz, seed, omega_m.
+    Returns ids, positions, and P and u0 of every voxel."""
+    n = int(q["n"])
+    nv = n ** 3
+    cap = nv if capacity is None else int(capacity)
+    bx = [np.ascontiguousarray(b, dtype=np.float32).ravel() for b in boxes]
+    pout = np.zeros(nv)
+    uout = np.zeros(nv)
+    ids = np.zeros(max(cap, 1), dtype=np.uint64)
+    pos = np.zeros((max(cap, 1), 3))
+    og = np.ascontiguousarray(q["origin"], dtype=np.float64)
+    zq = np.ascontiguousarray(q["z_box"], dtype=np.float64)
+    bl = np.ascontiguousarray(q["bias"], dtype=np.float64)
+    nb = np.ascontiguousarray(q["nbar"], dtype=np.float64)
+    cnt = lib().orc_qso_draw(q["omega_m"], _p(bx[0], C.c_float), _p(bx[1], C.c_float), _p(bx[2], C.c_float),
+                             int(stride), n, q["cell"], _p(og, C.c_double), _p(zq, C.c_double),
+                             _p(bl, C.c_double), q["xi_m5"], _p(nb, C.c_double), nb.size, q["nbar_z0"],
+                             q["nbar_dz"], int(q["seed"]) & 0xFFFFFFFFFFFFFFFF, _p(pout, C.c_double),
+                             _p(uout, C.c_double), _p(ids, C.c_uint64), _p(pos, C.c_double), cap)
+    k = min(cnt, cap)
+    return dict(count=int(cnt), ids=ids[:k].copy(), pos=pos[:k].copy(), P=pout, u=uout)

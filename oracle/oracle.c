@@ -214,6 +214,81 @@ void orc_box_noise(uint64_t seed, int32_t n, double *out) {
   }
 }
 
+/* Quasars from three lognormal quasar-density boxes (Sec. 2.2, App. A), one */
+/* voxel at a time in the order of the paper's recipe.  Writes the accept     */
+/* probability P and the uniform u0 of every voxel (n^3 each) and the ids and */
+/* positions of the accepted voxels (at most capacity); returns the count.    */
+static double orc_bias(const double *bl, double z) { return bl[0] * pow((1.0 + z) / (1.0 + bl[1]), bl[2]); }
+
+int64_t orc_qso_draw(double omega_m, const float *b1, const float *b2, const float *b3, int32_t stride, int32_t n,
+                     double cell, const double origin[3], const double zq[3], const double bl[3], double xi_m5,
+                     const double *nbar, int32_t n_nbar, double nbar_z0, double nbar_dz, uint64_t seed,
+                     double *p_out, double *u_out, uint64_t *ids, double *pos, int64_t capacity) {
+  const int64_t nv = (int64_t)n * n * n;
+  const float *box[3] = {b1, b2, b3};
+  double sig2[3];
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int64_t v = 0; v < nv; ++v) s += (double)box[i][v * stride] * (double)box[i][v * stride];
+    sig2[i] = s / (double)nv;
+  }
+  double xi0[3], bz[3];
+  for (int i = 0; i < 3; ++i) {
+    const double g = orc_growth(omega_m, zq[i]);
+    bz[i] = orc_bias(bl, zq[i]);
+    xi0[i] = bz[i] * bz[i] * g * g * xi_m5;
+  }
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  int64_t count = 0;
+  for (int64_t v = 0; v < nv; ++v) {
+    const int64_t x = v % n, y = (v / n) % n, zz = v / ((int64_t)n * n);
+    const double c[3] = {origin[0] + (x + 0.5) * cell, origin[1] + (y + 0.5) * cell, origin[2] + (zz + 0.5) * cell};
+    const double r = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    const double z = orc_z_of_distance(omega_m, r), g = orc_growth(omega_m, z), b = orc_bias(bl, z);
+    double a[3], xi[3];
+    for (int i = 0; i < 3; ++i) {
+      a[i] = b * (1.0 + zq[i]) / (bz[i] * (1.0 + z));
+      xi[i] = pow(1.0 + xi0[i], a[i] * a[i]) - 1.0;
+    }
+    const double t12 = (z - zq[0]) / (zq[1] - zq[0]), t23 = (z - zq[1]) / (zq[2] - zq[1]);
+    const double xi12 = (1.0 - t12) * xi[0] + t12 * xi[1], xi23 = (1.0 - t23) * xi[1] + t23 * xi[2];
+    const double xmod = b * b * g * g * xi_m5;
+    double lam = fabs(xi12 - xi23) > 0.0 ? (xmod - xi23) / (xi12 - xi23) : 0.5;
+    lam = lam < 0.0 ? 0.0 : (lam > 1.0 ? 1.0 : lam);
+    const double w[3] = {lam * (1.0 - t12), lam * t12 + (1.0 - lam) * (1.0 - t23), (1.0 - lam) * t23};
+    double p = 0.0, ep = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      p += w[i] * exp(a[i] * (double)box[i][v * stride]);
+      ep += w[i] * exp(0.5 * a[i] * a[i] * sig2[i]);
+    }
+    double nb = 0.0;
+    const double s = (z - nbar_z0) / nbar_dz;
+    if (s >= 0.0 && s <= (double)(n_nbar - 1)) {
+      int j = (int)floor(s);
+      if (j > n_nbar - 2) j = n_nbar - 2;
+      nb = nbar[j] + (s - j) * (nbar[j + 1] - nbar[j]);
+    }
+    double P = ep > 0.0 ? nb * cell * cell * cell * (p > 0.0 ? p : 0.0) / ep : 0.0;
+    if (P > 1.0) P = 1.0;
+    const uint32_t ctr[4] = {(uint32_t)v, (uint32_t)((uint64_t)v >> 32), 0x51534Fu, 0u};
+    uint32_t wd[4];
+    orc_philox4x32_10(ctr, key, wd);
+    const double u0 = ((double)wd[0] + 0.5) * 0x1p-32;
+    if (p_out) p_out[v] = P;
+    if (u_out) u_out[v] = u0;
+    if (u0 < P) {
+      if (count < capacity) {
+        ids[count] = (uint64_t)v;
+        pos[3 * count + 0] = origin[0] + (x + ((double)wd[1] + 0.5) * 0x1p-32) * cell;
+        pos[3 * count + 1] = origin[1] + (y + ((double)wd[2] + 0.5) * 0x1p-32) * cell;
+        pos[3 * count + 2] = origin[2] + (zz + ((double)wd[3] + 0.5) * 0x1p-32) * cell;
+      }
+      ++count;
+    }
+  }
+  return count;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Discrete Fourier transforms written as their defining sums.               */
 /* ------------------------------------------------------------------------ */

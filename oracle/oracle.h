@@ -104,6 +104,10 @@ double orc_growth(double omega_m, double z);
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 void orc_box_muller(uint32_t xu1, uint32_t xu2, double *e1, double *e2);
 void orc_box_noise(uint64_t seed, int32_t n, double *out);
+int64_t orc_qso_draw(double omega_m, const float *b1, const float *b2, const float *b3, int32_t stride, int32_t n,
+                     double cell, const double origin[3], const double zq[3], const double bl[3], double xi_m5,
+                     const double *nbar, int32_t n_nbar, double nbar_z0, double nbar_dz, uint64_t seed,
+                     double *p_out, double *u_out, uint64_t *ids, double *pos, int64_t capacity);
 
 /* ---- discrete Fourier transforms, O(N^2) ---- */
 void orc_dft_forward_real(const double *x, int32_t n, double *re, double *im);

@@ -31,7 +31,8 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
-           "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box"]
+           "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box", "mk_xi_of_pk",
+           "mk_lognormal_pk", "mk_draw_qso"]
 
 
 class MkError(RuntimeError):
@@ -101,6 +102,12 @@ class TuneTarget(C.Structure):
 
 
 PS_TUNE_MAX_PASSES = 128
+
+
+class QsoDrawParams(C.Structure):
+    _fields_ = [("n", C.c_int32), ("cell", C.c_double), ("origin", C.c_double * 3), ("z_box", C.c_double * 3),
+                ("bias", C.c_double * 3), ("xi_m5", C.c_double), ("h_nbar", C.POINTER(C.c_double)),
+                ("n_nbar", C.c_int32), ("nbar_z0", C.c_double), ("nbar_dz", C.c_double), ("seed", C.c_uint64)]
 
 
 class PsTuneReport(C.Structure):
@@ -185,6 +192,9 @@ def lib():
                 "mk_fit_a_bsigma": (C.c_int, [C.c_double, C.c_double, P(C.c_double), P(C.c_double)]),
                 "mk_tune_ps": (C.c_int, [vp, vp, vp, i64, P(SkewerParams), P(StatBins), P(TuneTarget), i32,
                                          i32, vp, vp, P(C.c_double), P(FgpaNodes), P(PsTuneReport)]),
+                "mk_xi_of_pk": (C.c_int, [P(C.c_double), i32, C.c_double, P(C.c_double), i32, P(C.c_double)]),
+                "mk_lognormal_pk": (C.c_int, [P(C.c_double), i32, C.c_double, C.c_double, P(C.c_double)]),
+                "mk_draw_qso": (C.c_int, [vp, P(QsoDrawParams), P(vp), i32, vp, i64, P(i64)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -377,6 +387,27 @@ class Context:
         self._check(lib().mk_synth_box(self.h, n, cell, int(seed) & 0xFFFFFFFFFFFFFFFF, _dp(pk), pk.size, dk,
                                        layout, _ptr(work), _ptr(spec), _ptr(out)))
         return out
+
+    def draw_qso(self, q, boxes, stride=2, capacity=None):
+        """Quasars from three quasar-density boxes (Sec. 2.2, App. A); q: dict with
+        n, cell, origin, z_box, bias, xi_m5, nbar, nbar_z0, nbar_dz, seed.  boxes:
+        three device tensors (stride 2: mk_synth_box interleaved pairs).  Returns
+        (catalogue tensor of mk_qso records, count)."""
+        torch = self._torch
+        n = int(q["n"])
+        cap = int(capacity) if capacity is not None else max(16, int(4 * n ** 3 * max(q["nbar"]) * q["cell"] ** 3) + 4096)
+        out = torch.empty(max(cap, 1) * QSO_DTYPE.itemsize, dtype=torch.uint8, device=boxes[0].device)
+        nb = np.ascontiguousarray(q["nbar"], dtype=np.float64)
+        p = QsoDrawParams(n=n, cell=q["cell"], xi_m5=q["xi_m5"], h_nbar=_dp(nb), n_nbar=nb.size,
+                          nbar_z0=q["nbar_z0"], nbar_dz=q["nbar_dz"], seed=int(q["seed"]) & 0xFFFFFFFFFFFFFFFF)
+        for d in range(3):
+            p.origin[d], p.z_box[d], p.bias[d] = q["origin"][d], q["z_box"][d], q["bias"][d]
+        ptrs = (C.c_void_p * 3)(*[b.data_ptr() for b in boxes])
+        cnt = C.c_int64()
+        self._stream()
+        rc = lib().mk_draw_qso(self.h, C.byref(p), ptrs, stride, _ptr(out), cap, C.byref(cnt))
+        self._check(rc)
+        return out[: cnt.value * QSO_DTYPE.itemsize], cnt.value
 
     # skewers
     def plan(self, box, qso, n_qso, w):
@@ -629,3 +660,24 @@ def tune_ps(ctx, box, qso, n_qso, w, target, p_s0, n_outer=5, n_inner=10):
     ctx._check(lib().mk_tune_ps(ctx.h, box.handle, _ptr(qso), n_qso, C.byref(p), C.byref(b), C.byref(target),
                                 n_outer, n_inner, _ptr(sk), _ptr(off), _dp(ps), C.byref(nd), C.byref(rep)))
     return nd, ps, rep
+
+
+def xi_of_pk(pk, dk, r):
+    """xi(r) of a tabulated isotropic power spectrum (host)."""
+    pk = np.ascontiguousarray(pk, dtype=np.float64)
+    r = np.ascontiguousarray(np.atleast_1d(r), dtype=np.float64)
+    out = np.zeros(r.size)
+    rc = lib().mk_xi_of_pk(_dp(pk), pk.size, dk, _dp(r), r.size, _dp(out))
+    if rc != MK_OK:
+        raise MkError(rc, "mk_xi_of_pk: bad argument")
+    return out
+
+
+def lognormal_pk(pk, dk, B):
+    """Spectrum of the Gaussian field whose exponential has correlation B xi(r) (host)."""
+    pk = np.ascontiguousarray(pk, dtype=np.float64)
+    out = np.zeros(pk.size)
+    rc = lib().mk_lognormal_pk(_dp(pk), pk.size, dk, B, _dp(out))
+    if rc != MK_OK:
+        raise MkError(rc, "mk_lognormal_pk: bad argument or 1 + B xi <= 0")
+    return out

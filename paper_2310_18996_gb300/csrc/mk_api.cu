@@ -1317,6 +1317,10 @@ namespace mkhost {
 cudaStream_t ctx_stream(mk_ctx *c) { return c->stream; }
 int ctx_device(mk_ctx *c) { return c->device; }
 int ctx_fail(mk_ctx *c, int code, const char *msg) { return fail(c, code, "%s", msg); }
+int ctx_sms(mk_ctx *c) { return c->sms; }
+double ctx_z_of(mk_ctx *c, double r) { return c->cos.z_of(r); }
+double ctx_growth(mk_ctx *c, double z) { return c->cos.growth(z); }
+double ctx_distance(mk_ctx *c, double z) { return c->cos.distance(z); }
 
 int ctx_pixel_histogram(mk_ctx *ctx, double dr, const mk_skewer *d_sk, int64_t n_sk, std::vector<double> &z,
                         std::vector<int64_t> &count, double *ms) {

@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2310_18996_gb300 as mk
@@ -89,3 +90,26 @@ def test_fit_a_bsigma_rejects_unreachable_targets():
             mk.fit_a_bsigma(fbar, sf)
     with pytest.raises(mk.MkError):
         mk.fgpa_gauss_moments(-1.0, 0.5)
+
+
+# ------------------------------------------------------------ Sec. 2.2 lognormal field (host)
+def test_xi_and_lognormal_pk_match_oracle():
+    from oracle import lognormal
+    n = 1500
+    dk = 6.0 / (n - 1)
+    k = dk * np.arange(n)
+    pk = np.where(k > 0, 80.0 * k ** 0.96 * np.exp(-(k / 1.5) ** 2), 0.0)
+    r = np.array([0.0, 0.7, 5.0, 20.0, 80.0])
+    np.testing.assert_allclose(mk.xi_of_pk(pk, dk, r), lognormal.xi_of_pk(pk, dk, r), rtol=1e-11, atol=1e-14)
+    for B in (0.0, 0.3, 1.0):
+        got = mk.lognormal_pk(pk, dk, B)
+        ref = lognormal.lognormal_pk(pk, dk, B)
+        np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-12 * np.abs(ref).max() + 1e-300)
+    # B large enough that 1 + B xi < 0 in a negative lobe of xi: both reject it
+    xmin = lognormal.xi_of_pk(pk, dk, np.pi / (dk * (n - 1)) * np.arange(n)).min()
+    assert xmin < 0
+    with pytest.raises(ValueError):
+        lognormal.lognormal_pk(pk, dk, -2.0 / xmin)
+    for B in (-1.0, -2.0 / xmin):
+        with pytest.raises(mk.MkError):
+            mk.lognormal_pk(pk, dk, B)

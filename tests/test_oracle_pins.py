@@ -821,3 +821,85 @@ def test_box_eta_axes_by_finite_differences():
     assert np.abs(d2(eta[2], X) - d2(eta[0], Z)).max() < 0.05 * np.abs(d2(eta[2], X)).max()
     # and it fails if eta_yy were taken for eta_zz
     assert np.abs(d2(eta[1], X) - d2(eta[0], Z)).max() > 0.2 * scale
+
+
+# ------------------------------------------------------------ lognormal quasar field (Sec. 2.2, App. A)
+from oracle import lognormal  # noqa: E402
+
+
+def _gauss_pk(s, n=3000, kmax=12.0):
+    # P(k) = (2 pi s^2)^(3/2) exp(-k^2 s^2 / 2)  <->  xi(r) = exp(-r^2 / (2 s^2))
+    dk = kmax / (n - 1)
+    k = dk * np.arange(n)
+    return dk, (2 * math.pi * s * s) ** 1.5 * np.exp(-0.5 * (k * s) ** 2)
+
+
+def test_xi_of_gaussian_spectrum_is_gaussian():
+    s = 4.0
+    dk, pk = _gauss_pk(s)
+    r = np.array([0.0, 1.0, 3.0, 5.0, 8.0, 12.0])
+    np.testing.assert_allclose(lognormal.xi_of_pk(pk, dk, r), np.exp(-r ** 2 / (2 * s * s)), atol=1e-10)
+
+
+def test_lognormal_pk_second_order_closed_form():
+    # ln(1 + B xi) = B xi - B^2 xi^2 / 2 + O(B^3), and xi^2 is the Gaussian of
+    # width s / sqrt 2: P_q = B P - (B^2 / 2)(pi s^2)^(3/2) exp(-k^2 s^2 / 4) + O(B^3)
+    s, B = 4.0, 1e-3
+    dk, pk = _gauss_pk(s)
+    k = dk * np.arange(pk.size)
+    got = lognormal.lognormal_pk(pk, dk, B)
+    ref = B * pk - 0.5 * B * B * (math.pi * s * s) ** 1.5 * np.exp(-0.25 * (k * s) ** 2)
+    m = k < 0.8
+    scale = B * pk[0]
+    assert np.abs(got[m] - ref[m]).max() < 2 * B ** 3 * pk[0] * 3 + 1e-9 * scale
+
+
+def test_qso_draw_uniform_field_follows_mean_density():
+    # delta_q = 0: p = sum of the weights = 1 and E[p] = 1, so every voxel has
+    # P = nbar cell^3; the count is binomial and positions stay in their voxel
+    n, cell = 32, 2.19
+    q = dict(n=n, cell=cell, origin=(3700.0 - n * cell / 2, -n * cell / 2, -n * cell / 2), z_box=(1.9, 2.75, 3.6),
+             bias=(3.7, 2.33, 1.7), xi_m5=0.5, nbar=[2e-3] * 10, nbar_z0=1.5, nbar_dz=0.5, seed=7, omega_m=OM)
+    z = np.zeros((n, n, n), np.float32)
+    r = oracle.qso_draw(q, [z, z, z])
+    P = 2e-3 * cell ** 3
+    np.testing.assert_allclose(r["P"], P, rtol=1e-12)
+    assert abs(r["count"] - n ** 3 * P) < 5 * math.sqrt(n ** 3 * P * (1 - P))
+    ids = r["ids"].astype(np.int64)
+    assert np.all(np.diff(ids) > 0)
+    idx = np.stack([ids % n, (ids // n) % n, ids // (n * n)], axis=1)
+    cell_of = np.floor((r["pos"] - np.asarray(q["origin"])) / cell)
+    np.testing.assert_array_equal(cell_of, idx)
+    assert np.all((r["u"] < r["P"]).sum() == r["count"])
+
+
+def test_qso_draw_exponent_weights_at_the_middle_box():
+    # a voxel at z = z_2 has t12 = 1 and t23 = 0: p = p_2 = exp(delta_2) (a_2 = 1),
+    # E[p] = exp(sigma_2^2 / 2), whatever lambda is
+    n, cell, om = 16, 2.19, OM
+    z2 = 2.75
+    r2 = dc_closed(om, z2)
+    rng = np.random.default_rng(3)
+    b = [rng.standard_normal((n, n, n)).astype(np.float32) * 0.3 for _ in range(3)]
+    # put voxel (x=0, y=n/2, z=n/2) of the box centred on the axis at distance r2
+    origin = (r2 - 0.5 * cell, -n * cell / 2, -n * cell / 2)
+    q = dict(n=n, cell=cell, origin=origin, z_box=(1.9, z2, 3.6), bias=(3.7, 2.33, 1.7), xi_m5=0.7,
+             nbar=[1e-3] * 10, nbar_z0=1.5, nbar_dz=0.5, seed=1, omega_m=om)
+    res = oracle.qso_draw(q, b)
+    v = (n // 2 * n + n // 2) * n
+    s2 = float(np.mean(b[1].astype(np.float64) ** 2))
+    ref = 1e-3 * cell ** 3 * math.exp(float(b[1].ravel()[v])) / math.exp(0.5 * s2)
+    assert abs(res["P"][v] / ref - 1) < 1e-6  # the voxel centre sits within 1e-6 of z_2 in its weights
+
+
+def test_qso_draw_expected_count_is_nbar_volume():
+    # Gaussian boxes: E[P] = nbar cell^3 in every voxel when P stays below 1
+    n, cell = 32, 2.19
+    rng = np.random.default_rng(11)
+    b = [rng.standard_normal((n, n, n)).astype(np.float32) * 0.5 for _ in range(3)]
+    q = dict(n=n, cell=cell, origin=(4000.0, -n * cell / 2, -n * cell / 2), z_box=(1.9, 2.75, 3.6),
+             bias=(3.7, 2.33, 1.7), xi_m5=0.4, nbar=[1e-3] * 10, nbar_z0=1.5, nbar_dz=0.5, seed=2, omega_m=OM)
+    r = oracle.qso_draw(q, b)
+    exp_mean = 1e-3 * cell ** 3
+    assert abs(r["P"].mean() / exp_mean - 1) < 0.02
+    assert abs(r["count"] - r["P"].sum()) < 5 * math.sqrt(r["P"].sum())
