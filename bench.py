@@ -306,13 +306,43 @@ def box_synth_leg(ctx, mk, w, dev, peak, reps=3):
         res[name] = e0.elapsed_time(e1) / reps
     del work, out
     torch.cuda.empty_cache()
+    # the quasar chain (Sec. 2.2, App. A): three delta_q boxes of one white noise,
+    # then the voxel draw at nbar = 1e-4 (h/Mpc)^3 (about 1.1M quasars at 1024^3)
+    zb = (1.9, 2.75, 3.6)
+    pq = []
+    for z in zb:
+        g = ctx.cosmo_eval(z)[1]
+        pq.append(mk.lognormal_pk(tab, dk, (3.7 * ((1 + z) / 3.33) ** 1.7) ** 2 * g * g))
+    q = dict(n=n, cell=cell, origin=w["origin"], z_box=zb, bias=(3.7, 2.33, 1.7),
+             xi_m5=float(mk.xi_of_pk(tab, dk, 5.0)[0]), nbar=[1e-4] * 20, nbar_z0=1.0, nbar_dz=0.25, seed=77)
+    boxes = [torch.empty(2 * n ** 3, dtype=torch.float32, device=dev) for _ in range(3)]
+    for i in range(3):  # untimed run
+        ctx.synth_box(n, cell, 5, pq[i], dk, layout=mk.BOX_INTERLEAVED, work=boxes[i])
+    ctx.draw_qso(q, boxes, stride=2)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for i in range(3):
+        ctx.synth_box(n, cell, 6, pq[i], dk, layout=mk.BOX_INTERLEAVED, work=boxes[i])
+    e1.record(st)
+    e1.synchronize()
+    synth3 = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    _, cnt = ctx.draw_qso(q, boxes, stride=2)
+    draw_ms = 1000.0 * (time.perf_counter() - t0)
+    del boxes
+    torch.cuda.empty_cache()
     # bytes of the five passes: noise+x (write), y, z (read+write each), inverse y,
     # inverse x (read, padded write)
     b = 8.0 * n ** 3 * (1 + 2 + 2 + 2 + 1) + 8.0 * (n + 1) ** 3
     return {"box": f"{n}^3, cell {cell}, delta + eta_xx into the padded layout",
             "ms": res["library"], "fixture_ms": res["torch_cufft_fixture"],
             "pass_bytes": b, "achieved_gbs": b / (res["library"] * 1e6), "frac_of_hbm_peak": b / (res["library"] * 1e6) / peak,
-            "design": "5 passes: Philox noise + FFT x | FFT y | FFT z, filter, inverse z | inverse y | inverse x + layout"}
+            "design": "5 passes: Philox noise + FFT x | FFT y | FFT z, filter, inverse z | inverse y | inverse x + layout",
+            "qso_chain": {"what": "three quasar-density boxes (z 1.9, 2.75, 3.6) from one white noise, interleaved "
+                                  "layout, then mk_draw_qso (App. A) at nbar 1e-4 (h/Mpc)^3",
+                          "synth_3_boxes_ms": synth3, "draw_wall_ms": draw_ms, "quasars": cnt,
+                          "draw_note": "wall time of the synchronous call: box moments, r table on the host, "
+                                       "count pass, host scan, write pass"}}
 
 
 # ---------------------------------------------------------------- Sec. 2.6 P_S tuning

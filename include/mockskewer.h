@@ -194,6 +194,11 @@ int mk_create(mk_ctx **out, int device, void *cuda_stream, const mk_cosmo *cosmo
 /* Release everything the context owns (not caller buffers).  NULL is a no-op. */
 void mk_destroy(mk_ctx *ctx);
 
+/* The context's FP64 cosmology at redshift z (Sec. 2, Table 1): comoving
+   distance D_C(z) in h^-1 Mpc and linear growth G(z), G(0) = 1.  Host only.
+   MK_EINVAL for z outside [0, 12) or NULL outputs. */
+int mk_cosmo_eval(mk_ctx *ctx, double z, double *d_c, double *growth);
+
 /* Message of the last failing call on this context ("" if none).  The string
    is owned by the context and valid until its next call. */
 const char *mk_last_error(const mk_ctx *ctx);

@@ -32,7 +32,7 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
            "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box", "mk_xi_of_pk",
-           "mk_lognormal_pk", "mk_draw_qso"]
+           "mk_lognormal_pk", "mk_draw_qso", "mk_cosmo_eval"]
 
 
 class MkError(RuntimeError):
@@ -195,6 +195,7 @@ def lib():
                 "mk_xi_of_pk": (C.c_int, [P(C.c_double), i32, C.c_double, P(C.c_double), i32, P(C.c_double)]),
                 "mk_lognormal_pk": (C.c_int, [P(C.c_double), i32, C.c_double, C.c_double, P(C.c_double)]),
                 "mk_draw_qso": (C.c_int, [vp, P(QsoDrawParams), P(vp), i32, vp, i64, P(i64)]),
+                "mk_cosmo_eval": (C.c_int, [vp, C.c_double, P(C.c_double), P(C.c_double)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -387,6 +388,12 @@ class Context:
         self._check(lib().mk_synth_box(self.h, n, cell, int(seed) & 0xFFFFFFFFFFFFFFFF, _dp(pk), pk.size, dk,
                                        layout, _ptr(work), _ptr(spec), _ptr(out)))
         return out
+
+    def cosmo_eval(self, z):
+        """(D_C(z), G(z)) of the context's cosmology."""
+        dc, g = C.c_double(), C.c_double()
+        self._check(lib().mk_cosmo_eval(self.h, z, C.byref(dc), C.byref(g)))
+        return dc.value, g.value
 
     def draw_qso(self, q, boxes, stride=2, capacity=None):
         """Quasars from three quasar-density boxes (Sec. 2.2, App. A); q: dict with

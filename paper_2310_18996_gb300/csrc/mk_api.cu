@@ -1443,3 +1443,11 @@ extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, 
   }
   return MK_OK;
 }
+
+extern "C" int mk_cosmo_eval(mk_ctx *ctx, double z, double *d_c, double *growth) {
+  if (!ctx) return MK_EINVAL;
+  if (!d_c || !growth || !(z >= 0.0 && z < kZMax)) return fail(ctx, MK_EINVAL, "mk_cosmo_eval: z outside [0, 12)");
+  *d_c = ctx->cos.distance(z);
+  *growth = ctx->cos.growth(z);
+  return MK_OK;
+}

@@ -126,3 +126,12 @@ def test_large_box_counts_follow_the_mean_density(ctx):
     nb = np.interp(zv, q["nbar_z0"] + q["nbar_dz"] * np.arange(len(q["nbar"])), q["nbar"])
     expect = nb.sum() * cell ** 3
     assert abs(cnt - expect) < 5 * math.sqrt(expect) + 1e-3 * expect
+
+
+def test_cosmo_eval_matches_oracle(ctx):
+    for z in (0.0, 1.9, 2.75, 3.6, 6.0):
+        dc, g = ctx.cosmo_eval(z)
+        assert abs(dc - oracle.comoving_distance(OM, z)) <= 1e-9 * max(dc, 1.0)
+        assert abs(g / oracle.growth(OM, z) - 1) < 1e-9
+    with pytest.raises(mk.MkError):
+        ctx.cosmo_eval(-0.5)
