@@ -295,6 +295,26 @@ def box_synth_leg(ctx, mk, w, dev, peak, reps=3):
         del d, e
 
     res = {}
+    big = None
+    if n == 1024 and torch.cuda.mem_get_info()[0] > work.numel() * 4 * 8 + out.numel() * 4 * 8 + 20e9:
+        # a 2048^3 box and its padded copy (137 GB) in core on one GPU
+        w2 = torch.empty(2 * 2048 ** 3, dtype=torch.float32, device=dev)
+        o2 = torch.empty(2 * 2049 ** 3, dtype=torch.float32, device=dev)
+
+        def big_once(seed):
+            ctx._stream()
+            ctx._check(mk.lib().mk_synth_box(ctx.h, 2048, cell, seed, mk._dp(tab), tab.size, dk, mk.BOX_PADDED,
+                                             mk._ptr(w2), None, mk._ptr(o2)))
+
+        big_once(1)
+        torch.cuda.synchronize()
+        e0.record(st)
+        big_once(2)
+        e1.record(st)
+        e1.synchronize()
+        big = e0.elapsed_time(e1)
+        del w2, o2
+        torch.cuda.empty_cache()
     for name, fn in (("library", lib_once), ("torch_cufft_fixture", torch_once)):
         fn(1)
         torch.cuda.synchronize()
@@ -338,6 +358,7 @@ def box_synth_leg(ctx, mk, w, dev, peak, reps=3):
             "ms": res["library"], "fixture_ms": res["torch_cufft_fixture"],
             "pass_bytes": b, "achieved_gbs": b / (res["library"] * 1e6), "frac_of_hbm_peak": b / (res["library"] * 1e6) / peak,
             "design": "5 passes: Philox noise + FFT x | FFT y | FFT z, filter, inverse z | inverse y | inverse x + layout",
+            "box_2048_padded_ms": big,
             "qso_chain": {"what": "three quasar-density boxes (z 1.9, 2.75, 3.6) from one white noise, interleaved "
                                   "layout, then mk_draw_qso (App. A) at nbar 1e-4 (h/Mpc)^3",
                           "synth_3_boxes_ms": synth3, "draw_wall_ms": draw_ms, "quasars": cnt,
@@ -505,6 +526,30 @@ def run_gb300(args, rank, world, local_rank):
         return {"value": world * total / (vms / 1000.0), "unit": UNIT, "ms_per_step": vms, "kernel_ms": vkms,
                 "launch": f"{vt} threads/CTA, occupancy target {vo}"}
 
+    # the same step as separate passes (a1-a5 storing delta, eta; FGPA + rebin;
+    # statistics), the shape of a per-stage pipeline, for comparison with the fused launch
+    split = None
+    if rank == 0 and world == 1 and not args.no_split:
+        def split_once():
+            r = ctx.make_skewers(box, qso, n_q, w)
+            f, off = ctx.flux(w, r["sk"], n_q, r["delta"], r["eta"])
+            return ctx.stats(w, r["sk"], n_q, off, f)
+
+        split_once()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        s0.record(stream)
+        for _ in range(reps):
+            split_once()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sms = s0.elapsed_time(s1) / reps
+        split = {"value": total / (sms / 1000.0), "unit": UNIT, "ms_per_step": sms,
+                 "path": "mk_make_skewers (plan + pass storing delta_tot, eta) -> mk_flux -> mk_stats, "
+                         "8 B/px stored and re-read, flux stored and re-read"}
+        torch.cuda.empty_cache()
+
     # the paper's Gaussian-kernel interpolation (7^3 voxels, Sec. 2.3) on the
     # same catalogue: the same fused step with the other gather
     gauss = None
@@ -587,6 +632,8 @@ def run_gb300(args, rank, world, local_rank):
             line["ps_tuning"] = pst
         if boxs:
             line["box_synth"] = boxs
+        if split:
+            line["split_path"] = split
         if gauss:
             line["gauss7"] = gauss
         if tens:
@@ -612,6 +659,7 @@ def main():
     ap.add_argument("--no-tuning", action="store_true")
     ap.add_argument("--no-ps-tuning", action="store_true")
     ap.add_argument("--no-box-synth", action="store_true")
+    ap.add_argument("--no-split", action="store_true")
     ap.add_argument("--ps-outer", type=int, default=5, help="outer loops of the Sec. 2.6 P_S tuning")
     ap.add_argument("--ps-inner", type=int, default=10, help="P_S ratio iterations per outer loop")
     ap.add_argument("--surrogate-draws", type=int, default=8000)

@@ -261,7 +261,8 @@ int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float
        mode and every mode with an index n/2 on an axis set to 0; k along an
        axis at index j is 2 pi (j or j - n) / (n cell);
      P(k): h_pk[i] at k = i dk, i < n_pk (2 .. 2^24), linear in between, 0 beyond.
-   n: 128, 256, 512 or 1024.  layout and d_out (caller-owned device memory):
+   n: 128, 256, 512, 1024 or 2048 (a 2048^3 box and its padded copy take
+   137 GB, in core on one GPU).  layout and d_out (caller-owned device memory):
      MK_BOX_INTERLEAVED: (delta, eta_xx) pairs, 2 n^3 floats (d_out may be d_work);
      MK_BOX_PADDED, MK_BOX_HALO: as mk_pack_box_padded / mk_pack_box_halo;
      MK_BOX_TENSOR: as mk_pack_box_tensor, and d_spec (2 n^3 floats) keeps the

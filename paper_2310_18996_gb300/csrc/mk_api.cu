@@ -174,7 +174,7 @@ struct mk_ctx {
   float *d_zwin = nullptr;  // window mean z per J for segments of zwin_n pixels
   int zwin_n = 0;
   double zwin_dr = -1.0;
-  float2 *d_tw[4] = {nullptr, nullptr, nullptr, nullptr};  // N = 256, 512, 1024, 2048
+  float2 *d_tw[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // N = 256 .. 4096 (4096: box lines of 2048)
   // workspaces
   int64_t *d_cnt_px = nullptr, *d_cnt_seg = nullptr, *d_segoff = nullptr;
   int64_t cnt_cap = 0;
@@ -303,9 +303,14 @@ int tw_slot(int n_fft) {
     case 512: return 1;
     case 1024: return 2;
     case 2048: return 3;
+    case 4096: return 4;
   }
   return -1;
 }
+
+// FFT lengths of the skewer and statistics kernels (the 4096 table serves the
+// box synthesis only)
+bool skewer_fft(int n_fft) { return n_fft == 256 || n_fft == 512 || n_fft == 1024 || n_fft == 2048; }
 
 int ensure_twiddles(mk_ctx *ctx, int n_fft) {
   const int slot = tw_slot(n_fft);
@@ -368,7 +373,7 @@ int check_params(mk_ctx *ctx, const mk_skewer_params *p, bool need_ps) {
   if (!(p->dr > 0.0) || p->dr > 100.0) return fail(ctx, MK_EINVAL, "dr must be in (0, 100]");
   if (!(p->lrf_min > 0.0) || !(p->lrf_max > p->lrf_min)) return fail(ctx, MK_EINVAL, "bad forest window");
   if (p->n_min < 0 || p->n_max < 0) return fail(ctx, MK_EINVAL, "n_min/n_max must be >= 0");
-  if (tw_slot(p->n_fft) < 0) return fail(ctx, MK_EINVAL, "n_fft must be 256, 512, 1024 or 2048");
+  if (!skewer_fft(p->n_fft)) return fail(ctx, MK_EINVAL, "n_fft must be 256, 512, 1024 or 2048");
   if (need_ps && !p->h_p_s) return fail(ctx, MK_EINVAL, "h_p_s is NULL");
   if (p->p_s_nodes < 0 || p->p_s_nodes > MK_MAX_NODES)
     return fail(ctx, MK_EINVAL, "p_s_nodes must be in [0, %d]", MK_MAX_NODES);
@@ -392,7 +397,7 @@ int check_nodes(mk_ctx *ctx, const mk_fgpa_nodes *nd) {
 int check_bins(mk_ctx *ctx, const mk_stat_bins *b) {
   if (!b || b->n_z < 1 || b->n_z > MK_MAX_ZBINS) return fail(ctx, MK_EINVAL, "bad n_z");
   if (!(b->dz > 0.0)) return fail(ctx, MK_EINVAL, "dz must be > 0");
-  if (tw_slot(b->n_fft) < 0) return fail(ctx, MK_EINVAL, "bins n_fft must be 256, 512, 1024 or 2048");
+  if (!skewer_fft(b->n_fft)) return fail(ctx, MK_EINVAL, "bins n_fft must be 256, 512, 1024 or 2048");
   if (b->n_k < 1 || b->n_k > MK_MAX_KBINS || (b->n_fft / 2) % b->n_k)
     return fail(ctx, MK_EINVAL, "n_k must divide n_fft/2 and be <= %d", MK_MAX_KBINS);
   return MK_OK;
@@ -1167,7 +1172,7 @@ int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_q
 int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box, uint32_t flags,
                      int32_t *threads, int32_t *occupancy) {
   if (!ctx || !threads || !occupancy) return MK_EINVAL;
-  if (tw_slot(n_fft) < 0) return fail(ctx, MK_EINVAL, "bad n_fft");
+  if (!skewer_fft(n_fft)) return fail(ctx, MK_EINVAL, "bad n_fft");
   LaunchCfg c = default_cfg(n_fft);
   auto it = ctx->tuned.find(tune_key(n_fft, layout, big_box ? 11 : 10, flags));
   if (it != ctx->tuned.end()) c = it->second;
@@ -1363,7 +1368,8 @@ extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, 
   if (!ctx) return MK_EINVAL;
   int lgn = 0;
   while ((1 << lgn) < n) ++lgn;
-  if (n < 128 || n > 1024 || (1 << lgn) != n) return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512 or 1024");
+  if (n < 128 || n > 2048 || (1 << lgn) != n)
+    return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512, 1024 or 2048");
   if (!(cell > 0.0) || !(dk > 0.0) || !h_pk || n_pk < 2 || n_pk > (1 << 24))
     return fail(ctx, MK_EINVAL, "bad cell, dk or P(k) table (2 .. 2^24 entries)");
   if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 7))

@@ -274,6 +274,7 @@ cudaError_t launch_box_pass(const BoxPassParams &P, int mode, int sms, cudaStrea
     case 8: return launch_n<512>(P, mode, sms, st);
     case 9: return launch_n<1024>(P, mode, sms, st);
     case 10: return launch_n<2048>(P, mode, sms, st);
+    case 11: return launch_n<4096>(P, mode, sms, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -139,10 +139,11 @@ template <int N>
 struct Fft {
   static constexpr int M = N / 2;  // complex points
   static constexpr int T = N / 8;  // threads per team (M/4)
-  static constexpr int LOGM = (M == 128) ? 7 : (M == 256) ? 8 : (M == 512) ? 9 : 10;
+  static constexpr int LOGM = (M == 128) ? 7 : (M == 256) ? 8 : (M == 512) ? 9 : (M == 1024) ? 10 : 11;
   static constexpr int P4 = LOGM / 2;          // radix-4 passes
   static constexpr bool R2 = (LOGM & 1) != 0;  // one radix-2 pass at the end
-  static_assert(N == 256 || N == 512 || N == 1024 || N == 2048, "unsupported N");
+  // 4096: complex lines of 2048 (box synthesis only)
+  static_assert(N == 256 || N == 512 || N == 1024 || N == 2048 || N == 4096, "unsupported N");
 };
 
 // Shared-memory swizzle of complex index i: xor the low bits with 5 times

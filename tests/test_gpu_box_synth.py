@@ -129,3 +129,44 @@ def test_bad_arguments(ctx):
     with pytest.raises(mk.MkError):  # tensor output without the mode buffer
         ctx._check(mk.lib().mk_synth_box(ctx.h, 128, 1.0, 1, mk._dp(tab), tab.size, dk, mk.BOX_TENSOR,
                                          mk._ptr(w), None, mk._ptr(t)))
+
+
+def test_box_2048_in_core_moments(ctx):
+    # 2048^3 (68.7 GB of pairs, in place): the sample moments of delta and
+    # eta_xx match the ensemble expectations of the realised discrete spectrum,
+    #   <delta^2> = sum_k P / V,  <eta_xx^2> = sum_k mu^4 P / V,  <delta eta_xx> = -sum_k mu^2 P / V,
+    # summed over the kept modes (no zero mode, no Nyquist planes), V = (n cell)^3
+    n, cell = 2048, 2.0
+    if torch.cuda.mem_get_info()[0] < 80e9:
+        pytest.skip("needs 80 GB of free device memory")
+    dk, tab = table(cell)
+    out = ctx.synth_box(n, cell, 2048, tab, dk, layout=mk.BOX_INTERLEAVED)
+    v = out.view(n, n * n, 2)
+    s = torch.zeros(3, dtype=torch.float64, device=out.device)
+    for z in range(0, n, 64):
+        blk = v[z:z + 64].double()
+        d, e = blk[..., 0], blk[..., 1]
+        s += torch.stack([(d * d).sum(), (e * e).sum(), (d * e).sum()])
+    s = (s / float(n) ** 3).cpu().numpy()
+    del out, v
+    torch.cuda.empty_cache()
+    k1 = 2.0 * math.pi * torch.fft.fftfreq(n, d=cell, device="cuda", dtype=torch.float64)
+    keep = torch.ones(n, dtype=torch.bool, device="cuda")
+    keep[n // 2] = False
+    kx, ky = k1[None, :], k1[:, None]
+    ptab = torch.from_numpy(tab).cuda()
+    e = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for iz in range(n):
+        if iz == n // 2:
+            continue
+        kz = k1[iz]
+        k2 = kx * kx + ky * ky + kz * kz
+        u = torch.sqrt(k2) / dk
+        j = torch.clamp(u.floor().long(), max=tab.size - 2)
+        p = ptab[j] + (u - j) * (ptab[j + 1] - ptab[j])
+        m = keep[None, :] & keep[:, None] & (k2 > 0)
+        mu2 = torch.where(k2 > 0, kx * kx / torch.where(k2 > 0, k2, 1.0), torch.zeros_like(k2))
+        p = torch.where(m, p, torch.zeros_like(p))
+        e += torch.stack([p.sum(), (mu2 * mu2 * p).sum(), -(mu2 * p).sum()])
+    e = (e / (n * cell) ** 3).cpu().numpy()
+    np.testing.assert_allclose(s, e, rtol=2e-3)
