@@ -263,6 +263,8 @@ int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float
      P(k): h_pk[i] at k = i dk, i < n_pk (2 .. 2^24), linear in between, 0 beyond.
    n: 128, 256, 512, 1024 or 2048 (a 2048^3 box and its padded copy take
    137 GB, in core on one GPU).  layout and d_out (caller-owned device memory):
+     MK_BOX_PLANAR: delta alone, n^3 floats (eta_xx is dropped; the
+       quasar-density boxes of mk_draw_qso need no eta);
      MK_BOX_INTERLEAVED: (delta, eta_xx) pairs, 2 n^3 floats (d_out may be d_work);
      MK_BOX_PADDED, MK_BOX_HALO: as mk_pack_box_padded / mk_pack_box_halo;
      MK_BOX_TENSOR: as mk_pack_box_tensor, and d_spec (2 n^3 floats) keeps the
@@ -294,7 +296,7 @@ int mk_lognormal_pk(const double *h_pk, int32_t n_pk, double dk, double B, doubl
 
 /* Parameters of the quasar draw (Sec. 2.2 and App. A). */
 typedef struct mk_qso_draw_params {
-  int32_t n;           /* box side (voxels), box index [z][y][x] */
+  int32_t n;           /* box side (voxels, a power of two <= 2048), box index [z][y][x] */
   double cell;         /* voxel side, h^-1 Mpc */
   double origin[3];    /* box corner relative to the observer */
   double z_box[3];     /* redshifts z_1 < z_2 < z_3 of the three quasar-density boxes */

@@ -377,7 +377,7 @@ class Context:
         torch = self._torch
         dev = torch.device("cuda", self.device)
         pk = np.ascontiguousarray(pk, dtype=np.float64)
-        side, stride = {BOX_INTERLEAVED: (n, 2), BOX_PADDED: (n + 1, 2), BOX_HALO: (n + 6, 2),
+        side, stride = {BOX_PLANAR: (n, 1), BOX_INTERLEAVED: (n, 2), BOX_PADDED: (n + 1, 2), BOX_HALO: (n + 6, 2),
                         BOX_TENSOR: (n + 1, 8)}[layout]
         if work is None:
             work = torch.empty(2 * n ** 3, dtype=torch.float32, device=dev)

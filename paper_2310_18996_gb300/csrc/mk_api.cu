@@ -1372,11 +1372,13 @@ extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, 
     return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512, 1024 or 2048");
   if (!(cell > 0.0) || !(dk > 0.0) || !h_pk || n_pk < 2 || n_pk > (1 << 24))
     return fail(ctx, MK_EINVAL, "bad cell, dk or P(k) table (2 .. 2^24 entries)");
-  if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 7))
-    return fail(ctx, MK_EINVAL, "d_work must be 16-byte and d_out 8-byte aligned device pointers");
+  if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 3) ||
+      (layout != MK_BOX_PLANAR && (reinterpret_cast<uintptr_t>(d_out) & 7)))
+    return fail(ctx, MK_EINVAL, "d_work must be 16-byte and d_out 8-byte (planar: 4-byte) aligned device pointers");
   const int64_t nv = static_cast<int64_t>(n) * n * n;
   int side = n, margin = 0, stride = 2, pairs = 1;
   switch (layout) {
+    case MK_BOX_PLANAR: stride = 1; break;
     case MK_BOX_INTERLEAVED: break;
     case MK_BOX_PADDED: side = n + 1; break;
     case MK_BOX_HALO: side = n + 6; margin = 3; break;
@@ -1388,7 +1390,7 @@ extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, 
         return fail(ctx, MK_EINVAL, "MK_BOX_TENSOR needs an 8-byte aligned d_spec of 2 n^3 floats");
       if ((reinterpret_cast<uintptr_t>(d_out) & 15)) return fail(ctx, MK_EINVAL, "MK_BOX_TENSOR: d_out not 16-byte aligned");
       break;
-    default: return fail(ctx, MK_EINVAL, "layout must be interleaved, padded, halo or tensor");
+    default: return fail(ctx, MK_EINVAL, "layout must be planar, interleaved, padded, halo or tensor");
   }
   auto overlap = [](const float *a, int64_t na, const float *b, int64_t nb) { return a < b + nb && b < a + na; };
   const int64_t nout = static_cast<int64_t>(side) * side * side * stride;

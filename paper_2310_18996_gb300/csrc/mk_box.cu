@@ -206,8 +206,12 @@ __global__ void __launch_bounds__(kBoxThreads, 2) k_box_pass(BoxPassParams P) {
               for (int xp = threadIdx.x; xp < S; xp += kBoxThreads) {
                 const int x = ((xp - mg) % M + M) % M;
                 const float2 v = lines[c * LS + x];
-                *reinterpret_cast<float2 *>(row + static_cast<int64_t>(xp) * P.out_stride) =
-                    make_float2(v.x, (P.pair == 3) ? 0.0f : v.y);
+                if (P.out_stride == 1) {  // delta alone
+                  row[xp] = v.x;
+                } else {
+                  *reinterpret_cast<float2 *>(row + static_cast<int64_t>(xp) * P.out_stride) =
+                      make_float2(v.x, (P.pair == 3) ? 0.0f : v.y);
+                }
               }
             }
           }

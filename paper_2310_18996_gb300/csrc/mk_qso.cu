@@ -48,7 +48,7 @@ double xi_at(const double *pk, int n, double dk, double r) {
 struct DrawParams {
   const float *box[3];
   int32_t stride;
-  int32_t n;
+  int32_t n, lgn;  // n = 2^lgn
   float cell;
   float origin[3];
   const float4 *tab;  // per r node: (a_1, a_2, a_3, nbar cell^3 / E[p]), (w_1, w_2, w_3, 0)
@@ -65,10 +65,10 @@ struct DrawParams {
 
 // Accept decision of voxel v (and its Philox words for the position).
 __device__ __forceinline__ bool voxel_accept(const DrawParams &P, int64_t v, u32x4 &w, int &x, int &y, int &z) {
-  const int n = P.n;
-  x = static_cast<int>(v % n);
-  y = static_cast<int>((v / n) % n);
-  z = static_cast<int>(v / (static_cast<int64_t>(n) * n));
+  const int mask = P.n - 1;
+  x = static_cast<int>(v) & mask;
+  y = static_cast<int>(v >> P.lgn) & mask;
+  z = static_cast<int>(v >> (2 * P.lgn));
   const float cx = P.origin[0] + (x + 0.5f) * P.cell, cy = P.origin[1] + (y + 0.5f) * P.cell,
               cz = P.origin[2] + (z + 0.5f) * P.cell;
   const float r = sqrtf(cx * cx + cy * cy + cz * cz);
@@ -218,8 +218,10 @@ extern "C" int mk_draw_qso(mk_ctx *ctx, const mk_qso_draw_params *q, const float
   if (!q || !d_box_q || !d_box_q[0] || !d_box_q[1] || !d_box_q[2] || !h_count || (capacity > 0 && !d_qso) ||
       capacity < 0)
     return qfail(ctx, MK_EINVAL, "mk_draw_qso: NULL argument");
-  if (q->n < 2 || q->n > 2048 || !(q->cell > 0.0) || (box_stride != 1 && box_stride != 2))
-    return qfail(ctx, MK_EINVAL, "mk_draw_qso: bad box side, cell or stride");
+  int lgn = 0;
+  while (lgn < 12 && (1 << lgn) < q->n) ++lgn;
+  if (q->n < 2 || q->n > 2048 || (1 << lgn) != q->n || !(q->cell > 0.0) || (box_stride != 1 && box_stride != 2))
+    return qfail(ctx, MK_EINVAL, "mk_draw_qso: box side must be a power of two in [2, 2048]; bad cell or stride");
   if (!(q->z_box[0] < q->z_box[1] && q->z_box[1] < q->z_box[2]) || !(q->bias[0] > 0.0))
     return qfail(ctx, MK_EINVAL, "mk_draw_qso: box redshifts must increase and the bias be > 0");
   if (!q->h_nbar || q->n_nbar < 2 || !(q->nbar_dz > 0.0)) return qfail(ctx, MK_EINVAL, "mk_draw_qso: bad nbar table");
@@ -293,6 +295,7 @@ extern "C" int mk_draw_qso(mk_ctx *ctx, const mk_qso_draw_params *q, const float
   for (int i = 0; i < 3; ++i) P.box[i] = d_box_q[i];
   P.stride = box_stride;
   P.n = q->n;
+  P.lgn = lgn;
   P.cell = static_cast<float>(q->cell);
   for (int d = 0; d < 3; ++d) {
     P.origin[d] = static_cast<float>(q->origin[d]);

@@ -61,6 +61,8 @@ def test_padded_and_halo_layouts_repeat_the_box(ctx):
     h = ctx.synth_box(n, cell, seed, tab, dk, layout=mk.BOX_HALO).view(n + 6, n + 6, n + 6, 2).cpu().numpy()
     idx = (np.arange(n + 6) - 3) % n
     np.testing.assert_array_equal(h, g[np.ix_(idx, idx, idx)])
+    d = ctx.synth_box(n, cell, seed, tab, dk, layout=mk.BOX_PLANAR).view(n, n, n).cpu().numpy()
+    np.testing.assert_array_equal(d, g[..., 0])
 
 
 def test_tensor_box_matches_oracle(ctx):
