@@ -55,9 +55,8 @@ struct DrawParams {
   int32_t n_tab;
   float r0, inv_dr;
   uint32_t key0, key1;
-  int64_t tile;       // voxels per tile
-  int64_t *count;     // per tile (count pass)
-  const int64_t *offset;  // per tile (write pass)
+  int32_t *count32;       // per sub-range (count pass)
+  const int64_t *offset;  // per sub-range (write pass)
   mk_qso *out;
   int64_t capacity;
   double origin_d[3], cell_d;
@@ -91,84 +90,81 @@ __device__ __forceinline__ bool voxel_accept(const DrawParams &P, int64_t v, u32
 }
 
 constexpr int kDrawThreads = 256;
+constexpr int kSub = 1024;  // voxels per warp sub-range (count and write passes)
 
+// Record of an accepted voxel.  Out of line, so that its FP64 arithmetic runs
+// only for accepted voxels instead of being predicated into every iteration.
+__device__ __noinline__ void write_qso(const DrawParams &P, int64_t o, int64_t v, u32x4 w, int x, int y, int z) {
+  mk_qso q;
+  q.pos[0] = P.origin_d[0] + (x + (static_cast<double>(w.y) + 0.5) * 0x1p-32) * P.cell_d;
+  q.pos[1] = P.origin_d[1] + (y + (static_cast<double>(w.z) + 0.5) * 0x1p-32) * P.cell_d;
+  q.pos[2] = P.origin_d[2] + (z + (static_cast<double>(w.w) + 0.5) * 0x1p-32) * P.cell_d;
+  q.id = static_cast<uint64_t>(v);
+  P.out[o] = q;
+}
+
+// One warp per sub-range of kSub voxels: the accepted count (ballot/popc).
 __global__ void __launch_bounds__(kDrawThreads) k_qso_count(DrawParams P) {
-  __shared__ int64_t warp_sum[kDrawThreads / 32];
   const int64_t nv = static_cast<int64_t>(P.n) * P.n * P.n;
-  const int64_t tiles = (nv + P.tile - 1) / P.tile;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t v0 = t * P.tile, v1 = min(nv, v0 + P.tile);
-    int64_t c = 0;
-    for (int64_t v = v0 + threadIdx.x; v < v1; v += kDrawThreads) {
+  const int64_t subs = (nv + kSub - 1) / kSub;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (kDrawThreads / 32);
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(kDrawThreads / 32) + (threadIdx.x >> 5); s < subs; s += warps) {
+    const int64_t v0 = s * kSub, v1 = min(nv, v0 + kSub);
+    int c = 0;
+    for (int64_t c0 = v0; c0 < v1; c0 += 32) {
+      const int64_t v = c0 + lane;
       u32x4 w;
       int x, y, z;
-      c += voxel_accept(P, v, w, x, y, z) ? 1 : 0;
+      const bool acc = v < v1 && voxel_accept(P, v, w, x, y, z);
+      c += __popc(__ballot_sync(0xffffffffu, acc));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t s = 0;
-      for (int i = 0; i < kDrawThreads / 32; ++i) s += warp_sum[i];
-      P.count[t] = s;
-    }
-    __syncthreads();
+    if (lane == 0) P.count32[s] = c;
   }
 }
 
+// The same decisions, written in voxel order from each sub-range's offset.
 __global__ void __launch_bounds__(kDrawThreads) k_qso_write(DrawParams P) {
-  __shared__ int warp_cnt[kDrawThreads / 32];
-  __shared__ int64_t base_s;
   const int64_t nv = static_cast<int64_t>(P.n) * P.n * P.n;
-  const int64_t tiles = (nv + P.tile - 1) / P.tile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int64_t v0 = t * P.tile, v1 = min(nv, v0 + P.tile);
-    if (threadIdx.x == 0) base_s = P.offset[t];
-    __syncthreads();
-    int64_t base = base_s;
-    // chunks of kDrawThreads voxels in order; ballot + warp prefix keep the voxel order
-    for (int64_t c0 = v0; c0 < v1; c0 += kDrawThreads) {
-      const int64_t v = c0 + threadIdx.x;
+  const int64_t subs = (nv + kSub - 1) / kSub;
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (kDrawThreads / 32);
+  for (int64_t s = blockIdx.x * static_cast<int64_t>(kDrawThreads / 32) + (threadIdx.x >> 5); s < subs; s += warps) {
+    const int64_t v0 = s * kSub, v1 = min(nv, v0 + kSub);
+    int64_t base = P.offset[s];
+    for (int64_t c0 = v0; c0 < v1; c0 += 32) {
+      const int64_t v = c0 + lane;
       u32x4 w{0u, 0u, 0u, 0u};
       int x = 0, y = 0, z = 0;
       const bool acc = v < v1 && voxel_accept(P, v, w, x, y, z);
       const uint32_t m = __ballot_sync(0xffffffffu, acc);
-      if (lane == 0) warp_cnt[warp] = __popc(m);
-      __syncthreads();
-      int before = 0, total = 0;
-      for (int i = 0; i < kDrawThreads / 32; ++i) {
-        before += (i < warp) ? warp_cnt[i] : 0;
-        total += warp_cnt[i];
+      if (m != 0u) {  // warp-uniform: most chunks of 32 voxels accept none
+        const int64_t o = base + __popc(m & ((1u << lane) - 1u));
+        if (acc && o < P.capacity) write_qso(P, o, v, w, x, y, z);
       }
-      if (acc) {
-        const int64_t o = base + before + __popc(m & ((1u << lane) - 1u));
-        if (o < P.capacity) {
-          mk_qso q;
-          q.pos[0] = P.origin_d[0] + (x + (static_cast<double>(w.y) + 0.5) * 0x1p-32) * P.cell_d;
-          q.pos[1] = P.origin_d[1] + (y + (static_cast<double>(w.z) + 0.5) * 0x1p-32) * P.cell_d;
-          q.pos[2] = P.origin_d[2] + (z + (static_cast<double>(w.w) + 0.5) * 0x1p-32) * P.cell_d;
-          q.id = static_cast<uint64_t>(v);
-          P.out[o] = q;
-        }
-      }
-      base += total;
-      __syncthreads();
+      base += __popc(m);
     }
   }
 }
 
-__global__ void k_box_sq_sum(const float *b0, const float *b1, const float *b2, int32_t stride, int64_t nv,
-                             double *partial) {
+// Sums of delta_q,i^2 (FP32 over runs of 32 elements per thread, FP64 across
+// runs and threads), one partial per block, summed on the host in order.
+__global__ void __launch_bounds__(kDrawThreads) k_box_sq_sum(const float *b0, const float *b1, const float *b2,
+                                                             int32_t stride, int64_t nv, double *partial) {
   __shared__ double red[3][kDrawThreads];
   double s[3] = {0.0, 0.0, 0.0};
-  for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < nv;
-       v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const float a = __ldg(b0 + v * stride), b = __ldg(b1 + v * stride), c = __ldg(b2 + v * stride);
-    s[0] += static_cast<double>(a) * a;
-    s[1] += static_cast<double>(b) * b;
-    s[2] += static_cast<double>(c) * c;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  while (v < nv) {
+    float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll 8
+    for (int r = 0; r < 32 && v < nv; ++r, v += step) {
+      const float a = __ldg(b0 + v * stride), b = __ldg(b1 + v * stride), c = __ldg(b2 + v * stride);
+      f[0] = fmaf(a, a, f[0]);
+      f[1] = fmaf(b, b, f[1]);
+      f[2] = fmaf(c, c, f[2]);
+    }
+    for (int i = 0; i < 3; ++i) s[i] += f[i];
   }
   for (int i = 0; i < 3; ++i) red[i][threadIdx.x] = s[i];
   __syncthreads();
@@ -307,34 +303,37 @@ extern "C" int mk_draw_qso(mk_ctx *ctx, const mk_qso_draw_params *q, const float
   P.inv_dr = static_cast<float>(1.0 / dr);
   P.key0 = static_cast<uint32_t>(q->seed);
   P.key1 = static_cast<uint32_t>(q->seed >> 32);
-  P.tile = 8192;
   P.out = d_qso;
   P.capacity = capacity;
-  const int64_t tiles = (nv + P.tile - 1) / P.tile;
+  const int64_t subs = (nv + kSub - 1) / kSub;
   float4 *d_tab = nullptr;
-  int64_t *d_cnt = nullptr, *d_off = nullptr;
-  std::vector<int64_t> cnt(tiles), off(tiles);
+  int32_t *d_cnt = nullptr;
+  int64_t *d_off = nullptr;
+  std::vector<int32_t> cnt(subs);
+  std::vector<int64_t> off(subs);
   e = cudaMalloc(&d_tab, sizeof(float4) * tab.size());
-  if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int64_t) * tiles);
-  if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * tiles);
+  if (e == cudaSuccess) e = cudaMalloc(&d_cnt, sizeof(int32_t) * subs);
+  if (e == cudaSuccess) e = cudaMalloc(&d_off, sizeof(int64_t) * subs);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d_tab, tab.data(), sizeof(float4) * tab.size(), cudaMemcpyHostToDevice, st);
-  const int grid = static_cast<int>(std::min<int64_t>(tiles, 8 * mkhost::ctx_sms(ctx)));
+  const int64_t warps_per_block = kDrawThreads / 32;
+  const int grid = static_cast<int>(
+      std::min<int64_t>((subs + warps_per_block - 1) / warps_per_block, 8 * mkhost::ctx_sms(ctx)));
   P.tab = d_tab;
-  P.count = d_cnt;
+  P.count32 = d_cnt;
   P.offset = d_off;
   if (e == cudaSuccess) {
     k_qso_count<<<grid, kDrawThreads, 0, st>>>(P);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int64_t) * tiles, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), d_cnt, sizeof(int32_t) * subs, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   int64_t total = 0;
   if (e == cudaSuccess) {
-    for (int64_t t = 0; t < tiles; ++t) {
+    for (int64_t t = 0; t < subs; ++t) {
       off[t] = total;
       total += cnt[t];
     }
-    e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * tiles, cudaMemcpyHostToDevice, st);
+    e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * subs, cudaMemcpyHostToDevice, st);
   }
   if (e == cudaSuccess && capacity > 0) {
     k_qso_write<<<grid, kDrawThreads, 0, st>>>(P);
