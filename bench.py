@@ -688,7 +688,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-chunks", type=int, default=8)
+    ap.add_argument("--e2e-chunks", type=int, default=16)
     ap.add_argument("--no-gauss7", action="store_true")
     ap.add_argument("--no-tensor", action="store_true")
     ap.add_argument("--no-tuning", action="store_true")
