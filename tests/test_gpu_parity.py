@@ -580,6 +580,15 @@ def test_batched_workload_sampled(ctx):
     _full_size_check(ctx, si.workload("batched"), 40, 6)
 
 
+def test_batched_workload_sampled_z_dependent_p_s(ctx):
+    # the P_S node tables at the 12 bin centres (the instance the Sec. 2.6
+    # tuning runs), full size, sampled skewers against the oracle
+    w = si.workload("batched")
+    zs = [w["z_bin_lo"] + (i + 0.5) * w["dz_bin"] for i in range(w["n_zbins"])]
+    ps = np.stack([np.asarray(w["p_s"]) * (1.0 + 0.3 * (z - 2.6)) for z in zs])
+    _full_size_check(ctx, si.shrink(w, p_s=ps, p_s_z=zs), 16, 9)
+
+
 def test_scale_workload_sampled_tensor(ctx):
     w = si.shrink(si.workload("scale"), eta_mode=1)
     torch.cuda.empty_cache()
