@@ -654,6 +654,29 @@ int mk_tune_ps(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qs
                int32_t n_outer, int32_t n_inner, mk_skewer *d_sk, int64_t *d_offsets, double *h_p_s,
                mk_fgpa_nodes *out, mk_ps_tune_report *report);
 
+/* ------------------------------------------- saved pre-production (Sec. 3) */
+
+/* Write stored pre-FGPA skewers to a file, so that later post-production runs
+   (FGPA and statistics with new a, b, c: mk_flux, mk_flux_stats, mk_tune)
+   start from them instead of re-synthesising (the paper saves its
+   pre-production the same way).  Little-endian file: the 8 bytes
+   "MKSKEW01", int64 n_sk, int64 total pixels, n_sk mk_skewer records,
+   n_sk + 1 int64 offsets, total FP32 delta_tot, total FP32 eta.  Device
+   inputs as mk_make_skewers wrote them; copied through a pinned staging
+   buffer of the context's stream.  Synchronous.  MK_EINVAL for NULL
+   pointers or a file that cannot be written. */
+int mk_save_skewers(mk_ctx *ctx, const char *path, const mk_skewer *d_sk, int64_t n_sk, const int64_t *d_offsets,
+                    const float *d_delta, const float *d_eta);
+
+/* Read a file of mk_save_skewers into caller-owned device buffers: up to
+   cap_sk records (and cap_sk + 1 offsets) and cap_px pixels of delta_tot and
+   eta.  *n_sk and *total_px receive the file's sizes; with NULL buffers (or
+   too small capacities, then MK_ERANGE) nothing else is read, which makes
+   the call a size query.  Synchronous.  MK_EINVAL for a missing or
+   malformed file. */
+int mk_load_skewers(mk_ctx *ctx, const char *path, mk_skewer *d_sk, int64_t cap_sk, int64_t *d_offsets,
+                    float *d_delta, float *d_eta, int64_t cap_px, int64_t *n_sk, int64_t *total_px);
+
 /* ---------------------------------------------------------------- timing */
 
 /* When on (non-zero), the library records CUDA events on the context's

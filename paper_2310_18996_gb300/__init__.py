@@ -32,7 +32,7 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
            "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box", "mk_xi_of_pk",
-           "mk_lognormal_pk", "mk_draw_qso", "mk_cosmo_eval"]
+           "mk_lognormal_pk", "mk_draw_qso", "mk_cosmo_eval", "mk_save_skewers", "mk_load_skewers"]
 
 
 class MkError(RuntimeError):
@@ -196,6 +196,8 @@ def lib():
                 "mk_lognormal_pk": (C.c_int, [P(C.c_double), i32, C.c_double, C.c_double, P(C.c_double)]),
                 "mk_draw_qso": (C.c_int, [vp, P(QsoDrawParams), P(vp), i32, vp, i64, P(i64)]),
                 "mk_cosmo_eval": (C.c_int, [vp, C.c_double, P(C.c_double), P(C.c_double)]),
+                "mk_save_skewers": (C.c_int, [vp, C.c_char_p, vp, i64, vp, vp, vp]),
+                "mk_load_skewers": (C.c_int, [vp, C.c_char_p, vp, i64, vp, vp, vp, i64, P(i64), P(i64)]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -388,6 +390,29 @@ class Context:
         self._check(lib().mk_synth_box(self.h, n, cell, int(seed) & 0xFFFFFFFFFFFFFFFF, _dp(pk), pk.size, dk,
                                        layout, _ptr(work), _ptr(spec), _ptr(out)))
         return out
+
+    def save_skewers(self, path, r, n_sk):
+        """Write stored pre-FGPA skewers (make_skewers' dict) to `path`."""
+        self._stream()
+        self._check(lib().mk_save_skewers(self.h, os.fsencode(path), _ptr(r["sk"]), n_sk, _ptr(r["offsets"]),
+                                          _ptr(r["delta"]), _ptr(r["eta"])))
+
+    def load_skewers(self, path):
+        """Read a file of save_skewers into new device tensors: dict(sk, offsets,
+        delta, eta, total) and the skewer count."""
+        torch = self._torch
+        ns, tp = C.c_int64(), C.c_int64()
+        self._check(lib().mk_load_skewers(self.h, os.fsencode(path), None, 0, None, None, None, 0, C.byref(ns),
+                                          C.byref(tp)))
+        dev = torch.device("cuda", self.device)
+        r = dict(sk=torch.empty(max(ns.value, 1) * SKEWER_BYTES, dtype=torch.uint8, device=dev),
+                 offsets=torch.empty(ns.value + 1, dtype=torch.int64, device=dev),
+                 delta=torch.empty(max(tp.value, 1), dtype=torch.float32, device=dev),
+                 eta=torch.empty(max(tp.value, 1), dtype=torch.float32, device=dev), total=tp.value)
+        self._stream()
+        self._check(lib().mk_load_skewers(self.h, os.fsencode(path), _ptr(r["sk"]), ns.value, _ptr(r["offsets"]),
+                                          _ptr(r["delta"]), _ptr(r["eta"]), tp.value, C.byref(ns), C.byref(tp)))
+        return r, ns.value
 
     def cosmo_eval(self, z):
         """(D_C(z), G(z)) of the context's cosmology."""

@@ -292,6 +292,40 @@ def test_tensor_isotropic_diagonal_equals_single_box_path(ctx, tiny, tensor):
     assert_field_close(g6["eta"][:tot].cpu().numpy(), g1["eta"][:tot].cpu().numpy().astype(np.float64), "eta")
 
 
+def test_saved_pre_production_round_trip(ctx, tiny, tmp_path):
+    # Sec. 3: pre-FGPA skewers written once, post-production (FGPA and
+    # statistics with other parameters) run from the file
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    f = tmp_path / "pre.mksk"
+    ctx.save_skewers(str(f), r, n)
+    assert f.stat().st_size == 24 + n * mk.SKEWER_BYTES + 8 * (n + 1) + 8 * r["total"]
+    q, nq = ctx.load_skewers(str(f))
+    assert nq == n and q["total"] == r["total"]
+    assert torch.equal(q["sk"][: n * mk.SKEWER_BYTES], r["sk"][: n * mk.SKEWER_BYTES])
+    assert torch.equal(q["offsets"], r["offsets"])
+    tot = r["total"]
+    assert torch.equal(q["delta"][:tot], r["delta"][:tot]) and torch.equal(q["eta"][:tot], r["eta"][:tot])
+    w2 = dict(w)
+    w2["node_b"] = [1.3] * len(w["node_z"])
+    a = ctx.flux_stats(w2, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+    b = ctx.flux_stats(w2, q["sk"], n, q["offsets"], q["delta"], q["eta"])
+    for k in ("sums", "p1d_sum", "n_seg"):
+        np.testing.assert_array_equal(a[k], b[k])
+    # a truncated or foreign file is refused, the context stays usable
+    bad = tmp_path / "bad.mksk"
+    bad.write_bytes(f.read_bytes()[:100])
+    with pytest.raises(mk.MkError):
+        ctx.load_skewers(str(bad))
+    bad.write_bytes(b"NOTASKEW" + bytes(16))
+    with pytest.raises(mk.MkError):
+        ctx.load_skewers(str(bad))
+    c = ctx.flux_stats(w2, q["sk"], n, q["offsets"], q["delta"], q["eta"])
+    np.testing.assert_array_equal(c["sums"], a["sums"])
+
+
 def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
     # zero box: delta_tot is delta_S; each segment's DFT over its amplitude gives
     # back the oracle's modes
