@@ -244,21 +244,23 @@ __global__ void __launch_bounds__(BoxSmem<N2, REG>::THREADS, 2) k_box_pass(BoxPa
           float s = 0.0f;
           if (!zero) {
             // linear in the table, 0 beyond its last entry (n_pk <= 2^24: the
-            // comparison is exact and j <= n_pk - 2 below)
-            const float u = sqrtf(k2) * P.inv_dk, last = static_cast<float>(P.n_pk - 1);
+            // comparison is exact and j <= n_pk - 2 below); |k| and the roots
+            // through rsqrt (a few ulp, far inside the synthesis tolerance)
+            const float u = k2 * rsqrtf(k2) * P.inv_dk, last = static_cast<float>(P.n_pk - 1);
+            float pk = -1.0f;
             if (u < last) {
               const int j = static_cast<int>(u);
               const float f = u - static_cast<float>(j);
-              const float pk = fmaf(f, __ldg(P.pk + j + 1) - __ldg(P.pk + j), __ldg(P.pk + j));
-              s = sqrtf(fmaxf(pk, 0.0f)) * P.amp;
+              pk = fmaf(f, __ldg(P.pk + j + 1) - __ldg(P.pk + j), __ldg(P.pk + j));
             } else if (u == last) {
-              s = sqrtf(fmaxf(__ldg(P.pk + P.n_pk - 1), 0.0f)) * P.amp;
+              pk = __ldg(P.pk + P.n_pk - 1);
             }
+            s = pk > 0.0f ? pk * rsqrtf(pk) * P.amp : 0.0f;
           }
           d = make_float2(d.x * s, d.y * s);
           if (P.spec) P.spec[line_addr(2, g, c, e, M)] = d;
         }
-        const float2 f = k2 > 0.0f ? pair_filter(P.pair, kx, ky, kz, 1.0f / k2) : make_float2(0.f, 0.f);
+        const float2 f = k2 > 0.0f ? pair_filter(P.pair, kx, ky, kz, __frcp_rn(k2)) : make_float2(0.f, 0.f);
         lines[c * LS + e] = make_float2(d.x * f.x - d.y * f.y, d.y * f.x + d.x * f.y);
       }
       __syncthreads();
