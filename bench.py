@@ -583,6 +583,49 @@ def run_gb300(args, rank, world, local_rank):
         batched = {"value": total / (bms / 1000.0), "unit": UNIT, "ms_per_step": bms, "launches": (n_q + nb - 1) // nb,
                    "path": "mk_run (fused, statistics read back) per batch of 500 quasars, no graph"}
 
+    # the same sight lines at distances that make the skewer lengths uniform in
+    # [200, 1500] pixels (each quasar's distance bisected on the library's geometry)
+    uni = None
+    if rank == 0 and world == 1 and not args.no_split:
+        rng_u = np.random.default_rng(17)
+        target = rng_u.integers(200, 1501, n_q)
+        udir = pos / np.linalg.norm(pos, axis=1, keepdims=True)
+        lo = np.full(n_q, ctx.cosmo_eval(1.9)[0])
+        hi = np.full(n_q, ctx.cosmo_eval(4.6)[0])
+        for _ in range(44):
+            mid = 0.5 * (lo + hi)
+            sk_m, _, _ = ctx.plan(box, mk.catalogue_tensor(udir * mid[:, None], ids, dev), n_q, w)
+            nm = mk.skewer_records(sk_m, n_q)["n"]
+            short = nm < target
+            lo = np.where(short, mid, lo)
+            hi = np.where(short, hi, mid)
+        qu = mk.catalogue_tensor(udir * hi[:, None], ids, dev)
+        sk_u, off_u, tot_u = ctx.plan(box, qu, n_q, w)
+        nu = mk.skewer_records(sk_u, n_q)["n"]
+        ou = {"sk": sk_u, "offsets": off_u, "flux": torch.empty(tot_u, dtype=torch.float32, device=dev)}
+
+        def ustep(extra=mk.GRAPH):
+            return ctx.run(box, qu, n_q, w, flags=flags | extra, capacity=tot_u, outputs=ou)
+
+        ustep(mk.AUTOTUNE)
+        for _ in range(args.warmup):
+            ustep()
+        torch.cuda.synchronize()
+        u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        u0.record(stream)
+        for _ in range(args.steps):
+            ustep()
+        u1.record(stream)
+        torch.cuda.synchronize()
+        ums = u0.elapsed_time(u1) / args.steps
+        uni = {"value": tot_u / (ums / 1000.0), "unit": UNIT, "ms_per_step": ums, "pixels_per_step": int(tot_u),
+               "lengths": f"min {int(nu.min())}, max {int(nu.max())}, mean {float(nu.mean()):.1f}, "
+                          f"{float(np.mean(nu == target)):.3f} exactly on target",
+               "catalogue": "the benchmark's 1M sight lines, each quasar's distance set so that its skewer "
+                            "has a length drawn uniformly from [200, 1500] pixels"}
+        del ou
+        torch.cuda.empty_cache()
+
     # the paper's Gaussian-kernel interpolation (7^3 voxels, Sec. 2.3) on the
     # same catalogue: the same fused step with the other gather
     gauss = None
@@ -669,6 +712,8 @@ def run_gb300(args, rank, world, local_rank):
             line["split_path"] = split
         if batched:
             line["batched_launches"] = batched
+        if uni:
+            line["uniform_lengths"] = uni
         if gauss:
             line["gauss7"] = gauss
         if tens:
