@@ -246,6 +246,8 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
     t0 = time.perf_counter()
     norm, losses = mlp.fit(hx, ht, batch=256, epochs=epochs, lr=2e-3, seed=5)
     t_fit = time.perf_counter() - t0
+    if source == "subset":  # labelled on the first n_lab skewers of this catalogue: calibrate on them
+        norm.calib_skewers = n_lab
     nd_s, rep_s = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
                           method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm, max_passes=60)
     mlp.close()
@@ -253,7 +255,8 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
     torch.cuda.empty_cache()
 
     def rep(x):
-        return {"converged": bool(x.converged), "passes": x.passes, "gpu_ms": x.gpu_ms, "wall_ms": x.wall_ms,
+        return {"converged": bool(x.converged), "passes": x.passes, "calib_passes": x.calib_passes,
+                "gpu_ms": x.gpu_ms, "wall_ms": x.wall_ms,
                 "max_abs_dfbar": x.max_abs_dfbar, "max_rel_p1d": x.max_rel_p1d, "max_rel_beta": x.max_rel_beta}
 
     return {"workload": "stored skewers of the benchmark catalogue (1024^3, 1M quasars), 12 z nodes, target "

@@ -523,10 +523,16 @@ typedef struct mk_surrogate_space {
 
 /* Affine normalisation between physical surrogate inputs/outputs and the
    MLP's: x_mlp = (x - x_mean)/x_std, t = t_mlp t_std + t_mean.  Inputs are
-   (z, ln a, b, c); outputs (Fbar, b_F, beta_F, ln P1D_dF of 32 k bins). */
+   (z, ln a, b, c); outputs (Fbar, b_F, beta_F, ln P1D_dF of 32 k bins).
+   calib_skewers: when the surrogate was labelled on the first calib_skewers
+   skewers of the catalogue being tuned (0 otherwise; mk_surrogate_fit writes
+   0), mk_tune runs one pass over those skewers at the surrogate's first fit
+   and refits on the surrogate shifted by that pass's discrepancy before its
+   first full pass. */
 typedef struct mk_surrogate_norm {
   double x_mean[MK_MLP_IN], x_std[MK_MLP_IN];
   double t_mean[MK_MLP_OUT], t_std[MK_MLP_OUT];
+  int64_t calib_skewers;
 } mk_surrogate_norm;
 
 /* Training set of the surrogate: n_draws parameter sets drawn uniformly in
@@ -570,9 +576,10 @@ typedef struct mk_tune_report {
   int32_t converged;  /* 1 when every active bin met the tolerances on a full pass */
   int32_t passes;     /* full tuning passes over the skewers */
   int32_t iterations; /* parameter updates */
-  double gpu_ms;      /* GPU time of the passes and of the surrogate inference */
+  double gpu_ms;      /* GPU time of all passes (calibration included) and of the surrogate inference */
   double wall_ms;
   double max_abs_dfbar, max_rel_p1d, max_rel_beta; /* of the last full pass */
+  int32_t calib_passes; /* surrogate calibration passes over norm->calib_skewers skewers */
 } mk_tune_report;
 
 /* Solve for ln a, b, c at the z nodes in *inout (count = bins->n_z, nodes at
@@ -586,7 +593,9 @@ typedef struct mk_tune_report {
    surrogate alone; every later iteration is one verifying pass, after which
    the fit is redone on the surrogate shifted by that pass's discrepancy
    (true minus predicted residual) plus a linear term in the parameter change
-   whose slope is Broyden-updated from successive passes.  Nodes of inactive
+   whose slope is Broyden-updated from successive passes (when
+   norm->calib_skewers > 0, a pass over that labelled subset first corrects
+   the surrogate's own error at its fit).  Nodes of inactive
    bins follow the nearest active node (ties: the lower one).  Stops when a
    pass meets the tolerances or after max_passes passes.  Synchronous. */
 int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,

@@ -90,7 +90,7 @@ class SurrogateSpace(C.Structure):
 
 class SurrogateNorm(C.Structure):
     _fields_ = [("x_mean", C.c_double * 4), ("x_std", C.c_double * 4),
-                ("t_mean", C.c_double * 35), ("t_std", C.c_double * 35)]
+                ("t_mean", C.c_double * 35), ("t_std", C.c_double * 35), ("calib_skewers", C.c_int64)]
 
 
 class TuneTarget(C.Structure):
@@ -121,7 +121,7 @@ class PsTuneReport(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("converged", C.c_int32), ("passes", C.c_int32), ("iterations", C.c_int32),
                 ("gpu_ms", C.c_double), ("wall_ms", C.c_double), ("max_abs_dfbar", C.c_double),
-                ("max_rel_p1d", C.c_double), ("max_rel_beta", C.c_double)]
+                ("max_rel_p1d", C.c_double), ("max_rel_beta", C.c_double), ("calib_passes", C.c_int32)]
 
 
 MLP_NPARAM = 38179

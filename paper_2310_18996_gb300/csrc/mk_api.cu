@@ -849,6 +849,7 @@ int stats_pass(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_s
   P.rebin = rebin;
   P.zbin = ctx->d_zbin;
   P.segzbin = ctx->d_segzbin;
+  P.bin_end = ctx->d_bin_end;
   P.p1d_scale = static_cast<float>(rebin * params->dr / bins->n_fft);
   P.cumz = ctx->d_cumz;
   P.tw = ctx->d_tw[tw_slot(bins->n_fft)];
@@ -1297,6 +1298,7 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
   P.rebin = rebin;
   P.zbin = ctx->d_zbin;
   P.segzbin = ctx->d_segzbin;
+  P.bin_end = ctx->d_bin_end;
   P.p1d_scale = static_cast<float>(rebin * params->dr / bins->n_fft);
   P.cumz = ctx->d_cumz;
   P.tw = ctx->d_tw[tw_slot(bins->n_fft)];

@@ -93,6 +93,7 @@ struct StatParams {
   int32_t rebin;
   const int16_t *zbin;
   const int16_t *segzbin;
+  const int32_t *bin_end;  // first pixel J past each z bin (index zbin + 1), as in SkewerParams
   const double *cumz;
   const float2 *tw;
   int32_t j_max;

@@ -260,6 +260,12 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
   const int64_t uend = (g + 1) * nunits / G;
   int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
   const int R = P.rebin;
+  const int wlo0 = t & ~31;  // first team pixel of this warp
+  // R = 1: pixel sums in registers across segments while the warp's pixels
+  // stay in one z bin, flushed at the bin's end (as in k_skewer)
+  PixelSums acc;
+  acc.zero();
+  int zc = -2;
   team_sync<T>(team);
 
   for (; u < uend; ++u) {
@@ -276,11 +282,17 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
       const double fz = floor(((P.cumz[J + R] - P.cumz[J]) / R - P.z_lo) / P.dz);
       return fz < 0.0 ? -1 : (fz >= P.n_z ? P.n_z : static_cast<int>(fz));
     };
-    const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
-    float a0[MK_NSUM], a1[MK_NSUM];
-#pragma unroll
-    for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
     if (R == 1) {
+      const int jb = sk.j_lo + static_cast<int>(k0);
+      const int zs = __ldg(P.zbin + jb);
+      if (zs != zc) {
+        if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
+        acc.zero();
+        zc = zs;
+      }
+      int pend = __ldg(P.bin_end + zc + 1) - jb;  // segment pixel where bin zc ends
+      // warp-uniform: this warp's pixels of the segment all lie before pend
+      const bool one_bin = min(T * 7 + wlo0 + 32, npx) <= pend;
       // streaming case: issue every load of the thread's 8 pixels before any use
       float dv[8], ev[8], fv[8];
       float4 tb[8];
@@ -302,16 +314,33 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
       for (int q = 0; q < 8; ++q) {
         const int p = t + T * q;
         float f = 0.f;
-        if (p < npx) {
-          f = P.pixtab ? fgpa(tb[q], dv[q], ev[q]) : fv[q];
-          const int zb = (zf == zl) ? zf : __ldg(P.zbin + sk.j_lo + k0 + p);
-          if (zb == zf) add_pixel(a0, f, dv[q], ev[q]);
-          else if (zb == zf + 1) add_pixel(a1, f, dv[q], ev[q]);
-          else if (zb >= 0 && zb < P.n_z) add_pixel_slow(W, zb, f, dv[q], ev[q]);
+        if (p < npx) f = P.pixtab ? fgpa(tb[q], dv[q], ev[q]) : fv[q];
+        const float2 x = make_float2(dv[q], ev[q]);
+        if (one_bin) {
+          if (p < npx) acc.add(f, x);
+        } else {
+          // this warp's pixels at q: T q + wlo0 + lane; flush while they pass pend
+          const int hi = min(T * q + wlo0 + 32, npx);
+          bool todo = p < npx;
+          while (hi > pend) {
+            if (todo && p < pend) {
+              acc.add(f, x);
+              todo = false;
+            }
+            flush_bin_sums(W, P.n_z, zc, acc, lane);
+            acc.zero();
+            ++zc;
+            pend = __ldg(P.bin_end + zc + 1) - jb;
+          }
+          if (todo) acc.add(f, x);
         }
         fb[p] = f;
       }
     } else {
+      const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
+      float a0[MK_NSUM], a1[MK_NSUM];
+#pragma unroll
+      for (int q = 0; q < MK_NSUM; ++q) a0[q] = a1[q] = 0.f;
 #pragma unroll 2
       for (int q = 0; q < 8; ++q) {
         const int p = t + T * q;
@@ -335,8 +364,8 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
         }
         fb[p] = f;
       }
+      flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
     }
-    flush_pixel_sums(W, P.n_z, zf, zl > zf, a0, a1, lane);
     if (npx == N) {
       int zs;
       if (R == 1) {
@@ -358,6 +387,7 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
     }
     team_sync<T>(team);
   }
+  if (R == 1 && zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
   flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
 }
 

@@ -776,12 +776,64 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       if (big < kSurrogateStop) break;
     }
     E.nodes(tb, nd);
-      fill_inactive(nd, S);
+    fill_inactive(nd, S);
+    // refit on the surrogate shifted by `off` (true minus predicted residual at
+    // theta) plus the per-bin linear term B (theta_eff - theta)
+    auto refit = [&](const std::vector<double> &off, const std::vector<double> &theta,
+                     const std::vector<double> &B, std::vector<double> &rs) -> int {
+      int rr_rc = MK_OK;
+      for (int it = 0; it < 12; ++it) {
+        if (it > 0 && (rr_rc = sg.model(S, zc, tb, rs, J))) return rr_rc;
+        double big = 0.0;
+        for (int zb = 0; zb < nz; ++zb) {
+          if (!S.active(zb)) continue;
+          std::vector<double> rr(m), JJ(static_cast<size_t>(m) * 3);
+          for (int i = 0; i < m; ++i) {
+            const size_t row = static_cast<size_t>(zb) * m + i;
+            double lin = 0.0;
+            for (int p = 0; p < 3; ++p) {
+              lin += B[row * 3 + p] * (tb[3 * zb + p] - theta[3 * zb + p]);
+              JJ[i * 3 + p] = J[row * 3 + p] + B[row * 3 + p];
+            }
+            rr[i] = rs[row] + off[row] + lin;
+          }
+          double d[3];
+          lm_step(JJ.data(), rr.data(), m, 1e-2, d);
+          big = std::max(big, apply_step_eff(tb, zb, d));
+        }
+        if (big < kSurrogateStop) break;
+      }
+      return MK_OK;
+    };
+    std::vector<double> B(static_cast<size_t>(nz) * m * 3, 0.0), prev_off, prev_theta;
+    // calibration: a pass over the skewers the surrogate was labelled on gives
+    // its own error at the fit, free of the subset-to-catalogue difference
+    if (rc == MK_OK && norm->calib_skewers > 0 && norm->calib_skewers < n_sk && max_passes > 1) {
+      TuneState Sc = S;
+      Sc.n_sk = norm->calib_skewers;
+      std::vector<double> rt, rs;
+      mk_stats_out sc;
+      const int full_before = report->passes;
+      if ((rc = full_pass(Sc, nd, sc, rt)) == MK_OK) {
+        report->passes = full_before;  // counted apart: a fraction of a full pass
+        report->calib_passes += 1;
+        E.eff(nd, tb);
+        if ((rc = sg.model(S, zc, tb, rs, J)) == MK_OK) {
+          std::vector<double> off(rs.size());
+          for (size_t i = 0; i < rs.size(); ++i) off[i] = rt[i] - rs[i];
+          const std::vector<double> theta = tb;
+          if ((rc = refit(off, theta, B, rs)) == MK_OK) {
+            E.nodes(tb, nd);
+            fill_inactive(nd, S);
+            report->iterations += 1;
+          }
+        }
+      }
+    }
     // verify on full passes; between passes re-solve on the surrogate with the
     // last pass's discrepancy (true minus predicted residual) as an offset,
     // plus a per-bin linear term B (theta_eff - theta_eff,i) for how the
     // discrepancy changes with the parameters (Broyden updates from successive passes)
-    std::vector<double> B(static_cast<size_t>(nz) * m * 3, 0.0), prev_off, prev_theta;
     while (rc == MK_OK && report->passes < max_passes) {
       std::vector<double> rt;
       if ((rc = full_pass(S, nd, st, rt))) break;
@@ -816,27 +868,7 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       }
       prev_off = off;
       prev_theta = theta;
-      for (int it = 0; it < 12 && rc == MK_OK; ++it) {
-        if (it > 0 && (rc = sg.model(S, zc, tb, rs, J))) break;
-        double big = 0.0;
-        for (int zb = 0; zb < nz; ++zb) {
-          if (!S.active(zb)) continue;
-          std::vector<double> rr(m), JJ(static_cast<size_t>(m) * 3);
-          for (int i = 0; i < m; ++i) {
-            const size_t row = static_cast<size_t>(zb) * m + i;
-            double lin = 0.0;
-            for (int p = 0; p < 3; ++p) {
-              lin += B[row * 3 + p] * (tb[3 * zb + p] - theta[3 * zb + p]);
-              JJ[i * 3 + p] = J[row * 3 + p] + B[row * 3 + p];
-            }
-            rr[i] = rs[row] + off[row] + lin;
-          }
-          double d[3];
-          lm_step(JJ.data(), rr.data(), m, 1e-2, d);
-          big = std::max(big, apply_step_eff(tb, zb, d));
-        }
-        if (big < kSurrogateStop) break;
-      }
+      if ((rc = refit(off, theta, B, rs))) break;
       E.nodes(tb, nd);
       fill_inactive(nd, S);
       report->iterations += 1;
