@@ -137,5 +137,16 @@ def test_plain_and_surrogate_tuning_reach_the_target(ctx, stored):
                           method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm, max_passes=40)
     assert rep_s.converged, (rep_s.passes, rep_s.max_abs_dfbar, rep_s.max_rel_p1d, rep_s.max_rel_beta)
     assert 2 * rep_s.passes <= rep_p.passes, (rep_s.passes, rep_p.passes)
+    assert rep_s.calib_passes == 0
     _check_with_oracle(stored, nd_s, target)
+    # calibrated on a labelled subset: the first half of the skewers, relabelled
+    hx2, ht2 = mk.surrogate_labels(ctx, w, r["sk"], n // 2, r["offsets"], r["delta"], r["eta"], n_draws=2000,
+                                   seed=9)
+    norm2, _ = mlp.fit(hx2, ht2, batch=256, epochs=200, lr=2e-3, seed=4)
+    norm2.calib_skewers = n // 2
+    nd_c, rep_c = mk.tune(ctx, w, r["sk"], n, r["offsets"], r["delta"], r["eta"], target, nd0,
+                          method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm2, max_passes=40)
+    assert rep_c.converged and rep_c.calib_passes == 1, (rep_c.passes, rep_c.calib_passes)
+    assert 2 * rep_c.passes <= rep_p.passes, (rep_c.passes, rep_p.passes)
+    _check_with_oracle(stored, nd_c, target)
     mlp.close()
