@@ -248,6 +248,20 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
     t_fit = time.perf_counter() - t0
     if source == "subset":  # labelled on the first n_lab skewers of this catalogue: calibrate on them
         norm.calib_skewers = n_lab
+    # held-out check: fresh draws (another seed) through the trained network
+    vx, vt = mk.surrogate_labels(ctx, ws, rs["sk"], n_lab, rs["offsets"], rs["delta"], rs["eta"],
+                                 n_draws=max(draws // 10, 10), seed=12, slopes=slopes)
+    xm, xs = np.ctypeslib.as_array(norm.x_mean), np.ctypeslib.as_array(norm.x_std)
+    tm, ts = np.ctypeslib.as_array(norm.t_mean), np.ctypeslib.as_array(norm.t_std)
+    xin = torch.from_numpy(((vx - xm) / xs).astype(np.float32)).to(dev)
+    pred = torch.cat([mlp.forward(xin[i:i + 1024].contiguous()) for i in range(0, xin.shape[0], 1024)])
+    pred = pred.double().cpu().numpy() * ts + tm
+    err = pred - vt
+    held = {"samples": int(vx.shape[0]), "draws": max(draws // 10, 10),
+            "mean_flux_rms": float(np.sqrt(np.mean(err[:, 0] ** 2))),
+            "mean_flux_max": float(np.abs(err[:, 0]).max()),
+            "beta_rel_rms": float(np.sqrt(np.mean((err[:, 2] / vt[:, 2]) ** 2))),
+            "ln_p1d_rms": float(np.sqrt(np.mean(err[:, 3:] ** 2)))}
     nd_s, rep_s = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
                           method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm, max_passes=60)
     mlp.close()
@@ -269,7 +283,8 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
                                    "profiles": ("linear in z, slopes up to d ln a/dz, db/dz, dc/dz = "
                                                 f"{slopes[0]}, {slopes[1]}, {slopes[2]}" if slopes else "constant"),
                                    "label_s": t_lab, "fit_s": t_fit, "epochs": epochs,
-                                   "final_loss": float(losses[-1]) if len(losses) else None}}
+                                   "final_loss": float(losses[-1]) if len(losses) else None,
+                                   "held_out": held}}
 
 
 # ---------------------------------------------------------------- box synthesis (Sec. 2.1)
