@@ -646,7 +646,9 @@ typedef struct mk_ps_tune_report {
         target's equal-count k-bin means (the Nyquist mode: the last bin's mean);
      3. n_outer times: one pass gives sigma_g^2 = var(delta_tot + c eta) over
         each bin's pixels (sigma_L^2 + sigma_S^2 + c^2 sigma_eta^2 + 2 c cov),
-        then b = s / sigma_g; then n_inner passes, after each of which every
+        then b = s / sigma_g, and from the second loop on one Newton step in
+        ln a on that pass's F-bar (slope of the Gaussian-field moments, step
+        capped at 0.5) keeps the mean flux; then n_inner passes, after each of which every
         P_S mode m of node i is multiplied by target P1D / measured P1D_dF of
         bin i in the k bin that holds P1D mode round(m bins->n_fft / n_fft)
         (clamped to 1 .. bins->n_fft/2);

@@ -27,8 +27,10 @@ Readings (the library takes the same ones; each is one line here):
   and the covariance), so no separate box moments are needed;
 - a P_s mode m of an N_fft-pixel segment takes the ratio of the k bin that
   holds P1D mode round(m N_p1d R / N_fft), clamped to 1 .. N_p1d / 2;
-- the outer loop only re-derives b from sigma_g (the paper's extra a, b
-  adjustments follow from a correlation-function prediction, out of scope).
+- the outer loop re-derives b from sigma_g and, after the first loop, takes
+  one Newton step in ln a on the pass's mean flux (slope from the Gaussian
+  model), the paper's small adjustments of a that keep F-bar; the bias-driven
+  adjustments of b follow from a correlation-function prediction (out of scope).
 
 Moments use composite Simpson over xi in [-12, 12]; the fit of (a, s) nests
 two bisections, each on a quantity that is monotone in its variable.
@@ -55,6 +57,12 @@ def fgpa_gauss_moments(a, s):
     m1 = float(np.sum(_SIMPSON * _PHI * f))
     m2 = float(np.sum(_SIMPSON * _PHI * f * f))
     return m1, float(np.sqrt(max(m2 - m1 * m1, 0.0)))
+
+
+def dfbar_dlna(a, s):
+    """d F-bar / d ln a of F = exp(-a exp(s xi)): -E[tau F], tau = a exp(s xi)."""
+    tau = a * np.exp(s * _XI)
+    return float(-np.sum(_SIMPSON * _PHI * tau * np.exp(-tau)))
 
 
 def _bisect(fn, lo, hi, n=80):
@@ -156,12 +164,18 @@ def tune_ps(w, d, e, pos, ids, target, p_s0, n_outer=5, n_inner=10, rebin=1, n_t
     p_s = np.array(p_s0, dtype=np.float64).reshape(nz, w["n_fft"] // 2 + 1).copy()
     mb = mode_bins(w["n_fft"], w["n_fft_p1d"], rebin, nk)
     passes = 0
-    for _ in range(n_outer):
-        # step 3
+    for o in range(n_outer):
+        # step 3 (and, after the first outer loop, a Newton step in ln a on this
+        # pass's mean flux: the paper's small adjustments of a that keep F-bar)
         st = _pass(w, d, e, pos, ids, dict(z=z, a=a, b=b, c=c), p_s, rebin, n_threads)
         passes += 1
         for i in np.flatnonzero(active):
             b[i] = s[i] / np.sqrt(sigma_g2(st["sums"][i], c[i]))
+            if o > 0:
+                slope = dfbar_dlna(a[i], s[i])
+                if slope < 0.0:
+                    a[i] *= np.exp(np.clip((st["mean_flux"][i] - target["mean_flux"][i]) / -slope, -0.5, 0.5))
+        a = a[src]
         b = b[src]
         # step 4
         for _ in range(n_inner):

@@ -263,8 +263,20 @@ extern "C" int mk_tune_ps(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, i
       }
       report->sigma_g[i] = std::sqrt(v);
       b[i] = s[i] / std::sqrt(v);
+      if (o > 0) {
+        // keep F-bar (Sec. 2.6 makes small adjustments of a between outer
+        // loops): one Newton step in ln a on this pass's mean flux, with the
+        // slope of the Gaussian-field model at (a, b sigma_g)
+        double f, sg, J[2][2];
+        gauss_moments(a[i], s[i], &f, &sg, J);
+        if (J[0][0] < 0.0) {
+          const double dla = (st.mean_flux[i] - target->mean_flux[i]) / (-J[0][0]);
+          a[i] *= std::exp(std::max(-0.5, std::min(0.5, dla)));
+        }
+      }
     }
     if (rc) break;
+    follow(a);
     follow(b);
     // step 4: ratio iteration of P_S
     for (int it = 0; it < n_inner && rc == MK_OK; ++it) {

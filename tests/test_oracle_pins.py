@@ -903,3 +903,11 @@ def test_qso_draw_expected_count_is_nbar_volume():
     exp_mean = 1e-3 * cell ** 3
     assert abs(r["P"].mean() / exp_mean - 1) < 0.02
     assert abs(r["count"] - r["P"].sum()) < 5 * math.sqrt(r["P"].sum())
+
+
+def test_dfbar_dlna_is_the_slope_of_the_moments():
+    for a, s in ((0.3, 0.8), (1.2, 1.6), (0.05, 2.2)):
+        h = 1e-5
+        fd = (ps_tuning.fgpa_gauss_moments(a * math.exp(h), s)[0]
+              - ps_tuning.fgpa_gauss_moments(a * math.exp(-h), s)[0]) / (2 * h)
+        assert abs(ps_tuning.dfbar_dlna(a, s) - fd) < 1e-8
