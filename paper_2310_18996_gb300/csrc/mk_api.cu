@@ -1368,10 +1368,10 @@ int ctx_pixel_histogram(mk_ctx *ctx, double dr, const mk_skewer *d_sk, int64_t n
 extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, const double *h_pk, int32_t n_pk,
                             double dk, int32_t layout, float *d_work, float *d_spec, float *d_out) {
   if (!ctx) return MK_EINVAL;
+  if (n < 128 || n > 2048 || (n & (n - 1)))
+    return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512, 1024 or 2048");
   int lgn = 0;
   while ((1 << lgn) < n) ++lgn;
-  if (n < 128 || n > 2048 || (1 << lgn) != n)
-    return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512, 1024 or 2048");
   if (!(cell > 0.0) || !(dk > 0.0) || !h_pk || n_pk < 2 || n_pk > (1 << 24))
     return fail(ctx, MK_EINVAL, "bad cell, dk or P(k) table (2 .. 2^24 entries)");
   if (!d_work || !d_out || (reinterpret_cast<uintptr_t>(d_work) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 3) ||
