@@ -357,7 +357,10 @@ int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t
 /* FGPA and rebin (Eq. FGPA): F = exp[-a exp(b (delta + c eta))] per fine
    pixel, then the mean of `rebin` consecutive pixels (incomplete tail
    dropped).  Writes d_offsets_out (n_sk + 1 entries, floor(n_i/rebin) per
-   skewer) and d_flux (capacity_out entries). */
+   skewer) and d_flux (capacity_out entries).  Asynchronous; mk_sync reports
+   MK_ERANGE for output past capacity_out or for a record whose pixels run
+   past the redshift tables of params->dr (records made with another pixel
+   length); such records are skipped. */
 int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
             const float *d_delta, const float *d_eta, const mk_fgpa_nodes *nodes,
             int32_t rebin, float *d_flux, int64_t *d_offsets_out, int64_t capacity_out);
@@ -683,8 +686,12 @@ int mk_save_skewers(mk_ctx *ctx, const char *path, const mk_skewer *d_sk, int64_
    cap_sk records (and cap_sk + 1 offsets) and cap_px pixels of delta_tot and
    eta.  *n_sk and *total_px receive the file's sizes; with NULL buffers (or
    too small capacities, then MK_ERANGE) nothing else is read, which makes
-   the call a size query.  Synchronous.  MK_EINVAL for a missing or
-   malformed file. */
+   the call a size query.  Synchronous.  MK_EINVAL for a missing, truncated
+   or malformed file; malformed includes records and offsets that do not
+   tile [0, total): record i must start where record i - 1 ends (offset 0
+   for the first), have n >= 0 and j_lo >= 0, and offsets[i] must equal its
+   start, offsets[n_sk] the total (checked on the host while staging, before
+   anything is copied to the device). */
 int mk_load_skewers(mk_ctx *ctx, const char *path, mk_skewer *d_sk, int64_t cap_sk, int64_t *d_offsets,
                     float *d_delta, float *d_eta, int64_t cap_px, int64_t *n_sk, int64_t *total_px);
 

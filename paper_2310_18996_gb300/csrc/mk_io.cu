@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "../../include/mockskewer.h"
 #include "mk_host.h"
@@ -35,13 +36,18 @@ bool dump(FILE *f, const void *d, size_t bytes, void *h, cudaStream_t st) {
   return true;
 }
 
-// file -> device in pieces of kStage bytes
-bool fill(FILE *f, void *d, size_t bytes, void *h, cudaStream_t st) {
-  char *dst = static_cast<char *>(d);
-  for (size_t o = 0; o < bytes; o += kStage) {
-    const size_t b = std::min(kStage, bytes - o);
+// file -> device in pieces of whole elements, at most kStage bytes each;
+// check(first element, pointer, count) sees each piece in host memory before
+// it is copied and may refuse it
+template <class T, class Check>
+bool fill(FILE *f, T *d, int64_t count, void *h, cudaStream_t st, Check check) {
+  const int64_t per = static_cast<int64_t>(kStage / sizeof(T));
+  for (int64_t o = 0; o < count; o += per) {
+    const int64_t c = std::min(per, count - o);
+    const size_t b = sizeof(T) * static_cast<size_t>(c);
     if (std::fread(h, 1, b, f) != b) return false;
-    if (cudaMemcpyAsync(dst + o, h, b, cudaMemcpyHostToDevice, st) != cudaSuccess) return false;
+    if (!check(o, static_cast<const T *>(h), c)) return false;
+    if (cudaMemcpyAsync(d + o, h, b, cudaMemcpyHostToDevice, st) != cudaSuccess) return false;
     if (cudaStreamSynchronize(st) != cudaSuccess) return false;
   }
   return true;
@@ -108,10 +114,31 @@ extern "C" int mk_load_skewers(mk_ctx *ctx, const char *path, mk_skewer *d_sk, i
     std::fclose(f);
     return iofail(ctx, MK_ENOMEM, "mk_load_skewers: staging buffer");
   }
-  bool ok = fill(f, d_sk, sizeof(mk_skewer) * static_cast<size_t>(ns), s.h, st);
-  ok = ok && fill(f, d_offsets, sizeof(int64_t) * static_cast<size_t>(ns + 1), s.h, st);
-  ok = ok && fill(f, d_delta, sizeof(float) * static_cast<size_t>(tp), s.h, st);
-  ok = ok && fill(f, d_eta, sizeof(float) * static_cast<size_t>(tp), s.h, st);
+  // The records and offsets drive every later index into the pixel arrays,
+  // so they must describe consecutive pixel ranges that tile [0, total):
+  // record i starts where record i - 1 ends, and offsets[i] is its start.
+  std::vector<int64_t> start(static_cast<size_t>(ns) + 1);
+  int64_t run = 0;
+  const auto records = [&](int64_t i0, const mk_skewer *r, int64_t c) {
+    for (int64_t k = 0; k < c; ++k) {
+      if (r[k].offset != run || r[k].n < 0 || r[k].j_lo < 0 || r[k].n > tp - run) return false;
+      start[static_cast<size_t>(i0 + k)] = run;
+      run += r[k].n;
+    }
+    return true;
+  };
+  const auto offsets = [&](int64_t i0, const int64_t *v, int64_t c) {
+    for (int64_t k = 0; k < c; ++k)
+      if (v[k] != start[static_cast<size_t>(i0 + k)]) return false;
+    return true;
+  };
+  const auto any = [](int64_t, const float *, int64_t) { return true; };
+  const bool rec_ok = fill(f, d_sk, ns, s.h, st, records) && run == tp;
+  start[static_cast<size_t>(ns)] = tp;
+  const bool off_ok = rec_ok && fill(f, d_offsets, ns + 1, s.h, st, offsets);
+  const bool px_ok = off_ok && fill(f, d_delta, tp, s.h, st, any) && fill(f, d_eta, tp, s.h, st, any);
   std::fclose(f);
-  return ok ? MK_OK : iofail(ctx, MK_EINVAL, "mk_load_skewers: truncated file");
+  if (!rec_ok || !off_ok)
+    return iofail(ctx, MK_EINVAL, "mk_load_skewers: truncated file, or records and offsets that do not tile the pixels");
+  return px_ok ? MK_OK : iofail(ctx, MK_EINVAL, "mk_load_skewers: truncated file");
 }

@@ -328,6 +328,12 @@ __global__ void __launch_bounds__(256) k_flux(FluxParams P) {
       if (lane == 0) raise_error(P.err, ERR_CAPACITY);
       continue;
     }
+    // records made for another pixel length (read back from a file) may run
+    // past the pixel tables
+    if (sk.j_lo < 0 || sk.j_lo + nout * P.rebin > P.j_max) {
+      if (lane == 0) raise_error(P.err, ERR_RANGE);
+      continue;
+    }
     for (int64_t k = lane; k < nout; k += 32) {
       float s = 0.f;
       for (int r = 0; r < P.rebin; ++r) {

@@ -322,8 +322,35 @@ def test_saved_pre_production_round_trip(ctx, tiny, tmp_path):
     bad.write_bytes(b"NOTASKEW" + bytes(16))
     with pytest.raises(mk.MkError):
         ctx.load_skewers(str(bad))
+    # records or offsets that do not tile the pixel arrays are refused
+    raw = f.read_bytes()
+    for at in (24 + mk.SKEWER_BYTES, 24 + n * mk.SKEWER_BYTES + 8):  # record 1's offset; offsets[1]
+        v = int.from_bytes(raw[at:at + 8], "little") + 1
+        bad.write_bytes(raw[:at] + v.to_bytes(8, "little") + raw[at + 8:])
+        with pytest.raises(mk.MkError) as ei:
+            ctx.load_skewers(str(bad))
+        assert ei.value.code == mk.MK_EINVAL
     c = ctx.flux_stats(w2, q["sk"], n, q["offsets"], q["delta"], q["eta"])
     np.testing.assert_array_equal(c["sums"], a["sums"])
+
+
+def test_flux_refuses_records_past_the_pixel_tables(ctx, tiny):
+    # records whose pixels lie beyond the pixel tables (made for another pixel
+    # length) set the range error instead of reading past the tables
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    ctx.sync()
+    sk = r["sk"].clone()
+    sk[: n * mk.SKEWER_BYTES].view(torch.int32).view(n, mk.SKEWER_BYTES // 4)[:, 3] = 1 << 30  # j_lo
+    ctx.flux(w, sk, n, r["delta"], r["eta"])
+    with pytest.raises(mk.MkError) as ei:
+        ctx.sync()
+    assert ei.value.code == mk.MK_ERANGE
+    f, _ = ctx.flux(w, r["sk"], n, r["delta"], r["eta"])
+    ctx.sync()
+    assert torch.isfinite(f[: r["total"]]).all()
 
 
 def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
