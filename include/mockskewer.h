@@ -369,7 +369,10 @@ int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, 
    mk_flux).  d_delta / d_eta are the fine-resolution fields (averaged over
    the same pixels) or NULL (their sums are then zero).  The z of an output
    pixel is the mean z of its fine pixels; a P1D segment's z is the mean over
-   the segment.  Synchronous: fills *h_out. */
+   the segment.  Synchronous: fills *h_out.  MK_ERANGE (statistics not
+   written) when a record's pixels run past the redshift tables of
+   params->dr, as in mk_flux; mk_flux_stats and the tuning passes check the
+   same. */
 int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
              const int64_t *d_offsets_out, const float *d_flux, int32_t rebin,
              const float *d_delta, const float *d_eta, const mk_stat_bins *bins,

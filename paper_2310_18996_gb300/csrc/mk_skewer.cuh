@@ -274,6 +274,12 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
     const mk_skewer sk = P.sk[i];
     const int64_t o = P.off_out[i];
     const int64_t nout = P.off_out[i + 1] - o;
+    // records made for another pixel length may run past the pixel tables
+    // (team-uniform: the whole team skips the segment)
+    if (sk.j_lo < 0 || sk.j_lo + nout * R > P.j_max) {
+      if (t == 0) raise_error(P.err, ERR_RANGE);
+      continue;
+    }
     const int64_t k0 = static_cast<int64_t>(s) * N;
     const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
     auto zbin_of = [&](int64_t kk) -> int {

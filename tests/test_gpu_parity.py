@@ -348,9 +348,14 @@ def test_flux_refuses_records_past_the_pixel_tables(ctx, tiny):
     with pytest.raises(mk.MkError) as ei:
         ctx.sync()
     assert ei.value.code == mk.MK_ERANGE
+    with pytest.raises(mk.MkError) as ei:  # the tuning pass (k_stats) checks them too
+        ctx.flux_stats(w, sk, n, r["offsets"], r["delta"], r["eta"])
+    assert ei.value.code == mk.MK_ERANGE
     f, _ = ctx.flux(w, r["sk"], n, r["delta"], r["eta"])
     ctx.sync()
     assert torch.isfinite(f[: r["total"]]).all()
+    st = ctx.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+    assert st["sums"][:, 0].sum() > 0
 
 
 def test_small_scale_field_is_whitened_philox_modes(ctx, tiny):
