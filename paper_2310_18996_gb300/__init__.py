@@ -128,6 +128,8 @@ MLP_NPARAM = 38179
 TUNE_PLAIN, TUNE_SURROGATE = 0, 1
 SKEWER_BYTES = 72  # sizeof(mk_skewer)
 QSO_DTYPE = np.dtype([("pos", np.float64, 3), ("id", np.uint64)])  # mk_qso, 32 bytes
+SKEWER_DTYPE = np.dtype([("offset", np.int64), ("n", np.int32), ("j_lo", np.int32), ("p0", np.int64, 3),
+                         ("step", np.int64, 3), ("id", np.uint64)])  # mk_skewer
 
 _lib = None
 _lock = threading.Lock()
@@ -543,10 +545,7 @@ class Context:
 
 def skewer_records(sk, n):
     """Host view of mk_skewer records (offset, n, j_lo, p0[3], step[3], id)."""
-    dt = np.dtype([("offset", np.int64), ("n", np.int32), ("j_lo", np.int32),
-                   ("p0", np.int64, 3), ("step", np.int64, 3), ("id", np.uint64)])
-    assert dt.itemsize == SKEWER_BYTES
-    return sk[: n * SKEWER_BYTES].cpu().numpy().view(dt)
+    return sk[: n * SKEWER_BYTES].cpu().numpy().view(SKEWER_DTYPE)
 
 
 # ------------------------------------------------------------------ surrogate and tuning

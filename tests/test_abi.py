@@ -113,3 +113,46 @@ def test_xi_and_lognormal_pk_match_oracle():
     for B in (-1.0, -2.0 / xmin):
         with pytest.raises(mk.MkError):
             mk.lognormal_pk(pk, dk, B)
+
+
+# every ctypes structure of the binding and the C struct it mirrors
+CTYPES_STRUCTS = {
+    "mk_cosmo": mk.Cosmo, "mk_box_desc": mk.BoxDesc, "mk_skewer_params": mk.SkewerParams,
+    "mk_fgpa_nodes": mk.FgpaNodes, "mk_stat_bins": mk.StatBins, "mk_stats_out": mk.StatsOut,
+    "mk_surrogate_space": mk.SurrogateSpace, "mk_surrogate_norm": mk.SurrogateNorm,
+    "mk_tune_target": mk.TuneTarget, "mk_tune_report": mk.TuneReport,
+    "mk_qso_draw_params": mk.QsoDrawParams, "mk_ps_tune_report": mk.PsTuneReport,
+}
+NUMPY_RECORDS = {"mk_qso": mk.QSO_DTYPE, "mk_skewer": mk.SKEWER_DTYPE}
+
+
+def test_binding_layouts_match_the_c_compiler(tmp_path):
+    # sizeof and offsetof of every mirrored field, as gcc lays out the header
+    # (plain C99), against the ctypes structures and numpy record dtypes
+    import shutil
+    import subprocess
+
+    if not shutil.which("gcc"):
+        pytest.skip("no gcc")
+    body, expect = [], []
+    for cname, cls in CTYPES_STRUCTS.items():
+        body.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(C.sizeof(cls))
+        for f in cls._fields_:
+            body.append(f'  printf("%zu\\n", offsetof({cname}, {f[0]}));')
+            expect.append(getattr(cls, f[0]).offset)
+    for cname, dt in NUMPY_RECORDS.items():
+        body.append(f'  printf("%zu\\n", sizeof({cname}));')
+        expect.append(dt.itemsize)
+        for name in dt.names:
+            body.append(f'  printf("%zu\\n", offsetof({cname}, {name}));')
+            expect.append(dt.fields[name][1])
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"mockskewer.h\"\nint main(void) {\n"
+                   + "\n".join(body) + "\n  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got == expect
+    assert mk.SKEWER_DTYPE.itemsize == mk.SKEWER_BYTES
