@@ -366,7 +366,9 @@ int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, 
             int32_t rebin, float *d_flux, int64_t *d_offsets_out, int64_t capacity_out);
 
 /* Statistics of ragged flux at output resolution `rebin` (d_offsets_out from
-   mk_flux).  d_delta / d_eta are the fine-resolution fields (averaged over
+   mk_flux): per z bin the mean flux and sigma_F, P1D of delta_F over n_fft
+   segments (Sec. 2.6, Sec. 4.1) and the pixel regression of F on (delta,
+   eta) for b_F and beta_F (layout in mk_stats_out).  d_delta / d_eta are the fine-resolution fields (averaged over
    the same pixels) or NULL (their sums are then zero).  The z of an output
    pixel is the mean z of its fine pixels; a P1D segment's z is the mean over
    the segment.  Synchronous: fills *h_out.  MK_ERANGE (statistics not
@@ -382,14 +384,18 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
    Sec. 3, re-run for new FGPA parameters, Sec. 2.6): the FGPA of d_delta /
    d_eta with `nodes` (Eq. FGPA) and the statistics of that flux at full
    resolution (as mk_stats with rebin 1), without storing the flux.
-   d_offsets are the skewer offsets (n_sk + 1).  Synchronous. */
+   d_offsets are the skewer offsets (n_sk + 1).  Synchronous.  MK_EINVAL for
+   bad parameters, nodes, bins or pointers; MK_ERANGE as mk_stats. */
 int mk_flux_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
                   const int64_t *d_offsets, const float *d_delta, const float *d_eta,
                   const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, mk_stats_out *h_out);
 
 /* The whole path in one pass (rebin 1): geometry, gather, growth, delta_S,
-   FGPA and statistics in one persistent kernel, skipping the stores that
-   `flags` does not ask for.  P1D segments coincide with delta_S segments
+   FGPA and statistics (steps 1-7 above: Sec. 2.3, Sec. 2.4 and Eq. FGPA,
+   Sec. 2.6) in one persistent kernel, skipping the stores that `flags` does
+   not ask for.  MK_EINVAL for bad parameters, flags or pointers; MK_ERANGE
+   (at the synchronisation) for stores past capacity_px or pixels outside
+   the redshift tables.  P1D segments coincide with delta_S segments
    (bins->n_fft must equal params->n_fft).  d_delta_out / d_eta_out /
    d_flux_out may be NULL when not stored; they may also point to page-locked
    host memory (cudaHostAlloc; unified addressing makes it device-accessible),
