@@ -671,7 +671,10 @@ typedef struct mk_ps_tune_report {
    d_sk (n_qso records), d_offsets (n_qso + 1): caller-owned device scratch.
    h_p_s: bins->n_z tables of n_fft/2 + 1 values (host, FP64), in: the start,
    out: the tuned tables.  out: bins->n_z nodes (z, ln a, b, c).
-   n_outer >= 1, n_inner >= 0, passes <= MK_PS_TUNE_MAX_PASSES.  Synchronous. */
+   n_outer >= 1, n_inner >= 0, passes <= MK_PS_TUNE_MAX_PASSES.  Synchronous.
+   MK_EINVAL for arguments outside these ranges, a target that the (a, b
+   sigma_g) fit cannot reach, or a tuned bin without pixels or P1D segments;
+   the errors of mk_run otherwise. */
 int mk_tune_ps(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
                const mk_skewer_params *params, const mk_stat_bins *bins, const mk_tune_target *target,
                int32_t n_outer, int32_t n_inner, mk_skewer *d_sk, int64_t *d_offsets, double *h_p_s,
