@@ -493,7 +493,11 @@ int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer
    b0, W1 [128x128], b1, W2 [128x128], b2, W3 [35x128], b3, each W row-major
    [out][in].  The kernels use the weights in BF16, rounded from an FP32 master
    copy that Adam updates; biases, activations and all accumulation are FP32.
-   Device arrays are row-major: x n x 4, outputs n x 35. */
+   Device arrays are row-major: x n x 4, outputs n x 35.
+   Errors: MK_EINVAL for NULL pointers or sizes outside the ranges stated
+   below (max_batch in [1, 2^24]; n in [1, max_batch] for mk_mlp_loss_grad;
+   1 <= batch <= max_batch and lr > 0 for mk_mlp_train and mk_surrogate_fit),
+   MK_ENOMEM when the MLP's own device scratch cannot be allocated. */
 #define MK_MLP_NPARAM 38179
 #define MK_MLP_IN 4
 #define MK_MLP_OUT 35
