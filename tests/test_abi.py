@@ -156,3 +156,54 @@ def test_binding_layouts_match_the_c_compiler(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
     assert got == expect
     assert mk.SKEWER_DTYPE.itemsize == mk.SKEWER_BYTES
+
+
+def declared_signatures():
+    # {name: [parameter declarations]} of every function in the header
+    src = open(os.path.join(ROOT, "include", "mockskewer.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(mk_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", src):
+        params = [p.strip() for p in m.group(2).split(",")]
+        out[m.group(1)] = [] if params == ["void"] else params
+    return out
+
+
+def c_kind(decl):
+    # argument class of a C parameter declaration
+    if "*" in decl or "[" in decl:
+        return "ptr"
+    for t, k in (("uint64_t", "u64"), ("int64_t", "i64"), ("uint32_t", "u32"), ("int32_t", "i32"),
+                 ("double", "f64"), ("float", "f32"), ("int", "i32")):
+        if re.search(rf"\b{t}\b", decl):
+            return k
+    raise AssertionError(decl)
+
+
+def ctypes_kind(t):
+    if t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer):
+        return "ptr"
+    for ct, k in ((C.c_uint64, "u64"), (C.c_int64, "i64"), (C.c_uint32, "u32"), (C.c_int32, "i32"),
+                  (C.c_double, "f64"), (C.c_float, "f32")):
+        if C.sizeof(t) == C.sizeof(ct) and t._type_ == ct._type_:
+            return k
+    raise AssertionError(t)
+
+
+def test_binding_signatures_match_the_header():
+    # every declared function is bound with as many arguments as the header
+    # gives it, each of the same class (pointer, integer width, float)
+    L = mk.lib()
+    sigs = declared_signatures()
+    assert sorted(sigs) == declared_symbols()
+    for name, params in sigs.items():
+        got = [ctypes_kind(t) for t in getattr(L, name).argtypes]
+        assert got == [c_kind(p) for p in params], name
+    # and the result: int status codes, void, or the error string
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "mockskewer.h")).read(), flags=re.S)
+    ret = {m.group(2): m.group(1).strip()
+           for m in re.finditer(r"^([A-Za-z_][A-Za-z_0-9 ]*?\s*\**)\s*(mk_[a-z_0-9]+)\s*\(", src, re.M)}
+    assert sorted(ret) == sorted(sigs)
+    want = {"int": C.c_int, "void": None, "const char *": C.c_char_p}
+    for name, r in ret.items():
+        assert getattr(L, name).restype is want[r], name
