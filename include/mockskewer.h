@@ -380,6 +380,18 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
              const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
              mk_stats_out *h_out);
 
+/* Statistics of a catalogue split into parts, e.g. one part per GPU of the
+   paper's parallel runs (Sec. 3 splits the sky into slices processed apart):
+   the raw sums (sums, p1d_sum, n_seg) of parts[0 .. n_parts-1], each the
+   result of mk_stats / mk_flux_stats / mk_run over one part with the same
+   bins, are added in index order, and the derived statistics (mean_flux,
+   sigma_f, p1d_f, p1d_df, b_f, beta_f) are computed once from the totals, as
+   the statistics calls do for a whole catalogue.  Only the raw sums of the
+   parts are read: a caller that has already added them (an all-reduce over
+   ranks) passes one part.  Host arithmetic; no context, no device.  *out may
+   be one of the parts.  MK_EINVAL for NULL pointers, n_parts < 1 or bad bins. */
+int mk_stats_merge(const mk_stats_out *parts, int32_t n_parts, const mk_stat_bins *bins, mk_stats_out *out);
+
 /* Tuning pass over stored pre-FGPA skewers (the paper's post-production,
    Sec. 3, re-run for new FGPA parameters, Sec. 2.6): the FGPA of d_delta /
    d_eta with `nodes` (Eq. FGPA) and the statistics of that flux at full
@@ -465,12 +477,17 @@ int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box
    Limits and conditions:
    - n_sk <= MK_STATIC_MAX_SKEWERS, otherwise MK_EINVAL and nothing runs.
    - The context must already hold the tables the call reads: the pixel tables
-     of params->dr and the FFT twiddles of bins->n_fft.  Any earlier
-     mk_make_skewers, mk_flux, mk_stats or mk_run on this context with the same
-     dr and n_fft builds them; otherwise MK_EINVAL.
-   - The first call on each device performs a set-up step (it looks up the
-     device address of the array); make that first call before any stream
-     capture.
+     of params->dr, the FFT twiddles of bins->n_fft and the z-bin tables.  An
+     earlier allocating statistics call on this context with the same dr and
+     bins->n_fft builds all three: mk_stats, mk_flux_stats, or mk_run /
+     mk_run_host with MK_STATS (whose n_fft is bins->n_fft).  Without them the
+     call returns MK_EINVAL and runs nothing.  For other bins of the same n_fft
+     it rebuilds the z-bin tables with kernels into the memory that exists.
+   - The first call on each context performs a set-up step (it looks up the
+     device address of the array, with the context's device current); make
+     that first call before any stream capture.
+   - With mk_set_timing on, mk_last_kernel_ms reports the statistics kernel of
+     this call.
    - All calls share the one array, which keeps the contents of the last call.
      Calls that overlap on the GPU (other threads, streams or contexts of the
      same process) race on it and corrupt each other's results.

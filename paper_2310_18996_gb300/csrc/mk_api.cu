@@ -7,7 +7,6 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -193,6 +192,7 @@ struct mk_ctx {
   uint64_t generation = 0;  // bumped whenever a table or workspace moves
   bool timing = false;
   bool timed = false;
+  unsigned char *static_scratch = nullptr;  // device address of mk_stats_static's array
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // mk_run_host: device copies of the catalogue and records, two staging
   // buffers, slice boundaries, copy streams and their events
@@ -1207,6 +1207,27 @@ int mk_last_kernel_ms(mk_ctx *ctx, double *ms) {
 
 }  // extern "C"
 
+// ====================================================================== merge of per-part statistics
+extern "C" int mk_stats_merge(const mk_stats_out *parts, int32_t n_parts, const mk_stat_bins *bins,
+                              mk_stats_out *out) {
+  if (!parts || !out || !bins || n_parts < 1) return MK_EINVAL;
+  if (bins->n_z < 1 || bins->n_z > MK_MAX_ZBINS || bins->n_k < 1 || bins->n_k > MK_MAX_KBINS ||
+      !skewer_fft(bins->n_fft) || (bins->n_fft / 2) % bins->n_k)
+    return MK_EINVAL;
+  mk_stats_out tot;
+  std::memset(&tot, 0, sizeof(tot));
+  for (int32_t p = 0; p < n_parts; ++p)
+    for (int zb = 0; zb < bins->n_z; ++zb) {
+      for (int i = 0; i < MK_NSUM; ++i) tot.sums[zb][i] += parts[p].sums[zb][i];
+      for (int k = 0; k < bins->n_k; ++k) tot.p1d_sum[zb][k] += parts[p].p1d_sum[zb][k];
+      tot.n_seg[zb] += parts[p].n_seg[zb];
+    }
+  const double per_bin = static_cast<double>(bins->n_fft / 2) / bins->n_k;
+  for (int zb = 0; zb < bins->n_z; ++zb) finalize_bin(&tot, zb, bins->n_k, per_bin);
+  std::memcpy(out, &tot, sizeof(tot));
+  return MK_OK;
+}
+
 // ====================================================================== statistics without allocation
 // Scratch of mk_stats_static: one fixed array in the library's device memory
 // instead of the context's growable workspace.  Layout, in 256-byte aligned
@@ -1216,26 +1237,21 @@ static __device__ __align__(256) unsigned char g_stats_scratch[MK_STATIC_SCRATCH
 
 namespace {
 
-constexpr int kMaxStaticDevices = 64;
-void *g_stats_scratch_ptr[kMaxStaticDevices] = {};
-std::mutex g_stats_scratch_mu;
-
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
-// Device address of the array on the context's device (looked up once per
-// device, with that device current).
+// Device address of the array on the context's device, looked up by the
+// first call on each context with its device current.  A context lives in
+// one CUDA context of its device, so the address cannot go stale under it
+// (a cudaDeviceReset ends the contexts created before it).
 int stats_scratch_address(mk_ctx *ctx, unsigned char **out) {
-  if (ctx->device < 0 || ctx->device >= kMaxStaticDevices)
-    return fail(ctx, MK_EINVAL, "device %d out of range for the static scratch", ctx->device);
-  std::lock_guard<std::mutex> lock(g_stats_scratch_mu);
-  if (!g_stats_scratch_ptr[ctx->device]) {
+  if (!ctx->static_scratch) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_stats_scratch);
     if (e != cudaSuccess || !p)
       return fail(ctx, MK_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
-    g_stats_scratch_ptr[ctx->device] = p;
+    ctx->static_scratch = static_cast<unsigned char *>(p);
   }
-  *out = static_cast<unsigned char *>(g_stats_scratch_ptr[ctx->device]);
+  *out = ctx->static_scratch;
   return MK_OK;
 }
 
@@ -1262,7 +1278,14 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
   if (!ctx->d_tw[tw_slot(bins->n_fft)])
     return fail(ctx, MK_EINVAL, "no FFT twiddles for n_fft = %d on this context: run an allocating call first",
                 bins->n_fft);
-  if ((rc = ensure_zbin(ctx, bins))) return rc;  // kernel into the existing table
+  // the z-bin tables: the per-pixel ones come with the pixel tables, the
+  // bin-end table with the first allocating statistics call; rebuilding them
+  // for other bins only runs kernels into that memory
+  if (!ctx->d_bin_end)
+    return fail(ctx, MK_EINVAL,
+                "no z-bin tables on this context: run an allocating statistics call (mk_stats, mk_flux_stats, "
+                "or mk_run with MK_STATS) first");
+  if ((rc = ensure_zbin(ctx, bins))) return rc;
   unsigned char *base = nullptr;
   if ((rc = stats_scratch_address(ctx, &base))) return rc;
 
@@ -1310,7 +1333,9 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
   P.dr = params->dr;
   P.partials = d_part;
   P.err = ctx->d_err;
+  if ((rc = time_begin(ctx))) return rc;
   CK(launch_stats(P, bins->n_fft, grid, threads, ctx->stream));
+  if ((rc = time_end(ctx))) return rc;
   CK(launch_finalize(d_part, grid, bins->n_z, bins->n_k, bins->n_fft, d_out, ctx->stream));
   CK(cudaMemcpyAsync(ctx->h_stats, d_out, sizeof(mk_stats_out), cudaMemcpyDeviceToHost, ctx->stream));
   if ((rc = read_error_word(ctx))) return rc;  // synchronises

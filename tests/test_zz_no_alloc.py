@@ -53,8 +53,54 @@ def test_static_scratch_statistics_match_allocating_call():
         assert rc == mk.MK_OK, mk.lib().mk_last_error(ctx.h).decode()
         assert_stats_close(st, ref)
         np.testing.assert_allclose(st["sums"], ref["sums"], rtol=1e-4, atol=1e-9)
+    # with timing on, the kernel time reported is this call's
+    ctx.set_timing(True)
+    rc, _ = _static_stats(ctx, w, r["sk"], n, off, f, r["delta"], r["eta"])
+    assert rc == mk.MK_OK
+    assert ctx.last_kernel_ms() > 0.0
+    ctx.set_timing(False)
     # beyond the stated maximum the call refuses before running anything
     rc, _ = _static_stats(ctx, w, r["sk"], mk.STATIC_MAX_SKEWERS + 1, off, f, r["delta"], r["eta"])
     assert rc == mk.MK_EINVAL
     assert b"MK_STATIC_MAX_SKEWERS" in mk.lib().mk_last_error(ctx.h)
+    ctx.close()
+
+
+def test_static_scratch_needs_tables_and_allocates_nothing():
+    """A context that has not yet run an allocating statistics call lacks the
+    z-bin tables: the call refuses (MK_EINVAL) instead of allocating them.  A
+    fresh context lacks every table.  Once an allocating statistics call has
+    run, the call leaves the device's free memory unchanged."""
+    w = si.workload("tiny")
+    d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"], backend="numpy")
+    n = 200
+    pos, ids = si.catalogue(w, n_q=n)
+    ctx = mk.Context(0)
+    # nothing has run: no pixel tables
+    dummy = torch.zeros(16, dtype=torch.float32, device="cuda")
+    off0 = torch.zeros(2, dtype=torch.int64, device="cuda")
+    rc, _ = _static_stats(ctx, w, dummy, 0, off0, dummy, None, None)
+    assert rc == mk.MK_EINVAL and b"pixel tables" in mk.lib().mk_last_error(ctx.h)
+    # synthesis and flux only (no statistics call): no z-bin tables
+    box = ctx.load_box(w, torch.from_numpy(d).cuda(), torch.from_numpy(e).cuda())
+    r = ctx.make_skewers(box, mk.catalogue_tensor(pos, ids), n, w)
+    f, off = ctx.flux(w, r["sk"], n, r["delta"], r["eta"])
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    rc, _ = _static_stats(ctx, w, r["sk"], n, off, f, r["delta"], r["eta"])
+    assert rc == mk.MK_EINVAL and b"z-bin tables" in mk.lib().mk_last_error(ctx.h)
+    assert torch.cuda.mem_get_info()[0] == free0
+    # after one allocating statistics call the static call allocates nothing
+    # (the first static call may make the driver load the library's device
+    # image, which holds the fixed array: free memory is compared after it)
+    ref = ctx.stats(w, r["sk"], n, off, f, delta=r["delta"], eta=r["eta"])
+    rc, _ = _static_stats(ctx, w, r["sk"], n, off, f, r["delta"], r["eta"])
+    assert rc == mk.MK_OK, mk.lib().mk_last_error(ctx.h).decode()
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        rc, st = _static_stats(ctx, w, r["sk"], n, off, f, r["delta"], r["eta"])
+        assert rc == mk.MK_OK, mk.lib().mk_last_error(ctx.h).decode()
+        assert_stats_close(st, ref)
+    assert torch.cuda.mem_get_info()[0] == free1
     ctx.close()
