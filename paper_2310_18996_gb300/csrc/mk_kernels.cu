@@ -366,31 +366,8 @@ __global__ void k_finalize(const double *__restrict__ partials, int nparts, int 
   for (int zb = threadIdx.x; zb < n_z; zb += blockDim.x) {
     for (int i = 0; i < MK_NSUM; ++i) out->sums[zb][i] = tot[L.sums(zb, i)];
     for (int k = 0; k < n_k; ++k) out->p1d_sum[zb][k] = tot[L.p1d(zb, k)];
-    const double ns = tot[L.nseg(zb)];
-    out->n_seg[zb] = ns;
-    const double *s = &tot[L.sums(zb, 0)];
-    const double n = s[0];
-    if (n <= 0.0) continue;
-    const double fbar = s[1] / n;
-    out->mean_flux[zb] = fbar;
-    const double varf = s[2] / n - fbar * fbar;
-    out->sigma_f[zb] = varf > 0.0 ? sqrt(varf) : 0.0;
-    const double md = s[3] / n, me = s[4] / n;
-    const double cdd = s[5] / n - md * md, cee = s[6] / n - me * me, cde = s[7] / n - md * me;
-    const double vfd = s[8] / n - fbar * md, vfe = s[9] / n - fbar * me;
-    const double det = cdd * cee - cde * cde;
-    if (det != 0.0) {
-      const double kd = (cee * vfd - cde * vfe) / det;
-      const double ke = (cdd * vfe - cde * vfd) / det;
-      out->b_f[zb] = kd / fbar;
-      out->beta_f[zb] = kd != 0.0 ? ke / kd : 0.0;
-    }
-    if (ns > 0.0) {
-      for (int k = 0; k < n_k; ++k) {
-        out->p1d_f[zb][k] = tot[L.p1d(zb, k)] / (ns * per_bin);
-        out->p1d_df[zb][k] = out->p1d_f[zb][k] / (fbar * fbar);
-      }
-    }
+    out->n_seg[zb] = tot[L.nseg(zb)];
+    finalize_bin(out, zb, n_k, per_bin);
   }
 }
 
@@ -489,57 +466,34 @@ cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t 
 }
 
 // ------------------------------------------------------------------ dispatch by FFT length
-#define MK_DECL(NN)                                                                                      \
-  size_t skewer_smem_bytes_##NN(int threads, int n_z, int n_k, bool stats);                              \
-  int skewer_blocks_per_sm_##NN(int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats); \
-  cudaError_t launch_skewer_##NN(const SkewerParams &P, int variant, int minb, int grid, int threads,      \
-                                 cudaStream_t st);                                                      \
-  int stats_blocks_per_sm_##NN(int threads, int n_z, int n_k);                                          \
-  cudaError_t launch_stats_##NN(const StatParams &P, int grid, int threads, cudaStream_t st);
-MK_DECL(256)
-MK_DECL(512)
-MK_DECL(1024)
-MK_DECL(2048)
-#undef MK_DECL
-
-#define MK_SWITCH(EXPR, FAIL)     \
-  switch (n_fft) {                \
-    case 256: return EXPR(256);   \
-    case 512: return EXPR(512);   \
-    case 1024: return EXPR(1024); \
-    case 2048: return EXPR(2048); \
-  }                               \
+#define MK_SWITCH(EXPR, FAIL)                  \
+  switch (n_fft) {                             \
+    case 256: return SkewerUnit<256>::EXPR;    \
+    case 512: return SkewerUnit<512>::EXPR;    \
+    case 1024: return SkewerUnit<1024>::EXPR;  \
+    case 2048: return SkewerUnit<2048>::EXPR;  \
+  }                                            \
   return FAIL;
 
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats) {
-#define E(NN) skewer_smem_bytes_##NN(threads, n_z, n_k, stats)
-  MK_SWITCH(E, 0)
-#undef E
+  MK_SWITCH(smem_bytes(threads, n_z, n_k, stats), 0)
 }
 
 int skewer_blocks_per_sm(int n_fft, int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
-#define E(NN) skewer_blocks_per_sm_##NN(variant, lgn, minb, threads, n_z, n_k, stats)
-  MK_SWITCH(E, 1)
-#undef E
+  MK_SWITCH(blocks_per_sm(variant, lgn, minb, threads, n_z, n_k, stats), 1)
 }
 
 cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int variant, int minb, int grid, int threads,
                           cudaStream_t st) {
-#define E(NN) launch_skewer_##NN(P, variant, minb, grid, threads, st)
-  MK_SWITCH(E, cudaErrorInvalidValue)
-#undef E
+  MK_SWITCH(launch(P, variant, minb, grid, threads, st), cudaErrorInvalidValue)
 }
 
 int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k) {
-#define E(NN) stats_blocks_per_sm_##NN(threads, n_z, n_k)
-  MK_SWITCH(E, 1)
-#undef E
+  MK_SWITCH(stats_blocks_per_sm(threads, n_z, n_k), 1)
 }
 
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st) {
-#define E(NN) launch_stats_##NN(P, grid, threads, st)
-  MK_SWITCH(E, cudaErrorInvalidValue)
-#undef E
+  MK_SWITCH(launch_stats(P, grid, threads, st), cudaErrorInvalidValue)
 }
 #undef MK_SWITCH
 

@@ -40,6 +40,21 @@ size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
 // (2, 3 or 4)
 cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int variant, int minb, int grid, int threads,
                           cudaStream_t st);
+// The fused skewer kernel and the statistics kernel for FFT length N: launch
+// and occupancy helpers, defined in mk_skewer_unit.cuh and instantiated once
+// per length (256, 512, 1024, 2048) in mk_skewer_<N>.cu.
+template <int N>
+struct SkewerUnit {
+  static size_t smem_bytes(int threads, int n_z, int n_k, bool stats);
+  static int blocks_per_sm(int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
+  static cudaError_t launch(const SkewerParams &P, int variant, int minb, int grid, int threads, cudaStream_t st);
+  static int stats_blocks_per_sm(int threads, int n_z, int n_k);
+  static cudaError_t launch_stats(const StatParams &P, int grid, int threads, cudaStream_t st);
+};
+extern template struct SkewerUnit<256>;
+extern template struct SkewerUnit<512>;
+extern template struct SkewerUnit<1024>;
+extern template struct SkewerUnit<2048>;
 cudaError_t launch_flux(const FluxParams &P, int sms, cudaStream_t st);
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st);
 // One pass of the box synthesis: batched line FFTs of an n^3 complex box
