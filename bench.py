@@ -119,6 +119,31 @@ def profiled_traffic(total_px):
     return rec["dram_bytes_per_pixel"] * total_px
 
 
+def workload_config(w, n_q):
+    """The `config` of both arms' JSON lines (the same workload)."""
+    return {"workload": f"{w['n']}^3 box (delta+eta FP32 pairs, periodic ghost layer), {n_q} quasars "
+                        "z 2.04-4.0, 200-1500 px skewers, N_fft 256",
+            "skewers_per_gpu": n_q, "l2": "inputs larger than L2 (8.6 GB box)",
+            "outputs": "flux + FP64 statistics (mean flux, sigma_F, P1D, b_F, beta_F in 12 z bins)"}
+
+
+def profiled_kernel_record():
+    """The fused kernel's committed ncu record (instruction counts per pixel,
+    issue activity), or None when the kernel sources changed since it was taken."""
+    import hashlib
+
+    p = os.path.join(ROOT, "profiles", "k_skewer_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        rec = json.load(f)
+    h = hashlib.sha256()
+    for src in rec["sources"]:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            h.update(f.read())
+    return rec if h.hexdigest() == rec["sha256"] else None
+
+
 def algorithmic_bytes(pos, npix, w):
     """Bytes a launch must move: each skewer's distinct trilinear voxels (8 B,
     a (delta, eta) pair), its flux (4 B/pixel), catalogue and record traffic."""
@@ -202,10 +227,10 @@ def run_reference(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "1024^3 box, 1M quasars z 1.8-4.0, 200-1500 px skewers",
-                   "sample": "oracle per step on ~6 s of skewers in catalogue order"},
+        "config": workload_config(w, len(ids)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{pxs} pixels over {args.steps} steps"},
+                         "sample": f"each step ~6 s of skewers in catalogue order (fields, flux, statistics); "
+                                   f"{pxs} pixels over {args.steps} steps"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -412,7 +437,9 @@ def ps_tuning_leg(ctx, mk, box, qso, n_q, w, n_outer, n_inner):
             "outer": n_outer, "inner": n_inner, "passes": rep.passes, "gpu_ms": rep.gpu_ms,
             "ms_per_pass": rep.gpu_ms / max(rep.passes, 1), "wall_ms": rep.wall_ms,
             "max_abs_dfbar": rep.max_abs_dfbar, "max_rel_p1d": rep.max_rel_p1d, "max_rel_beta": rep.max_rel_beta,
-            "max_rel_p1d_per_pass": hist}
+            "max_rel_p1d_first_pass": hist[0] if hist else None,
+            "max_rel_p1d_end_of_outer_loop": [hist[min(len(hist) - 1, (k + 1) * (n_inner + 1) - 1)]
+                                              for k in range(n_outer)] if hist else None}
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -685,57 +712,55 @@ def run_gb300(args, rank, world, local_rank):
     pst = None
     if rank == 0 and world == 1 and not args.no_ps_tuning:
         pst = ps_tuning_leg(ctx, mk, box, qso, n_q, w, args.ps_outer, args.ps_inner)
+    merged = None
+    if dist:  # catalogue-wide statistics: one all-gather of the raw sums, then mk_stats_merge
+        mst = mk.merge_stats_across_ranks(st, w, dist, device=dev)
+        merged = {"ranks": world, "pixels": int(mst["sums"][:, 0].sum()), "p1d_segments": int(mst["n_seg"].sum()),
+                  "mean_flux": [round(float(x), 6) for x in mst["mean_flux"]],
+                  "how": "all-gather of each rank's raw sums (sums, p1d_sum, n_seg), mk_stats_merge in rank order"}
     cpu = None
     if want_cpu:
-        rate, px, n, dt = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds, os.cpu_count() or 1)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count() or 1, "kind": "oracle",
-               "sample": f"{n} skewers ({px} pixels) of the same catalogue, {dt:.1f} s, "
-                         f"fields+flux+stats"}
+        cores = os.cpu_count() or 1
+        rate, px, n, dt = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds, cores)
+        rate1, px1, n1, dt1 = oracle_rate(w, dh, eh, pos, ids, args.cpu_seconds / 3.0, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} skewers ({px} pixels) of the same catalogue, {dt:.1f} s, fields+flux+stats",
+               "one_core": {"value": rate1, "cores": 1, "sample": f"{n1} skewers ({px1} pixels), {dt1:.1f} s"}}
     if rank == 0:
+        prof = profiled_kernel_record()
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(total), "peak_kind": peak_kind,
+                "kernel": f"k_skewer<256,padded> {threads} threads/CTA, occupancy "
+                          f"target {occ}{' (autotuned)' if tuned else ''}", "kernel_ms": kms,
+                "algorithmic_bytes": alg, "algorithmic_bytes_per_pixel": alg / total}
+        if prof:  # the compute side, from the committed ncu record of the same kernel source
+            roof.update({k: prof[k] for k in ("warp_inst_per_px", "issue_active", "fp32_inst_per_px") if k in prof})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{w['n']}^3 box (delta+eta FP32 pairs, periodic ghost layer), {n_q} quasars "
-                                   "z 2.04-4.0, 200-1500 px skewers, N_fft 256, fused persistent launch",
-                       "pixels_per_step_per_gpu": int(total), "skewers_per_gpu": n_q,
-                       "l2": "inputs larger than L2 (8.6 GB box)",
-                       "outputs": "flux stored + FP64 statistics"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(total), "peak_kind": peak_kind,
-                         "kernel": f"k_skewer<256,padded> {threads} threads/CTA, occupancy "
-                                   f"target {occ}{' (autotuned)' if tuned else ''}", "kernel_ms": kms,
-                         "algorithmic_bytes": alg},
+            "config": workload_config(w, n_q),
+            "pixels_per_step_per_gpu": int(total),
+            "roofline": roof,
             "e2e": {"value": world * total / (e2e_ms / 1000.0), "unit": UNIT,
                     "h2d_bytes_per_step": int(host_cat.numel()),
                     "d2h_bytes_per_step": int(total * 4 + mk.C.sizeof(mk.StatsOut)),
                     "ms_per_step": e2e_ms,
-                    "method": f"mk_run_host: catalogue H2D from pinned memory, geometry, {args.e2e_chunks} "
-                              "slices computed while the previous slice's flux is copied to pinned host "
-                              "memory on 2 copy streams, statistics D2H",
+                    "method": f"mk_run_host: catalogue H2D from pinned memory, {args.e2e_chunks} slices, each "
+                              "slice's flux copied to pinned host memory while the next is computed",
                     "sequential_ms_per_step": e2e_copy_ms},
             "gpu_launches": 6 * args.steps,  # per step: geometry, 3 scan passes, fused kernel, finalize
-            "launch": "CUDA graph per step (mk_run MK_GRAPH), launch shape autotuned at warm-up",
+            "launch": "CUDA graph per step (mk_run MK_GRAPH), fused persistent kernel, launch shape autotuned",
             "clocks": clk,
         }
         if cpu:
             line["cpu_baseline"] = cpu
-        if tune:
-            line["tuning"] = tune
-        if pst:
-            line["ps_tuning"] = pst
-        if boxs:
-            line["box_synth"] = boxs
-        if split:
-            line["split_path"] = split
-        if batched:
-            line["batched_launches"] = batched
-        if uni:
-            line["uniform_lengths"] = uni
-        if gauss:
-            line["gauss7"] = gauss
-        if tens:
-            line["eta_tensor"] = tens
+        # the other legs; the tuning A/B last, so that the end of the line carries it
+        for key, val in (("gauss7", gauss), ("eta_tensor", tens), ("split_path", split),
+                         ("batched_launches", batched), ("uniform_lengths", uni), ("box_synth", boxs),
+                         ("ps_tuning", pst), ("stats_merge", merged), ("tuning", tune)):
+            if val:
+                line[key] = val
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -28,7 +28,8 @@ STORE_FIELDS, STORE_FLUX, STATS, AUTOTUNE, GRAPH = 1, 2, 4, 8, 16
 
 EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync", "mk_load_box",
            "mk_free_box", "mk_pack_box", "mk_pack_box_padded", "mk_pack_box_halo", "mk_pack_box_tensor", "mk_make_skewers", "mk_run_host", "mk_flux", "mk_stats", "mk_run",
-           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_launch_config", "mk_flux_stats",
+           "mk_set_timing", "mk_last_kernel_ms", "mk_stats_static", "mk_stats_merge", "mk_launch_config",
+           "mk_flux_stats",
            "mk_mlp_create", "mk_mlp_destroy", "mk_mlp_set_params", "mk_mlp_get_params", "mk_mlp_forward",
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
            "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box", "mk_xi_of_pk",
@@ -170,6 +171,7 @@ def lib():
                                      u32, vp, vp, vp, vp, vp, i64, P(StatsOut)]),
                 "mk_stats_static": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, i32, vp, vp,
                                               P(StatBins), P(StatsOut)]),
+                "mk_stats_merge": (C.c_int, [P(StatsOut), i32, P(StatBins), P(StatsOut)]),
                 "mk_launch_config": (C.c_int, [vp, i32, i32, i32, u32, P(i32), P(i32)]),
                 "mk_flux_stats": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, vp, P(FgpaNodes),
                                             P(StatBins), P(StatsOut)]),
@@ -250,6 +252,52 @@ def stats_dict(st, n_z, n_k):
                 sigma_f=a(st.sigma_f)[:n_z].copy(), p1d_f=a(st.p1d_f)[:n_z, :n_k].copy(),
                 p1d_df=a(st.p1d_df)[:n_z, :n_k].copy(), b_f=a(st.b_f)[:n_z].copy(),
                 beta_f=a(st.beta_f)[:n_z].copy())
+
+
+RAW_KEYS = ("sums", "p1d_sum", "n_seg")
+
+
+def raw_sums_vector(st):
+    """The raw sums of a statistics dict (sums, p1d_sum, n_seg of its n_z bins)
+    as one flat FP64 array: what ranks exchange before mk_stats_merge."""
+    return np.concatenate([np.asarray(st[k], dtype=np.float64).ravel() for k in RAW_KEYS])
+
+
+def raw_sums_from_vector(v, n_z, n_k):
+    v = np.asarray(v, dtype=np.float64)
+    a, b = n_z * NSUM, n_z * NSUM + n_z * n_k
+    return {"sums": v[:a].reshape(n_z, NSUM), "p1d_sum": v[a:b].reshape(n_z, n_k), "n_seg": v[b:b + n_z]}
+
+
+def stats_merge(parts, w):
+    """mk_stats_merge: statistics of the union of catalogue parts from each
+    part's raw sums (dicts with sums, p1d_sum, n_seg), added in list order."""
+    b = stat_bins(w)
+    arr = (StatsOut * len(parts))()
+    for i, prt in enumerate(parts):
+        a = np.ctypeslib.as_array
+        a(arr[i].sums)[:b.n_z] = prt["sums"]
+        a(arr[i].p1d_sum)[:b.n_z, :b.n_k] = prt["p1d_sum"]
+        a(arr[i].n_seg)[:b.n_z] = prt["n_seg"]
+    out = StatsOut()
+    rc = lib().mk_stats_merge(arr, len(parts), C.byref(b), C.byref(out))
+    if rc != MK_OK:
+        raise MkError(rc, "mk_stats_merge: bad arguments")
+    return stats_dict(out, b.n_z, b.n_k)
+
+
+def merge_stats_across_ranks(st, w, dist, device="cpu"):
+    """Catalogue-wide statistics of a run split over the ranks of a process
+    group: one all-gather of every rank's raw sums (n_z (11 + n_k) FP64
+    values), then mk_stats_merge over the parts in rank order, so that every
+    rank gets the same result whatever the collective's summation order."""
+    import torch
+
+    b = stat_bins(w)
+    v = torch.from_numpy(raw_sums_vector(st)).to(device)
+    parts = [torch.empty_like(v) for _ in range(dist.get_world_size())]
+    dist.all_gather(parts, v)
+    return stats_merge([raw_sums_from_vector(p.cpu().numpy(), b.n_z, b.n_k) for p in parts], w)
 
 
 def catalogue_tensor(pos, ids, device="cuda"):

@@ -46,6 +46,38 @@ struct StatLayout {
   __host__ __device__ int size() const { return n_z * (MK_NSUM + n_k + 1); }
 };
 
+// Derived statistics of z bin zb from its raw sums (out->sums[zb],
+// p1d_sum[zb], n_seg[zb]), which the caller has filled: F-bar, sigma_F,
+// P1D_F per mode, P1D_F / F-bar^2, and b_F, beta_F from the least-squares
+// fit F ~ F0 + k_d delta + k_e eta (Sec. 2.6, Sec. 4.1).  per_bin: modes per k
+// bin, (n_fft / 2) / n_k.  The finalize kernel and the host-side merge of
+// per-rank sums (mk_stats_merge) both use it.
+__host__ __device__ inline void finalize_bin(mk_stats_out *out, int zb, int n_k, double per_bin) {
+  const double *s = out->sums[zb];
+  const double n = s[0];
+  if (n <= 0.0) return;
+  const double fbar = s[1] / n;
+  out->mean_flux[zb] = fbar;
+  const double varf = s[2] / n - fbar * fbar;
+  out->sigma_f[zb] = varf > 0.0 ? sqrt(varf) : 0.0;
+  const double md = s[3] / n, me = s[4] / n;
+  const double cdd = s[5] / n - md * md, cee = s[6] / n - me * me, cde = s[7] / n - md * me;
+  const double vfd = s[8] / n - fbar * md, vfe = s[9] / n - fbar * me;
+  const double det = cdd * cee - cde * cde;
+  if (det != 0.0) {
+    const double kd = (cee * vfd - cde * vfe) / det;
+    const double ke = (cdd * vfe - cde * vfd) / det;
+    out->b_f[zb] = kd / fbar;
+    out->beta_f[zb] = kd != 0.0 ? ke / kd : 0.0;
+  }
+  const double ns = out->n_seg[zb];
+  if (ns > 0.0) {
+    for (int k = 0; k < n_k; ++k) {
+      out->p1d_f[zb][k] = out->p1d_sum[zb][k] / (ns * per_bin);
+      out->p1d_df[zb][k] = out->p1d_f[zb][k] / (fbar * fbar);
+    }
+  }
+}
 
 // Everything the fused / split skewer kernels read.
 struct SkewerParams {
