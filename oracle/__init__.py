@@ -120,8 +120,10 @@ def lib():
                 "orc_stats_accumulate": (C.c_int, [P(Cfg), P(Bins), i32, P(i32), P(i64),
                                                    P(i64), i64, P(d), P(d), P(d), P(Stats)]),
                 "orc_stats_finalize": (None, [P(Bins), P(Stats)]),
-                "orc_mlp_forward": (None, [P(d), P(d), i64, P(d)]),
-                "orc_mlp_loss_grad": (d, [P(d), P(d), P(d), i64, P(d)]),
+                "orc_mlp_forward": (None, [P(d), P(d), i64, P(d), C.c_int]),
+                "orc_mlp_loss_grad": (d, [P(d), P(d), P(d), i64, P(d), C.c_int]),
+                "orc_bf16": (d, [d]),
+                "orc_adam_step": (None, [P(d), P(d), P(d), P(d), i64, i64, d, d, d, d]),
                 "orc_gelu": (d, [d]),
             }
             for name, (res, args) in sig.items():
@@ -378,24 +380,40 @@ def gelu(x):
     return lib().orc_gelu(float(x))
 
 
-def mlp_forward(params, x):
-    """FP64 forward of the 4-128-128-128-35 GELU MLP; x (n, 4) -> (n, 35)."""
+def mlp_forward(params, x, bf16=False):
+    """FP64 forward of the 4-128-128-128-35 GELU MLP; x (n, 4) -> (n, 35).
+    bf16: hidden activations rounded to BF16 (the tensor-core operands)."""
     p = np.ascontiguousarray(params, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
     y = np.zeros((x.shape[0], 35))
-    lib().orc_mlp_forward(_p(p, C.c_double), _p(x, C.c_double), x.shape[0], _p(y, C.c_double))
+    lib().orc_mlp_forward(_p(p, C.c_double), _p(x, C.c_double), x.shape[0], _p(y, C.c_double), int(bf16))
     return y
 
 
-def mlp_loss_grad(params, x, t):
-    """Mean squared error and its gradient (FP64) at params."""
+def mlp_loss_grad(params, x, t, bf16=False):
+    """Mean squared error and its gradient (FP64) at params; bf16: the
+    forward's and backward's tensor-core operands rounded to BF16."""
     p = np.ascontiguousarray(params, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
     t = np.ascontiguousarray(t, dtype=np.float64).reshape(-1, 35)
     g = np.zeros(MLP_NPARAM)
     loss = lib().orc_mlp_loss_grad(_p(p, C.c_double), _p(x, C.c_double), _p(t, C.c_double),
-                                   x.shape[0], _p(g, C.c_double))
+                                   x.shape[0], _p(g, C.c_double), int(bf16))
     return loss, g
+
+
+def bf16(x):
+    """x rounded to FP32, then to BF16 (nearest even), as a float."""
+    return lib().orc_bf16(float(x))
+
+
+def adam_step(p, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015, Algorithm 1) in place on FP64 arrays."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    lib().orc_adam_step(_p(p, C.c_double), _p(m, C.c_double), _p(v, C.c_double), _p(g, C.c_double),
+                        p.size, int(t), lr, b1, b2, eps)
 
 
 def qso_draw(q, boxes, stride=1, capacity=None):

@@ -743,9 +743,24 @@ static void mlp_offsets(int64_t w_off[4], int64_t b_off[4]) {
   }
 }
 
-/* forward of one sample; z[l], h[l] hold layer l's pre- and post-activation */
+/* The value as a tensor-core operand in BF16: rounded to FP32 (nearest even),
+   then to the 8 significant bits of BF16 (nearest even on the dropped 16
+   bits of the FP32 word).  Finite inputs only. */
+double orc_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, sizeof u);
+  const uint32_t lsb = (u >> 16) & 1u;
+  u = (u + 0x7FFFu + lsb) & 0xFFFF0000u;
+  memcpy(&f, &u, sizeof f);
+  return (double)f;
+}
+
+/* forward of one sample; z[l], h[l] hold layer l's pre- and post-activation.
+   bf16: the hidden activations are stored as BF16 operands (h[l] rounded);
+   the output layer stays unrounded. */
 static void mlp_sample(const double *p, const double *x, double z[4][128], double h[4][128],
-                       double *y) {
+                       double *y, int bf16) {
   int64_t wo[4], bo[4];
   mlp_offsets(wo, bo);
   const double *in = x;
@@ -756,19 +771,38 @@ static void mlp_sample(const double *p, const double *x, double z[4][128], doubl
       for (int k = 0; k < ni; ++k) s += p[wo[l] + (int64_t)j * ni + k] * in[k];
       z[l][j] = s;
       h[l][j] = (l < 3) ? orc_gelu(s) : s;
+      if (bf16 && l < 3) h[l][j] = orc_bf16(h[l][j]);
     }
     in = h[l];
   }
   for (int j = 0; j < mlp_dims[4]; ++j) y[j] = h[3][j];
 }
 
-void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y) {
+void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y, int bf16) {
   double z[4][128], h[4][128];
-  for (int64_t s = 0; s < n; ++s) mlp_sample(params, x + 4 * s, z, h, y + 35 * s);
+  for (int64_t s = 0; s < n; ++s) mlp_sample(params, x + 4 * s, z, h, y + 35 * s, bf16);
 }
 
+/* Adam (Kingma & Ba 2015, Algorithm 1), step t >= 1 on n parameters:
+   m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+   m_hat = m / (1 - b1^t), v_hat = v / (1 - b2^t),
+   p <- p - lr m_hat / (sqrt(v_hat) + eps). */
+void orc_adam_step(double *p, double *m, double *v, const double *g, int64_t n, int64_t t, double lr,
+                   double b1, double b2, double eps) {
+  const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    const double mh = m[i] / c1, vh = v[i] / c2;
+    p[i] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* bf16: the backward operands of the tensor-core products are BF16 too: the
+   output gradient dy and every dz = dh * GELU'(z) are rounded before they
+   enter the weight gradients, the bias gradients and the next dh. */
 double orc_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n,
-                         double *grad) {
+                         double *grad, int bf16) {
   int64_t wo[4], bo[4];
   mlp_offsets(wo, bo);
   if (grad) memset(grad, 0, sizeof(double) * ORC_MLP_NPARAM);
@@ -777,11 +811,12 @@ double orc_mlp_loss_grad(const double *params, const double *x, const double *t,
   const double scale = 1.0 / ((double)n * 35.0);
   for (int64_t s = 0; s < n; ++s) {
     const double *xs = x + 4 * s;
-    mlp_sample(params, xs, z, h, y);
+    mlp_sample(params, xs, z, h, y, bf16);
     for (int j = 0; j < 35; ++j) {
       double r = y[j] - t[35 * s + j];
       loss += r * r * scale;
       dz[j] = 2.0 * r * scale; /* d loss / d y (output layer is linear) */
+      if (bf16) dz[j] = orc_bf16(dz[j]);
     }
     if (!grad) continue;
     for (int l = 3; l >= 0; --l) {
@@ -797,7 +832,10 @@ double orc_mlp_loss_grad(const double *params, const double *x, const double *t,
         for (int j = 0; j < no; ++j) a += params[wo[l] + (int64_t)j * ni + k] * dz[j];
         dh[k] = a;
       }
-      for (int k = 0; k < ni; ++k) dz[k] = dh[k] * gelu_deriv(z[l - 1][k]);
+      for (int k = 0; k < ni; ++k) {
+        dz[k] = dh[k] * gelu_deriv(z[l - 1][k]);
+        if (bf16) dz[k] = orc_bf16(dz[k]);
+      }
     }
   }
   return loss;

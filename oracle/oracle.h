@@ -165,11 +165,19 @@ void orc_stats_finalize(const orc_bins *bins, orc_stats *st);
    Parameters in order W0 [128x4], b0, W1 [128x128], b1, W2 [128x128], b2,
    W3 [35x128], b3, each W row-major [out][in]; 38179 values. */
 #define ORC_MLP_NPARAM 38179
-void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y);
-/* mean squared error over n samples and 35 outputs, and its gradient */
+/* bf16 != 0: the hidden activations are rounded to BF16 (the operands the
+   tensor cores take); bf16 = 0: plain FP64 throughout. */
+void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y, int bf16);
+/* mean squared error over n samples and 35 outputs, and its gradient; with
+   bf16 the backward operands dy and dz are rounded to BF16 as well */
 double orc_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n,
-                         double *grad);
+                         double *grad, int bf16);
 double orc_gelu(double x);
+/* x rounded to FP32, then to BF16 (round to nearest even at both steps) */
+double orc_bf16(double x);
+/* one Adam step (Kingma & Ba 2015, Algorithm 1) at step t >= 1 */
+void orc_adam_step(double *p, double *m, double *v, const double *g, int64_t n, int64_t t, double lr,
+                   double b1, double b2, double eps);
 
 #ifdef __cplusplus
 }

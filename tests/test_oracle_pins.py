@@ -716,6 +716,113 @@ def test_mlp_gradient_matches_central_differences():
         assert g[i] == pytest.approx(fd, rel=2e-6, abs=1e-9), i
 
 
+def _bf16_torch(x):
+    """x -> FP32 -> BF16 through torch's conversions (round to nearest even)."""
+    import torch
+    return torch.tensor(float(x), dtype=torch.float64).to(torch.float32).to(torch.bfloat16).double().item()
+
+
+def test_bf16_rounding_is_nearest_even_via_fp32():
+    # ties between BF16 neighbours go to the even one; above a tie rounds up
+    assert oracle.bf16(1.0 + 2.0 ** -8) == 1.0
+    assert oracle.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert oracle.bf16(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7
+    assert oracle.bf16(-(1.0 + 3 * 2.0 ** -9)) == -(1.0 + 2.0 ** -7)
+    rng = np.random.default_rng(31)
+    for x in np.concatenate([rng.standard_normal(200) * 10.0 ** rng.integers(-6, 6, 200), [0.0, 2.0 ** -130]]):
+        assert oracle.bf16(x) == _bf16_torch(x), x
+
+
+def test_adam_first_steps_in_closed_form():
+    # step 1: m_hat = g, v_hat = g^2, so p moves by -lr g / (|g| + eps); eps sits
+    # outside the root, so a gradient of 1e-9 moves p by lr / 11, not ~lr 1e-5
+    lr, eps = 1e-3, 1e-8
+    g1 = np.array([0.5, -2.0, 1e-9, 0.0, 3e-4])
+    p = np.array([0.1, -0.2, 0.3, 0.4, 0.0])
+    m, v = np.zeros(5), np.zeros(5)
+    p0 = p.copy()
+    oracle.adam_step(p, m, v, g1, 1, lr)
+    np.testing.assert_allclose(p, p0 - lr * g1 / (np.abs(g1) + eps), rtol=1e-15, atol=1e-18)
+    assert p[2] == pytest.approx(0.3 - lr / 11.0, rel=1e-12) and p[3] == 0.4
+    # step 2 with another gradient: m = 0.09 g1 + 0.1 g2, v = 0.000999 g1^2 +
+    # 0.001 g2^2, bias corrections 1 - 0.9^2 = 0.19 and 1 - 0.999^2 = 0.001999
+    g2 = np.array([-0.25, 1.0, 2e-9, 1.0, 3e-4])
+    p1 = p.copy()
+    oracle.adam_step(p, m, v, g2, 2, lr)
+    mh = (0.09 * g1 + 0.1 * g2) / 0.19
+    vh = (0.000999 * g1 ** 2 + 0.001 * g2 ** 2) / 0.001999
+    np.testing.assert_allclose(p, p1 - lr * mh / (np.sqrt(vh) + eps), rtol=1e-14, atol=1e-18)
+    np.testing.assert_allclose(m, 0.09 * g1 + 0.1 * g2, rtol=1e-15)
+    np.testing.assert_allclose(v, 0.000999 * g1 ** 2 + 0.001 * g2 ** 2, rtol=1e-15)
+
+
+def _single_path_params(w1, w2, w3, v):
+    dims = oracle.MLP_DIMS
+    p = np.zeros(oracle.MLP_NPARAM)
+    offs, o = [], 0
+    for l in range(4):
+        offs.append(o)
+        o += dims[l + 1] * dims[l] + dims[l + 1]
+    p[offs[0]] = w1
+    p[offs[1]] = w2
+    p[offs[2]] = w3
+    p[offs[3]:offs[3] + 35 * 128].reshape(35, 128)[:, 0] = v
+    return p, offs
+
+
+def test_mlp_bf16_operands_single_path_closed_form():
+    """The BF16-operand forward and backward on one live path x0 -> h0 -> h1
+    -> h2 -> y, with the roundings written out: hidden activations, the
+    output gradient and each dz are BF16; the output y is not rounded."""
+    from scipy.special import ndtr
+    G = lambda z: z * ndtr(z)
+    dG = lambda z: ndtr(z) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
+    q = _bf16_torch
+    w1, w2, w3 = 0.7, -1.3, 0.9
+    v = np.linspace(-1, 1, 35)
+    p, offs = _single_path_params(w1, w2, w3, v)
+    x0 = 1.37
+    x = np.array([[x0, 5.0, -2.0, 1.0]])
+    t = np.random.default_rng(5).standard_normal((1, 35))
+    z0 = w1 * x0
+    h0 = q(G(z0))
+    z1 = w2 * h0
+    h1 = q(G(z1))
+    z2 = w3 * h1
+    h2 = q(G(z2))
+    y = v * h2
+    np.testing.assert_allclose(oracle.mlp_forward(p, x, bf16=True)[0], y, rtol=1e-14, atol=1e-16)
+    loss, g = oracle.mlp_loss_grad(p, x, t, bf16=True)
+    assert loss == pytest.approx(np.mean((y - t[0]) ** 2), rel=1e-13)
+    dy = np.array([q(2.0 * (y[j] - t[0, j]) / 35.0) for j in range(35)])
+    dz2 = q(np.dot(v, dy) * dG(z2))
+    dz1 = q(w3 * dz2 * dG(z1))
+    dz0 = q(w2 * dz1 * dG(z0))
+    w3_block = g[offs[3]:offs[3] + 35 * 128].reshape(35, 128)
+    np.testing.assert_allclose(w3_block[:, 0], dy * h2, rtol=1e-14, atol=1e-18)
+    np.testing.assert_allclose(g[offs[3] + 35 * 128:offs[3] + 35 * 128 + 35], dy, rtol=1e-14, atol=1e-18)
+    assert g[offs[2]] == pytest.approx(dz2 * h1, rel=1e-13)                 # W2[0][0]
+    assert g[offs[2] + 128 * 128] == pytest.approx(dz2, rel=1e-13)          # b2[0]
+    assert g[offs[1]] == pytest.approx(dz1 * h0, rel=1e-13)                 # W1[0][0]
+    assert g[offs[0]] == pytest.approx(dz0 * x0, rel=1e-13)                 # W0[0][0]
+    assert g[offs[0] + 1] == pytest.approx(dz0 * 5.0, rel=1e-13)            # W0[0][1]
+    assert g[offs[0] + 128 * 4] == pytest.approx(dz0, rel=1e-13)            # b0[0]
+    # every other hidden unit is dead: G(0) = 0, so no other weight moves
+    # except the first-layer row of unit 0 and the output layer's column 0
+    mask = np.ones(oracle.MLP_NPARAM, bool)
+    mask[offs[0]:offs[0] + 4] = False
+    mask[offs[0] + 512] = False
+    mask[offs[1]] = mask[offs[1] + 128 * 128] = False
+    mask[offs[2]] = mask[offs[2] + 128 * 128] = False
+    mask[offs[3]:] = False
+    # dead units still pass gradient to their biases through GELU'(0) = 1/2
+    # times a zero dh, so their gradients are exactly zero
+    assert np.all(g[mask] == 0.0)
+    # without BF16 operands the same path gives the unrounded closed form
+    loss64, g64 = oracle.mlp_loss_grad(p, x, t)
+    assert g64[offs[2]] != g[offs[2]]
+
+
 # ------------------------------------------------------------ Gaussian box synthesis (Sec. 2.1)
 from oracle import box_synth  # noqa: E402
 
