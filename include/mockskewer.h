@@ -728,6 +728,19 @@ int mk_save_skewers(mk_ctx *ctx, const char *path, const mk_skewer *d_sk, int64_
 int mk_load_skewers(mk_ctx *ctx, const char *path, mk_skewer *d_sk, int64_t cap_sk, int64_t *d_offsets,
                     float *d_delta, float *d_eta, int64_t cap_px, int64_t *n_sk, int64_t *total_px);
 
+/* ---------------------------------------------------------------- launch cap */
+
+/* At most max_ctas CTAs for the persistent skewer and statistics kernels
+   (mk_make_skewers, mk_run, mk_run_host, mk_stats, mk_flux_stats and the
+   tuning passes); 0 (the default) lifts the cap, and the grids then hold as
+   many CTAs as the SMs keep resident.  Results do not depend on the grid
+   except through the order of floating-point additions.  With a small cap
+   each team of threads runs many consecutive segments, keeping its pixel
+   sums in registers across segments and z bins; it also leaves SMs free for
+   other work on the GPU.  Takes effect at the next call.  MK_EINVAL for
+   max_ctas < 0. */
+int mk_set_grid_cap(mk_ctx *ctx, int32_t max_ctas);
+
 /* ---------------------------------------------------------------- timing */
 
 /* When on (non-zero), the library records CUDA events on the context's

@@ -193,6 +193,7 @@ struct mk_ctx {
   bool timing = false;
   bool timed = false;
   unsigned char *static_scratch = nullptr;  // device address of mk_stats_static's array
+  int grid_cap = 0;  // at most this many CTAs for the persistent kernels (0: no cap)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // mk_run_host: device copies of the catalogue and records, two staging
   // buffers, slice boundaries, copy streams and their events
@@ -453,9 +454,12 @@ int time_end(mk_ctx *ctx) {
 }
 
 // persistent grids: as many resident CTAs as the SMs hold
+// (at most ctx->grid_cap CTAs when a cap is set)
+int capped(mk_ctx *ctx, int grid) { return ctx->grid_cap > 0 && grid > ctx->grid_cap ? ctx->grid_cap : grid; }
+
 int skewer_grid(mk_ctx *ctx, int n_fft, int variant, int lgn, LaunchCfg cfg, const mk_stat_bins *bins) {
-  return ctx->sms * skewer_blocks_per_sm(n_fft, variant, lgn, cfg.minb, cfg.threads,
-                                         bins ? bins->n_z : 0, bins ? bins->n_k : 0, bins != nullptr);
+  return capped(ctx, ctx->sms * skewer_blocks_per_sm(n_fft, variant, lgn, cfg.minb, cfg.threads,
+                                                     bins ? bins->n_z : 0, bins ? bins->n_k : 0, bins != nullptr));
 }
 
 // default launch: 256-thread CTAs with the register budget of three per SM
@@ -484,7 +488,7 @@ uint64_t tune_key(int n_fft, int variant, int lgn, uint32_t flags) {
 }
 
 int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads) {
-  return ctx->sms * stats_blocks_per_sm(bins->n_fft, threads, bins->n_z, bins->n_k);
+  return capped(ctx, ctx->sms * stats_blocks_per_sm(bins->n_fft, threads, bins->n_z, bins->n_k));
 }
 
 GeomParams geom_params(mk_ctx *ctx, const mk_box *box, const mk_skewer_params *p) {
@@ -1180,6 +1184,13 @@ int mk_launch_config(mk_ctx *ctx, int32_t n_fft, int32_t layout, int32_t big_box
   *threads = c.threads;
   *occupancy = c.minb;
   return it != ctx->tuned.end() ? MK_OK : MK_ERANGE;
+}
+
+int mk_set_grid_cap(mk_ctx *ctx, int32_t max_ctas) {
+  if (!ctx) return MK_EINVAL;
+  if (max_ctas < 0) return fail(ctx, MK_EINVAL, "max_ctas must be >= 0");
+  ctx->grid_cap = max_ctas;
+  return MK_OK;
 }
 
 int mk_set_timing(mk_ctx *ctx, int on) {

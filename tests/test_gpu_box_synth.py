@@ -29,11 +29,37 @@ def table(cell, n_tab=2000):
     return dk, np.where(k > 0, 40.0 * k ** 0.96 * np.exp(-(k / 1.5) ** 2) * (1.0 + 0.05 * np.sin(15.0 * k)), 0.0)
 
 
+U32 = 2.0 ** -24  # unit roundoff of FP32
+
+
+def fft_error_bound(n):
+    """Worst-case relative error, in the 2-norm over the n^3 voxels, of an
+    FP32 box made by one forward and one inverse 3D FFT (Higham, Accuracy and
+    Stability of Numerical Algorithms, 2nd ed., Thm. 24.2: a radix-2 FFT of
+    length 2^t has ||err|| / ||y|| <= t eta / (1 - t eta), eta = mu + g4 (sqrt 2
+    + mu), g4 = 4u / (1 - 4u), mu the twiddle error; twiddles are FP64 values
+    rounded to FP32, mu = u).  Both 3D transforms together take
+    t = 2 * 3 * log2 n radix-2-equivalent stages; the filter adds one rounding."""
+    t = 2 * 3 * int(round(math.log2(n)))
+    g4 = 4 * U32 / (1 - 4 * U32)
+    eta = U32 + g4 * (math.sqrt(2.0) + U32)
+    return t * eta / (1 - t * eta) + U32
+
+
 def close(gpu, ref, what, rel=2e-5):
+    """Every voxel within rel x RMS of the oracle's box, and the RMS error
+    within the worst-case FFT bound.  rel: the rounding errors of the FFT
+    stages act as independent noise of RMS ~ u sqrt(t) per voxel (t stages),
+    so the largest of n^3 voxel errors is ~ sqrt(2 ln n^3) ~ 6 times that,
+    ~2.4e-6 x RMS at n = 256; 2e-5 leaves a factor 8 for the constant."""
     gpu = np.asarray(gpu, dtype=np.float64)
+    n = round(ref.size ** (1.0 / 3.0))
     rms = math.sqrt(np.mean(ref ** 2))
-    err = np.abs(gpu - ref).max()
-    assert err <= rel * rms, f"{what}: max error {err:.3e} > {rel:.0e} x RMS {rms:.3e}"
+    err = np.abs(gpu - ref)
+    assert err.max() <= rel * rms, f"{what}: max error {err.max():.3e} > {rel:.0e} x RMS {rms:.3e}"
+    rms_err = math.sqrt(np.mean(err ** 2))
+    bound = fft_error_bound(n)
+    assert rms_err <= bound * rms, f"{what}: RMS error {rms_err / rms:.3e} x RMS > bound {bound:.3e}"
 
 
 def pairs(out, n):

@@ -118,6 +118,37 @@ def test_flux_matches_oracle(ctx, tiny, rebin):
         assert_stats_close(st_g, st_o)
 
 
+@pytest.mark.parametrize("n_fft,cap", [(256, 1), (1024, 2)])
+def test_long_register_carry_matches_oracle(ctx, tiny, n_fft, cap):
+    """The whole tiny workload through one or two CTAs: every team runs
+    hundreds of consecutive segments, carrying its pixel sums in registers
+    across segments and z bins (flushed at bin ends), in the fused pass, the
+    statistics pass and the tuning pass."""
+    w = si.shrink(tiny["w"], n_fft=n_fft)
+    dv = tiny["dev"]
+    n = len(tiny["ids"])
+    o = oracle.run_skewers(w, tiny["d"], tiny["e"], tiny["pos"], tiny["ids"], n_threads=16)
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    box = ctx.load_box(w, ctx.pack_box(dv["d"], dv["e"], padded=True), None, layout=mk.BOX_PADDED)
+    ctx.set_grid_cap(cap)
+    try:
+        st, g = ctx.run(box, dv["qso"], n, w, flags=mk.STATS | mk.STORE_FIELDS | mk.STORE_FLUX)
+        tot = int(o["offsets"][-1])
+        assert_field_close(g["delta"][:tot].cpu().numpy(), o["delta"], "delta_tot")
+        assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
+        assert_stats_close(st, so)
+        st2 = ctx.stats(w, g["sk"], n, g["offsets"], g["flux"], delta=g["delta"], eta=g["eta"])
+        assert_stats_close(st2, so)
+        st3 = ctx.flux_stats(w, g["sk"], n, g["offsets"], g["delta"], g["eta"])
+        assert_stats_close(st3, so)
+    finally:
+        ctx.set_grid_cap(0)
+    # segments per team: the carry spans hundreds of segments
+    segs = int(np.sum((o["npix"] + n_fft - 1) // n_fft))
+    teams = cap * (256 // (n_fft // 8))
+    assert segs / teams >= 100
+
+
 def test_split_statistics_match_oracle(ctx, tiny):
     w, dv = tiny["w"], tiny["dev"]
     box = ctx.load_box(w, dv["d"], dv["e"])
@@ -634,6 +665,27 @@ def _full_size_check(ctx, w, n_sample, seed, lognormal=False, layout="padded"):
     np.testing.assert_array_equal(cnt.cpu().numpy(), st["sums"][:, 0])
     m = cnt.cpu().numpy() > 0
     np.testing.assert_allclose(st["mean_flux"][m], (fsum / cnt).cpu().numpy()[m], rtol=TOL_STAT)
+    # every statistic of the sampled skewers against the oracle: (1) the
+    # statistics pass over the sampled skewers' stored fields and flux,
+    # gathered into compact arrays; (2) the fused pass over the sampled
+    # quasars on the full-size box, in one CTA, so that each team carries its
+    # pixel sums across many segments and z bins
+    so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    assert so["n_seg"].sum() > 0
+    sel = torch.cat([torch.arange(int(off[q]), int(off[q + 1]), device="cuda") for q in idx])
+    rc = rec[idx].copy()
+    rc["offset"] = o["offsets"][:-1]
+    sk_c = torch.from_numpy(rc.view(np.uint8).reshape(-1).copy()).cuda()
+    off_c = torch.from_numpy(o["offsets"].astype(np.int64)).cuda()
+    st_c = ctx.stats(w, sk_c, len(idx), off_c, g["flux"][sel].contiguous(), delta=g["delta"][sel].contiguous(),
+                     eta=g["eta"][sel].contiguous())
+    assert_stats_close(st_c, so)
+    ctx.set_grid_cap(1)
+    try:
+        st_f, _ = ctx.run(box, mk.catalogue_tensor(pos[idx], ids[idx]), len(idx), w, flags=mk.STATS)
+    finally:
+        ctx.set_grid_cap(0)
+    assert_stats_close(st_f, so)
     del g, box
     torch.cuda.empty_cache()
 
