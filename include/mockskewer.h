@@ -509,7 +509,10 @@ int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer
    a linear output.  Parameters: MK_MLP_NPARAM floats in the order W0 [128x4],
    b0, W1 [128x128], b1, W2 [128x128], b2, W3 [35x128], b3, each W row-major
    [out][in].  The kernels use the weights in BF16, rounded from an FP32 master
-   copy that Adam updates; biases, activations and all accumulation are FP32.
+   copy that Adam updates.  The tensor-core products take BF16 operands (the
+   weights, the hidden activations, and in the backward pass the output
+   gradient and each dz = dh GELU'(z)) and accumulate in FP32; biases, the
+   4-wide first layer, the outputs and the loss are FP32.
    Device arrays are row-major: x n x 4, outputs n x 35.
    Errors: MK_EINVAL for NULL pointers or sizes outside the ranges stated
    below (max_batch in [1, 2^24]; n in [1, max_batch] for mk_mlp_loss_grad;
@@ -535,10 +538,19 @@ int mk_mlp_forward(mk_mlp *mlp, const float *d_x, int64_t n, float *d_y);
    weights, without an update.  n <= max_batch.  Synchronous. */
 int mk_mlp_loss_grad(mk_mlp *mlp, const float *d_x, const float *d_t, int64_t n, double *h_loss,
                      float *h_grad);
+/* One Adam step (Kingma & Ba 2015, Algorithm 1; beta 0.9, 0.999, eps 1e-8,
+   bias-corrected with the MLP's step count, which it advances) on the FP32
+   master parameters with the caller's gradient d_grad (MK_MLP_NPARAM floats,
+   device); the BF16 copy follows.  The training kernels apply the same
+   update after each minibatch.  Asynchronous.  MK_EINVAL for a NULL gradient
+   or lr <= 0. */
+int mk_mlp_adam_step(mk_mlp *mlp, const float *d_grad, float lr);
 /* Adam (beta 0.9, 0.999, eps 1e-8) on shuffled minibatches of `batch` (<=
    max_batch) samples for `epochs` epochs, learning rate lr decayed on a cosine
    to lr/20; h_epoch_loss (epochs values) receives each epoch's mean training
-   loss, or NULL.  Synchronous. */
+   loss, or NULL.  Each epoch runs as one launch of a cluster of 8 CTAs (one
+   GPC's worth of SMs): the minibatch gradient is summed in a fixed order, so
+   training is deterministic for a given seed.  Synchronous. */
 int mk_mlp_train(mk_mlp *mlp, const float *d_x, const float *d_t, int64_t n, int32_t batch,
                  int32_t epochs, float lr, uint64_t seed, double *h_epoch_loss);
 

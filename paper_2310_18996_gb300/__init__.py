@@ -34,7 +34,7 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
            "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box", "mk_xi_of_pk",
            "mk_lognormal_pk", "mk_draw_qso", "mk_cosmo_eval", "mk_save_skewers", "mk_load_skewers",
-           "mk_set_grid_cap"]
+           "mk_set_grid_cap", "mk_mlp_adam_step"]
 
 
 class MkError(RuntimeError):
@@ -182,6 +182,7 @@ def lib():
                 "mk_mlp_get_params": (C.c_int, [vp, P(C.c_float), P(C.c_uint16)]),
                 "mk_mlp_forward": (C.c_int, [vp, vp, i64, vp]),
                 "mk_mlp_loss_grad": (C.c_int, [vp, vp, vp, i64, P(C.c_double), P(C.c_float)]),
+                "mk_mlp_adam_step": (C.c_int, [vp, vp, C.c_float]),
                 "mk_mlp_train": (C.c_int, [vp, vp, vp, i64, i32, i32, C.c_float, C.c_uint64,
                                            P(C.c_double)]),
                 "mk_surrogate_labels": (C.c_int, [vp, P(SkewerParams), vp, i64, vp, vp, vp, P(StatBins),
@@ -657,6 +658,11 @@ class Mlp:
         self.ctx._check(lib().mk_mlp_loss_grad(self.h, _ptr(x), _ptr(t), x.shape[0], C.byref(loss),
                                                g.ctypes.data_as(C.POINTER(C.c_float))))
         return loss.value, g
+
+    def adam_step(self, grad, lr):
+        """One Adam step with a device gradient (MLP_NPARAM float32 values)."""
+        self.ctx._stream()
+        self.ctx._check(lib().mk_mlp_adam_step(self.h, _ptr(grad), lr))
 
     def train(self, x, t, batch=2048, epochs=10, lr=2e-3, seed=0):
         losses = np.zeros(max(epochs, 1))

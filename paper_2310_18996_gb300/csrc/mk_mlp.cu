@@ -1,257 +1,671 @@
 // Surrogate MLP kernels: 4 -> 128 -> 128 -> 128 -> 35, GELU hidden units.
 //
-// Weights are used in BF16 (a copy refreshed from the FP32 master after each
-// Adam step); biases, activations and every accumulation are FP32.  Layout of
-// the parameter vector: W0 [128x4], b0, W1 [128x128], b1, W2 [128x128], b2,
+// Tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation) run
+// every 128-wide product: the hidden layers, the output layer, the backward
+// products dh = dz W and the weight gradients dW = dz^T h.  Operand precision
+// (the same on the FP64 oracle's BF16 path): weights BF16 (rounded from an
+// FP32 master copy that Adam updates); hidden activations stored as BF16; the
+// output y in FP32; the backward operands dy and dz = dh * GELU'(z) rounded to
+// BF16, with GELU'(z) from the FP32 pre-activation.  The 4-wide first layer
+// and its weight gradient run on the FP32 cores with FP32 inputs.
+//
+// Training: one cluster of 8 CTAs runs a whole epoch in one launch.  Each CTA
+// takes 32 samples of a step; per layer it writes its partial weight and bias
+// gradients to shared memory, and after a cluster barrier every CTA sums one
+// eighth of that layer's parameters over the 8 CTAs' partials (distributed
+// shared memory, fixed order), applies Adam to them and writes the new
+// weights into every CTA's shared-memory copy (no CTA uses that layer again
+// in the step).  The weights reach global memory only through the host,
+// which refreshes the global image from the FP32 master after the launch.
+//
+// Parameter vector: W0 [128x4], b0, W1 [128x128], b1, W2 [128x128], b2,
 // W3 [35x128], b3, each W row-major [out][in].
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "mk_mlp.h"
 
 namespace mk {
+namespace {
 
-__host__ __device__ constexpr int mlp_dim(int l) { return l == 0 ? 4 : (l == 4 ? 35 : 128); }
-constexpr int kTile = 32;  // samples per CTA
-constexpr int kThreads = 128;
+constexpr int kS = 32;        // samples per CTA pass
+constexpr int kCl = 8;        // CTAs of the training cluster
+constexpr int kThr = 256;     // threads per CTA (8 warps)
+constexpr int kLd = 136;      // BF16 row stride of 128-wide buffers (272 B: conflict-free ldmatrix rows)
+constexpr int kLdY = 56;      // BF16 row stride of the output-gradient buffer (48 columns used)
+constexpr int kW3R = 48;      // rows of W3 in the image (35 real, zero rows after)
+constexpr int kLdP = 136;     // FP32 row stride of the gradient partials
+constexpr int kOutP = 40;     // outputs padded to 5 tiles of 8
 
-struct MlpOffsets {
-  int w[4], b[4];
+__host__ __device__ constexpr int dim(int l) { return l == 0 ? 4 : (l == 4 ? 35 : 128); }
+
+// canonical offsets of W_l and b_l in the parameter vector
+__host__ __device__ constexpr int w_off(int l) {
+  return l == 0 ? 0 : w_off(l - 1) + dim(l) * dim(l - 1) + dim(l);
+}
+__host__ __device__ constexpr int b_off(int l) { return w_off(l) + dim(l + 1) * dim(l); }
+
+// Weight image (bytes), identical in global and shared memory.
+struct Img {
+  static constexpr int W1 = 0;
+  static constexpr int W2 = W1 + 128 * kLd * 2;
+  static constexpr int W3 = W2 + 128 * kLd * 2;
+  static constexpr int W0 = W3 + kW3R * kLd * 2;  // FP32 [128][4]
+  static constexpr int B0 = W0 + 128 * 4 * 4;
+  static constexpr int B1 = B0 + 128 * 4;
+  static constexpr int B2 = B1 + 128 * 4;
+  static constexpr int B3 = B2 + 128 * 4;
+  static constexpr int BYTES = B3 + kOutP * 4;
 };
+static_assert(Img::BYTES % 16 == 0, "image is copied in 16-byte pieces");
 
-__host__ __device__ inline MlpOffsets mlp_offsets() {
-  MlpOffsets o;
-  int p = 0;
-  for (int l = 0; l < 4; ++l) {
-    o.w[l] = p;
-    p += mlp_dim(l + 1) * mlp_dim(l);
-    o.b[l] = p;
-    p += mlp_dim(l + 1);
-  }
-  return o;
+// Work buffers after the image (bytes from the start of shared memory).
+struct Wk {
+  static constexpr int X = Img::BYTES;          // FP32 [32][4]
+  static constexpr int H0 = X + kS * 4 * 4;      // BF16 [32][kLd] each
+  static constexpr int H1 = H0 + kS * kLd * 2;
+  static constexpr int H2 = H1 + kS * kLd * 2;
+  static constexpr int Y = H2 + kS * kLd * 2;    // FP32 [32][kOutP]
+  static constexpr int FWD_END = Y + kS * kOutP * 4;
+  static constexpr int DA = FWD_END;             // BF16 [32][kLd]: dz ping-pong
+  static constexpr int DB = DA + kS * kLd * 2;
+  static constexpr int DY = DB + kS * kLd * 2;   // BF16 [32][kLdY]
+  static constexpr int P = DY + kS * kLdY * 2;   // FP32 [128][kLdP] weight-gradient partials
+  static constexpr int PB = P + 128 * kLdP * 4;  // FP32 [128] bias-gradient partials
+  static constexpr int RED = PB + 128 * 4;       // FP64 [8] warp loss partials, [8] CTA loss
+  static constexpr int END = RED + 16 * 8;
+};
+static_assert(Wk::END <= 227 * 1024, "shared memory plan exceeds 227 KB");
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t saddr(const void *p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void ldsm4(uint32_t a, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldsm4t(uint32_t a, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+// d += a b: A 16x16 (row), B 16x8 (col), BF16 in, FP32 accumulate
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// the same shared-memory location in CTA `rank` of the cluster (generic pointer)
+template <typename T>
+__device__ __forceinline__ const T *remote(const T *p, uint32_t rank) {
+  return static_cast<const T *>(__cluster_map_shared_rank(const_cast<T *>(p), rank));
 }
 
 __device__ __forceinline__ float gelu(float x) { return 0.5f * x * erfcf(-x * 0.70710678118654752f); }
-
 __device__ __forceinline__ float gelu_deriv(float x) {
   return 0.5f * erfcf(-x * 0.70710678118654752f) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+__device__ __forceinline__ float bf16_val(float a) { return __bfloat162float(__float2bfloat16_rn(a)); }
 
-// Forward over a tile of kTile samples.  rows[i] (or i) selects the sample.
-// When acts is set, stores z_l and h_l of the three hidden layers
-// (acts + l * 2 * n * 128: z, then h) and the outputs y for the backward pass.
-__global__ void __launch_bounds__(kThreads) k_mlp_fwd(const __nv_bfloat16 *__restrict__ wbf,
-                                                      const float *__restrict__ master, const float *__restrict__ x,
-                                                      const int32_t *__restrict__ rows, int64_t n, float *y,
-                                                      float *acts) {
-  __shared__ float in[kTile][128];         // inputs of the current layer, then its outputs
-  __shared__ __nv_bfloat16 wt[128][128];  // transposed weights of the current layer: wt[k][j]
-  const MlpOffsets O = mlp_offsets();
-  const int64_t s0 = static_cast<int64_t>(blockIdx.x) * kTile;
-  const int j = threadIdx.x;
-  for (int i = threadIdx.x; i < kTile * 4; i += kThreads) {
-    const int s = i / 4, k = i % 4;
-    const int64_t g = s0 + s;
-    float v = 0.f;
-    if (g < n) v = x[(rows ? rows[g] : g) * 4 + k];
-    in[s][k] = v;
+// Adam (Kingma & Ba 2015, Algorithm 1) on one parameter; c1 = 1/(1 - b1^t),
+// c2 = 1/(1 - b2^t).  Returns the new value.
+__device__ __forceinline__ float adam_one(float &p, float &m, float &v, float g, float lr, float b1, float b2,
+                                          float eps, float c1, float c2) {
+  m = b1 * m + (1.f - b1) * g;
+  v = b2 * v + (1.f - b2) * (g * g);
+  p = p - lr * (m * c1) / (sqrtf(v * c2) + eps);
+  return p;
+}
+
+// Where canonical parameter i sits in the image: byte offset, and whether it
+// is kept as BF16 (the 128-wide weights) or as FP32 (biases; W0 as the FP32
+// value of its BF16 rounding).
+struct Slot {
+  int off;
+  bool bf16;
+};
+__device__ __forceinline__ Slot image_slot(int i) {
+  if (i < b_off(0)) return {Img::W0 + 4 * i, false};
+  if (i < w_off(1)) return {Img::B0 + 4 * (i - b_off(0)), false};
+  if (i < b_off(1)) {
+    const int q = i - w_off(1);
+    return {Img::W1 + 2 * ((q / 128) * kLd + q % 128), true};
   }
-  for (int l = 0; l < 4; ++l) {
-    const int ni = mlp_dim(l), no = mlp_dim(l + 1);
-    __syncthreads();
-    for (int i = threadIdx.x; i < ni * no; i += kThreads) {
-      const int jj = i / ni, kk = i % ni;
-      wt[kk][jj] = wbf[O.w[l] + i];
+  if (i < w_off(2)) return {Img::B1 + 4 * (i - b_off(1)), false};
+  if (i < b_off(2)) {
+    const int q = i - w_off(2);
+    return {Img::W2 + 2 * ((q / 128) * kLd + q % 128), true};
+  }
+  if (i < w_off(3)) return {Img::B2 + 4 * (i - b_off(2)), false};
+  if (i < b_off(3)) {
+    const int q = i - w_off(3);
+    return {Img::W3 + 2 * ((q / 128) * kLd + q % 128), true};
+  }
+  return {Img::B3 + 4 * (i - b_off(3)), false};
+}
+
+// The value the kernels keep for parameter i (p its FP32 master value).
+__device__ __forceinline__ float image_value(int i, float p) { return i < b_off(0) ? bf16_val(p) : p; }
+
+// Write the kernels' copy of canonical parameter i (value p) into an image.
+__device__ __forceinline__ void image_put(unsigned char *img, int i, float p) {
+  const Slot sl = image_slot(i);
+  if (sl.bf16) {
+    *reinterpret_cast<__nv_bfloat16 *>(img + sl.off) = __float2bfloat16_rn(p);
+  } else {
+    *reinterpret_cast<float *>(img + sl.off) = image_value(i, p);
+  }
+}
+
+// The same, into the shared-memory image of every CTA of the cluster.
+__device__ __forceinline__ void image_put_cluster(unsigned char *sm, int i, float p) {
+  const Slot sl = image_slot(i);
+  if (sl.bf16) {
+    const __nv_bfloat16 v = __float2bfloat16_rn(p);
+#pragma unroll
+    for (int c = 0; c < kCl; ++c)
+      *static_cast<__nv_bfloat16 *>(__cluster_map_shared_rank(static_cast<void *>(sm + sl.off), c)) = v;
+  } else {
+    const float v = image_value(i, p);
+#pragma unroll
+    for (int c = 0; c < kCl; ++c)
+      *static_cast<float *>(__cluster_map_shared_rank(static_cast<void *>(sm + sl.off), c)) = v;
+  }
+}
+
+// Copy the image from global memory (L2, bypassing L1: other CTAs wrote it).
+__device__ __forceinline__ void load_image(unsigned char *sm, const unsigned char *gimg) {
+  const uint4 *src = reinterpret_cast<const uint4 *>(gimg);
+  uint4 *dst = reinterpret_cast<uint4 *>(sm);
+  for (int i = threadIdx.x; i < Img::BYTES / 16; i += blockDim.x) dst[i] = __ldcg(src + i);
+}
+
+// ------------------------------------------------------------------ products
+// Sample-major product out[32][N] = A[32][K] B, A BF16 [s][k] (row stride lda
+// elements).  TRANS_W = false: B(k, n) = W[n][k] (forward); true: B(k, n) =
+// W[k][n] (backward).  Warp w: rows 16 (w & 1) .. + 15, columns
+// 32 (w >> 1) .. + 31 (4 tiles of 8); acc[nt][0..3] is the m16n8 fragment.
+template <bool TRANS_W>
+__device__ __forceinline__ void gemm_s(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *W, int ldw, int K,
+                                       float (&acc)[4][4]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int s0 = 16 * (w & 1), n0 = 32 * (w >> 1);
+  const int q = lane >> 3, r8 = lane & 7;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+  const uint32_t a_base = saddr(A + (s0 + r8 + 8 * (q & 1)) * lda + 8 * (q >> 1));
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    ldsm4(a_base + 2 * k0, a);
+#pragma unroll
+    for (int np = 0; np < 2; ++np) {  // pairs of n tiles
+      const int nb = n0 + 16 * np;
+      uint32_t b[4];
+      if (!TRANS_W) {
+        ldsm4(saddr(W + (nb + 8 * (q >> 1) + r8) * ldw + k0 + 8 * (q & 1)), b);
+      } else {
+        ldsm4t(saddr(W + (k0 + 8 * (q & 1) + r8) * ldw + nb + 8 * (q >> 1)), b);
+      }
+      mma16816(acc[2 * np], a, b[0], b[1]);
+      mma16816(acc[2 * np + 1], a, b[2], b[3]);
     }
+  }
+}
+
+// Element (s, j) of fragment slot (nt, i) of gemm_s: s = s0 + g + 8 (i >> 1),
+// j = n0 + 8 nt + 2 t + (i & 1).
+__device__ __forceinline__ void frag_pos(int nt, int i, int &s, int &j) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  s = 16 * (w & 1) + (lane >> 2) + 8 * (i >> 1);
+  j = 32 * (w >> 1) + 8 * nt + 2 * (lane & 3) + (i & 1);
+}
+
+// Weight-gradient product P[j][k] = sum_s D[s][j] H[s][k] over 32 samples: M
+// tile mt (rows 16 mt ..), NT tiles of 8 columns from column k0.  D BF16 [s][j]
+// (stride ldd), H BF16 [s][k] (stride kLd).
+template <int NT>
+__device__ __forceinline__ void gemm_w(const __nv_bfloat16 *D, int ldd, const __nv_bfloat16 *H, int mt, int k0,
+                                       float *P) {
+  const int lane = threadIdx.x & 31;
+  const int q = lane >> 3, r8 = lane & 7;
+  float acc[NT][4];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+#pragma unroll
+  for (int s0 = 0; s0 < kS; s0 += 16) {
+    uint32_t a[4];
+    ldsm4t(saddr(D + (s0 + 8 * (q >> 1) + r8) * ldd + 16 * mt + 8 * (q & 1)), a);
+#pragma unroll
+    for (int np = 0; np < NT / 2; ++np) {
+      uint32_t b[4];
+      ldsm4t(saddr(H + (s0 + 8 * (q & 1) + r8) * kLd + k0 + 16 * np + 8 * (q >> 1)), b);
+      mma16816(acc[2 * np], a, b[0], b[1]);
+      mma16816(acc[2 * np + 1], a, b[2], b[3]);
+    }
+  }
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt) {
+    const int col = k0 + 8 * nt + 2 * t;
+    *reinterpret_cast<float2 *>(P + (16 * mt + g) * kLdP + col) = make_float2(acc[nt][0], acc[nt][1]);
+    *reinterpret_cast<float2 *>(P + (16 * mt + g + 8) * kLdP + col) = make_float2(acc[nt][2], acc[nt][3]);
+  }
+}
+
+// ------------------------------------------------------------------ forward of 32 samples
+// X (FP32 [32][4]) in shared memory -> H0, H1, H2 (BF16) and Y (FP32
+// [32][kOutP], 35 used).  With KEEP_G the GELU derivatives of the three hidden
+// layers stay in G[l] in the fragment layout of gemm_s.
+template <bool KEEP_G>
+__device__ __forceinline__ void forward32(unsigned char *sm, float (&G)[3][4][4]) {
+  const float *X = reinterpret_cast<const float *>(sm + Wk::X);
+  const float *W0 = reinterpret_cast<const float *>(sm + Img::W0);
+  __nv_bfloat16 *H[3] = {reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H0),
+                         reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H1),
+                         reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H2)};
+  const float *B[3] = {reinterpret_cast<const float *>(sm + Img::B0), reinterpret_cast<const float *>(sm + Img::B1),
+                       reinterpret_cast<const float *>(sm + Img::B2)};
+  const __nv_bfloat16 *Wl[3] = {nullptr, reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W1),
+                                reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W2)};
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    float acc[4][4];
+    if (l == 0) {  // 4 inputs: FP32 cores, FP32 inputs
+#pragma unroll
+      for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          int s, j;
+          frag_pos(nt, i, s, j);
+          const float4 wv = *reinterpret_cast<const float4 *>(W0 + 4 * j);
+          const float4 xv = *reinterpret_cast<const float4 *>(X + 4 * s);
+          acc[nt][i] = fmaf(wv.w, xv.w, fmaf(wv.z, xv.z, fmaf(wv.y, xv.y, wv.x * xv.x)));
+        }
+    } else {
+      gemm_s<false>(H[l - 1], kLd, Wl[l], kLd, 128, acc);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        int s, j;
+        frag_pos(nt, 2 * h, s, j);
+        const float z0 = acc[nt][2 * h] + B[l][j], z1 = acc[nt][2 * h + 1] + B[l][j + 1];
+        if (KEEP_G) {
+          G[l][nt][2 * h] = gelu_deriv(z0);
+          G[l][nt][2 * h + 1] = gelu_deriv(z1);
+        }
+        *reinterpret_cast<uint32_t *>(H[l] + s * kLd + j) = pack_bf16(gelu(z0), gelu(z1));
+      }
     __syncthreads();
-    float acc[kTile];
-    if (j < no) {
-      const float b = master[O.b[l] + j];
+  }
+  // output layer: 5 column tiles (40 columns, 35 real), both row tiles, warps 0..4
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w < 5) {
+    const __nv_bfloat16 *W3 = reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W3);
+    const int q = lane >> 3, r8 = lane & 7;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    for (int k0 = 0; k0 < 128; k0 += 16) {
+      uint32_t b[4];  // tiles w and w + 1 (rows up to 47 exist: zero padding)
+      ldsm4(saddr(W3 + (8 * w + 8 * (q >> 1) + r8) * kLd + k0 + 8 * (q & 1)), b);
 #pragma unroll
-      for (int s = 0; s < kTile; ++s) acc[s] = b;
-      for (int k = 0; k < ni; ++k) {
-        const float w = __bfloat162float(wt[k][j]);
-#pragma unroll
-        for (int s = 0; s < kTile; ++s) acc[s] = fmaf(in[s][k], w, acc[s]);
+      for (int mt = 0; mt < 2; ++mt) {
+        uint32_t a[4];
+        ldsm4(saddr(H[2] + (16 * mt + r8 + 8 * (q & 1)) * kLd + k0 + 8 * (q >> 1)), a);
+        mma16816(acc[mt], a, b[0], b[1]);
       }
     }
-    __syncthreads();  // every thread has read `in`
-    if (j < no) {
+    float *Y = reinterpret_cast<float *>(sm + Wk::Y);
+    const float *B3 = reinterpret_cast<const float *>(sm + Img::B3);
+    const int g = lane >> 2, t = lane & 3, j = 8 * w + 2 * t;
 #pragma unroll
-      for (int s = 0; s < kTile; ++s) {
-        const int64_t g = s0 + s;
-        const float h = (l < 3) ? gelu(acc[s]) : acc[s];
-        in[s][j] = h;
-        if (g < n) {
-          if (l < 3) {
-            if (acts) {
-              acts[(static_cast<int64_t>(l) * 2 * n + g) * 128 + j] = acc[s];
-              acts[(static_cast<int64_t>(l) * 2 * n + n + g) * 128 + j] = h;
-            }
-          } else {
-            y[g * 35 + j] = h;
+    for (int mt = 0; mt < 2; ++mt) {
+      Y[(16 * mt + g) * kOutP + j] = acc[mt][0] + B3[j];
+      Y[(16 * mt + g) * kOutP + j + 1] = acc[mt][1] + B3[j + 1];
+      Y[(16 * mt + g + 8) * kOutP + j] = acc[mt][2] + B3[j];
+      Y[(16 * mt + g + 8) * kOutP + j + 1] = acc[mt][3] + B3[j + 1];
+    }
+  }
+  __syncthreads();
+}
+
+// Load the inputs of samples [i0, i0 + cnt) (cnt <= 32; rows or base + i) as
+// X; rows past cnt are zero.  Returns nothing; ends with a barrier.
+__device__ __forceinline__ void load_x(unsigned char *sm, const float *x, const int32_t *rows, int64_t base,
+                                       int64_t i0, int cnt) {
+  float *X = reinterpret_cast<float *>(sm + Wk::X);
+  if (threadIdx.x < kS * 4) {
+    const int s = threadIdx.x >> 2, k = threadIdx.x & 3;
+    float v = 0.f;
+    if (s < cnt) {
+      const int64_t i = i0 + s;
+      const int64_t row = rows ? rows[base + i] : base + i;
+      v = x[row * 4 + k];
+    }
+    X[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ inference
+__global__ void __launch_bounds__(kThr, 1) k_mlp_forward(const unsigned char *__restrict__ gimg,
+                                                          const float *__restrict__ x, int64_t n, float *y) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  load_image(sm, gimg);
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kS;
+  const int cnt = static_cast<int>(n - i0 < kS ? n - i0 : kS);
+  load_x(sm, x, nullptr, 0, i0, cnt);  // (its barrier also covers the image)
+  float G[3][4][4];
+  forward32<false>(sm, G);
+  const float *Y = reinterpret_cast<const float *>(sm + Wk::Y);
+  for (int e = threadIdx.x; e < cnt * kMlpOut; e += blockDim.x) {
+    const int s = e / kMlpOut, j = e % kMlpOut;
+    y[(i0 + s) * kMlpOut + j] = Y[s * kOutP + j];
+  }
+}
+
+// ------------------------------------------------------------------ training cluster
+// Owned slice of layer l's gradient (weights then bias, canonical order):
+// [rank L / 8, (rank + 1) L / 8), L = dim(l+1) (dim(l) + 1).  Sums the 8 CTAs'
+// partials (ranks in order).  adam: apply the Adam step to the slice at once
+// (the step has one pass) and write the new weights into every CTA's
+// shared-memory image; otherwise store (or add) the sums into grad.
+struct AdamArgs {
+  float lr, b1, b2, eps, c1, c2;
+};
+__device__ __forceinline__ void reduce_owned(unsigned char *sm, int l, uint32_t rank, const MlpRun &R, bool add,
+                                             bool adam, const AdamArgs &A) {
+  const int ni = dim(l), no = dim(l + 1), L = no * (ni + 1);
+  const int q0 = static_cast<int>(rank) * L / kCl, q1 = (static_cast<int>(rank) + 1) * L / kCl;
+  const float *P = reinterpret_cast<const float *>(sm + Wk::P);
+  const float *PB = reinterpret_cast<const float *>(sm + Wk::PB);
+  float *__restrict__ master = R.master;
+  float *__restrict__ mm = R.m;
+  float *__restrict__ vv = R.v;
+  float *__restrict__ grad = R.grad;
+  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+    const int i = w_off(l) + q;
+    float p = 0.f, m = 0.f, v = 0.f;
+    if (adam) {  // issued before the partials are read
+      p = master[i];
+      m = mm[i];
+      v = vv[i];
+    }
+    const float *a = q < no * ni ? P + (q / ni) * kLdP + q % ni : PB + (q - no * ni);
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < kCl; ++c) s += *remote(a, c);
+    if (adam) {
+      adam_one(p, m, v, s, A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+      master[i] = p;
+      mm[i] = m;
+      vv[i] = v;
+      image_put_cluster(sm, i, p);
+    } else {
+      grad[i] = add ? grad[i] + s : s;
+    }
+  }
+}
+
+// Samples of chunk `c` of step `st` for this CTA: [i0, i0 + cnt) of the launch.
+__device__ __forceinline__ void chunk_range(const MlpRun &R, int st, int c, uint32_t rank, int64_t &i0, int &cnt,
+                                            int &step_n) {
+  const int64_t s0 = static_cast<int64_t>(st) * R.batch;
+  const int64_t s1 = s0 + R.batch < R.n ? s0 + R.batch : R.n;
+  step_n = static_cast<int>(s1 - s0);
+  i0 = s0 + static_cast<int64_t>(c) * kMlpChunk + static_cast<int64_t>(rank) * kS;
+  const int64_t e = i0 + kS < s1 ? i0 + kS : s1;
+  cnt = e > i0 ? static_cast<int>(e - i0) : 0;
+}
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_train(MlpRun R) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const uint32_t rank = cluster_rank();
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const unsigned char *gimg = static_cast<const unsigned char *>(R.img);
+  __nv_bfloat16 *H0 = reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H0);
+  __nv_bfloat16 *H1 = reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H1);
+  __nv_bfloat16 *H2 = reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H2);
+  __nv_bfloat16 *DA = reinterpret_cast<__nv_bfloat16 *>(sm + Wk::DA);
+  __nv_bfloat16 *DB = reinterpret_cast<__nv_bfloat16 *>(sm + Wk::DB);
+  __nv_bfloat16 *DY = reinterpret_cast<__nv_bfloat16 *>(sm + Wk::DY);
+  const __nv_bfloat16 *W1 = reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W1);
+  const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W2);
+  const __nv_bfloat16 *W3 = reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W3);
+  float *P = reinterpret_cast<float *>(sm + Wk::P);
+  float *PB = reinterpret_cast<float *>(sm + Wk::PB);
+  double *RED = reinterpret_cast<double *>(sm + Wk::RED);
+  const float *X = reinterpret_cast<const float *>(sm + Wk::X);
+  const float *Y = reinterpret_cast<const float *>(sm + Wk::Y);
+
+  load_image(sm, gimg);
+  __syncthreads();
+
+  for (int st = 0; st < R.steps; ++st) {
+    int64_t i0;
+    int cnt, step_n;
+    chunk_range(R, st, 0, rank, i0, cnt, step_n);
+    const int chunks = (step_n + kMlpChunk - 1) / kMlpChunk;
+    const double inv = R.inv_count > 0.0 ? R.inv_count : 1.0 / (static_cast<double>(step_n) * kMlpOut);
+    // a one-pass training step updates each layer right after its gradient is
+    // summed (no CTA uses that layer's weights again in this step)
+    const bool fuse = R.train && chunks == 1;
+    AdamArgs A{};
+    if (R.train) {
+      const int64_t t = R.t0 + 1 + st;
+      A = AdamArgs{R.lr, R.b1, R.b2, R.eps,
+                   static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(R.b1), static_cast<double>(t)))),
+                   static_cast<float>(1.0 / (1.0 - pow(static_cast<double>(R.b2), static_cast<double>(t))))};
+    }
+    double step_loss = 0.0;  // CTA 0
+    for (int c = 0; c < chunks; ++c) {
+      chunk_range(R, st, c, rank, i0, cnt, step_n);
+      const bool add = R.accumulate || c > 0;
+      load_x(sm, R.x, R.rows, R.base, i0, cnt);
+      float G[3][4][4];
+      forward32<true>(sm, G);
+
+      // ---- loss and output gradient dy (BF16), zero past the valid samples and outputs
+      double lsum = 0.0;
+      for (int e = tid; e < kS * 48; e += kThr) {
+        const int s = e / 48, j = e % 48;
+        float d = 0.f;
+        if (s < cnt && j < kMlpOut) {
+          const int64_t i = i0 + s;
+          const int64_t row = R.rows ? R.rows[R.base + i] : R.base + i;
+          const float r = Y[s * kOutP + j] - R.t[row * kMlpOut + j];
+          lsum += static_cast<double>(r) * r * inv;
+          d = static_cast<float>(2.0 * inv) * r;
+        }
+        DY[s * kLdY + j] = __float2bfloat16_rn(d);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+      if (lane == 0) RED[w] = lsum;
+      __syncthreads();
+      if (tid == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kThr / 32; ++i) s += RED[i];
+        RED[8] = s;  // this CTA's loss of the chunk
+      }
+
+      // ---- layer 3: dW3 = dy^T h2 (48 x 128 tiles on warps 0..5), db3; dh2 = dy W3
+      if (w < 6) gemm_w<8>(DY, kLdY, H2, w % 3, 64 * (w / 3), P);
+      if (tid < kMlpOut) {
+        float s = 0.f;
+        for (int i = 0; i < kS; ++i) s += __bfloat162float(DY[i * kLdY + tid]);
+        PB[tid] = s;
+      }
+      {
+        float acc[4][4];
+        gemm_s<true>(DY, kLdY, W3, kLd, 48, acc);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            int s, j;
+            frag_pos(nt, 2 * h, s, j);
+            *reinterpret_cast<uint32_t *>(DA + s * kLd + j) =
+                pack_bf16(acc[nt][2 * h] * G[2][nt][2 * h], acc[nt][2 * h + 1] * G[2][nt][2 * h + 1]);
           }
+      }
+      cluster_sync();  // partials of layer 3 complete everywhere
+      if (rank == 0 && tid == 0)
+        for (int cc = 0; cc < kCl; ++cc) step_loss += *remote(RED + 8, cc);
+      reduce_owned(sm, 3, rank, R, add, fuse, A);
+      cluster_sync();  // partials read
+
+      // ---- layers 2 and 1: dW = dz^T h, db; dh = dz W, dz' = dh * GELU'(z)
+#pragma unroll
+      for (int l = 2; l >= 1; --l) {
+        const __nv_bfloat16 *D = (l == 2) ? DA : DB;
+        __nv_bfloat16 *Dn = (l == 2) ? DB : DA;
+        const __nv_bfloat16 *Hin = (l == 2) ? H1 : H0;
+        const __nv_bfloat16 *Wm = (l == 2) ? W2 : W1;
+        gemm_w<8>(D, kLd, Hin, w, 0, P);  // two halves of 8 column tiles keep registers for G
+        gemm_w<8>(D, kLd, Hin, w, 64, P);
+        if (tid < 128) {
+          float s = 0.f;
+          for (int i = 0; i < kS; ++i) s += __bfloat162float(D[i * kLd + tid]);
+          PB[tid] = s;
+        }
+        float acc[4][4];
+        gemm_s<true>(D, kLd, Wm, kLd, 128, acc);
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            int s, j;
+            frag_pos(nt, 2 * h, s, j);
+            *reinterpret_cast<uint32_t *>(Dn + s * kLd + j) = pack_bf16(acc[nt][2 * h] * G[l - 1][nt][2 * h],
+                                                                       acc[nt][2 * h + 1] * G[l - 1][nt][2 * h + 1]);
+          }
+        cluster_sync();
+        reduce_owned(sm, l, rank, R, add, fuse, A);
+        cluster_sync();
+      }
+
+      // ---- layer 0 (FP32 inputs): dW0 = dz0^T x, db0 (dz0 in DA)
+      for (int e = tid; e < 128 * 4; e += kThr) {
+        const int j = e >> 2, k = e & 3;
+        float s = 0.f;
+        for (int i = 0; i < kS; ++i) s = fmaf(__bfloat162float(DA[i * kLd + j]), X[i * 4 + k], s);
+        P[j * kLdP + k] = s;
+      }
+      if (tid < 128) {
+        float s = 0.f;
+        for (int i = 0; i < kS; ++i) s += __bfloat162float(DA[i * kLd + tid]);
+        PB[tid] = s;
+      }
+      cluster_sync();
+      reduce_owned(sm, 0, rank, R, add, fuse, A);
+      cluster_sync();  // partials read (the next chunk rewrites them)
+    }
+    if (rank == 0 && tid == 0 && R.loss_out) R.loss_out[st] = step_loss;
+    if (R.train && !fuse) {
+      // several passes: Adam on this CTA's eighth of every layer from the
+      // summed gradient; the new weights go to every CTA's image
+      for (int l = 0; l < 4; ++l) {
+        const int L = dim(l + 1) * (dim(l) + 1);
+        const int q0 = static_cast<int>(rank) * L / kCl, q1 = (static_cast<int>(rank) + 1) * L / kCl;
+        for (int q = q0 + tid; q < q1; q += kThr) {
+          const int i = w_off(l) + q;
+          float p = R.master[i], m = R.m[i], v = R.v[i];
+          adam_one(p, m, v, R.grad[i], A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+          R.master[i] = p;
+          R.m[i] = m;
+          R.v[i] = v;
+          image_put_cluster(sm, i, p);
         }
       }
+      cluster_sync();  // every CTA's image is complete before the next forward
     }
   }
+  cluster_sync();  // no CTA leaves while others may read its shared memory
 }
 
-// dy = 2 (y - t) / (n_total * 35) and the per-CTA loss partial (FP64).
-__global__ void k_mlp_loss(const float *__restrict__ y, const float *__restrict__ t,
-                           const int32_t *__restrict__ rows, int64_t n, double inv_count, float *dy,
-                           double *loss_part) {
-  __shared__ double red[256];
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n * 35;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t s = i / 35, o = i % 35;
-    const float r = y[i] - t[(rows ? rows[s] : s) * 35 + o];
-    dy[i] = static_cast<float>(2.0 * inv_count) * r;
-    acc += static_cast<double>(r) * r * inv_count;
-  }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
-}
-
-// Backward through the hidden layers for a tile: dz_l = (W_{l+1}^T dz_{l+1}) * GELU'(z_l),
-// l = 2, 1, 0, stored in dzs + l * n * 128.
-__global__ void __launch_bounds__(kThreads) k_mlp_bwd(const __nv_bfloat16 *__restrict__ wbf,
-                                                      const float *__restrict__ acts, const float *__restrict__ dy,
-                                                      int64_t n, float *dzs) {
-  __shared__ float din[kTile][128];      // dz of layer l + 1, then of layer l
-  __shared__ __nv_bfloat16 w[128][128];  // W_{l+1} as [out j][in k]
-  const MlpOffsets O = mlp_offsets();
-  const int64_t s0 = static_cast<int64_t>(blockIdx.x) * kTile;
-  const int k = threadIdx.x;
-  for (int i = threadIdx.x; i < kTile * 35; i += kThreads) {
-    const int s = i / 35, o = i % 35;
-    const int64_t g = s0 + s;
-    din[s][o] = g < n ? dy[g * 35 + o] : 0.f;
-  }
-  for (int l = 2; l >= 0; --l) {
-    const int no = mlp_dim(l + 2);  // outputs of layer l + 1
-    __syncthreads();
-    for (int i = threadIdx.x; i < no * 128; i += kThreads) w[i / 128][i % 128] = wbf[O.w[l + 1] + i];
-    __syncthreads();
-    float acc[kTile];
-#pragma unroll
-    for (int s = 0; s < kTile; ++s) acc[s] = 0.f;
-    for (int jj = 0; jj < no; ++jj) {
-      const float wv = __bfloat162float(w[jj][k]);
-#pragma unroll
-      for (int s = 0; s < kTile; ++s) acc[s] = fmaf(din[s][jj], wv, acc[s]);
-    }
-    __syncthreads();  // every thread has read `din`
-#pragma unroll
-    for (int s = 0; s < kTile; ++s) {
-      const int64_t g = s0 + s;
-      float d = 0.f;
-      if (g < n) {
-        const float z = acts[(static_cast<int64_t>(l) * 2 * n + g) * 128 + k];
-        d = acc[s] * gelu_deriv(z);
-        dzs[(static_cast<int64_t>(l) * n + g) * 128 + k] = d;
-      }
-      din[s][k] = d;
-    }
-  }
-}
-
-// Weight and bias gradients of layer l: dW[j][k] = sum_s d[s][j] in[s][k],
-// db[j] = sum_s d[s][j]; one thread per entry, samples summed in order.
-__global__ void k_mlp_wgrad(const float *__restrict__ d, int64_t ldd, const float *__restrict__ in, int64_t ldi,
-                            const float *__restrict__ x, const int32_t *__restrict__ rows, int no, int ni,
-                            int64_t n, float *gw, float *gb) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < no * ni) {
-    const int j = idx / ni, k = idx % ni;
-    float acc = 0.f;
-    for (int64_t s = 0; s < n; ++s) {
-      const float a = in ? in[s * ldi + k] : x[(rows ? rows[s] : s) * 4 + k];
-      acc = fmaf(d[s * ldd + j], a, acc);
-    }
-    gw[idx] = acc;
-  } else if (idx < no * ni + no) {
-    const int j = idx - no * ni;
-    float acc = 0.f;
-    for (int64_t s = 0; s < n; ++s) acc += d[s * ldd + j];
-    gb[j] = acc;
-  }
-}
-
-// Adam on the FP32 master, then the BF16 copy.
-__global__ void k_mlp_adam(float *master, __nv_bfloat16 *wbf, const float *__restrict__ g, float *m, float *v,
-                           int np, float lr, float b1, float b2, float eps, float c1, float c2) {
+// ------------------------------------------------------------------ small kernels
+__global__ void k_mlp_pack(const float *__restrict__ master, unsigned char *img, __nv_bfloat16 *wbf) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= np) return;
-  const float gi = g[i];
-  const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
-  const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+  if (i >= kMlpParams) return;
+  const float p = master[i];
+  image_put(img, i, p);
+  if (wbf) wbf[i] = __float2bfloat16_rn(p);
+}
+
+__global__ void k_mlp_adam(float *master, float *m, float *v, const float *__restrict__ g, unsigned char *img,
+                           float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= kMlpParams) return;
+  float p = master[i], mi = m[i], vi = v[i];
+  adam_one(p, mi, vi, g[i], lr, b1, b2, eps, c1, c2);
+  master[i] = p;
   m[i] = mi;
   v[i] = vi;
-  const float p = master[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
-  master[i] = p;
-  wbf[i] = __float2bfloat16_rn(p);
+  image_put(img, i, p);
 }
 
-__global__ void k_mlp_to_bf16(const float *master, __nv_bfloat16 *wbf, int np) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < np) wbf[i] = __float2bfloat16_rn(master[i]);
-}
+}  // namespace
 
 // ---------------------------------------------------------------- launchers
-cudaError_t mlp_to_bf16(const float *master, void *wbf, cudaStream_t st) {
-  k_mlp_to_bf16<<<(kMlpParams + 255) / 256, 256, 0, st>>>(master, static_cast<__nv_bfloat16 *>(wbf), kMlpParams);
-  return cudaGetLastError();
-}
+size_t mlp_image_bytes() { return Img::BYTES; }
 
-cudaError_t mlp_forward(const void *wbf, const float *master, const float *x, const int32_t *rows, int64_t n,
-                        float *y, float *acts, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  const int64_t grid = (n + kTile - 1) / kTile;
-  k_mlp_fwd<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(static_cast<const __nv_bfloat16 *>(wbf), master, x,
-                                                             rows, n, y, acts);
-  return cudaGetLastError();
-}
-
-// One gradient evaluation on n samples: forward with activations, loss and
-// dy, backward, weight gradients into grad (kMlpParams floats).  loss_part
-// holds kLossParts doubles (the caller sums them).
-cudaError_t mlp_gradient(const void *wbf, const float *master, const float *x, const float *t,
-                         const int32_t *rows, int64_t n, double inv_count, float *y, float *dy, float *acts,
-                         float *dzs, float *grad, double *loss_part, cudaStream_t st) {
-  cudaError_t e = mlp_forward(wbf, master, x, rows, n, y, acts, st);
+cudaError_t mlp_pack(const float *master, void *img, void *wbf, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(img, 0, Img::BYTES, st);  // padding rows and columns stay zero
   if (e != cudaSuccess) return e;
-  k_mlp_loss<<<kLossParts, 256, 0, st>>>(y, t, rows, n, inv_count, dy, loss_part);
-  const int64_t grid = (n + kTile - 1) / kTile;
-  k_mlp_bwd<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(static_cast<const __nv_bfloat16 *>(wbf), acts, dy,
-                                                              n, dzs);
-  const MlpOffsets O = mlp_offsets();
-  for (int l = 0; l < 4; ++l) {
-    const int no = mlp_dim(l + 1), ni = mlp_dim(l);
-    const float *d = (l == 3) ? dy : dzs + static_cast<int64_t>(l) * n * 128;
-    const int64_t ldd = (l == 3) ? 35 : 128;
-    const float *in = (l == 0) ? nullptr : acts + (static_cast<int64_t>(l - 1) * 2 * n + n) * 128;
-    const int cnt = no * ni + no;
-    k_mlp_wgrad<<<(cnt + 127) / 128, 128, 0, st>>>(d, ldd, in, 128, x, rows, no, ni, n, grad + O.w[l],
-                                                    grad + O.b[l]);
-  }
+  k_mlp_pack<<<(kMlpParams + 255) / 256, 256, 0, st>>>(master, static_cast<unsigned char *>(img),
+                                                        static_cast<__nv_bfloat16 *>(wbf));
   return cudaGetLastError();
 }
 
-cudaError_t mlp_adam(float *master, void *wbf, const float *grad, float *m, float *v, float lr, float b1, float b2,
+cudaError_t mlp_forward(const void *img, const float *x, int64_t n, float *y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int smem = Wk::FWD_END;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t grid = (n + kS - 1) / kS;
+  k_mlp_forward<<<static_cast<unsigned>(grid), kThr, smem, st>>>(static_cast<const unsigned char *>(img), x, n, y);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_cluster_run(const MlpRun &R, cudaStream_t st) {
+  if (R.steps == 0) return cudaSuccess;
+  const int smem = Wk::END;
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_mlp_train<<<kCl, kThr, smem, st>>>(R);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(float *master, float *m, float *v, const float *grad, void *img, float lr, float b1, float b2,
                      float eps, int64_t step, cudaStream_t st) {
   const double c1 = 1.0 / (1.0 - pow(static_cast<double>(b1), static_cast<double>(step)));
   const double c2 = 1.0 / (1.0 - pow(static_cast<double>(b2), static_cast<double>(step)));
-  k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, st>>>(master, static_cast<__nv_bfloat16 *>(wbf), grad, m, v,
-                                                        kMlpParams, lr, b1, b2, eps, static_cast<float>(c1),
+  k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, st>>>(master, m, v, grad, static_cast<unsigned char *>(img), lr,
+                                                        b1, b2, eps, static_cast<float>(c1),
                                                         static_cast<float>(c2));
   return cudaGetLastError();
 }

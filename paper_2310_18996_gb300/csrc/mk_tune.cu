@@ -20,9 +20,10 @@ struct mk_mlp {
   int device = 0;  // kept so that destruction does not depend on the context
   int64_t cap = 0;
   float *master = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
-  void *wbf = nullptr;
-  float *y = nullptr, *dy = nullptr, *acts = nullptr, *dzs = nullptr;
-  double *loss_part = nullptr, *h_loss_part = nullptr;
+  void *wbf = nullptr;  // canonical BF16 copy (mk_mlp_get_params)
+  void *img = nullptr;  // weight image the tensor-core kernels read
+  double *d_loss = nullptr, *h_loss = nullptr;  // per-step losses (pinned host copy)
+  int64_t loss_cap = 0;
   int64_t step = 0;
 };
 
@@ -46,23 +47,37 @@ void mlp_free(mk_mlp *p) {
   cudaFree(p->v);
   cudaFree(p->grad);
   cudaFree(p->wbf);
-  cudaFree(p->y);
-  cudaFree(p->dy);
-  cudaFree(p->acts);
-  cudaFree(p->dzs);
-  cudaFree(p->loss_part);
-  cudaFreeHost(p->h_loss_part);
+  cudaFree(p->img);
+  cudaFree(p->d_loss);
+  cudaFreeHost(p->h_loss);
 }
 
-// Mean squared error from the per-CTA partials of the last gradient evaluation.
-int read_loss(mk_mlp *p, double *loss) {
-  cudaStream_t st = mkhost::ctx_stream(p->ctx);
-  CKM(p->ctx, cudaMemcpyAsync(p->h_loss_part, p->loss_part, sizeof(double) * kLossParts, cudaMemcpyDeviceToHost, st));
-  CKM(p->ctx, cudaStreamSynchronize(st));
-  double s = 0.0;
-  for (int i = 0; i < kLossParts; ++i) s += p->h_loss_part[i];
-  *loss = s;
+// room for n per-step losses
+int ensure_loss(mk_mlp *p, int64_t n) {
+  if (n <= p->loss_cap) return MK_OK;
+  cudaFree(p->d_loss);
+  cudaFreeHost(p->h_loss);
+  p->d_loss = nullptr;
+  p->h_loss = nullptr;
+  p->loss_cap = 0;
+  if (cudaMalloc(&p->d_loss, sizeof(double) * n) != cudaSuccess ||
+      cudaMallocHost(&p->h_loss, sizeof(double) * n) != cudaSuccess)
+    return mfail(p->ctx, MK_ENOMEM, "surrogate MLP loss buffer");
+  p->loss_cap = n;
   return MK_OK;
+}
+
+MlpRun run_args(mk_mlp *p) {
+  MlpRun R{};
+  R.b1 = 0.9f;
+  R.b2 = 0.999f;
+  R.eps = 1e-8f;
+  R.master = p->master;
+  R.m = p->m;
+  R.v = p->v;
+  R.grad = p->grad;
+  R.img = p->img;
+  return R;
 }
 
 }  // namespace
@@ -78,15 +93,10 @@ extern "C" int mk_mlp_create(mk_ctx *ctx, mk_mlp **out, int64_t max_batch, uint6
   p->device = mkhost::ctx_device(ctx);
   p->cap = max_batch;
   const size_t np = sizeof(float) * kMlpParams;
-  const size_t nh = sizeof(float) * static_cast<size_t>(max_batch) * kMlpHidden;
   if (cudaMalloc(&p->master, np) != cudaSuccess || cudaMalloc(&p->m, np) != cudaSuccess ||
       cudaMalloc(&p->v, np) != cudaSuccess || cudaMalloc(&p->grad, np) != cudaSuccess ||
       cudaMalloc(&p->wbf, sizeof(uint16_t) * kMlpParams) != cudaSuccess ||
-      cudaMalloc(&p->y, sizeof(float) * max_batch * kMlpOut) != cudaSuccess ||
-      cudaMalloc(&p->dy, sizeof(float) * max_batch * kMlpOut) != cudaSuccess ||
-      cudaMalloc(&p->acts, 6 * nh) != cudaSuccess || cudaMalloc(&p->dzs, 3 * nh) != cudaSuccess ||
-      cudaMalloc(&p->loss_part, sizeof(double) * kLossParts) != cudaSuccess ||
-      cudaMallocHost(&p->h_loss_part, sizeof(double) * kLossParts) != cudaSuccess) {
+      cudaMalloc(&p->img, mlp_image_bytes()) != cudaSuccess) {
     mlp_free(p);
     delete p;
     return mfail(ctx, MK_ENOMEM, "surrogate MLP allocation");
@@ -121,7 +131,7 @@ extern "C" int mk_mlp_set_params(mk_mlp *p, const float *h_params) {
   CKM(ctx, cudaMemcpyAsync(p->master, h_params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice, st));
   CKM(ctx, cudaMemsetAsync(p->m, 0, sizeof(float) * kMlpParams, st));
   CKM(ctx, cudaMemsetAsync(p->v, 0, sizeof(float) * kMlpParams, st));
-  CKM(ctx, mlp_to_bf16(p->master, p->wbf, st));
+  CKM(ctx, mlp_pack(p->master, p->img, p->wbf, st));
   CKM(ctx, cudaStreamSynchronize(st));
   p->step = 0;
   return MK_OK;
@@ -134,7 +144,10 @@ extern "C" int mk_mlp_get_params(mk_mlp *p, float *h_params, uint16_t *h_bf16) {
   CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
   if (h_params)
     CKM(ctx, cudaMemcpyAsync(h_params, p->master, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st));
-  if (h_bf16) CKM(ctx, cudaMemcpyAsync(h_bf16, p->wbf, sizeof(uint16_t) * kMlpParams, cudaMemcpyDeviceToHost, st));
+  if (h_bf16) {
+    CKM(ctx, mlp_pack(p->master, p->img, p->wbf, st));  // the BF16 copy of the current master
+    CKM(ctx, cudaMemcpyAsync(h_bf16, p->wbf, sizeof(uint16_t) * kMlpParams, cudaMemcpyDeviceToHost, st));
+  }
   CKM(ctx, cudaStreamSynchronize(st));
   return MK_OK;
 }
@@ -143,7 +156,7 @@ extern "C" int mk_mlp_forward(mk_mlp *p, const float *d_x, int64_t n, float *d_y
   if (!p) return MK_EINVAL;
   if (n < 0 || (n > 0 && (!d_x || !d_y))) return mfail(p->ctx, MK_EINVAL, "bad forward arguments");
   CKM(p->ctx, cudaSetDevice(mkhost::ctx_device(p->ctx)));
-  CKM(p->ctx, mlp_forward(p->wbf, p->master, d_x, nullptr, n, d_y, nullptr, mkhost::ctx_stream(p->ctx)));
+  CKM(p->ctx, mlp_forward(p->img, d_x, n, d_y, mkhost::ctx_stream(p->ctx)));
   return MK_OK;
 }
 
@@ -154,14 +167,33 @@ extern "C" int mk_mlp_loss_grad(mk_mlp *p, const float *d_x, const float *d_t, i
   mk_ctx *ctx = p->ctx;
   cudaStream_t st = mkhost::ctx_stream(ctx);
   CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
-  CKM(ctx, mlp_gradient(p->wbf, p->master, d_x, d_t, nullptr, n, 1.0 / (static_cast<double>(n) * kMlpOut), p->y,
-                        p->dy, p->acts, p->dzs, p->grad, p->loss_part, st));
+  int rc = ensure_loss(p, 1);
+  if (rc) return rc;
+  // one step over all n samples (passes of kMlpChunk), no update
+  MlpRun R = run_args(p);
+  R.x = d_x;
+  R.t = d_t;
+  R.n = n;
+  R.batch = static_cast<int32_t>(std::min<int64_t>(n, INT32_MAX));
+  R.steps = 1;
+  R.inv_count = 1.0 / (static_cast<double>(n) * kMlpOut);
+  R.loss_out = p->d_loss;
+  CKM(ctx, mlp_cluster_run(R, st));
   if (h_grad)
     CKM(ctx, cudaMemcpyAsync(h_grad, p->grad, sizeof(float) * kMlpParams, cudaMemcpyDeviceToHost, st));
-  double loss = 0.0;
-  int rc = read_loss(p, &loss);  // synchronises
-  if (rc) return rc;
-  if (h_loss) *h_loss = loss;
+  CKM(ctx, cudaMemcpyAsync(p->h_loss, p->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKM(ctx, cudaStreamSynchronize(st));
+  if (h_loss) *h_loss = p->h_loss[0];
+  return MK_OK;
+}
+
+extern "C" int mk_mlp_adam_step(mk_mlp *p, const float *d_grad, float lr) {
+  if (!p) return MK_EINVAL;
+  if (!d_grad || !(lr > 0.f)) return mfail(p->ctx, MK_EINVAL, "mk_mlp_adam_step needs a gradient and lr > 0");
+  mk_ctx *ctx = p->ctx;
+  CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
+  CKM(ctx, mlp_adam(p->master, p->m, p->v, d_grad, p->img, lr, 0.9f, 0.999f, 1e-8f, ++p->step,
+                    mkhost::ctx_stream(ctx)));
   return MK_OK;
 }
 
@@ -174,42 +206,77 @@ extern "C" int mk_mlp_train(mk_mlp *p, const float *d_x, const float *d_t, int64
   if (n > INT32_MAX) return mfail(ctx, MK_EINVAL, "too many samples");
   cudaStream_t st = mkhost::ctx_stream(ctx);
   CKM(ctx, cudaSetDevice(mkhost::ctx_device(ctx)));
-  int32_t *d_rows = nullptr;
-  if (cudaMalloc(&d_rows, sizeof(int32_t) * n) != cudaSuccess) return mfail(ctx, MK_ENOMEM, "training index array");
+  const int64_t steps = (n + batch - 1) / batch;
+  int rc = ensure_loss(p, std::max<int64_t>(1, steps * epochs));
+  if (rc) return rc;
+  // per epoch: a shuffled sample order (host RNG), uploaded through two
+  // pinned buffers so that the next shuffle overlaps the running epoch
+  int32_t *d_rows[2] = {nullptr, nullptr}, *h_rows[2] = {nullptr, nullptr};
+  cudaEvent_t up[2] = {nullptr, nullptr};
+  bool ok = true;
+  for (int k = 0; k < 2 && ok; ++k)
+    ok = cudaMalloc(&d_rows[k], sizeof(int32_t) * n) == cudaSuccess &&
+         cudaMallocHost(&h_rows[k], sizeof(int32_t) * n) == cudaSuccess &&
+         cudaEventCreateWithFlags(&up[k], cudaEventDisableTiming) == cudaSuccess;
   std::vector<int32_t> perm(n);
   std::iota(perm.begin(), perm.end(), 0);
   std::mt19937_64 rng(seed);
-  int rc = MK_OK;
+  if (!ok) rc = mfail(ctx, MK_ENOMEM, "training index arrays");
   for (int e = 0; e < epochs && rc == MK_OK; ++e) {
     std::shuffle(perm.begin(), perm.end(), rng);
-    if (cudaMemcpyAsync(d_rows, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    const int k = e & 1;
+    if (e >= 2 && cudaEventSynchronize(up[k]) != cudaSuccess) {  // the copy from this buffer is done
       rc = mfail(ctx, MK_ECUDA, "training index upload");
       break;
     }
-    const double lr_e = lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * e / std::max(1, epochs))));
-    double esum = 0.0;
-    for (int64_t b0 = 0; b0 < n && rc == MK_OK; b0 += batch) {
-      const int64_t nb = std::min<int64_t>(batch, n - b0);
-      cudaError_t ce = mlp_gradient(p->wbf, p->master, d_x, d_t, d_rows + b0, nb,
-                                    1.0 / (static_cast<double>(nb) * kMlpOut), p->y, p->dy, p->acts, p->dzs, p->grad,
-                                    p->loss_part, st);
-      if (ce == cudaSuccess)
-        ce = mlp_adam(p->master, p->wbf, p->grad, p->m, p->v, static_cast<float>(lr_e), 0.9f, 0.999f, 1e-8f,
-                      ++p->step, st);
-      if (ce != cudaSuccess) {
-        rc = mfail(ctx, MK_ECUDA, cudaGetErrorString(ce));
-        break;
-      }
-      if (h_epoch_loss) {
-        double l = 0.0;
-        if ((rc = read_loss(p, &l))) break;
-        esum += l * nb;
-      }
+    std::memcpy(h_rows[k], perm.data(), sizeof(int32_t) * n);
+    if (cudaMemcpyAsync(d_rows[k], h_rows[k], sizeof(int32_t) * n, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(up[k], st) != cudaSuccess) {
+      rc = mfail(ctx, MK_ECUDA, "training index upload");
+      break;
     }
-    if (h_epoch_loss) h_epoch_loss[e] = esum / n;
+    MlpRun R = run_args(p);
+    R.x = d_x;
+    R.t = d_t;
+    R.rows = d_rows[k];
+    R.n = n;
+    R.batch = batch;
+    R.steps = static_cast<int32_t>(steps);
+    R.train = 1;
+    R.lr = static_cast<float>(lr * (0.05 + 0.95 * 0.5 * (1.0 + std::cos(M_PI * e / std::max(1, epochs)))));
+    R.t0 = p->step;
+    R.loss_out = p->d_loss + static_cast<int64_t>(e) * steps;
+    cudaError_t ce = mlp_cluster_run(R, st);
+    // the kernel updated the weight images in shared memory only: refresh the
+    // global image (the next launch and inference read it)
+    if (ce == cudaSuccess) ce = mlp_pack(p->master, p->img, nullptr, st);
+    if (ce != cudaSuccess) {
+      rc = mfail(ctx, MK_ECUDA, cudaGetErrorString(ce));
+      break;
+    }
+    p->step += steps;
   }
-  cudaStreamSynchronize(st);
-  cudaFree(d_rows);
+  if (rc == MK_OK && h_epoch_loss && epochs > 0) {
+    if (cudaMemcpyAsync(p->h_loss, p->d_loss, sizeof(double) * steps * epochs, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+      rc = mfail(ctx, MK_ECUDA, "training loss readback");
+  }
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == MK_OK) rc = mfail(ctx, MK_ECUDA, "training");
+  if (rc == MK_OK && h_epoch_loss) {
+    for (int e = 0; e < epochs; ++e) {  // mean over the epoch's samples
+      double s = 0.0;
+      for (int64_t i = 0; i < steps; ++i) {
+        const int64_t nb = std::min<int64_t>(batch, n - i * batch);
+        s += p->h_loss[e * steps + i] * nb;
+      }
+      h_epoch_loss[e] = s / n;
+    }
+  }
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(d_rows[k]);
+    cudaFreeHost(h_rows[k]);
+    if (up[k]) cudaEventDestroy(up[k]);
+  }
   return rc;
 }
 
