@@ -169,30 +169,50 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
     const int64_t out0 = sk.offset + j0;
     // warp-uniform: this warp's pixels of the segment all lie before pend
     const bool one_bin = min(T * 7 + wlo0 + 32, npx) <= pend;
+    // pixel p: gather, growth, small-scale field, FGPA, stores; returns F
+    auto synth = [&](int p, float2 &x) -> float {
+      float2 de;
+      if constexpr (INTERP == MK_INTERP_GAUSS7) {
+        static_assert(LAYOUT == MK_BOX_HALO, "the Gaussian kernel reads a halo box");
+        de = gather_gauss7<BIG>(P.box_d, P.lgn, px, py, pz);
+      } else if constexpr (LAYOUT == MK_BOX_TENSOR) {
+        de = gather_tensor<BIG>(P.box_d, P.lgn, px, py, pz, uu);
+      } else {
+        de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
+      }
+      const float4 tb = __ldg(P.pixtab + jb + p);
+      x = make_float2(fmaf(tb.x, de.x, fb[p]), tb.x * de.y);
+      const float f = fgpa(tb, x.x, x.y);
+      if (P.delta_out) {
+        P.delta_out[out0 + p] = x.x;
+        P.eta_out[out0 + p] = x.y;
+      }
+      if (P.flux_out) P.flux_out[out0 + p] = f;
+      return f;
+    };
+    // (the tensor and Gaussian-kernel gathers keep one loop: their registers
+    // do not leave room for a second copy)
+    constexpr bool kLean = LAYOUT != MK_BOX_TENSOR && INTERP == MK_INTERP_TRILINEAR;
+    if (kLean && npx == N && (!P.do_stats || one_bin)) {
+      // a full segment inside one z bin (most segments): no per-pixel bounds or bin checks
+#pragma unroll 2
+      for (int k = 0; k < 8; ++k) {
+        const int p = t + T * k;
+        float2 x;
+        const float f = synth(p, x);
+        if (P.do_stats) acc.add(f, x);
+        fb[p] = f;
+        px += sx;
+        py += sy;
+        pz += sz;
+      }
+    } else {
 #pragma unroll 2
     for (int k = 0; k < 8; ++k) {
       const int p = t + T * k;
       float f = 0.f;
       float2 x = make_float2(0.f, 0.f);
-      if (p < npx) {
-        float2 de;
-        if constexpr (INTERP == MK_INTERP_GAUSS7) {
-          static_assert(LAYOUT == MK_BOX_HALO, "the Gaussian kernel reads a halo box");
-          de = gather_gauss7<BIG>(P.box_d, P.lgn, px, py, pz);
-        } else if constexpr (LAYOUT == MK_BOX_TENSOR) {
-          de = gather_tensor<BIG>(P.box_d, P.lgn, px, py, pz, uu);
-        } else {
-          de = gather<LAYOUT, BIG>(P.box_d, P.box_e, P.lgn, px, py, pz);
-        }
-        const float4 tb = __ldg(P.pixtab + jb + p);
-        x = make_float2(fmaf(tb.x, de.x, fb[p]), tb.x * de.y);
-        f = fgpa(tb, x.x, x.y);
-        if (P.delta_out) {
-          P.delta_out[out0 + p] = x.x;
-          P.eta_out[out0 + p] = x.y;
-        }
-        if (P.flux_out) P.flux_out[out0 + p] = f;
-      }
+      if (p < npx) f = synth(p, x);
       if (P.do_stats && one_bin) {
         if (p < npx) acc.add(f, x);
       } else if (P.do_stats) {
@@ -215,6 +235,7 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
       px += sx;
       py += sy;
       pz += sz;
+    }
     }
 
     // ---- P1D of the segment
@@ -299,6 +320,25 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
       int pend = __ldg(P.bin_end + zc + 1) - jb;  // segment pixel where bin zc ends
       // warp-uniform: this warp's pixels of the segment all lie before pend
       const bool one_bin = min(T * 7 + wlo0 + 32, npx) <= pend;
+      if (npx == N && one_bin && P.pixtab) {
+        // tuning pass over a full segment inside one z bin: no bounds or bin checks
+        const float *dp = P.delta + sk.offset + k0 + t, *ep = P.eta + sk.offset + k0 + t;
+        const float4 *tp = P.pixtab + sk.j_lo + k0 + t;
+        float dv[8], ev[8];
+        float4 tb[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          dv[q] = __ldg(dp + T * q);
+          ev[q] = __ldg(ep + T * q);
+          tb[q] = __ldg(tp + T * q);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float f = fgpa(tb[q], dv[q], ev[q]);
+          acc.add(f, make_float2(dv[q], ev[q]));
+          fb[t + T * q] = f;
+        }
+      } else {
       // streaming case: issue every load of the thread's 8 pixels before any use
       float dv[8], ev[8], fv[8];
       float4 tb[8];
@@ -341,6 +381,7 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
           if (todo) acc.add(f, x);
         }
         fb[p] = f;
+      }
       }
     } else {
       const int zf = zbin_of(k0), zl = zbin_of(k0 + npx - 1);
