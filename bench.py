@@ -237,24 +237,18 @@ def run_reference(args, rank):
 
 
 # ---------------------------------------------------------------- tuning A/B
-def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None):
-    """Plain vs surrogate tuning of ln a, b, c at the 12 z nodes on the stored
-    skewers of the benchmark catalogue; the surrogate is trained on
-    constant-parameter passes over 100k quasars: the first 100k of the same
-    catalogue ("subset") or a separate 512^3 box ("box512")."""
+def surrogate_leg(ctx, mk, w, r, n_q, target, nd0, dev, draws, held, epochs, source, slopes):
+    """Train the surrogate on constant-parameter passes over 100k quasars (the
+    first 100k stored skewers of the benchmark catalogue, "subset", or a
+    separate 512^3 box with its own 100k quasars, "box512"), measure it on
+    `held` fresh draws, and run the surrogate-driven tuning of the benchmark
+    catalogue with it (every accepted set verified by full plain passes)."""
     import torch
-    from paper_2310_18996_gb300 import tuning
 
-    r = ctx.make_skewers(box, qso, n_q, w)  # stored pre-FGPA skewers (untimed)
-    target, _ = tuning.make_target(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], seed=7)
-    nd0 = tuning.start_nodes(w)
-    nd_p, rep_p = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
-                          method=mk.TUNE_PLAIN, max_passes=200)
-    # surrogate training set: constant-parameter passes over 100k quasars
-    if source == "subset":   # the first 100k stored skewers of the same box
+    if source == "subset":
         ws, n_lab = w, 100_000
         rs = {"sk": r["sk"], "offsets": r["offsets"], "delta": r["delta"], "eta": r["eta"]}
-    else:                    # a separate 512^3 box, same recipe and binning
+    else:
         ws = si.shrink(w, n=512, n_q=100_000)
         ws["seed_box"], ws["seed_cat"] = w["seed_box"] + 1, w["seed_cat"] + 1
         d, e = si.gaussian_box(ws["n"], ws["cell"], ws["seed_box"], backend="torch", device=dev)
@@ -273,43 +267,62 @@ def tuning_ab(ctx, mk, box, qso, n_q, w, dev, draws, epochs, source, slopes=None
     t_fit = time.perf_counter() - t0
     if source == "subset":  # labelled on the first n_lab skewers of this catalogue: calibrate on them
         norm.calib_skewers = n_lab
-    # held-out check: fresh draws (another seed) through the trained network
     vx, vt = mk.surrogate_labels(ctx, ws, rs["sk"], n_lab, rs["offsets"], rs["delta"], rs["eta"],
-                                 n_draws=max(draws // 10, 10), seed=12, slopes=slopes)
+                                 n_draws=held, seed=12, slopes=slopes)
     xm, xs = np.ctypeslib.as_array(norm.x_mean), np.ctypeslib.as_array(norm.x_std)
     tm, ts = np.ctypeslib.as_array(norm.t_mean), np.ctypeslib.as_array(norm.t_std)
     xin = torch.from_numpy(((vx - xm) / xs).astype(np.float32)).to(dev)
     pred = torch.cat([mlp.forward(xin[i:i + 1024].contiguous()) for i in range(0, xin.shape[0], 1024)])
     pred = pred.double().cpu().numpy() * ts + tm
     err = pred - vt
-    held = {"samples": int(vx.shape[0]), "draws": max(draws // 10, 10),
-            "mean_flux_rms": float(np.sqrt(np.mean(err[:, 0] ** 2))),
-            "mean_flux_max": float(np.abs(err[:, 0]).max()),
-            "beta_rel_rms": float(np.sqrt(np.mean((err[:, 2] / vt[:, 2]) ** 2))),
-            "ln_p1d_rms": float(np.sqrt(np.mean(err[:, 3:] ** 2)))}
-    nd_s, rep_s = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
-                          method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm, max_passes=60)
+    held_out = {"draws": held, "samples": int(vx.shape[0]),
+                "mean_flux_rms": float(np.sqrt(np.mean(err[:, 0] ** 2))),
+                "mean_flux_max": float(np.abs(err[:, 0]).max()),
+                "beta_rel_rms": float(np.sqrt(np.mean((err[:, 2] / vt[:, 2]) ** 2))),
+                "ln_p1d_rms": float(np.sqrt(np.mean(err[:, 3:] ** 2)))}
+    _, rep_s = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
+                       method=mk.TUNE_SURROGATE, mlp=mlp, norm=norm, max_passes=60)
     mlp.close()
-    del r, rs
+    del rs
     torch.cuda.empty_cache()
+    return rep_s, {"source": source, "box": "1024^3 (first 100k skewers)" if source == "subset" else "512^3",
+                   "quasars": 100_000, "draws": draws, "samples": int(hx.shape[0]), "epochs": epochs,
+                   "profiles": ("linear in z, slopes up to d ln a/dz, db/dz, dc/dz = "
+                                f"{slopes[0]}, {slopes[1]}, {slopes[2]}" if slopes else "constant"),
+                   "label_s": t_lab, "fit_s": t_fit, "final_loss": float(losses[-1]) if len(losses) else None,
+                   "held_out": held_out}
+
+
+def tuning_ab(ctx, mk, box, qso, n_q, w, dev, legs, epochs, slopes=None):
+    """Plain vs surrogate tuning of ln a, b, c at the 12 z nodes on the stored
+    skewers of the benchmark catalogue; one surrogate run per (source, draws,
+    held-out draws) leg."""
+    import torch
+    from paper_2310_18996_gb300 import tuning
+
+    r = ctx.make_skewers(box, qso, n_q, w)  # stored pre-FGPA skewers (untimed)
+    target, _ = tuning.make_target(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], seed=7)
+    nd0 = tuning.start_nodes(w)
+    _, rep_p = mk.tune(ctx, w, r["sk"], n_q, r["offsets"], r["delta"], r["eta"], target, nd0,
+                       method=mk.TUNE_PLAIN, max_passes=200)
 
     def rep(x):
         return {"converged": bool(x.converged), "passes": x.passes, "calib_passes": x.calib_passes,
                 "gpu_ms": x.gpu_ms, "wall_ms": x.wall_ms,
                 "max_abs_dfbar": x.max_abs_dfbar, "max_rel_p1d": x.max_rel_p1d, "max_rel_beta": x.max_rel_beta}
 
-    return {"workload": "stored skewers of the benchmark catalogue (1024^3, 1M quasars), 12 z nodes, target "
-                        "Fbar = exp(-0.0025 (1+z)^3.7) +- 1e-3, P1D and beta_F of seeded hidden power laws +- 2%",
-            "plain": rep(rep_p), "surrogate": rep(rep_s),
-            "gpu_time_ratio_plain_over_surrogate": rep_p.gpu_ms / max(rep_s.gpu_ms, 1e-9),
-            "wall_time_ratio_including_training": rep_p.wall_ms / (rep_s.wall_ms + 1000.0 * (t_lab + t_fit)),
-            "surrogate_training": {"source": source, "box": "1024^3" if source == "subset" else "512^3",
-                                   "quasars": 100_000, "draws": draws, "samples": int(hx.shape[0]),
-                                   "profiles": ("linear in z, slopes up to d ln a/dz, db/dz, dc/dz = "
-                                                f"{slopes[0]}, {slopes[1]}, {slopes[2]}" if slopes else "constant"),
-                                   "label_s": t_lab, "fit_s": t_fit, "epochs": epochs,
-                                   "final_loss": float(losses[-1]) if len(losses) else None,
-                                   "held_out": held}}
+    out = {"workload": "stored skewers of the benchmark catalogue (1024^3, 1M quasars), 12 z nodes, target "
+                       "Fbar = exp(-0.0025 (1+z)^3.7) +- 1e-3, P1D and beta_F of seeded hidden power laws +- 2%",
+           "plain": rep(rep_p)}
+    for name, source, draws, held in legs:
+        rep_s, info = surrogate_leg(ctx, mk, w, r, n_q, target, nd0, dev, draws, held, epochs, source, slopes)
+        out[name] = {"surrogate": rep(rep_s), "training": info,
+                     "gpu_time_ratio_plain_over_surrogate": rep_p.gpu_ms / max(rep_s.gpu_ms, 1e-9),
+                     "wall_time_ratio_including_training":
+                         rep_p.wall_ms / (rep_s.wall_ms + 1000.0 * (info["label_s"] + info["fit_s"]))}
+    del r
+    torch.cuda.empty_cache()
+    return out
 
 
 # ---------------------------------------------------------------- box synthesis (Sec. 2.1)
@@ -704,8 +717,10 @@ def run_gb300(args, rank, world, local_rank):
     tune = None
     if rank == 0 and world == 1 and not args.no_tuning:
         slopes = None if args.surrogate_slopes == "none" else tuple(float(v) for v in args.surrogate_slopes.split(","))
-        tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, args.surrogate_draws, args.surrogate_epochs,
-                         args.surrogate_source, slopes)
+        legs = [("surrogate_subset", "subset", args.surrogate_draws, max(args.surrogate_draws // 10, 10))]
+        if args.config4_draws > 0:
+            legs.append(("surrogate_512", "box512", args.config4_draws, args.config4_held))
+        tune = tuning_ab(ctx, mk, box, qso, n_q, w, dev, legs, args.surrogate_epochs, slopes)
     boxs = None
     if rank == 0 and world == 1 and not args.no_box_synth and w["n"] in (128, 256, 512, 1024):
         boxs = box_synth_leg(ctx, mk, w, dev, peak)
@@ -789,7 +804,9 @@ def main():
     ap.add_argument("--surrogate-epochs", type=int, default=300)
     ap.add_argument("--surrogate-slopes", default="1.8,0.45,0.45",
                     help="maxima of d ln a/dz, db/dz, dc/dz of the training profiles, or 'none'")
-    ap.add_argument("--surrogate-source", default="subset", choices=["subset", "box512"])
+    ap.add_argument("--config4-draws", type=int, default=20000,
+                    help="draws of the surrogate labelled on a separate 512^3 box (0: leg off)")
+    ap.add_argument("--config4-held", type=int, default=2000, help="held-out draws of that surrogate")
     ap.add_argument("--box-n", type=int, default=None, help="smaller box (profiling runs)")
     ap.add_argument("--n-q", type=int, default=None, help="fewer quasars (profiling runs)")
     args = ap.parse_args()
