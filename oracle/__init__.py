@@ -120,7 +120,7 @@ def lib():
                 "orc_stats_accumulate": (C.c_int, [P(Cfg), P(Bins), i32, P(i32), P(i64),
                                                    P(i64), i64, P(d), P(d), P(d), P(Stats)]),
                 "orc_stats_finalize": (None, [P(Bins), P(Stats)]),
-                "orc_mlp_forward": (None, [P(d), P(d), i64, P(d), C.c_int, P(d)]),
+                "orc_mlp_forward": (None, [P(d), P(d), i64, P(d), C.c_int]),
                 "orc_mlp_loss_grad": (d, [P(d), P(d), P(d), i64, P(d), C.c_int]),
                 "orc_bf16": (d, [d]),
                 "orc_adam_step": (None, [P(d), P(d), P(d), P(d), i64, i64, d, d, d, d]),
@@ -380,18 +380,15 @@ def gelu(x):
     return lib().orc_gelu(float(x))
 
 
-def mlp_forward(params, x, bf16=False, margin=False):
+def mlp_forward(params, x, bf16=False):
     """FP64 forward of the 4-128-128-128-35 GELU MLP; x (n, 4) -> (n, 35).
-    bf16: hidden activations rounded to BF16 (the tensor-core operands).
-    margin: also return, per sample, the smallest relative distance of a
-    rounded activation from a BF16 rounding boundary."""
+    bf16: hidden activations rounded to BF16 (the tensor-core operands of
+    training)."""
     p = np.ascontiguousarray(params, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 4)
     y = np.zeros((x.shape[0], 35))
-    mg = np.zeros(x.shape[0])
-    lib().orc_mlp_forward(_p(p, C.c_double), _p(x, C.c_double), x.shape[0], _p(y, C.c_double), int(bf16),
-                          _p(mg, C.c_double))
-    return (y, mg) if margin else y
+    lib().orc_mlp_forward(_p(p, C.c_double), _p(x, C.c_double), x.shape[0], _p(y, C.c_double), int(bf16))
+    return y
 
 
 def mlp_loss_grad(params, x, t, bf16=False):

@@ -756,29 +756,11 @@ double orc_bf16(double x) {
   return (double)f;
 }
 
-/* Relative distance of x from the nearest point where its BF16 rounding
-   changes (the midpoint between the two BF16 values around x); infinite for
-   0.  A kernel that computes x with relative error e may round it the other
-   way only where this is below e. */
-static double bf16_margin(double x) {
-  if (x == 0.0 || !isfinite(x)) return INFINITY;
-  const float f = (float)x;
-  uint32_t u;
-  memcpy(&u, &f, sizeof u);
-  const uint32_t lo_bits = u & 0xFFFF0000u, hi_bits = lo_bits + 0x10000u;
-  float lo, hi;
-  memcpy(&lo, &lo_bits, sizeof lo);
-  memcpy(&hi, &hi_bits, sizeof hi);
-  return fabs(x - 0.5 * ((double)lo + (double)hi)) / fabs(x);
-}
-
 /* forward of one sample; z[l], h[l] hold layer l's pre- and post-activation.
    bf16: the hidden activations are stored as BF16 operands (h[l] rounded);
-   the output layer stays unrounded.  Returns the smallest bf16_margin of the
-   rounded activations (infinite without bf16). */
-static double mlp_sample(const double *p, const double *x, double z[4][128], double h[4][128],
-                         double *y, int bf16) {
-  double margin = INFINITY;
+   the output layer stays unrounded. */
+static void mlp_sample(const double *p, const double *x, double z[4][128], double h[4][128],
+                       double *y, int bf16) {
   int64_t wo[4], bo[4];
   mlp_offsets(wo, bo);
   const double *in = x;
@@ -789,25 +771,16 @@ static double mlp_sample(const double *p, const double *x, double z[4][128], dou
       for (int k = 0; k < ni; ++k) s += p[wo[l] + (int64_t)j * ni + k] * in[k];
       z[l][j] = s;
       h[l][j] = (l < 3) ? orc_gelu(s) : s;
-      if (bf16 && l < 3) {
-        const double mg = bf16_margin(h[l][j]);
-        if (mg < margin) margin = mg;
-        h[l][j] = orc_bf16(h[l][j]);
-      }
+      if (bf16 && l < 3) h[l][j] = orc_bf16(h[l][j]);
     }
     in = h[l];
   }
   for (int j = 0; j < mlp_dims[4]; ++j) y[j] = h[3][j];
-  return margin;
 }
 
-void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y, int bf16,
-                     double *margin) {
+void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y, int bf16) {
   double z[4][128], h[4][128];
-  for (int64_t s = 0; s < n; ++s) {
-    const double mg = mlp_sample(params, x + 4 * s, z, h, y + 35 * s, bf16);
-    if (margin) margin[s] = mg;
-  }
+  for (int64_t s = 0; s < n; ++s) mlp_sample(params, x + 4 * s, z, h, y + 35 * s, bf16);
 }
 
 /* Adam (Kingma & Ba 2015, Algorithm 1), step t >= 1 on n parameters:

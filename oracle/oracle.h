@@ -166,11 +166,8 @@ void orc_stats_finalize(const orc_bins *bins, orc_stats *st);
    W3 [35x128], b3, each W row-major [out][in]; 38179 values. */
 #define ORC_MLP_NPARAM 38179
 /* bf16 != 0: the hidden activations are rounded to BF16 (the operands the
-   tensor cores take); bf16 = 0: plain FP64 throughout.  margin (n values, or
-   NULL): per sample, the smallest relative distance of a rounded activation
-   from the point where its BF16 rounding would change. */
-void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y, int bf16,
-                     double *margin);
+   tensor cores take in training); bf16 = 0: plain FP64 throughout. */
+void orc_mlp_forward(const double *params, const double *x, int64_t n, double *y, int bf16);
 /* mean squared error over n samples and 35 outputs, and its gradient; with
    bf16 the backward operands dy and dz are rounded to BF16 as well */
 double orc_mlp_loss_grad(const double *params, const double *x, const double *t, int64_t n,

@@ -3,11 +3,14 @@
 // Tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation) run
 // every 128-wide product: the hidden layers, the output layer, the backward
 // products dh = dz W and the weight gradients dW = dz^T h.  Operand precision
-// (the same on the FP64 oracle's BF16 path): weights BF16 (rounded from an
-// FP32 master copy that Adam updates); hidden activations stored as BF16; the
-// output y in FP32; the backward operands dy and dz = dh * GELU'(z) rounded to
-// BF16, with GELU'(z) from the FP32 pre-activation.  The 4-wide first layer
-// and its weight gradient run on the FP32 cores with FP32 inputs.
+// in training (the same on the FP64 oracle's BF16 path): weights BF16
+// (rounded from an FP32 master copy that Adam updates); hidden activations
+// stored as BF16; the output y in FP32; the backward operands dy and
+// dz = dh * GELU'(z) rounded to BF16, with GELU'(z) from the FP32
+// pre-activation.  Inference takes each hidden activation as two BF16 terms
+// (hi + lo), so that its outputs are smooth in the inputs: the tuning
+// differentiates them.  The 4-wide first layer and its weight gradient run
+// on the FP32 cores with FP32 inputs.
 //
 // Training: one cluster of 8 CTAs runs a whole epoch in one launch.  Each CTA
 // takes 32 samples of a step; per layer it writes its partial weight and bias
@@ -70,13 +73,21 @@ struct Wk {
   static constexpr int H2 = H1 + kS * kLd * 2;
   static constexpr int Y = H2 + kS * kLd * 2;    // FP32 [32][kOutP]
   static constexpr int FWD_END = Y + kS * kOutP * 4;
+  // inference keeps each hidden activation as two BF16 terms: the low terms
+  // (BF16 [32][kLd] each) in space the training buffers use
+  static constexpr int HL0 = FWD_END;
+  static constexpr int HL1 = HL0 + kS * kLd * 2;
+  static constexpr int HL2 = HL1 + kS * kLd * 2;
+  static constexpr int INFER_END = HL2 + kS * kLd * 2;
   static constexpr int DA = FWD_END;             // BF16 [32][kLd]: dz ping-pong
   static constexpr int DB = DA + kS * kLd * 2;
   static constexpr int DY = DB + kS * kLd * 2;   // BF16 [32][kLdY]
   static constexpr int P = DY + kS * kLdY * 2;   // FP32 [128][kLdP] weight-gradient partials
   static constexpr int PB = P + 128 * kLdP * 4;  // FP32 [128] bias-gradient partials
   static constexpr int RED = PB + 128 * 4;       // FP64 [8] warp loss partials, [8] CTA loss
-  static constexpr int END = RED + 16 * 8;
+  static constexpr int TG = RED + 16 * 8;        // FP32 [32][36] targets of the pass
+  static constexpr int ROWS = TG + kS * 36 * 4;  // int64 [32] sample rows of the pass
+  static constexpr int END = ROWS + kS * 8;
 };
 static_assert(Wk::END <= 227 * 1024, "shared memory plan exceeds 227 KB");
 
@@ -116,9 +127,10 @@ __device__ __forceinline__ const T *remote(const T *p, uint32_t rank) {
   return static_cast<const T *>(__cluster_map_shared_rank(const_cast<T *>(p), rank));
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * erfcf(-x * 0.70710678118654752f); }
-__device__ __forceinline__ float gelu_deriv(float x) {
-  return 0.5f * erfcf(-x * 0.70710678118654752f) + x * 0.39894228040143268f * __expf(-0.5f * x * x);
+// GELU(x) = x Phi(x) and its derivative Phi(x) + x phi(x), from one erfc
+__device__ __forceinline__ float normal_cdf(float x) { return 0.5f * erfcf(-x * 0.70710678118654752f); }
+__device__ __forceinline__ float gelu_deriv_from(float x, float cdf) {
+  return cdf + x * 0.39894228040143268f * __expf(-0.5f * x * x);
 }
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -204,16 +216,18 @@ __device__ __forceinline__ void load_image(unsigned char *sm, const unsigned cha
 // elements).  TRANS_W = false: B(k, n) = W[n][k] (forward); true: B(k, n) =
 // W[k][n] (backward).  Warp w: rows 16 (w & 1) .. + 15, columns
 // 32 (w >> 1) .. + 31 (4 tiles of 8); acc[nt][0..3] is the m16n8 fragment.
-template <bool TRANS_W>
+template <bool TRANS_W, bool ZERO = true>
 __device__ __forceinline__ void gemm_s(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *W, int ldw, int K,
                                        float (&acc)[4][4]) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int s0 = 16 * (w & 1), n0 = 32 * (w >> 1);
   const int q = lane >> 3, r8 = lane & 7;
+  if (ZERO) {
 #pragma unroll
-  for (int nt = 0; nt < 4; ++nt)
+    for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
-    for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+      for (int i = 0; i < 4; ++i) acc[nt][i] = 0.f;
+  }
   const uint32_t a_base = saddr(A + (s0 + r8 + 8 * (q & 1)) * lda + 8 * (q >> 1));
   for (int k0 = 0; k0 < K; k0 += 16) {
     uint32_t a[4];
@@ -278,14 +292,21 @@ __device__ __forceinline__ void gemm_w(const __nv_bfloat16 *D, int ldd, const __
 // ------------------------------------------------------------------ forward of 32 samples
 // X (FP32 [32][4]) in shared memory -> H0, H1, H2 (BF16) and Y (FP32
 // [32][kOutP], 35 used).  With KEEP_G the GELU derivatives of the three hidden
-// layers stay in G[l] in the fragment layout of gemm_s.
-template <bool KEEP_G>
+// layers stay in G[l] in the fragment layout of gemm_s.  SPLIT (inference):
+// each activation h is kept as hi = bf16(h) in H and lo = bf16(h - hi) in
+// HL, and every product takes both terms, so the activations enter the
+// tensor cores with ~16 significant bits and the outputs are a smooth
+// function of the inputs (training rounds them to one BF16 term).
+template <bool KEEP_G, bool SPLIT = false>
 __device__ __forceinline__ void forward32(unsigned char *sm, float (&G)[3][4][4]) {
   const float *X = reinterpret_cast<const float *>(sm + Wk::X);
   const float *W0 = reinterpret_cast<const float *>(sm + Img::W0);
   __nv_bfloat16 *H[3] = {reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H0),
                          reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H1),
                          reinterpret_cast<__nv_bfloat16 *>(sm + Wk::H2)};
+  __nv_bfloat16 *HL[3] = {reinterpret_cast<__nv_bfloat16 *>(sm + Wk::HL0),
+                          reinterpret_cast<__nv_bfloat16 *>(sm + Wk::HL1),
+                          reinterpret_cast<__nv_bfloat16 *>(sm + Wk::HL2)};
   const float *B[3] = {reinterpret_cast<const float *>(sm + Img::B0), reinterpret_cast<const float *>(sm + Img::B1),
                        reinterpret_cast<const float *>(sm + Img::B2)};
   const __nv_bfloat16 *Wl[3] = {nullptr, reinterpret_cast<const __nv_bfloat16 *>(sm + Img::W1),
@@ -306,6 +327,7 @@ __device__ __forceinline__ void forward32(unsigned char *sm, float (&G)[3][4][4]
         }
     } else {
       gemm_s<false>(H[l - 1], kLd, Wl[l], kLd, 128, acc);
+      if (SPLIT) gemm_s<false, false>(HL[l - 1], kLd, Wl[l], kLd, 128, acc);
     }
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
@@ -314,11 +336,15 @@ __device__ __forceinline__ void forward32(unsigned char *sm, float (&G)[3][4][4]
         int s, j;
         frag_pos(nt, 2 * h, s, j);
         const float z0 = acc[nt][2 * h] + B[l][j], z1 = acc[nt][2 * h + 1] + B[l][j + 1];
+        const float p0 = normal_cdf(z0), p1 = normal_cdf(z1);
         if (KEEP_G) {
-          G[l][nt][2 * h] = gelu_deriv(z0);
-          G[l][nt][2 * h + 1] = gelu_deriv(z1);
+          G[l][nt][2 * h] = gelu_deriv_from(z0, p0);
+          G[l][nt][2 * h + 1] = gelu_deriv_from(z1, p1);
         }
-        *reinterpret_cast<uint32_t *>(H[l] + s * kLd + j) = pack_bf16(gelu(z0), gelu(z1));
+        const float h0 = z0 * p0, h1 = z1 * p1;
+        *reinterpret_cast<uint32_t *>(H[l] + s * kLd + j) = pack_bf16(h0, h1);
+        if (SPLIT)
+          *reinterpret_cast<uint32_t *>(HL[l] + s * kLd + j) = pack_bf16(h0 - bf16_val(h0), h1 - bf16_val(h1));
       }
     __syncthreads();
   }
@@ -336,6 +362,10 @@ __device__ __forceinline__ void forward32(unsigned char *sm, float (&G)[3][4][4]
         uint32_t a[4];
         ldsm4(saddr(H[2] + (16 * mt + r8 + 8 * (q & 1)) * kLd + k0 + 8 * (q >> 1)), a);
         mma16816(acc[mt], a, b[0], b[1]);
+        if (SPLIT) {
+          ldsm4(saddr(HL[2] + (16 * mt + r8 + 8 * (q & 1)) * kLd + k0 + 8 * (q >> 1)), a);
+          mma16816(acc[mt], a, b[0], b[1]);
+        }
       }
     }
     float *Y = reinterpret_cast<float *>(sm + Wk::Y);
@@ -370,6 +400,36 @@ __device__ __forceinline__ void load_x(unsigned char *sm, const float *x, const 
   __syncthreads();
 }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Training pass of samples [i0, i0 + cnt): their rows, their inputs X (ready
+// on return), and their targets, copied asynchronously into TG (complete
+// after cp_async_wait_all and a barrier).
+__device__ __forceinline__ void load_pass(unsigned char *sm, const MlpRun &R, int64_t i0, int cnt) {
+  int64_t *rows = reinterpret_cast<int64_t *>(sm + Wk::ROWS);
+  if (threadIdx.x < kS) {
+    const int64_t i = i0 + threadIdx.x;
+    rows[threadIdx.x] = threadIdx.x < cnt ? (R.rows ? R.rows[R.base + i] : R.base + i) : 0;
+  }
+  __syncthreads();
+  float *X = reinterpret_cast<float *>(sm + Wk::X);
+  if (threadIdx.x < kS * 4) {
+    const int s = threadIdx.x >> 2, k = threadIdx.x & 3;
+    X[threadIdx.x] = s < cnt ? R.x[rows[s] * 4 + k] : 0.f;
+  }
+  float *T = reinterpret_cast<float *>(sm + Wk::TG);
+  for (int e = threadIdx.x; e < cnt * kMlpOut; e += blockDim.x) {
+    const int s = e / kMlpOut, j = e % kMlpOut;
+    cp_async4(T + s * 36 + j, R.t + rows[s] * kMlpOut + j);
+  }
+  cp_async_commit();
+  __syncthreads();
+}
+
 // ------------------------------------------------------------------ inference
 __global__ void __launch_bounds__(kThr, 1) k_mlp_forward(const unsigned char *__restrict__ gimg,
                                                           const float *__restrict__ x, int64_t n, float *y) {
@@ -379,7 +439,7 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_forward(const unsigned char *__
   const int cnt = static_cast<int>(n - i0 < kS ? n - i0 : kS);
   load_x(sm, x, nullptr, 0, i0, cnt);  // (its barrier also covers the image)
   float G[3][4][4];
-  forward32<false>(sm, G);
+  forward32<false, true>(sm, G);
   const float *Y = reinterpret_cast<const float *>(sm + Wk::Y);
   for (int e = threadIdx.x; e < cnt * kMlpOut; e += blockDim.x) {
     const int s = e / kMlpOut, j = e % kMlpOut;
@@ -388,8 +448,34 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_forward(const unsigned char *__
 }
 
 // ------------------------------------------------------------------ training cluster
-// Owned slice of layer l's gradient (weights then bias, canonical order):
-// [rank L / 8, (rank + 1) L / 8), L = dim(l+1) (dim(l) + 1).  Sums the 8 CTAs'
+// Four consecutive parameters i .. i + 3 (i a multiple of 4, inside one
+// weight row or among the biases) into every CTA's shared-memory image.
+__device__ __forceinline__ void image_put4_cluster(unsigned char *sm, int i, float4 p) {
+  const Slot sl = image_slot(i);
+  if (sl.bf16) {
+    uint2 v;
+    v.x = pack_bf16(p.x, p.y);
+    v.y = pack_bf16(p.z, p.w);
+#pragma unroll
+    for (int c = 0; c < kCl; ++c)
+      *static_cast<uint2 *>(__cluster_map_shared_rank(static_cast<void *>(sm + sl.off), c)) = v;
+  } else {
+    const float4 v = make_float4(image_value(i, p.x), image_value(i, p.y), image_value(i, p.z), image_value(i, p.w));
+#pragma unroll
+    for (int c = 0; c < kCl; ++c)
+      *static_cast<float4 *>(__cluster_map_shared_rank(static_cast<void *>(sm + sl.off), c)) = v;
+  }
+}
+
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// Owned slice of layer l's gradient (weights then bias, canonical order), in
+// groups of four parameters: groups [rank G / 8, (rank + 1) G / 8) of the
+// layer's G = ceil(L / 4), L = dim(l+1) (dim(l) + 1).  Sums the 8 CTAs'
 // partials (ranks in order).  adam: apply the Adam step to the slice at once
 // (the step has one pass) and write the new weights into every CTA's
 // shared-memory image; otherwise store (or add) the sums into grad.
@@ -398,34 +484,55 @@ struct AdamArgs {
 };
 __device__ __forceinline__ void reduce_owned(unsigned char *sm, int l, uint32_t rank, const MlpRun &R, bool add,
                                              bool adam, const AdamArgs &A) {
-  const int ni = dim(l), no = dim(l + 1), L = no * (ni + 1);
-  const int q0 = static_cast<int>(rank) * L / kCl, q1 = (static_cast<int>(rank) + 1) * L / kCl;
+  const int ni = dim(l), no = dim(l + 1), L = no * (ni + 1), G = (L + 3) / 4;
+  const int g0 = static_cast<int>(rank) * G / kCl, g1 = (static_cast<int>(rank) + 1) * G / kCl;
   const float *P = reinterpret_cast<const float *>(sm + Wk::P);
   const float *PB = reinterpret_cast<const float *>(sm + Wk::PB);
   float *__restrict__ master = R.master;
   float *__restrict__ mm = R.m;
   float *__restrict__ vv = R.v;
   float *__restrict__ grad = R.grad;
-  for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-    const int i = w_off(l) + q;
-    float p = 0.f, m = 0.f, v = 0.f;
-    if (adam) {  // issued before the partials are read
-      p = master[i];
-      m = mm[i];
-      v = vv[i];
+  for (int gi = g0 + threadIdx.x; gi < g1; gi += blockDim.x) {
+    const int q = 4 * gi, i = w_off(l) + q;
+    const bool full = q + 4 <= L;  // only the last group of a layer may be short
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), m = p, v = p;
+    if (adam && full) {  // issued before the partials are read
+      p = ld4(master + i);
+      m = ld4(mm + i);
+      v = ld4(vv + i);
     }
+    // (rows of P and the bias partials both hold the whole group, in bounds)
     const float *a = q < no * ni ? P + (q / ni) * kLdP + q % ni : PB + (q - no * ni);
-    float s = 0.f;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int c = 0; c < kCl; ++c) s += *remote(a, c);
-    if (adam) {
-      adam_one(p, m, v, s, A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
-      master[i] = p;
-      mm[i] = m;
-      vv[i] = v;
-      image_put_cluster(sm, i, p);
+    for (int c = 0; c < kCl; ++c) s = add4(s, ld4(remote(a, c)));
+    if (full) {
+      if (adam) {
+        adam_one(p.x, m.x, v.x, s.x, A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+        adam_one(p.y, m.y, v.y, s.y, A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+        adam_one(p.z, m.z, v.z, s.z, A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+        adam_one(p.w, m.w, v.w, s.w, A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+        st4(master + i, p);
+        st4(mm + i, m);
+        st4(vv + i, v);
+        image_put4_cluster(sm, i, p);
+      } else {
+        st4(grad + i, add ? add4(ld4(grad + i), s) : s);
+      }
     } else {
-      grad[i] = add ? grad[i] + s : s;
+      const float sv[4] = {s.x, s.y, s.z, s.w};
+      for (int e = 0; e < L - q; ++e) {
+        if (adam) {
+          float pe = master[i + e], me = mm[i + e], ve = vv[i + e];
+          adam_one(pe, me, ve, sv[e], A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
+          master[i + e] = pe;
+          mm[i + e] = me;
+          vv[i + e] = ve;
+          image_put_cluster(sm, i + e, pe);
+        } else {
+          grad[i + e] = add ? grad[i + e] + sv[e] : sv[e];
+        }
+      }
     }
   }
 }
@@ -484,19 +591,20 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_tra
     for (int c = 0; c < chunks; ++c) {
       chunk_range(R, st, c, rank, i0, cnt, step_n);
       const bool add = R.accumulate || c > 0;
-      load_x(sm, R.x, R.rows, R.base, i0, cnt);
+      load_pass(sm, R, i0, cnt);
       float G[3][4][4];
       forward32<true>(sm, G);
+      cp_async_wait_all();  // the targets (copied during the forward pass)
+      __syncthreads();
 
       // ---- loss and output gradient dy (BF16), zero past the valid samples and outputs
+      const float *T = reinterpret_cast<const float *>(sm + Wk::TG);
       double lsum = 0.0;
       for (int e = tid; e < kS * 48; e += kThr) {
         const int s = e / 48, j = e % 48;
         float d = 0.f;
         if (s < cnt && j < kMlpOut) {
-          const int64_t i = i0 + s;
-          const int64_t row = R.rows ? R.rows[R.base + i] : R.base + i;
-          const float r = Y[s * kOutP + j] - R.t[row * kMlpOut + j];
+          const float r = Y[s * kOutP + j] - T[s * 36 + j];
           lsum += static_cast<double>(r) * r * inv;
           d = static_cast<float>(2.0 * inv) * r;
         }
@@ -588,10 +696,10 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_tra
     if (R.train && !fuse) {
       // several passes: Adam on this CTA's eighth of every layer from the
       // summed gradient; the new weights go to every CTA's image
-      for (int l = 0; l < 4; ++l) {
-        const int L = dim(l + 1) * (dim(l) + 1);
-        const int q0 = static_cast<int>(rank) * L / kCl, q1 = (static_cast<int>(rank) + 1) * L / kCl;
-        for (int q = q0 + tid; q < q1; q += kThr) {
+      for (int l = 0; l < 4; ++l) {  // the groups reduce_owned wrote
+        const int L = dim(l + 1) * (dim(l) + 1), G = (L + 3) / 4;
+        const int g0 = static_cast<int>(rank) * G / kCl, g1 = (static_cast<int>(rank) + 1) * G / kCl;
+        for (int q = 4 * g0 + tid; q < min(4 * g1, L); q += kThr) {
           const int i = w_off(l) + q;
           float p = R.master[i], m = R.m[i], v = R.v[i];
           adam_one(p, m, v, R.grad[i], A.lr, A.b1, A.b2, A.eps, A.c1, A.c2);
@@ -643,7 +751,7 @@ cudaError_t mlp_pack(const float *master, void *img, void *wbf, cudaStream_t st)
 
 cudaError_t mlp_forward(const void *img, const float *x, int64_t n, float *y, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  const int smem = Wk::FWD_END;
+  const int smem = Wk::INFER_END;
   cudaError_t e = cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const int64_t grid = (n + kS - 1) / kS;

@@ -710,35 +710,41 @@ struct Surrogate {
       for (int c = 0; c < 35; ++c) t[35 * i + c] = ys[35 * i + c] * norm->t_std[c] + norm->t_mean[c];
     return MK_OK;
   }
-  // residuals and finite-difference Jacobians of all active bins at the
-  // effective parameters tb (3 per bin) and bin centres zc
+  // residuals and central-difference Jacobians of all active bins at the
+  // effective parameters tb (3 per bin) and bin centres zc (inference is
+  // smooth in its inputs: its activations carry ~16 bits)
   int model(TuneState &S, const double *zc, const std::vector<double> &tb, std::vector<double> &r,
             std::vector<double> &J) {
     const double h[3] = {0.02, 0.02, 0.02};
+    constexpr int kV = 7;  // centre, then (+h, -h) per parameter
     const int nz = S.bins->n_z, m = S.m();
-    std::vector<double> x(static_cast<size_t>(nz) * 4 * 4), t;
+    std::vector<double> x(static_cast<size_t>(nz) * kV * 4), t;
     for (int zb = 0; zb < nz; ++zb)
-      for (int v = 0; v < 4; ++v) {
-        double *xi = &x[(static_cast<size_t>(zb) * 4 + v) * 4];
+      for (int v = 0; v < kV; ++v) {
+        double *xi = &x[(static_cast<size_t>(zb) * kV + v) * 4];
+        const int p = (v - 1) / 2;
+        const double d = v == 0 ? 0.0 : ((v - 1) % 2 == 0 ? h[p] : -h[p]);
         xi[0] = zc[zb];
-        xi[1] = tb[3 * zb] + (v == 1 ? h[0] : 0.0);
-        xi[2] = tb[3 * zb + 1] + (v == 2 ? h[1] : 0.0);
-        xi[3] = tb[3 * zb + 2] + (v == 3 ? h[2] : 0.0);
+        xi[1] = tb[3 * zb] + (v > 0 && p == 0 ? d : 0.0);
+        xi[2] = tb[3 * zb + 1] + (v > 0 && p == 1 ? d : 0.0);
+        xi[3] = tb[3 * zb + 2] + (v > 0 && p == 2 ? d : 0.0);
       }
     int rc = eval(S, x, t);
     if (rc) return rc;
     r.assign(static_cast<size_t>(nz) * m, 0.0);
     J.assign(static_cast<size_t>(nz) * m * 3, 0.0);
-    std::vector<double> rv(m);
+    std::vector<double> rp(m), rm(m);
     for (int zb = 0; zb < nz; ++zb) {
       if (!S.active(zb)) continue;
-      for (int v = 0; v < 4; ++v) {
-        const double *ti = &t[(static_cast<size_t>(zb) * 4 + v) * 35];
-        double *dst = (v == 0) ? &r[static_cast<size_t>(zb) * m] : rv.data();
-        residual(S, zb, ti[0], ti[2], ti + 3, dst);  // ti[3 + k] = ln P1D of k bin k
-        if (v > 0)
-          for (int i = 0; i < m; ++i)
-            J[(static_cast<size_t>(zb) * m + i) * 3 + (v - 1)] = (rv[i] - r[static_cast<size_t>(zb) * m + i]) / h[v - 1];
+      const double *t0 = &t[(static_cast<size_t>(zb) * kV) * 35];
+      residual(S, zb, t0[0], t0[2], t0 + 3, &r[static_cast<size_t>(zb) * m]);  // t[3 + k] = ln P1D of k bin k
+      for (int p = 0; p < 3; ++p) {
+        const double *tp = &t[(static_cast<size_t>(zb) * kV + 1 + 2 * p) * 35];
+        const double *tm = &t[(static_cast<size_t>(zb) * kV + 2 + 2 * p) * 35];
+        residual(S, zb, tp[0], tp[2], tp + 3, rp.data());
+        residual(S, zb, tm[0], tm[2], tm + 3, rm.data());
+        for (int i = 0; i < m; ++i)
+          J[(static_cast<size_t>(zb) * m + i) * 3 + p] = (rp[i] - rm[i]) / (2.0 * h[p]);
       }
     }
     return MK_OK;

@@ -48,11 +48,11 @@ def ctx():
 
 
 def test_mlp_forward_and_gradient_match_oracle(ctx):
-    """Tensor-core forward and backward against the oracle's BF16-operand
-    path at the same BF16 weights.  A hidden activation whose value lies
-    within the kernels' FP32 error of a BF16 rounding boundary may round
-    either way (both are valid): samples holding one (oracle margin < 2e-6)
-    get a bound for one such flip; all others match to 1e-4."""
+    """Tensor-core inference and training gradients against the oracle at the
+    same BF16 weights.  Inference takes each hidden activation as two BF16
+    terms (~16 bits), so it matches the plain FP64 forward to 1e-4; the
+    gradient follows the training precision (one BF16 term per activation
+    and backward operand) and is compared with the oracle's BF16 path."""
     rng = np.random.default_rng(11)
     mlp = mk.Mlp(ctx, max_batch=512, seed=3)
     p = (rng.standard_normal(mk.MLP_NPARAM) * 0.15).astype(np.float32)
@@ -66,12 +66,12 @@ def test_mlp_forward_and_gradient_match_oracle(ctx):
     t = rng.standard_normal((n, 35)).astype(np.float32)
     xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
     y = mlp.forward(xd).cpu().numpy()
-    yo, margin = oracle.mlp_forward(eff, x.astype(np.float64), bf16=True, margin=True)
+    yo = oracle.mlp_forward(eff, x.astype(np.float64))
     scale = np.abs(yo).max()
-    clean = margin >= 2e-6
-    assert clean.sum() >= 0.5 * n, clean.sum()
-    np.testing.assert_allclose(y[clean], yo[clean], rtol=1e-4, atol=1e-5 * scale)
-    assert np.abs(y - yo).max() <= 2e-3 * scale
+    np.testing.assert_allclose(y, yo, rtol=1e-4, atol=1e-5 * scale)
+    # one BF16 term per activation would be ~100x further off
+    yq = oracle.mlp_forward(eff, x.astype(np.float64), bf16=True)
+    assert np.abs(y - yo).max() < 0.1 * np.abs(yq - yo).max()
     loss, g = mlp.loss_grad(xd, td)
     lo, go = oracle.mlp_loss_grad(eff, x.astype(np.float64), t.astype(np.float64), bf16=True)
     assert loss == pytest.approx(lo, rel=1e-5)
