@@ -265,8 +265,11 @@ def surrogate_leg(ctx, mk, w, r, n_q, target, nd0, dev, draws, held, epochs, sou
     t0 = time.perf_counter()
     norm, losses = mlp.fit(hx, ht, batch=256, epochs=epochs, lr=2e-3, seed=5)
     t_fit = time.perf_counter() - t0
-    if source == "subset":  # labelled on the first n_lab skewers of this catalogue: calibrate on them
-        norm.calib_skewers = n_lab
+    # one calibration pass over the first 100k skewers of the catalogue being
+    # tuned: for the subset those are the labelled skewers (the surrogate's own
+    # error, free of sample variance); for the 512^3 box it also measures the
+    # box-to-box offset
+    norm.calib_skewers = 100_000
     vx, vt = mk.surrogate_labels(ctx, ws, rs["sk"], n_lab, rs["offsets"], rs["delta"], rs["eta"],
                                  n_draws=held, seed=12, slopes=slopes)
     xm, xs = np.ctypeslib.as_array(norm.x_mean), np.ctypeslib.as_array(norm.x_std)

@@ -569,11 +569,13 @@ typedef struct mk_surrogate_space {
 /* Affine normalisation between physical surrogate inputs/outputs and the
    MLP's: x_mlp = (x - x_mean)/x_std, t = t_mlp t_std + t_mean.  Inputs are
    (z, ln a, b, c); outputs (Fbar, b_F, beta_F, ln P1D_dF of 32 k bins).
-   calib_skewers: when the surrogate was labelled on the first calib_skewers
-   skewers of the catalogue being tuned (0 otherwise; mk_surrogate_fit writes
-   0), mk_tune runs one pass over those skewers at the surrogate's first fit
-   and refits on the surrogate shifted by that pass's discrepancy before its
-   first full pass. */
+   calib_skewers: when > 0 (mk_surrogate_fit writes 0), mk_tune runs one pass
+   over the first calib_skewers skewers of the catalogue being tuned at the
+   surrogate's first fit and refits on the surrogate shifted by that pass's
+   discrepancy before its first full pass.  When the surrogate was labelled on
+   those very skewers the pass measures its own error free of sample
+   variance; a surrogate labelled on another box also gets the offset between
+   the boxes from it (up to the subset's sample variance). */
 typedef struct mk_surrogate_norm {
   double x_mean[MK_MLP_IN], x_std[MK_MLP_IN];
   double t_mean[MK_MLP_OUT], t_std[MK_MLP_OUT];
@@ -639,8 +641,8 @@ typedef struct mk_tune_report {
    the fit is redone on the surrogate shifted by that pass's discrepancy
    (true minus predicted residual) plus a linear term in the parameter change
    whose slope is Broyden-updated from successive passes (when
-   norm->calib_skewers > 0, a pass over that labelled subset first corrects
-   the surrogate's own error at its fit).  Nodes of inactive
+   norm->calib_skewers > 0, a pass over that subset of the catalogue first
+   corrects the surrogate's error at its fit).  Nodes of inactive
    bins follow the nearest active node (ties: the lower one).  Stops when a
    pass meets the tolerances or after max_passes passes.  Synchronous. */
 int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,

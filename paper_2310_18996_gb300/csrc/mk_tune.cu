@@ -879,8 +879,9 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
       return MK_OK;
     };
     std::vector<double> B(static_cast<size_t>(nz) * m * 3, 0.0), prev_off, prev_theta;
-    // calibration: a pass over the skewers the surrogate was labelled on gives
-    // its own error at the fit, free of the subset-to-catalogue difference
+    // calibration: a pass over the first calib_skewers skewers gives the
+    // surrogate's error at its fit (free of the subset-to-catalogue difference
+    // when it was labelled on those skewers)
     if (rc == MK_OK && norm->calib_skewers > 0 && norm->calib_skewers < n_sk && max_passes > 1) {
       TuneState Sc = S;
       Sc.n_sk = norm->calib_skewers;
