@@ -487,8 +487,8 @@ uint64_t tune_key(int n_fft, int variant, int lgn, uint32_t flags) {
          (static_cast<uint64_t>(lgn > 10) << 8) | (flags & (MK_STORE_FIELDS | MK_STORE_FLUX | MK_STATS));
 }
 
-int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads) {
-  return capped(ctx, ctx->sms * stats_blocks_per_sm(bins->n_fft, threads, bins->n_z, bins->n_k));
+int stats_grid(mk_ctx *ctx, const mk_stat_bins *bins, int threads, bool tune = false) {
+  return capped(ctx, ctx->sms * stats_blocks_per_sm(bins->n_fft, threads, bins->n_z, bins->n_k, tune));
 }
 
 GeomParams geom_params(mk_ctx *ctx, const mk_box *box, const mk_skewer_params *p) {
@@ -835,7 +835,7 @@ int stats_pass(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_s
   if (nodes && (rc = ensure_pixtab(ctx, nodes))) return rc;
   const int threads = 256;
   const StatLayout L{bins->n_z, bins->n_k};
-  const int grid = stats_grid(ctx, bins, threads);
+  const int grid = stats_grid(ctx, bins, threads, tune_kernel(nodes ? ctx->d_pixtab : nullptr, d_delta, d_eta, rebin));
   if ((rc = grow(ctx, reinterpret_cast<void **>(&ctx->d_partials), &ctx->partials_cap,
                  sizeof(double) * static_cast<size_t>(grid) * L.size())))
     return rc;

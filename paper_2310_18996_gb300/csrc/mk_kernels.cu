@@ -488,8 +488,8 @@ cudaError_t launch_skewer(const SkewerParams &P, int n_fft, int variant, int min
   MK_SWITCH(launch(P, variant, minb, grid, threads, st), cudaErrorInvalidValue)
 }
 
-int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k) {
-  MK_SWITCH(stats_blocks_per_sm(threads, n_z, n_k), 1)
+int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k, bool tune) {
+  MK_SWITCH(stats_blocks_per_sm(threads, n_z, n_k, tune), 1)
 }
 
 cudaError_t launch_stats(const StatParams &P, int n_fft, int grid, int threads, cudaStream_t st) {

@@ -32,7 +32,13 @@ cudaError_t launch_bin_end(const int16_t *zbin, int32_t j_max, int n_z, int32_t 
 cudaError_t launch_out_counts(const mk_skewer *sk, int64_t n, int rebin, int64_t *cnt, cudaStream_t st);
 cudaError_t launch_seg_counts(const int64_t *off, int64_t n, int n_fft, int64_t *cnt, cudaStream_t st);
 int skewer_blocks_per_sm(int n_fft, int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
-int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k);
+// The tuning pass (FGPA table set, rebin 1, 16-byte aligned fields) runs the
+// staged kernel k_tune_stats; every other statistics pass runs k_stats.
+inline bool tune_kernel(const void *pixtab, const float *delta, const float *eta, int rebin) {
+  return pixtab && delta && eta && rebin == 1 &&
+         ((reinterpret_cast<uintptr_t>(delta) | reinterpret_cast<uintptr_t>(eta)) & 15) == 0;
+}
+int stats_blocks_per_sm(int n_fft, int threads, int n_z, int n_k, bool tune);
 size_t skewer_smem_bytes(int n_fft, int threads, int n_z, int n_k, bool stats);
 // variant: box layout, plus kGauss7Variant for the Gaussian-kernel interpolation,
 // plus kPsNodesVariant for z-dependent P_s (built for register budget 3 only);
@@ -48,7 +54,7 @@ struct SkewerUnit {
   static size_t smem_bytes(int threads, int n_z, int n_k, bool stats);
   static int blocks_per_sm(int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats);
   static cudaError_t launch(const SkewerParams &P, int variant, int minb, int grid, int threads, cudaStream_t st);
-  static int stats_blocks_per_sm(int threads, int n_z, int n_k);
+  static int stats_blocks_per_sm(int threads, int n_z, int n_k, bool tune);
   static cudaError_t launch_stats(const StatParams &P, int grid, int threads, cudaStream_t st);
 };
 extern template struct SkewerUnit<256>;

@@ -247,6 +247,15 @@ __device__ __forceinline__ void gemm_s(const __nv_bfloat16 *A, int lda, const __
   }
 }
 
+// sum over the 32 samples of column j of a BF16 [32][ld] buffer (four
+// independent partial sums, added in a fixed order)
+__device__ __forceinline__ float column_sum(const __nv_bfloat16 *D, int ld, int j) {
+  float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < kS; ++i) a[i & 3] += __bfloat162float(D[i * ld + j]);
+  return (a[0] + a[1]) + (a[2] + a[3]);
+}
+
 // Element (s, j) of fragment slot (nt, i) of gemm_s: s = s0 + g + 8 (i >> 1),
 // j = n0 + 8 nt + 2 t + (i & 1).
 __device__ __forceinline__ void frag_pos(int nt, int i, int &s, int &j) {
@@ -599,17 +608,19 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_tra
 
       // ---- loss and output gradient dy (BF16), zero past the valid samples and outputs
       const float *T = reinterpret_cast<const float *>(sm + Wk::TG);
-      double lsum = 0.0;
+      float lf = 0.f;  // this thread's few squared residuals
+      const float two_inv = static_cast<float>(2.0 * inv);
       for (int e = tid; e < kS * 48; e += kThr) {
         const int s = e / 48, j = e % 48;
         float d = 0.f;
         if (s < cnt && j < kMlpOut) {
           const float r = Y[s * kOutP + j] - T[s * 36 + j];
-          lsum += static_cast<double>(r) * r * inv;
-          d = static_cast<float>(2.0 * inv) * r;
+          lf = fmaf(r, r, lf);
+          d = two_inv * r;
         }
         DY[s * kLdY + j] = __float2bfloat16_rn(d);
       }
+      double lsum = static_cast<double>(lf) * inv;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
       if (lane == 0) RED[w] = lsum;
@@ -622,11 +633,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_tra
 
       // ---- layer 3: dW3 = dy^T h2 (48 x 128 tiles on warps 0..5), db3; dh2 = dy W3
       if (w < 6) gemm_w<8>(DY, kLdY, H2, w % 3, 64 * (w / 3), P);
-      if (tid < kMlpOut) {
-        float s = 0.f;
-        for (int i = 0; i < kS; ++i) s += __bfloat162float(DY[i * kLdY + tid]);
-        PB[tid] = s;
-      }
+      if (tid < kMlpOut) PB[tid] = column_sum(DY, kLdY, tid);
       {
         float acc[4][4];
         gemm_s<true>(DY, kLdY, W3, kLd, 48, acc);
@@ -655,11 +662,7 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_tra
         const __nv_bfloat16 *Wm = (l == 2) ? W2 : W1;
         gemm_w<8>(D, kLd, Hin, w, 0, P);  // two halves of 8 column tiles keep registers for G
         gemm_w<8>(D, kLd, Hin, w, 64, P);
-        if (tid < 128) {
-          float s = 0.f;
-          for (int i = 0; i < kS; ++i) s += __bfloat162float(D[i * kLd + tid]);
-          PB[tid] = s;
-        }
+        if (tid < 128) PB[tid] = column_sum(D, kLd, tid);
         float acc[4][4];
         gemm_s<true>(D, kLd, Wm, kLd, 128, acc);
 #pragma unroll
@@ -679,15 +682,12 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThr, 1) k_mlp_tra
       // ---- layer 0 (FP32 inputs): dW0 = dz0^T x, db0 (dz0 in DA)
       for (int e = tid; e < 128 * 4; e += kThr) {
         const int j = e >> 2, k = e & 3;
-        float s = 0.f;
-        for (int i = 0; i < kS; ++i) s = fmaf(__bfloat162float(DA[i * kLd + j]), X[i * 4 + k], s);
-        P[j * kLdP + k] = s;
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < kS; ++i) a[i & 3] = fmaf(__bfloat162float(DA[i * kLd + j]), X[i * 4 + k], a[i & 3]);
+        P[j * kLdP + k] = (a[0] + a[1]) + (a[2] + a[3]);
       }
-      if (tid < 128) {
-        float s = 0.f;
-        for (int i = 0; i < kS; ++i) s += __bfloat162float(DA[i * kLd + tid]);
-        PB[tid] = s;
-      }
+      if (tid < 128) PB[tid] = column_sum(DA, kLd, tid);
       cluster_sync();
       reduce_owned(sm, 0, rank, R, add, fuse, A);
       cluster_sync();  // partials read (the next chunk rewrites them)

@@ -72,12 +72,21 @@ cudaError_t SkewerUnit<NN>::launch(const SkewerParams &P, int variant, int minb,
 }
 
 template <int NN>
-int SkewerUnit<NN>::stats_blocks_per_sm(int threads, int n_z, int n_k) {
+int SkewerUnit<NN>::stats_blocks_per_sm(int threads, int n_z, int n_k, bool tune) {
+  if (tune) return skewer_unit_detail::occupancy(k_tune_stats<NN>, threads, TuneSmem<NN>::bytes(threads, n_z, n_k));
   return skewer_unit_detail::occupancy(k_stats<NN>, threads, TeamSmem<NN>::bytes(threads, n_z, n_k, true));
 }
 
 template <int NN>
 cudaError_t SkewerUnit<NN>::launch_stats(const StatParams &P, int grid, int threads, cudaStream_t st) {
+  if (tune_kernel(P.pixtab, P.delta, P.eta, P.rebin)) {
+    const size_t smem = TuneSmem<NN>::bytes(threads, P.n_z, P.n_k);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tune_stats<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    k_tune_stats<NN><<<grid, threads, smem, st>>>(P);
+    return cudaGetLastError();
+  }
   const size_t smem = TeamSmem<NN>::bytes(threads, P.n_z, P.n_k, true);
   cudaError_t e = cudaFuncSetAttribute(k_stats<NN>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
