@@ -752,7 +752,8 @@ def run_gb300(args, rank, world, local_rank):
                           f"target {occ}{' (autotuned)' if tuned else ''}", "kernel_ms": kms,
                 "algorithmic_bytes": alg, "algorithmic_bytes_per_pixel": alg / total}
         if prof:  # the compute side, from the committed ncu record of the same kernel source
-            roof.update({k: prof[k] for k in ("warp_inst_per_px", "issue_active", "fp32_inst_per_px") if k in prof})
+            roof.update({k: prof[k] for k in ("warp_inst_per_px", "thread_inst_per_px", "issue_active",
+                                              "alu_pipe_active", "fma_pipe_active") if k in prof})
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

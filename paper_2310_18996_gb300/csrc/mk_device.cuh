@@ -365,15 +365,29 @@ __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(
 //   from the base corner and no index wraps.
 //   MK_BOX_HALO: pairs on (n+6)^3 points, a periodic margin of 3 on every
 //   side; the same fixed offsets from base index (x+3, y+3, z+3).
-template <int LAYOUT, bool BIG>
+// FIXLGN > 0 (padded layout, 32-bit indices): the box side is 2^FIXLGN, so
+// the row and plane strides are constants and the eight loads take immediate
+// offsets from one pointer (placed mid-way between the two planes, so that
+// every offset stays within the immediate range).
+template <int LAYOUT, bool BIG, int FIXLGN = 0>
 __device__ __forceinline__ float2 gather(const float *__restrict__ d, const float *__restrict__ e, int lgn,
                                          int64_t px, int64_t py, int64_t pz) {
-  const int mask = (1 << lgn) - 1;
+  const int mask = FIXLGN > 0 ? (1 << FIXLGN) - 1 : (1 << lgn) - 1;
   const int x0 = cell_of(px, mask), y0 = cell_of(py, mask), z0 = cell_of(pz, mask);
   const float tx = weight_of(px), ty = weight_of(py), tz = weight_of(pz);
   using I = typename std::conditional<BIG, int64_t, int32_t>::type;
   float2 v[8];
-  if constexpr (LAYOUT == MK_BOX_PADDED || LAYOUT == MK_BOX_HALO) {
+  if constexpr (FIXLGN > 0) {
+    static_assert(LAYOUT == MK_BOX_PADDED && !BIG, "fixed strides serve the padded layout with 32-bit indices");
+    constexpr int n1 = (1 << FIXLGN) + 1, plane = n1 * n1, half = plane / 2;
+    const float2 *mid = reinterpret_cast<const float2 *>(d) + (z0 * plane + y0 * n1 + x0 + half);
+    const float2 *a00 = mid - half, *a01 = a00 + n1;
+    const float2 *a10 = mid + (plane - half), *a11 = a10 + n1;
+    v[0] = __ldg(a00); v[1] = __ldg(a00 + 1);
+    v[2] = __ldg(a01); v[3] = __ldg(a01 + 1);
+    v[4] = __ldg(a10); v[5] = __ldg(a10 + 1);
+    v[6] = __ldg(a11); v[7] = __ldg(a11 + 1);
+  } else if constexpr (LAYOUT == MK_BOX_PADDED || LAYOUT == MK_BOX_HALO) {
     constexpr int h = LAYOUT == MK_BOX_HALO ? 3 : 0;
     const I n1 = mask + 1 + (LAYOUT == MK_BOX_HALO ? 6 : 1);
     const float2 *a00 =

@@ -6,6 +6,7 @@
 
 #include "mk_kernels.h"
 #include "mk_skewer.cuh"
+#include "mk_tune_stats.cuh"
 
 namespace mk {
 
@@ -21,11 +22,25 @@ cudaError_t with_layout(bool big, bool psz, int minb, F &&fn) {
   return big ? fn(k_skewer<NN, L, true, 2, INTERP>) : fn(k_skewer<NN, L, false, 2, INTERP>);
 }
 
+// Side 2^kFixLgn of the box whose padded-layout strides are compile-time
+// constants in the N = 256 instances (the 1024^3 box of the batched workload);
+// other sides take the strides at run time.
+constexpr int kFixLgn = 10;
+
 // Calls fn with the kernel instance for (kernel variant, box size, register budget).
 template <int NN, typename F>
-cudaError_t with_skewer_kernel(int variant, bool big, int minb, F &&fn) {
+cudaError_t with_skewer_kernel(int variant, int lgn, int minb, F &&fn) {
+  const bool big = lgn > 10;
   const bool psz = (variant & kPsNodesVariant) != 0;
   const int layout = variant & (kGauss7Variant - 1);
+  if constexpr (NN == 256) {
+    if (variant == MK_BOX_PADDED && lgn == kFixLgn) {
+      constexpr int L = MK_BOX_PADDED, I = MK_INTERP_TRILINEAR;
+      if (minb >= 4) return fn(k_skewer<NN, L, false, 4, I, false, kFixLgn>);
+      if (minb == 3) return fn(k_skewer<NN, L, false, 3, I, false, kFixLgn>);
+      return fn(k_skewer<NN, L, false, 2, I, false, kFixLgn>);
+    }
+  }
   if (variant & kGauss7Variant) return with_layout<NN, MK_BOX_HALO, MK_INTERP_GAUSS7>(big, psz, minb, fn);
   if (layout == MK_BOX_HALO) return with_layout<NN, MK_BOX_HALO, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
   if (layout == MK_BOX_TENSOR) return with_layout<NN, MK_BOX_TENSOR, MK_INTERP_TRILINEAR>(big, psz, minb, fn);
@@ -52,7 +67,7 @@ template <int NN>
 int SkewerUnit<NN>::blocks_per_sm(int variant, int lgn, int minb, int threads, int n_z, int n_k, bool stats) {
   const size_t smem = TeamSmem<NN>::bytes(threads, n_z, n_k, stats);
   int b = 1;
-  skewer_unit_detail::with_skewer_kernel<NN>(variant, lgn > 10, minb, [&](auto kern) {
+  skewer_unit_detail::with_skewer_kernel<NN>(variant, lgn, minb, [&](auto kern) {
     b = skewer_unit_detail::occupancy(kern, threads, smem);
     return cudaSuccess;
   });
@@ -63,7 +78,7 @@ template <int NN>
 cudaError_t SkewerUnit<NN>::launch(const SkewerParams &P, int variant, int minb, int grid, int threads,
                                    cudaStream_t st) {
   const size_t smem = TeamSmem<NN>::bytes(threads, P.n_z, P.n_k, P.do_stats != 0);
-  return skewer_unit_detail::with_skewer_kernel<NN>(variant, P.lgn > 10, minb, [&](auto kern) {
+  return skewer_unit_detail::with_skewer_kernel<NN>(variant, P.lgn, minb, [&](auto kern) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<grid, threads, smem, st>>>(P);

@@ -1,0 +1,195 @@
+// The tuning-pass kernel: the FGPA of stored delta, eta and its statistics,
+// with each team's next segment of the fields staged in shared memory.
+#pragma once
+
+#include "mk_skewer.cuh"
+
+namespace mk {
+
+// =================================================================== tuning-pass kernel
+// The tuning pass (FGPA of stored delta, eta at full resolution, then the
+// statistics): k_stats's pixel and P1D work, with each team's next segment of
+// delta and eta copied into shared memory (cp.async, 16-byte pieces) while
+// the current one is processed, so that the HBM latency hides behind the
+// current segment's FFT.
+template <int N>
+struct TuneSmem {
+  static constexpr int STAGE = N + 4;  // floats per field and buffer (a segment plus its 16-byte misalignment)
+  static size_t bytes(int threads, int n_z, int n_k) {
+    return TeamSmem<N>::bytes(threads, n_z, n_k, true) +
+           static_cast<size_t>(threads / (N / 8)) * 4 * STAGE * sizeof(float);
+  }
+};
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Copy the npx floats of a field from global index `start` into sd: 16-byte
+// pieces from start rounded down to 16 bytes (pixel p lands at sd[shift + p]),
+// 4-byte copies for the last piece when it would run past the segment.
+template <int T>
+__device__ __forceinline__ void stage_field(float *sd, const float *__restrict__ f, int64_t start, int npx, int t) {
+  const int shift = static_cast<int>(start & 3);
+  const float *base = f + (start - shift);
+  const int nch = (npx + shift + 3) >> 2;
+  for (int c = t; c < nch; c += T) {
+    const int r0 = 4 * c - shift;  // segment pixel of the piece's first float
+    if (r0 + 4 <= npx) {
+      cp_async16(sd + 4 * c, base + 4 * c);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (r0 + e >= 0 && r0 + e < npx) cp_async4(sd + 4 * c + e, base + 4 * c + e);
+    }
+  }
+}
+
+// P: a tuning pass (rebin 1, fields and FGPA table set; delta, eta 16-byte aligned).
+template <int N>
+__global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
+  constexpr int T = N / 8;
+  constexpr int BUF = TeamSmem<N>::BUF;
+  constexpr int STAGE = TuneSmem<N>::STAGE;
+  const int teams = blockDim.x / T;
+  const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
+  float2 *tws = reinterpret_cast<float2 *>(smem + nwarps * wbytes);
+  float2 *buf = tws + TwTab<N>::SLOTS * T + team * BUF;
+  float *fb = reinterpret_cast<float *>(buf);
+  // stage buffers b = 0, 1: delta at stage + 2 b STAGE, eta at stage + (2 b + 1) STAGE
+  float *stage = reinterpret_cast<float *>(smem + TeamSmem<N>::bytes(blockDim.x, P.n_z, P.n_k, true)) +
+                 team * 4 * STAGE;
+  const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
+  zero_warp_acc(smem + warp * wbytes, wbytes);
+  fill_twiddles<N>(tws, P.tw);
+
+  const int64_t nunits = P.segoff[P.n_sk];
+  const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
+  const int64_t G = static_cast<int64_t>(gridDim.x) * teams;
+  int64_t u = g * nunits / G;
+  const int64_t u_first = u;
+  const int64_t uend = (g + 1) * nunits / G;
+  int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
+  int64_t inext = i;  // skewer of the next segment to stage
+  const int wlo0 = t & ~31;
+  PixelSums acc;
+  acc.zero();
+  int zc = -2;
+
+  // copy segment uu (of skewer inext, advanced as needed) into buffer b
+  auto stage_segment = [&](int64_t uu, int b) {
+    while (P.segoff[inext + 1] <= uu) ++inext;
+    const int64_t o = P.off_out[inext];
+    const int64_t k0 = (uu - P.segoff[inext]) * N;
+    const int npx = static_cast<int>(min(static_cast<int64_t>(N), P.off_out[inext + 1] - o - k0));
+    const int64_t start = P.sk[inext].offset + k0;
+    stage_field<T>(stage + 2 * b * STAGE, P.delta, start, npx, t);
+    stage_field<T>(stage + (2 * b + 1) * STAGE, P.eta, start, npx, t);
+  };
+  if (u < uend) stage_segment(u, 0);
+  cp_async_commit();
+  team_sync<T>(team);
+
+  for (; u < uend; ++u) {
+    const int b = static_cast<int>((u - u_first) & 1);
+    if (u + 1 < uend) stage_segment(u + 1, b ^ 1);
+    cp_async_commit();  // one group per segment (possibly empty)
+    while (P.segoff[i + 1] <= u) ++i;
+    const int s = static_cast<int>(u - P.segoff[i]);
+    const mk_skewer sk = P.sk[i];
+    const int64_t nout = P.off_out[i + 1] - P.off_out[i];
+    const bool in_tables = sk.j_lo >= 0 && sk.j_lo + nout <= P.j_max;  // team-uniform
+    const int64_t k0 = static_cast<int64_t>(s) * N;
+    const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
+    const int jb = in_tables ? sk.j_lo + static_cast<int>(k0) : 0;
+    // the FGPA table and bin entries of this segment, requested before the
+    // wait for the staged fields so that their latency overlaps it
+    const float4 *tp = P.pixtab + jb + t;
+    float4 tb[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tb[q] = (in_tables && t + T * q < npx) ? __ldg(tp + T * q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int zs0 = in_tables ? __ldg(P.zbin + jb) : 0;
+    cp_async_wait_prior();  // this segment's copies are in
+    team_sync<T>(team);
+    if (!in_tables) {  // records made for another pixel length: skip, as in k_stats
+      if (t == 0) raise_error(P.err, ERR_RANGE);
+      team_sync<T>(team);
+      continue;
+    }
+    const int shift = static_cast<int>((sk.offset + k0) & 3);
+    const float *sd = stage + 2 * b * STAGE + shift, *se = stage + (2 * b + 1) * STAGE + shift;
+    if (zs0 != zc) {
+      if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
+      acc.zero();
+      zc = zs0;
+    }
+    int pend = __ldg(P.bin_end + zc + 1) - jb;
+    const bool one_bin = min(T * 7 + wlo0 + 32, npx) <= pend;
+    if (npx == N && one_bin) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int p = t + T * q;
+        const float2 x = make_float2(sd[p], se[p]);
+        const float f = fgpa(tb[q], x.x, x.y);
+        acc.add(f, x);
+        fb[p] = f;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {  // (unrolled: tb[q] stays in registers)
+        const int p = t + T * q;
+        float f = 0.f;
+        float2 x = make_float2(0.f, 0.f);
+        if (p < npx) {
+          x = make_float2(sd[p], se[p]);
+          f = fgpa(tb[q], x.x, x.y);
+        }
+        if (one_bin) {
+          if (p < npx) acc.add(f, x);
+        } else {
+          const int hi = min(T * q + wlo0 + 32, npx);
+          bool todo = p < npx;
+          while (hi > pend) {
+            if (todo && p < pend) {
+              acc.add(f, x);
+              todo = false;
+            }
+            flush_bin_sums(W, P.n_z, zc, acc, lane);
+            acc.zero();
+            ++zc;
+            pend = __ldg(P.bin_end + zc + 1) - jb;
+          }
+          if (todo) acc.add(f, x);
+        }
+        fb[p] = f;
+      }
+    }
+    if (npx == N) {
+      const int zs = __ldg(P.segzbin + jb);
+      if (zs >= 0 && zs < P.n_z) {
+        forward_packed_fft<N>(buf, tws, t, team);
+        float pk[4];
+        power_of_modes<N>(buf, P.tw, t, pk);
+        accumulate_p1d<N>(W, P.n_k, pk, P.p1d_scale, zs, t);
+        if (t == 0) W.nseg[zs] += 1u;
+      }
+    }
+    team_sync<T>(team);  // the stage buffer b and fb are free again
+  }
+  if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
+  flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
+}
+
+}  // namespace mk
