@@ -184,6 +184,27 @@ def test_tuning_pass_matches_oracle_and_split_path(ctx, tiny):
     assert_stats_close(st3, so2)
 
 
+def test_tuning_pass_unaligned_fields_match_oracle(ctx, tiny):
+    """Stored fields that do not start on a 16-byte boundary cannot be staged
+    with 16-byte asynchronous copies; the pass then runs the unstaged kernel,
+    which must give the same statistics."""
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    tot = r["total"]
+    d1 = torch.empty(tot + 1, dtype=torch.float32, device="cuda")
+    e1 = torch.empty(tot + 1, dtype=torch.float32, device="cuda")
+    d1[1:] = r["delta"]
+    e1[1:] = r["eta"]
+    assert d1[1:].data_ptr() % 16 != 0 and r["delta"].data_ptr() % 16 == 0
+    st_u = ctx.flux_stats(w, r["sk"], n, r["offsets"], d1[1:], e1[1:])
+    assert_stats_close(st_u, tiny["st"])
+    st_a = ctx.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+    for k in ("sums", "p1d_sum", "n_seg"):
+        np.testing.assert_array_equal(st_u[k], st_a[k])
+
+
 @pytest.mark.parametrize("layout", ["planar", "padded"])
 def test_fused_path_matches_split_path_and_oracle(ctx, tiny, layout):
     w, dv = tiny["w"], tiny["dev"]
