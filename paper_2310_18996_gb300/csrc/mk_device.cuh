@@ -250,6 +250,74 @@ __device__ __forceinline__ void fft_finish(float2 *buf, float2 (&v)[4], const fl
   team_sync<T>(team);
 }
 
+// ------------------------------------------------------------------ 256-point layouts
+// With N = 256 (a team is one warp) the skewer transforms keep their buffer
+// in two padded layouts instead of the swizzle: LA(i) = i + i/16 and
+// LB(i) = i + 4 (i/16) for complex index i <= M.  Every access of the
+// 256-point transforms is then a per-lane base plus a compile-time offset (no
+// index arithmetic per access), and each half warp still hits 16 distinct
+// 8-byte slots (apart from two 2-way conflicts among the mirror reads of the
+// untangle step).  LA holds the modes, the outputs of the first write and of
+// radix-4 pass 2, and the forward result; LB the output of radix-4 pass 1.
+// The arithmetic is that of fft_finish, so results are unchanged.
+constexpr int kBuf256 = 156;  // complex slots of a 256-point team buffer: LB(127) + 1
+__device__ __forceinline__ int lay_a(int i) { return i + (i >> 4); }
+__device__ __forceinline__ int lay_b(int i) { return i + 4 * (i >> 4); }
+
+// fft_finish for N = 256 in the padded layouts (input layout LA after the
+// first write; output plain with PLAIN, else LA)
+template <int SIGN, bool PLAIN>
+__device__ __forceinline__ void fft_finish256(float2 *buf, float2 (&v)[4], const float2 *tws, int t) {
+  constexpr int T = 32;
+  constexpr int R2 = TwTab<256>::R2;
+  __syncwarp();
+  {  // 4t + r -> LA: lay_a(4t) + r
+    const int b = lay_a(4 * t);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) buf[b + r] = v[r];
+  }
+#pragma unroll
+  for (int p = 1; p <= 2; ++p) {
+    __syncwarp();
+    // reads at t + 32 r: LA (pass 1) lay_a(t) + 34 r, LB (pass 2) lay_b(t) + 40 r
+    const int rb = p == 1 ? lay_a(t) : lay_b(t);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) v[r] = buf[rb + (p == 1 ? 34 : 40) * r];
+#pragma unroll
+    for (int r = 1; r < 4; ++r) {
+      const float2 w = tws[(3 * (p - 1) + r - 1) * T + t];
+      v[r] = cmul(v[r], SIGN < 0 ? w : cconj(w));
+    }
+    dft4<SIGN>(v[0], v[1], v[2], v[3]);
+    __syncwarp();
+    // writes at base + r ns: pass 1 (ns 4) into LB, lay_b(16 (t/4) + t%4) + 4 r;
+    // pass 2 (ns 16) into LA, lay_a(64 (t/16) + t%16) + 17 r
+    const int wb = p == 1 ? lay_b(16 * (t >> 2) + (t & 3)) : lay_a(64 * (t >> 4) + (t & 15));
+#pragma unroll
+    for (int r = 0; r < 4; ++r) buf[wb + (p == 1 ? 4 : 17) * r] = v[r];
+  }
+  __syncwarp();
+  // radix-2 pass: t, t + M/2, t + T, t + T + M/2 in LA = lay_a(t) + 0, 68, 34, 102
+  const int rb = lay_a(t);
+  float2 a0 = buf[rb], b0 = buf[rb + 68], a1 = buf[rb + 34], b1 = buf[rb + 102];
+  const float2 w0 = tws[R2 * T + t], w1 = tws[(R2 + 1) * T + t];
+  b0 = cmul(b0, SIGN < 0 ? w0 : cconj(w0));
+  b1 = cmul(b1, SIGN < 0 ? w1 : cconj(w1));
+  __syncwarp();
+  if (PLAIN) {
+    buf[t] = f2add(a0, b0);
+    buf[t + 64] = f2sub(a0, b0);
+    buf[t + 32] = f2add(a1, b1);
+    buf[t + 96] = f2sub(a1, b1);
+  } else {
+    buf[rb] = f2add(a0, b0);
+    buf[rb + 68] = f2sub(a0, b0);
+    buf[rb + 34] = f2add(a1, b1);
+    buf[rb + 102] = f2sub(a1, b1);
+  }
+  __syncwarp();
+}
+
 // Inverse real FFT of the Hermitian modes Y_0..Y_M held in buf (already
 // scaled by 1/N); on return the float view holds the N real outputs at plain
 // indices (pixel p at float p).
@@ -258,16 +326,22 @@ __device__ __forceinline__ void inverse_real_fft(float2 *buf, const float2 *tws,
   constexpr int T = Fft<N>::T;
   constexpr int M = Fft<N>::M;
   float2 v[4];
+  // N = 256: k = t + 32 r at lay_a(t) + 34 r, M - k at lay_a(32 - t) + 34 (3 - r)
+  const int ka = N == 256 ? lay_a(t) : 0, kb = N == 256 ? lay_a(32 - t) : 0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int k = t + r * T;
-    const float2 yk = buf[sw(k)];
-    const float2 ym = cconj(buf[sw(M - k)]);
+    const float2 yk = buf[N == 256 ? ka + 34 * r : sw(k)];
+    const float2 ym = cconj(buf[N == 256 ? kb + 34 * (3 - r) : sw(M - k)]);
     // Z_k = (Y_k + conj Y_{M-k}) + i (Y_k - conj Y_{M-k}) e^{+2 pi i k/N}
     v[r] = cadd(cadd(yk, ym), cmul_i<1>(cmul(csub(yk, ym), cconj(tws[(TwTab<N>::U + r) * T + t]))));
   }
   dft4<1>(v[0], v[1], v[2], v[3]);
-  fft_finish<N, 1, true>(buf, v, tws, t, team);
+  if constexpr (N == 256) {
+    fft_finish256<1, true>(buf, v, tws, t);
+  } else {
+    fft_finish<N, 1, true>(buf, v, tws, t, team);
+  }
 }
 
 // Forward complex FFT of the N reals in the float view of buf (plain
@@ -281,7 +355,11 @@ __device__ __forceinline__ void forward_packed_fft(float2 *buf, const float2 *tw
 #pragma unroll
   for (int r = 0; r < 4; ++r) v[r] = buf[t + r * T];
   dft4<-1>(v[0], v[1], v[2], v[3]);
-  fft_finish<N, -1>(buf, v, tws, t, team);
+  if constexpr (N == 256) {
+    fft_finish256<-1, false>(buf, v, tws, t);
+  } else {
+    fft_finish<N, -1>(buf, v, tws, t, team);
+  }
 }
 
 // |X_k|^2 of the real input for k = 4t+1 .. 4t+4 after forward_packed_fft:
@@ -291,11 +369,15 @@ template <int N>
 __device__ __forceinline__ void power_of_modes(const float2 *buf, const float2 *__restrict__ tab, int t,
                                                float (&pk)[4]) {
   constexpr int M = Fft<N>::M;
+  // N = 256 (layout LA): k = 4t + 1 + r at lay_a(4t) + 1 + r (r < 3), M - k at
+  // lay_a(4 (31 - t)) + 3 - r
+  const int pa = N == 256 ? lay_a(4 * t) : 0, pb = N == 256 ? lay_a(4 * (31 - t)) : 0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int k = 4 * t + 1 + r;
-    const float2 zk = buf[sw(k & (M - 1))];
-    const float2 zm = cconj(buf[sw((M - k) & (M - 1))]);
+    const int ik = N != 256 ? sw(k & (M - 1)) : (r < 3 ? pa + 1 + r : lay_a(k & (M - 1)));
+    const float2 zk = buf[ik];
+    const float2 zm = cconj(buf[N == 256 ? pb + 3 - r : sw((M - k) & (M - 1))]);
     const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
     const float2 dd = csub(zk, zm);
     const float2 o = make_float2(0.5f * dd.y, -0.5f * dd.x);
@@ -333,10 +415,13 @@ __device__ __forceinline__ void small_scale_modes(float2 *buf, const float *__re
     const float2 p0 = unit_phase(w.y), p1 = unit_phase(w.w);
     const float a0 = s0 * sqrt_pos((nyq ? 2.0f : 1.0f) * neg_log_uniform(w.x));
     const float a1 = s1 * sqrt_pos(neg_log_uniform(w.z));
-    buf[sw(m0)] = make_float2(a0 * p0.x, nyq ? 0.f : a0 * p0.y);
-    buf[sw(m1)] = make_float2(a1 * p1.x, a1 * p1.y);
+    // N = 256 (layout LA): mode 2c + e, c = t + 32 q, at lay_a(2t) + e + 68 q
+    const int i0 = N != 256 ? sw(m0) : (nyq ? lay_a(M) : lay_a(2 * t) + 68 * q);
+    const int i1 = N != 256 ? sw(m1) : lay_a(2 * t) + 1 + 68 * q;
+    buf[i0] = make_float2(a0 * p0.x, nyq ? 0.f : a0 * p0.y);
+    buf[i1] = make_float2(a1 * p1.x, a1 * p1.y);
   }
-  if (t == 0) buf[sw(0)] = make_float2(0.f, 0.f);
+  if (t == 0) buf[0] = make_float2(0.f, 0.f);  // sw(0) = lay_a(0) = 0
 }
 
 // ------------------------------------------------------------------ fixed-point gather

@@ -12,7 +12,7 @@ namespace mk {
 template <int N>
 struct TeamSmem {
   static constexpr int T = N / 8;
-  static constexpr int BUF = N / 2 + 2;
+  static constexpr int BUF = N == 256 ? kBuf256 : N / 2 + 2;  // complex slots per team buffer
   __host__ __device__ static size_t acc_bytes(int threads, int n_z, int n_k, bool stats) {
     return stats ? static_cast<size_t>(threads / 32) * WarpAcc::bytes(n_z, n_k) : 0;
   }

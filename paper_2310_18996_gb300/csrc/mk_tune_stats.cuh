@@ -21,36 +21,40 @@ struct TuneSmem {
   }
 };
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-               "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-               "l"(src)
+// 16-byte copy of which the first nb bytes come from src and the rest are zero
+// (nb = 0 reads nothing)
+__device__ __forceinline__ void cp_async16z(void *dst, const void *src, int nb) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+               "l"(src), "r"(nb)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Copy the npx floats of a field from global index `start` into sd: 16-byte
-// pieces from start rounded down to 16 bytes (pixel p lands at sd[shift + p]),
-// 4-byte copies for the last piece when it would run past the segment.
-template <int T>
+// Where the tuning pass finds a segment: its first field index, pixels,
+// first pixel-table index, and whether its pixels lie inside the tables.
+struct TuneSeg {
+  int64_t start;
+  int npx, jb;
+  bool ok;
+};
+
+// Stage the npx floats of a field from global index `start` into sd: N/4 + 1
+// 16-byte pieces from start rounded down to 16 bytes (pixel p lands at
+// sd[(start & 3) + p]); a piece's bytes past the segment are zero-filled, not
+// read.  Thread t of the team copies pieces t and t + T (and t = 0 the last).
+template <int N>
 __device__ __forceinline__ void stage_field(float *sd, const float *__restrict__ f, int64_t start, int npx, int t) {
+  constexpr int T = N / 8;
   const int shift = static_cast<int>(start & 3);
   const float *base = f + (start - shift);
-  const int nch = (npx + shift + 3) >> 2;
-  for (int c = t; c < nch; c += T) {
-    const int r0 = 4 * c - shift;  // segment pixel of the piece's first float
-    if (r0 + 4 <= npx) {
-      cp_async16(sd + 4 * c, base + 4 * c);
-    } else {
+  const int end = shift + npx;  // floats of the staged range that belong to the segment
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (r0 + e >= 0 && r0 + e < npx) cp_async4(sd + 4 * c + e, base + 4 * c + e);
-    }
+  for (int r = 0; r < 3; ++r) {
+    const int c = r < 2 ? t + r * T : N / 4;
+    if (r == 2 && t != 0) break;
+    const int nb = min(max(4 * (end - 4 * c), 0), 16);
+    cp_async16z(sd + 4 * c, nb ? base + 4 * c : base, nb);
   }
 }
 
@@ -69,8 +73,8 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
   float2 *buf = tws + TwTab<N>::SLOTS * T + team * BUF;
   float *fb = reinterpret_cast<float *>(buf);
   // stage buffers b = 0, 1: delta at stage + 2 b STAGE, eta at stage + (2 b + 1) STAGE
-  float *stage = reinterpret_cast<float *>(smem + TeamSmem<N>::bytes(blockDim.x, P.n_z, P.n_k, true)) +
-                 team * 4 * STAGE;
+  float *stage_buf = reinterpret_cast<float *>(smem + TeamSmem<N>::bytes(blockDim.x, P.n_z, P.n_k, true)) +
+                     team * 4 * STAGE;
   const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
   zero_warp_acc(smem + warp * wbytes, wbytes);
   fill_twiddles<N>(tws, P.tw);
@@ -82,54 +86,69 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
   const int64_t u_first = u;
   const int64_t uend = (g + 1) * nunits / G;
   int64_t i = u < uend ? upper_index(P.segoff, P.n_sk, u) : 0;
-  int64_t inext = i;  // skewer of the next segment to stage
+  int64_t inext = i;  // skewer of the segment to describe next
   const int wlo0 = t & ~31;
   PixelSums acc;
   acc.zero();
   int zc = -2;
 
-  // copy segment uu (of skewer inext, advanced as needed) into buffer b
-  auto stage_segment = [&](int64_t uu, int b) {
+  // describe segment uu (of skewer inext, advanced as needed); team-uniform
+  auto describe = [&](int64_t uu) -> TuneSeg {
     while (P.segoff[inext + 1] <= uu) ++inext;
-    const int64_t o = P.off_out[inext];
+    const int64_t o = P.off_out[inext], nout = P.off_out[inext + 1] - o;
     const int64_t k0 = (uu - P.segoff[inext]) * N;
-    const int npx = static_cast<int>(min(static_cast<int64_t>(N), P.off_out[inext + 1] - o - k0));
-    const int64_t start = P.sk[inext].offset + k0;
-    stage_field<T>(stage + 2 * b * STAGE, P.delta, start, npx, t);
-    stage_field<T>(stage + (2 * b + 1) * STAGE, P.eta, start, npx, t);
+    const int64_t off = P.sk[inext].offset;
+    const int j_lo = P.sk[inext].j_lo;
+    TuneSeg d;
+    d.start = off + k0;
+    d.npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
+    // records made for another pixel length may run past the pixel tables
+    d.ok = j_lo >= 0 && j_lo + nout <= P.j_max;
+    d.jb = d.ok ? j_lo + static_cast<int>(k0) : 0;
+    return d;
   };
-  if (u < uend) stage_segment(u, 0);
+  auto stage = [&](const TuneSeg &d, int b) {
+    stage_field<N>(stage_buf + 2 * b * STAGE, P.delta, d.start, d.npx, t);
+    stage_field<N>(stage_buf + (2 * b + 1) * STAGE, P.eta, d.start, d.npx, t);
+  };
+  TuneSeg cur{0, 0, 0, false};
+  if (u < uend) {
+    cur = describe(u);
+    stage(cur, 0);
+  }
   cp_async_commit();
   team_sync<T>(team);
 
   for (; u < uend; ++u) {
     const int b = static_cast<int>((u - u_first) & 1);
-    if (u + 1 < uend) stage_segment(u + 1, b ^ 1);
+    TuneSeg nxt = cur;
+    if (u + 1 < uend) {
+      nxt = describe(u + 1);
+      stage(nxt, b ^ 1);
+    }
     cp_async_commit();  // one group per segment (possibly empty)
-    while (P.segoff[i + 1] <= u) ++i;
-    const int s = static_cast<int>(u - P.segoff[i]);
-    const mk_skewer sk = P.sk[i];
-    const int64_t nout = P.off_out[i + 1] - P.off_out[i];
-    const bool in_tables = sk.j_lo >= 0 && sk.j_lo + nout <= P.j_max;  // team-uniform
-    const int64_t k0 = static_cast<int64_t>(s) * N;
-    const int npx = static_cast<int>(min(static_cast<int64_t>(N), nout - k0));
-    const int jb = in_tables ? sk.j_lo + static_cast<int>(k0) : 0;
+    const int npx = cur.npx, jb = cur.jb;
     // the FGPA table and bin entries of this segment, requested before the
     // wait for the staged fields so that their latency overlaps it
+    // (indices clamped to the segment's last pixel)
     const float4 *tp = P.pixtab + jb + t;
     float4 tb[8];
+    int zs0 = 0;
+    if (cur.ok) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) tb[q] = (in_tables && t + T * q < npx) ? __ldg(tp + T * q) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const int zs0 = in_tables ? __ldg(P.zbin + jb) : 0;
+      for (int q = 0; q < 8; ++q) tb[q] = __ldg(tp + min(T * q, npx - 1 - t));
+      zs0 = __ldg(P.zbin + jb);
+    }
     cp_async_wait_prior();  // this segment's copies are in
     team_sync<T>(team);
-    if (!in_tables) {  // records made for another pixel length: skip, as in k_stats
+    if (!cur.ok) {  // skip the segment, as k_stats does
       if (t == 0) raise_error(P.err, ERR_RANGE);
       team_sync<T>(team);
+      cur = nxt;
       continue;
     }
-    const int shift = static_cast<int>((sk.offset + k0) & 3);
-    const float *sd = stage + 2 * b * STAGE + shift, *se = stage + (2 * b + 1) * STAGE + shift;
+    const int shift = static_cast<int>(cur.start & 3);
+    const float *sd = stage_buf + 2 * b * STAGE + shift, *se = stage_buf + (2 * b + 1) * STAGE + shift;
     if (zs0 != zc) {
       if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
       acc.zero();
@@ -187,6 +206,7 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
       }
     }
     team_sync<T>(team);  // the stage buffer b and fb are free again
+    cur = nxt;
   }
   if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
   flush_warp_partials(smem, nwarps, wbytes, P.n_z, P.n_k, P.partials);
