@@ -753,6 +753,10 @@ struct PixelSums {
   }
   __device__ __forceinline__ void add(float F, float2 x) {
     n += 1.f;
+    add_sums(F, x);
+  }
+  // the sums without the count (a full segment adds its count once)
+  __device__ __forceinline__ void add_sums(float F, float2 x) {
     f += F;
     ff = fmaf(F, F, ff);
     de = fmaf(x.x, x.y, de);

@@ -201,12 +201,13 @@ __global__ void __launch_bounds__(256, MINB) k_skewer(SkewerParams P) {
         const int p = t + T * k;
         float2 x;
         const float f = synth(p, x);
-        if (P.do_stats) acc.add(f, x);
+        if (P.do_stats) acc.add_sums(f, x);
         fb[p] = f;
         px += sx;
         py += sy;
         pz += sz;
       }
+      acc.n += 8.f;  // this thread's pixels of the segment
     } else {
 #pragma unroll 2
     for (int k = 0; k < 8; ++k) {
@@ -336,9 +337,10 @@ __global__ void __launch_bounds__(256, 2) k_stats(StatParams P) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           const float f = fgpa(tb[q], dv[q], ev[q]);
-          acc.add(f, make_float2(dv[q], ev[q]));
+          acc.add_sums(f, make_float2(dv[q], ev[q]));
           fb[t + T * q] = f;
         }
+        acc.n += 8.f;
       } else {
       // streaming case: issue every load of the thread's 8 pixels before any use
       float dv[8], ev[8], fv[8];

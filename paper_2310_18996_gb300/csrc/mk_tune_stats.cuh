@@ -162,9 +162,10 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
         const int p = t + T * q;
         const float2 x = make_float2(sd[p], se[p]);
         const float f = fgpa(tb[q], x.x, x.y);
-        acc.add(f, x);
+        acc.add_sums(f, x);
         fb[p] = f;
       }
+      acc.n += 8.f;  // this thread's pixels of the segment
     } else {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {  // (unrolled: tb[q] stays in registers)
