@@ -12,11 +12,15 @@ namespace mk {
 // delta and eta copied into shared memory (cp.async, 16-byte pieces) while
 // the current one is processed, so that the HBM latency hides behind the
 // current segment's FFT.
+// Shared memory: per-warp accumulators, the twiddle table, then per team two
+// stage buffers of delta and eta (a segment's FFT runs in its own stage
+// buffer once its fields are read).
 template <int N>
 struct TuneSmem {
   static constexpr int STAGE = N + 4;  // floats per field and buffer (a segment plus its 16-byte misalignment)
+  static_assert(2 * STAGE >= 2 * TeamSmem<N>::BUF, "a stage buffer holds the FFT buffer");
   static size_t bytes(int threads, int n_z, int n_k) {
-    return TeamSmem<N>::bytes(threads, n_z, n_k, true) +
+    return TeamSmem<N>::acc_bytes(threads, n_z, n_k, true) + TwTab<N>::BYTES +
            static_cast<size_t>(threads / (N / 8)) * 4 * STAGE * sizeof(float);
   }
 };
@@ -62,7 +66,6 @@ __device__ __forceinline__ void stage_field(float *sd, const float *__restrict__
 template <int N>
 __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
   constexpr int T = N / 8;
-  constexpr int BUF = TeamSmem<N>::BUF;
   constexpr int STAGE = TuneSmem<N>::STAGE;
   const int teams = blockDim.x / T;
   const int team = threadIdx.x / T, t = threadIdx.x % T, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -70,11 +73,8 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
   float2 *tws = reinterpret_cast<float2 *>(smem + nwarps * wbytes);
-  float2 *buf = tws + TwTab<N>::SLOTS * T + team * BUF;
-  float *fb = reinterpret_cast<float *>(buf);
   // stage buffers b = 0, 1: delta at stage + 2 b STAGE, eta at stage + (2 b + 1) STAGE
-  float *stage_buf = reinterpret_cast<float *>(smem + TeamSmem<N>::bytes(blockDim.x, P.n_z, P.n_k, true)) +
-                     team * 4 * STAGE;
+  float *stage_buf = reinterpret_cast<float *>(smem + nwarps * wbytes + TwTab<N>::BYTES) + team * 4 * STAGE;
   const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
   zero_warp_acc(smem + warp * wbytes, wbytes);
   fill_twiddles<N>(tws, P.tw);
@@ -149,6 +149,10 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
     }
     const int shift = static_cast<int>(cur.start & 3);
     const float *sd = stage_buf + 2 * b * STAGE + shift, *se = stage_buf + (2 * b + 1) * STAGE + shift;
+    // the segment's FFT buffer: its own stage buffer, written once every
+    // field value of the segment has been read
+    float2 *buf = reinterpret_cast<float2 *>(stage_buf + 2 * b * STAGE);
+    float *fb = reinterpret_cast<float *>(buf);
     if (zs0 != zc) {
       if (zc != -2) flush_bin_sums(W, P.n_z, zc, acc, lane);
       acc.zero();
@@ -156,26 +160,26 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
     }
     int pend = __ldg(P.bin_end + zc + 1) - jb;
     const bool one_bin = min(T * 7 + wlo0 + 32, npx) <= pend;
+    float2 xv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      xv[q] = t + T * q < npx ? make_float2(sd[t + T * q], se[t + T * q]) : make_float2(0.f, 0.f);
+    team_sync<T>(team);  // every field value read before fb overwrites the buffer
     if (npx == N && one_bin) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        const int p = t + T * q;
-        const float2 x = make_float2(sd[p], se[p]);
-        const float f = fgpa(tb[q], x.x, x.y);
-        acc.add_sums(f, x);
-        fb[p] = f;
+        const float f = fgpa(tb[q], xv[q].x, xv[q].y);
+        acc.add_sums(f, xv[q]);
+        fb[t + T * q] = f;
       }
       acc.n += 8.f;  // this thread's pixels of the segment
     } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {  // (unrolled: tb[q] stays in registers)
+      for (int q = 0; q < 8; ++q) {  // (unrolled: tb[q] and xv[q] stay in registers)
         const int p = t + T * q;
         float f = 0.f;
-        float2 x = make_float2(0.f, 0.f);
-        if (p < npx) {
-          x = make_float2(sd[p], se[p]);
-          f = fgpa(tb[q], x.x, x.y);
-        }
+        const float2 x = xv[q];
+        if (p < npx) f = fgpa(tb[q], x.x, x.y);
         if (one_bin) {
           if (p < npx) acc.add(f, x);
         } else {
