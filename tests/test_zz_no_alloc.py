@@ -91,7 +91,7 @@ def test_static_scratch_needs_tables_and_allocates_nothing():
     assert rc == mk.MK_EINVAL and b"z-bin tables" in mk.lib().mk_last_error(ctx.h)
     assert torch.cuda.mem_get_info()[0] == free0
     # after one allocating statistics call the static call allocates nothing
-    # (the first static call may make the driver load the library's device
+    # (the first static call may make the CUDA driver load the library's device
     # image, which holds the fixed array: free memory is compared after it)
     ref = ctx.stats(w, r["sk"], n, off, f, delta=r["delta"], eta=r["eta"])
     rc, _ = _static_stats(ctx, w, r["sk"], n, off, f, r["delta"], r["eta"])
