@@ -9,58 +9,94 @@ namespace mk {
 // =================================================================== tuning-pass kernel
 // The tuning pass (FGPA of stored delta, eta at full resolution, then the
 // statistics): k_stats's pixel and P1D work, with each team's next segment of
-// delta and eta copied into shared memory (cp.async, 16-byte pieces) while
+// delta and eta copied into shared memory by the bulk-copy (TMA) engine while
 // the current one is processed, so that the HBM latency hides behind the
 // current segment's FFT.
-// Shared memory: per-warp accumulators, the twiddle table, then per team two
-// stage buffers of delta and eta (a segment's FFT runs in its own stage
-// buffer once its fields are read).
+// Shared memory: per-warp accumulators, the twiddle table, per team two stage
+// buffers of delta and eta (a segment's FFT runs in its own stage buffer once
+// its fields are read), then per team one mbarrier per stage buffer.
 template <int N>
 struct TuneSmem {
   static constexpr int STAGE = N + 4;  // floats per field and buffer (a segment plus its 16-byte misalignment)
   static_assert(2 * STAGE >= 2 * TeamSmem<N>::BUF, "a stage buffer holds the FFT buffer");
+  static_assert((STAGE * sizeof(float)) % 16 == 0, "stage buffers start on 16 bytes");
+  __host__ __device__ static size_t stage_bytes(int threads) {
+    return static_cast<size_t>(threads / (N / 8)) * 4 * STAGE * sizeof(float);
+  }
   static size_t bytes(int threads, int n_z, int n_k) {
-    return TeamSmem<N>::acc_bytes(threads, n_z, n_k, true) + TwTab<N>::BYTES +
-           static_cast<size_t>(threads / (N / 8)) * 4 * STAGE * sizeof(float);
+    return TeamSmem<N>::acc_bytes(threads, n_z, n_k, true) + TwTab<N>::BYTES + stage_bytes(threads) +
+           static_cast<size_t>(threads / (N / 8)) * 2 * sizeof(uint64_t);
   }
 };
 
-// 16-byte copy of which the first nb bytes come from src and the rest are zero
-// (nb = 0 reads nothing)
-__device__ __forceinline__ void cp_async16z(void *dst, const void *src, int nb) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-               "l"(src), "r"(nb)
+// ------------------------------------------------------------------ bulk copies
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+// the initialised barriers are visible to the bulk-copy engine
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// the one expected arrival of a phase, with the bytes its copies will bring
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for the phase of the given parity, for about a second at most (the
+// copies of a segment take microseconds); false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+// earlier generic accesses of shared memory are ordered before later bulk copies into it
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared memory
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// true when pred holds on every thread of the team (a barrier of the team)
+template <int T>
+__device__ __forceinline__ bool team_all(int team, bool pred) {
+  if constexpr (T == 32) {
+    return __all_sync(0xffffffffu, pred);
+  } else {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.and.pred po, %2, %3, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(pred)), "r"(team + 1), "r"(T)
+        : "memory");
+    return r != 0;
+  }
+}
 
 // Where the tuning pass finds a segment: its first field index, pixels,
-// first pixel-table index, and whether its pixels lie inside the tables.
+// first pixel-table index, whether its pixels lie inside the tables, and the
+// segment's last (shift + npx) mod 4 floats of delta and eta (thread t holds
+// float t of them), which the whole 16-byte pieces of the bulk copies leave.
 struct TuneSeg {
   int64_t start;
   int npx, jb;
   bool ok;
+  float td, te;
 };
-
-// Stage the npx floats of a field from global index `start` into sd: N/4 + 1
-// 16-byte pieces from start rounded down to 16 bytes (pixel p lands at
-// sd[(start & 3) + p]); a piece's bytes past the segment are zero-filled, not
-// read.  Thread t of the team copies pieces t and t + T (and t = 0 the last).
-template <int N>
-__device__ __forceinline__ void stage_field(float *sd, const float *__restrict__ f, int64_t start, int npx, int t) {
-  constexpr int T = N / 8;
-  const int shift = static_cast<int>(start & 3);
-  const float *base = f + (start - shift);
-  const int end = shift + npx;  // floats of the staged range that belong to the segment
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    const int c = r < 2 ? t + r * T : N / 4;
-    if (r == 2 && t != 0) break;
-    const int nb = min(max(4 * (end - 4 * c), 0), 16);
-    cp_async16z(sd + 4 * c, nb ? base + 4 * c : base, nb);
-  }
-}
 
 // P: a tuning pass (rebin 1, fields and FGPA table set; delta, eta 16-byte aligned).
 template <int N>
@@ -74,10 +110,17 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
   const size_t wbytes = WarpAcc::bytes(P.n_z, P.n_k);
   float2 *tws = reinterpret_cast<float2 *>(smem + nwarps * wbytes);
   // stage buffers b = 0, 1: delta at stage + 2 b STAGE, eta at stage + (2 b + 1) STAGE
-  float *stage_buf = reinterpret_cast<float *>(smem + nwarps * wbytes + TwTab<N>::BYTES) + team * 4 * STAGE;
+  unsigned char *stage_base = smem + nwarps * wbytes + TwTab<N>::BYTES;
+  float *stage_buf = reinterpret_cast<float *>(stage_base) + team * 4 * STAGE;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(stage_base + TuneSmem<N>::stage_bytes(blockDim.x)) + 2 * team;
   const WarpAcc W = WarpAcc::at(smem + warp * wbytes, P.n_z, P.n_k);
   zero_warp_acc(smem + warp * wbytes, wbytes);
-  fill_twiddles<N>(tws, P.tw);
+  if (t == 0) {
+    mbar_init(bars);
+    mbar_init(bars + 1);
+    mbar_init_fence();
+  }
+  fill_twiddles<N>(tws, P.tw);  // (ends with a CTA barrier)
 
   const int64_t nunits = P.segoff[P.n_sk];
   const int64_t g = static_cast<int64_t>(blockIdx.x) * teams + team;
@@ -107,26 +150,41 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
     d.jb = d.ok ? j_lo + static_cast<int>(k0) : 0;
     return d;
   };
-  auto stage = [&](const TuneSeg &d, int b) {
-    stage_field<N>(stage_buf + 2 * b * STAGE, P.delta, d.start, d.npx, t);
-    stage_field<N>(stage_buf + (2 * b + 1) * STAGE, P.eta, d.start, d.npx, t);
+  // Copy segment d's fields into stage buffer b: thread 0 of the team issues
+  // two bulk copies of the whole 16-byte pieces from d.start rounded down to
+  // 16 bytes (pixel p lands at (start & 3) + p), completing on bars[b]; the
+  // threads t < (shift + npx) mod 4 load the floats after the last piece.
+  auto stage = [&](TuneSeg &d, int b) {
+    const int shift = static_cast<int>(d.start & 3);
+    const int nfl = (shift + d.npx) & ~3, tail = shift + d.npx - nfl;
+    const float *bd = P.delta + (d.start - shift), *be = P.eta + (d.start - shift);
+    d.td = t < tail ? __ldg(bd + nfl + t) : 0.f;
+    d.te = t < tail ? __ldg(be + nfl + t) : 0.f;
+    if (t == 0) {
+      fence_async_shared();
+      mbar_arrive_tx(bars + b, static_cast<uint32_t>(8 * nfl));
+      if (nfl > 0) {
+        bulk_g2s(stage_buf + 2 * b * STAGE, bd, static_cast<uint32_t>(4 * nfl), bars + b);
+        bulk_g2s(stage_buf + (2 * b + 1) * STAGE, be, static_cast<uint32_t>(4 * nfl), bars + b);
+      }
+    }
   };
-  TuneSeg cur{0, 0, 0, false};
+  uint32_t parity = 0;  // bit b: parity of stage buffer b's next phase
+  bool staged_next = false;
+  TuneSeg cur{0, 0, 0, false, 0.f, 0.f};
   if (u < uend) {
     cur = describe(u);
     stage(cur, 0);
   }
-  cp_async_commit();
-  team_sync<T>(team);
 
   for (; u < uend; ++u) {
     const int b = static_cast<int>((u - u_first) & 1);
     TuneSeg nxt = cur;
-    if (u + 1 < uend) {
+    staged_next = u + 1 < uend;
+    if (staged_next) {
       nxt = describe(u + 1);
       stage(nxt, b ^ 1);
     }
-    cp_async_commit();  // one group per segment (possibly empty)
     const int npx = cur.npx, jb = cur.jb;
     // the FGPA table and bin entries of this segment, requested before the
     // wait for the staged fields so that their latency overlaps it
@@ -139,7 +197,22 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
       for (int q = 0; q < 8; ++q) tb[q] = __ldg(tp + min(T * q, npx - 1 - t));
       zs0 = __ldg(P.zbin + jb);
     }
-    cp_async_wait_prior();  // this segment's copies are in
+    // this segment's copies are in; its last floats join them from registers
+    const bool arrived = mbar_wait(bars + b, (parity >> b) & 1u);
+    parity ^= 1u << b;
+    if (!team_all<T>(team, arrived)) {  // (team-uniform) the copies never completed
+      if (t == 0) raise_error(P.err, ERR_TIMEOUT);
+      if (staged_next) mbar_wait(bars + (b ^ 1), (parity >> (b ^ 1)) & 1u);  // before leaving, with a limit
+      break;
+    }
+    {
+      const int shift = static_cast<int>(cur.start & 3);
+      const int nfl = (shift + npx) & ~3;
+      if (t < shift + npx - nfl) {
+        stage_buf[2 * b * STAGE + nfl + t] = cur.td;
+        stage_buf[(2 * b + 1) * STAGE + nfl + t] = cur.te;
+      }
+    }
     team_sync<T>(team);
     if (!cur.ok) {  // skip the segment, as k_stats does
       if (t == 0) raise_error(P.err, ERR_RANGE);
