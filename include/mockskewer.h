@@ -755,6 +755,16 @@ int mk_load_skewers(mk_ctx *ctx, const char *path, mk_skewer *d_sk, int64_t cap_
    max_ctas < 0. */
 int mk_set_grid_cap(mk_ctx *ctx, int32_t max_ctas);
 
+/* Test hook for the one device wait of the library: the tuning pass
+   (mk_flux_stats, the passes of mk_tune) waits for the bulk copies of each
+   segment's fields on an mbarrier, for about a second at most, and then
+   reports MK_ETIMEOUT (the context stays usable).  With on != 0 the pass
+   issues no copies while still expecting their bytes and gives up after
+   about 2^20 clock cycles, so that every such wait runs out; results are
+   then invalid and the call returns MK_ETIMEOUT.  0 (the default) restores
+   normal operation.  Takes effect at the next call. */
+int mk_set_wait_test(mk_ctx *ctx, int32_t on);
+
 /* ---------------------------------------------------------------- timing */
 
 /* When on (non-zero), the library records CUDA events on the context's

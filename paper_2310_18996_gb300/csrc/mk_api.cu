@@ -194,6 +194,7 @@ struct mk_ctx {
   bool timed = false;
   unsigned char *static_scratch = nullptr;  // device address of mk_stats_static's array
   int grid_cap = 0;  // at most this many CTAs for the persistent kernels (0: no cap)
+  int wait_test = 0;  // test hook of the tuning pass's bounded wait (mk_set_wait_test)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // mk_run_host: device copies of the catalogue and records, two staging
   // buffers, slice boundaries, copy streams and their events
@@ -865,6 +866,7 @@ int stats_pass(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_s
   P.dr = params->dr;
   P.partials = ctx->d_partials;
   P.err = ctx->d_err;
+  P.wait_test = ctx->wait_test;
   if ((rc = time_begin(ctx))) return rc;
   CK(launch_stats(P, bins->n_fft, grid, threads, ctx->stream));
   if ((rc = time_end(ctx))) return rc;
@@ -1190,6 +1192,12 @@ int mk_set_grid_cap(mk_ctx *ctx, int32_t max_ctas) {
   if (!ctx) return MK_EINVAL;
   if (max_ctas < 0) return fail(ctx, MK_EINVAL, "max_ctas must be >= 0");
   ctx->grid_cap = max_ctas;
+  return MK_OK;
+}
+
+int mk_set_wait_test(mk_ctx *ctx, int32_t on) {
+  if (!ctx) return MK_EINVAL;
+  ctx->wait_test = on != 0;
   return MK_OK;
 }
 

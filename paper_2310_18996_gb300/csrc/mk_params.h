@@ -134,6 +134,7 @@ struct StatParams {
   float p1d_scale;  // rebin dr / N
   double *partials;
   int *err;
+  int32_t wait_test;  // test hook: the tuning pass issues no bulk copies and waits ~2^20 cycles at most
 };
 
 struct FluxParams {

@@ -51,13 +51,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-// Wait for the phase of the given parity, for about a second at most (the
-// copies of a segment take microseconds); false when the wait gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the phase of the given parity for at most `limit` clock cycles
+// (the copies of a segment take microseconds); false when the wait gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
 // earlier generic accesses of shared memory are ordered before later bulk copies into it
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
     if (t == 0) {
       fence_async_shared();
       mbar_arrive_tx(bars + b, static_cast<uint32_t>(8 * nfl));
-      if (nfl > 0) {
+      if (nfl > 0 && !P.wait_test) {  // (the test hook leaves the expected bytes missing)
         bulk_g2s(stage_buf + 2 * b * STAGE, bd, static_cast<uint32_t>(4 * nfl), bars + b);
         bulk_g2s(stage_buf + (2 * b + 1) * STAGE, be, static_cast<uint32_t>(4 * nfl), bars + b);
       }
@@ -198,11 +198,12 @@ __global__ void __launch_bounds__(256, 2) k_tune_stats(StatParams P) {
       zs0 = __ldg(P.zbin + jb);
     }
     // this segment's copies are in; its last floats join them from registers
-    const bool arrived = mbar_wait(bars + b, (parity >> b) & 1u);
+    const long long limit = P.wait_test ? (1LL << 20) : (1LL << 31);  // cycles: ~0.5 ms, ~1 s
+    const bool arrived = mbar_wait(bars + b, (parity >> b) & 1u, limit);
     parity ^= 1u << b;
     if (!team_all<T>(team, arrived)) {  // (team-uniform) the copies never completed
       if (t == 0) raise_error(P.err, ERR_TIMEOUT);
-      if (staged_next) mbar_wait(bars + (b ^ 1), (parity >> (b ^ 1)) & 1u);  // before leaving, with a limit
+      if (staged_next) mbar_wait(bars + (b ^ 1), (parity >> (b ^ 1)) & 1u, limit);  // before leaving
       break;
     }
     {

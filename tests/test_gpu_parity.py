@@ -205,6 +205,27 @@ def test_tuning_pass_unaligned_fields_match_oracle(ctx, tiny):
         np.testing.assert_array_equal(st_u[k], st_a[k])
 
 
+def test_tuning_pass_wait_times_out_and_context_survives(ctx, tiny):
+    """The tuning pass's one device wait (the mbarrier of each segment's bulk
+    copies) is bounded: with the test hook no copy is issued, every team gives
+    up after a short wait, the call reports MK_ETIMEOUT, and the next pass on
+    the same context is correct."""
+    w, dv = tiny["w"], tiny["dev"]
+    box = ctx.load_box(w, dv["d"], dv["e"])
+    n = len(tiny["ids"])
+    r = ctx.make_skewers(box, dv["qso"], n, w)
+    assert r["delta"].data_ptr() % 16 == 0 and r["eta"].data_ptr() % 16 == 0  # the staged kernel runs
+    ctx.set_wait_test(True)
+    try:
+        with pytest.raises(mk.MkError) as ei:
+            ctx.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+        assert ei.value.code == mk.MK_ETIMEOUT
+    finally:
+        ctx.set_wait_test(False)
+    st = ctx.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+    assert_stats_close(st, tiny["st"])
+
+
 @pytest.mark.parametrize("layout", ["planar", "padded"])
 def test_fused_path_matches_split_path_and_oracle(ctx, tiny, layout):
     w, dv = tiny["w"], tiny["dev"]
