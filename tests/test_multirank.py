@@ -93,6 +93,50 @@ def _merge_worker(rank, world, port, out):
     dist.destroy_process_group()
 
 
+def _dead_rank_worker(rank, world, port, out):
+    """Rank 1 leaves after joining the group, before the statistics exchange
+    (a killed process); rank 0 must get an error from the exchange, not hang."""
+    import datetime
+    import sys
+    import time
+
+    sys.path.insert(0, ROOT)
+    import oracle
+    import paper_2310_18996_gb300 as mk
+    import skewer_inputs as si
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(0)  # no shutdown of the process group: its peer sees a dead rank
+    w = si.workload("tiny")
+    d, e = si.gaussian_box(w["n"], w["cell"], w["seed_box"], backend="numpy")
+    pos, ids = si.catalogue(w, n_q=20)
+    o = oracle.run_skewers(w, d, e, pos, ids)
+    st = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
+    t0 = time.monotonic()
+    try:
+        mk.merge_stats_across_ranks(st, w, dist)
+        out[rank] = ("merged", time.monotonic() - t0)
+    except RuntimeError as ex:  # gloo reports the lost peer (or the group's timeout)
+        out[rank] = ("error: " + str(ex)[:200], time.monotonic() - t0)
+
+
+def test_statistics_merge_with_a_dead_rank_fails_without_hanging():
+    """A rank that dies before the exchange of raw sums: the surviving rank's
+    merge raises within the process group's 10 s timeout instead of waiting
+    forever, so the job can report the failure."""
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_dead_rank_worker, args=(2, port, out), nprocs=2, join=True)
+        res = dict(out)
+    status, seconds = res[0]
+    assert status.startswith("error"), status
+    assert seconds < 60
+
+
 def test_two_rank_statistics_merge_equals_union():
     """Sec. 3 runs the mocks in independent slices; statistics of the whole
     catalogue follow from the slices' raw sums.  Two gloo ranks, each with the
