@@ -765,6 +765,18 @@ int mk_set_grid_cap(mk_ctx *ctx, int32_t max_ctas);
    normal operation.  Takes effect at the next call. */
 int mk_set_wait_test(mk_ctx *ctx, int32_t on);
 
+/* Test hook for the host-side error paths: the next step of the given kind
+   fails once, as if the CUDA call had failed, and the call that meets it
+   returns the matching code with nothing half done that a later call would
+   trust.  MK_FAULT_ALLOC: the next growth of a library workspace
+   (MK_ENOMEM).  MK_FAULT_LAUNCH: the next fused run (mk_run) or statistics
+   pass (mk_stats, mk_flux_stats) before its kernels are launched (MK_ECUDA).
+   MK_FAULT_NONE clears a pending fault.  MK_EINVAL for other kinds. */
+#define MK_FAULT_NONE 0
+#define MK_FAULT_ALLOC 1
+#define MK_FAULT_LAUNCH 2
+int mk_inject_fault(mk_ctx *ctx, int32_t kind);
+
 /* ---------------------------------------------------------------- timing */
 
 /* When on (non-zero), the library records CUDA events on the context's

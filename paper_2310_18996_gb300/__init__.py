@@ -19,6 +19,7 @@ import numpy as np
 from . import build as _build
 
 MK_OK, MK_EINVAL, MK_ECUDA, MK_ENOMEM, MK_ETIMEOUT, MK_ERANGE = range(6)
+FAULT_NONE, FAULT_ALLOC, FAULT_LAUNCH = range(3)
 MAX_NODES, MAX_ZBINS, MAX_KBINS, NSUM = 32, 32, 64, 10
 STATIC_MAX_SKEWERS = 131072
 BOX_PLANAR, BOX_INTERLEAVED, BOX_PADDED, BOX_HALO, BOX_TENSOR = 0, 1, 2, 3, 4
@@ -34,7 +35,7 @@ EXPORTS = ["mk_create", "mk_destroy", "mk_last_error", "mk_set_stream", "mk_sync
            "mk_mlp_loss_grad", "mk_mlp_train", "mk_surrogate_labels", "mk_surrogate_fit", "mk_tune",
            "mk_fgpa_gauss_moments", "mk_fit_a_bsigma", "mk_tune_ps", "mk_synth_box", "mk_xi_of_pk",
            "mk_lognormal_pk", "mk_draw_qso", "mk_cosmo_eval", "mk_save_skewers", "mk_load_skewers",
-           "mk_set_grid_cap", "mk_mlp_adam_step", "mk_set_wait_test"]
+           "mk_set_grid_cap", "mk_mlp_adam_step", "mk_set_wait_test", "mk_inject_fault"]
 
 
 class MkError(RuntimeError):
@@ -206,6 +207,7 @@ def lib():
                 "mk_load_skewers": (C.c_int, [vp, C.c_char_p, vp, i64, vp, vp, vp, i64, P(i64), P(i64)]),
                 "mk_set_grid_cap": (C.c_int, [vp, i32]),
                 "mk_set_wait_test": (C.c_int, [vp, i32]),
+                "mk_inject_fault": (C.c_int, [vp, i32]),
                 "mk_set_timing": (C.c_int, [vp, C.c_int]),
                 "mk_last_kernel_ms": (C.c_int, [vp, P(C.c_double)]),
             }
@@ -385,6 +387,10 @@ class Context:
     def set_grid_cap(self, max_ctas=0):
         """At most max_ctas CTAs for the persistent kernels (0: no cap)."""
         self._check(lib().mk_set_grid_cap(self.h, int(max_ctas)))
+
+    def inject_fault(self, kind):
+        """Test hook: the next step of this kind fails once (mk_inject_fault)."""
+        self._check(lib().mk_inject_fault(self.h, int(kind)))
 
     def set_wait_test(self, on):
         """Test hook: the tuning pass's bounded device wait runs out (mk_set_wait_test)."""

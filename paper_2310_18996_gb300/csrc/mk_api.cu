@@ -195,6 +195,7 @@ struct mk_ctx {
   unsigned char *static_scratch = nullptr;  // device address of mk_stats_static's array
   int grid_cap = 0;  // at most this many CTAs for the persistent kernels (0: no cap)
   int wait_test = 0;  // test hook of the tuning pass's bounded wait (mk_set_wait_test)
+  int fault = 0;      // test hook: MK_FAULT_ALLOC or MK_FAULT_LAUNCH fails the next such step once
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // mk_run_host: device copies of the catalogue and records, two staging
   // buffers, slice boundaries, copy streams and their events
@@ -227,8 +228,17 @@ int fail(mk_ctx *ctx, int code, const char *fmt, ...) {
     if (e_ != cudaSuccess) return fail(ctx, MK_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// the injected failure of kind `kind`, once (mk_inject_fault)
+int take_fault(mk_ctx *ctx, int kind) {
+  if (ctx->fault != kind) return MK_OK;
+  ctx->fault = 0;
+  return kind == MK_FAULT_ALLOC ? fail(ctx, MK_ENOMEM, "injected device allocation failure")
+                                : fail(ctx, MK_ECUDA, "injected kernel launch failure");
+}
+
 int grow(mk_ctx *ctx, void **p, size_t *cap, size_t need) {
   if (*cap >= need && *p) return MK_OK;
+  if (int rc = take_fault(ctx, MK_FAULT_ALLOC)) return rc;  // (the old buffer stays as it was)
   ++ctx->generation;
   if (*p) cudaFree(*p);
   *p = nullptr;
@@ -242,7 +252,8 @@ int grow(mk_ctx *ctx, void **p, size_t *cap, size_t need) {
 }
 
 int ensure_counts(mk_ctx *ctx, int64_t n) {
-  if (ctx->cnt_cap >= n + 1 && ctx->d_cnt_px) return MK_OK;
+  // (the scan workspace is checked as well: an earlier call may have failed to grow it)
+  if (ctx->cnt_cap >= n + 1 && ctx->d_cnt_px) return grow(ctx, &ctx->d_scan_ws, &ctx->scan_cap, scan_workspace_bytes(n));
   ++ctx->generation;
   cudaFree(ctx->d_cnt_px);
   cudaFree(ctx->d_cnt_seg);
@@ -867,6 +878,7 @@ int stats_pass(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_s
   P.partials = ctx->d_partials;
   P.err = ctx->d_err;
   P.wait_test = ctx->wait_test;
+  if ((rc = take_fault(ctx, MK_FAULT_LAUNCH))) return rc;
   if ((rc = time_begin(ctx))) return rc;
   CK(launch_stats(P, bins->n_fft, grid, threads, ctx->stream));
   if ((rc = time_end(ctx))) return rc;
@@ -916,6 +928,7 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
   if ((flags & MK_GRAPH) && !ctx->stream)
     return fail(ctx, MK_EINVAL, "MK_GRAPH needs a non-default stream (the legacy stream cannot be captured)");
   CK(cudaSetDevice(ctx->device));
+  if ((rc = take_fault(ctx, MK_FAULT_LAUNCH))) return rc;
   if ((rc = ensure_pixel_tables(ctx, params->dr)) || (rc = ensure_counts(ctx, n_qso)) ||
       (rc = ensure_twiddles(ctx, params->n_fft)) || (rc = ensure_amp(ctx, params)) ||
       (rc = ensure_pixtab(ctx, nodes)))
@@ -1192,6 +1205,13 @@ int mk_set_grid_cap(mk_ctx *ctx, int32_t max_ctas) {
   if (!ctx) return MK_EINVAL;
   if (max_ctas < 0) return fail(ctx, MK_EINVAL, "max_ctas must be >= 0");
   ctx->grid_cap = max_ctas;
+  return MK_OK;
+}
+
+int mk_inject_fault(mk_ctx *ctx, int32_t kind) {
+  if (!ctx) return MK_EINVAL;
+  if (kind < 0 || kind > MK_FAULT_LAUNCH) return fail(ctx, MK_EINVAL, "unknown fault kind %d", kind);
+  ctx->fault = kind;
   return MK_OK;
 }
 

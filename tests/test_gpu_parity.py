@@ -205,6 +205,41 @@ def test_tuning_pass_unaligned_fields_match_oracle(ctx, tiny):
         np.testing.assert_array_equal(st_u[k], st_a[k])
 
 
+def test_injected_faults_leave_the_context_usable(tiny):
+    """Host-side error paths (mk_inject_fault): on a fresh context an injected
+    workspace allocation failure makes the fused run return MK_ENOMEM, and an
+    injected launch failure makes the tuning pass and the fused run return
+    MK_ECUDA; each time the next call on the same context is correct."""
+    c = mk.Context(0)  # fresh, so that the run must grow its workspaces
+    try:
+        w, dv = tiny["w"], tiny["dev"]
+        box = c.load_box(w, dv["d"], dv["e"])
+        n = len(tiny["ids"])
+        c.inject_fault(mk.FAULT_ALLOC)
+        with pytest.raises(mk.MkError) as ei:
+            c.run(box, dv["qso"], n, w, flags=mk.STATS)
+        assert ei.value.code == mk.MK_ENOMEM
+        st, _ = c.run(box, dv["qso"], n, w, flags=mk.STATS)
+        assert_stats_close(st, tiny["st"])
+        r = c.make_skewers(box, dv["qso"], n, w)
+        c.inject_fault(mk.FAULT_LAUNCH)
+        with pytest.raises(mk.MkError) as ei:
+            c.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"])
+        assert ei.value.code == mk.MK_ECUDA
+        assert_stats_close(c.flux_stats(w, r["sk"], n, r["offsets"], r["delta"], r["eta"]), tiny["st"])
+        c.inject_fault(mk.FAULT_LAUNCH)
+        with pytest.raises(mk.MkError) as ei:
+            c.run(box, dv["qso"], n, w, flags=mk.STATS)
+        assert ei.value.code == mk.MK_ECUDA
+        st, _ = c.run(box, dv["qso"], n, w, flags=mk.STATS)
+        assert_stats_close(st, tiny["st"])
+        with pytest.raises(mk.MkError) as ei:
+            c.inject_fault(7)
+        assert ei.value.code == mk.MK_EINVAL
+    finally:
+        c.close()
+
+
 def test_tuning_pass_wait_times_out_and_context_survives(ctx, tiny):
     """The tuning pass's one device wait (the mbarrier of each segment's bulk
     copies) is bounded: with the test hook no copy is issued, every team gives
