@@ -12,6 +12,7 @@
 
 #include "../../include/mockskewer.h"
 #include "mk_kernels.h"
+#include "mk_trace.h"
 
 using namespace mk;
 
@@ -682,6 +683,7 @@ int mk_sync(mk_ctx *ctx) {
 }
 
 int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float *d_delta, const float *d_eta) {
+  MK_TRACE("mk_load_box");
   if (!ctx || !out) return MK_EINVAL;
   *out = nullptr;
   if (!desc) return fail(ctx, MK_EINVAL, "desc is NULL");
@@ -712,6 +714,7 @@ int mk_load_box(mk_ctx *ctx, mk_box **out, const mk_box_desc *desc, const float 
 void mk_free_box(mk_box *box) { delete box; }
 
 int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float *d_eta, float *d_out) {
+  MK_TRACE("mk_pack_box");
   if (!ctx) return MK_EINVAL;
   if (n_voxels < 0 || !d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
   CK(cudaSetDevice(ctx->device));
@@ -720,6 +723,7 @@ int mk_pack_box(mk_ctx *ctx, int64_t n_voxels, const float *d_delta, const float
 }
 
 int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out) {
+  MK_TRACE("mk_pack_box_padded");
   if (!ctx) return MK_EINVAL;
   if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
   if (!d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
@@ -732,6 +736,7 @@ int mk_pack_box_padded(mk_ctx *ctx, int32_t n, const float *d_delta, const float
 }
 
 int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta, float *d_out) {
+  MK_TRACE("mk_pack_box_halo");
   if (!ctx) return MK_EINVAL;
   if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
   if (!d_delta || !d_eta || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
@@ -744,6 +749,7 @@ int mk_pack_box_halo(mk_ctx *ctx, int32_t n, const float *d_delta, const float *
 }
 
 int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float *d_eta6, float *d_out) {
+  MK_TRACE("mk_pack_box_tensor");
   if (!ctx) return MK_EINVAL;
   if (n < 2 || n > 2048 || (n & (n - 1))) return fail(ctx, MK_EINVAL, "box n must be a power of two in [2, 2048]");
   if (!d_delta || !d_eta6 || !d_out) return fail(ctx, MK_EINVAL, "bad pack arguments");
@@ -758,6 +764,7 @@ int mk_pack_box_tensor(mk_ctx *ctx, int32_t n, const float *d_delta, const float
 int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso,
                     const mk_skewer_params *params, mk_skewer *d_sk, int64_t *d_offsets, float *d_delta_out,
                     float *d_eta_out, int64_t capacity_px, int64_t *h_total_px) {
+  MK_TRACE("mk_make_skewers");
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, d_delta_out != nullptr);
   if (rc) return rc;
@@ -798,6 +805,7 @@ int mk_make_skewers(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t
 int mk_flux(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk, const float *d_delta,
             const float *d_eta, const mk_fgpa_nodes *nodes, int32_t rebin, float *d_flux, int64_t *d_offsets_out,
             int64_t capacity_out) {
+  MK_TRACE("mk_flux");
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, false);
   if (rc || (rc = check_nodes(ctx, nodes))) return rc;
@@ -889,6 +897,7 @@ int stats_pass(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_s
 int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
              const int64_t *d_offsets_out, const float *d_flux, int32_t rebin, const float *d_delta,
              const float *d_eta, const mk_stat_bins *bins, mk_stats_out *h_out) {
+  MK_TRACE("mk_stats");
   if (!ctx) return MK_EINVAL;
   if (n_sk > 0 && !d_flux) return fail(ctx, MK_EINVAL, "d_flux is NULL");
   return stats_pass(ctx, params, d_sk, n_sk, d_offsets_out, d_flux, rebin, d_delta, d_eta, nullptr, bins, h_out);
@@ -897,6 +906,7 @@ int mk_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk,
 int mk_flux_stats(mk_ctx *ctx, const mk_skewer_params *params, const mk_skewer *d_sk, int64_t n_sk,
                   const int64_t *d_offsets, const float *d_delta, const float *d_eta, const mk_fgpa_nodes *nodes,
                   const mk_stat_bins *bins, mk_stats_out *h_out) {
+  MK_TRACE("mk_flux_stats");
   if (!ctx) return MK_EINVAL;
   int rc = check_nodes(ctx, nodes);
   if (rc) return rc;
@@ -908,6 +918,7 @@ int mk_run(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, int64_t n_qso, c
            const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, uint32_t flags, mk_skewer *d_sk,
            int64_t *d_offsets, float *d_delta_out, float *d_eta_out, float *d_flux_out, int64_t capacity_px,
            mk_stats_out *h_out) {
+  MK_TRACE("mk_run");
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, true);
   if (rc || (rc = check_nodes(ctx, nodes))) return rc;
@@ -1081,6 +1092,7 @@ int ensure_host_path(mk_ctx *ctx) {
 int mk_run_host(mk_ctx *ctx, const mk_box *box, const mk_qso *h_qso, int64_t n_qso, const mk_skewer_params *params,
                 const mk_fgpa_nodes *nodes, const mk_stat_bins *bins, uint32_t flags, int32_t n_chunks,
                 float *h_flux_out, int64_t capacity_px, int64_t *h_total_px, mk_stats_out *h_out) {
+  MK_TRACE("mk_run_host");
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, true);
   if (rc || (rc = check_nodes(ctx, nodes))) return rc;
@@ -1300,6 +1312,7 @@ extern "C" int mk_stats_static(mk_ctx *ctx, const mk_skewer_params *params, cons
                                const int64_t *d_offsets_out, const float *d_flux, int32_t rebin,
                                const float *d_delta, const float *d_eta, const mk_stat_bins *bins,
                                mk_stats_out *h_out) {
+  MK_TRACE("mk_stats_static");
   if (!ctx) return MK_EINVAL;
   int rc = check_params(ctx, params, false);
   if (rc || (rc = check_bins(ctx, bins))) return rc;
@@ -1431,6 +1444,7 @@ int ctx_pixel_histogram(mk_ctx *ctx, double dr, const mk_skewer *d_sk, int64_t n
 
 extern "C" int mk_synth_box(mk_ctx *ctx, int32_t n, double cell, uint64_t seed, const double *h_pk, int32_t n_pk,
                             double dk, int32_t layout, float *d_work, float *d_spec, float *d_out) {
+  MK_TRACE("mk_synth_box");
   if (!ctx) return MK_EINVAL;
   if (n < 128 || n > 2048 || (n & (n - 1)))
     return fail(ctx, MK_EINVAL, "box side must be 128, 256, 512, 1024 or 2048");

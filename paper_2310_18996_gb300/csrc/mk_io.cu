@@ -9,6 +9,7 @@
 
 #include "../../include/mockskewer.h"
 #include "mk_host.h"
+#include "mk_trace.h"
 
 namespace {
 
@@ -57,6 +58,7 @@ bool fill(FILE *f, T *d, int64_t count, void *h, cudaStream_t st, Check check) {
 
 extern "C" int mk_save_skewers(mk_ctx *ctx, const char *path, const mk_skewer *d_sk, int64_t n_sk,
                                const int64_t *d_offsets, const float *d_delta, const float *d_eta) {
+  MK_TRACE("mk_save_skewers");
   if (!ctx) return MK_EINVAL;
   if (!path || n_sk < 0 || !d_offsets || (n_sk > 0 && (!d_sk || !d_delta || !d_eta)))
     return iofail(ctx, MK_EINVAL, "mk_save_skewers: NULL argument");
@@ -82,6 +84,7 @@ extern "C" int mk_save_skewers(mk_ctx *ctx, const char *path, const mk_skewer *d
 
 extern "C" int mk_load_skewers(mk_ctx *ctx, const char *path, mk_skewer *d_sk, int64_t cap_sk, int64_t *d_offsets,
                                float *d_delta, float *d_eta, int64_t cap_px, int64_t *n_sk, int64_t *total_px) {
+  MK_TRACE("mk_load_skewers");
   if (!ctx) return MK_EINVAL;
   if (!path || !n_sk || !total_px) return iofail(ctx, MK_EINVAL, "mk_load_skewers: NULL argument");
   FILE *f = std::fopen(path, "rb");

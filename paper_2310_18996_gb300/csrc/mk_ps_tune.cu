@@ -12,6 +12,7 @@
 
 #include "../../include/mockskewer.h"
 #include "mk_host.h"
+#include "mk_trace.h"
 
 namespace {
 
@@ -147,6 +148,7 @@ extern "C" int mk_tune_ps(mk_ctx *ctx, const mk_box *box, const mk_qso *d_qso, i
                           const mk_skewer_params *params, const mk_stat_bins *bins, const mk_tune_target *target,
                           int32_t n_outer, int32_t n_inner, mk_skewer *d_sk, int64_t *d_offsets, double *h_p_s,
                           mk_fgpa_nodes *out, mk_ps_tune_report *report) {
+  MK_TRACE("mk_tune_ps");
   if (!ctx) return MK_EINVAL;
   if (!box || !params || !bins || !target || !h_p_s || !out || !report || !d_sk || !d_offsets)
     return pfail(ctx, MK_EINVAL, "mk_tune_ps: NULL argument");

@@ -12,6 +12,7 @@
 #include "../../include/mockskewer.h"
 #include "mk_device.cuh"
 #include "mk_host.h"
+#include "mk_trace.h"
 
 using namespace mk;
 
@@ -210,6 +211,7 @@ extern "C" int mk_lognormal_pk(const double *h_pk, int32_t n_pk, double dk, doub
 
 extern "C" int mk_draw_qso(mk_ctx *ctx, const mk_qso_draw_params *q, const float *const d_box_q[3], int32_t box_stride,
                            mk_qso *d_qso, int64_t capacity, int64_t *h_count) {
+  MK_TRACE("mk_draw_qso");
   if (!ctx) return MK_EINVAL;
   if (!q || !d_box_q || !d_box_q[0] || !d_box_q[1] || !d_box_q[2] || !h_count || (capacity > 0 && !d_qso) ||
       capacity < 0)

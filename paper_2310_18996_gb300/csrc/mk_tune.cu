@@ -12,6 +12,7 @@
 #include "../../include/mockskewer.h"
 #include "mk_host.h"
 #include "mk_mlp.h"
+#include "mk_trace.h"
 
 using namespace mk;
 
@@ -153,6 +154,7 @@ extern "C" int mk_mlp_get_params(mk_mlp *p, float *h_params, uint16_t *h_bf16) {
 }
 
 extern "C" int mk_mlp_forward(mk_mlp *p, const float *d_x, int64_t n, float *d_y) {
+  MK_TRACE("mk_mlp_forward");
   if (!p) return MK_EINVAL;
   if (n < 0 || (n > 0 && (!d_x || !d_y))) return mfail(p->ctx, MK_EINVAL, "bad forward arguments");
   CKM(p->ctx, cudaSetDevice(mkhost::ctx_device(p->ctx)));
@@ -162,6 +164,7 @@ extern "C" int mk_mlp_forward(mk_mlp *p, const float *d_x, int64_t n, float *d_y
 
 extern "C" int mk_mlp_loss_grad(mk_mlp *p, const float *d_x, const float *d_t, int64_t n, double *h_loss,
                                 float *h_grad) {
+  MK_TRACE("mk_mlp_loss_grad");
   if (!p) return MK_EINVAL;
   if (n < 1 || n > p->cap || !d_x || !d_t) return mfail(p->ctx, MK_EINVAL, "n must be in [1, max_batch]");
   mk_ctx *ctx = p->ctx;
@@ -199,6 +202,7 @@ extern "C" int mk_mlp_adam_step(mk_mlp *p, const float *d_grad, float lr) {
 
 extern "C" int mk_mlp_train(mk_mlp *p, const float *d_x, const float *d_t, int64_t n, int32_t batch,
                             int32_t epochs, float lr, uint64_t seed, double *h_epoch_loss) {
+  MK_TRACE("mk_mlp_train");
   if (!p) return MK_EINVAL;
   mk_ctx *ctx = p->ctx;
   if (n < 1 || !d_x || !d_t || batch < 1 || batch > p->cap || epochs < 0 || !(lr > 0.f))
@@ -437,6 +441,7 @@ extern "C" int mk_surrogate_labels(mk_ctx *ctx, const mk_skewer_params *params, 
                                    const int64_t *d_offsets, const float *d_delta, const float *d_eta,
                                    const mk_stat_bins *bins, const mk_surrogate_space *space, int32_t n_draws,
                                    uint64_t seed, double *h_x, double *h_t, int64_t *h_count) {
+  MK_TRACE("mk_surrogate_labels");
   if (!ctx) return MK_EINVAL;
   if (!bins || bins->n_k != 32 || !space || n_draws < 0 || !h_x || !h_t || !h_count)
     return mfail(ctx, MK_EINVAL, "surrogate labels need 32 k bins, a parameter space and host outputs");
@@ -489,6 +494,7 @@ extern "C" int mk_surrogate_labels(mk_ctx *ctx, const mk_skewer_params *params, 
 extern "C" int mk_surrogate_fit(mk_mlp *p, const double *h_x, const double *h_t, int64_t n, int32_t batch,
                                 int32_t epochs, float lr, uint64_t seed, mk_surrogate_norm *norm,
                                 double *h_epoch_loss) {
+  MK_TRACE("mk_surrogate_fit");
   if (!p) return MK_EINVAL;
   mk_ctx *ctx = p->ctx;
   if (n < 2 || !h_x || !h_t || !norm) return mfail(ctx, MK_EINVAL, "surrogate fit needs >= 2 samples and a norm");
@@ -762,6 +768,7 @@ extern "C" int mk_tune(mk_ctx *ctx, const mk_skewer_params *params, const mk_ske
                        const mk_tune_target *target, int32_t method, mk_mlp *surrogate,
                        const mk_surrogate_norm *norm, int32_t max_passes, mk_fgpa_nodes *inout,
                        mk_tune_report *report) {
+  MK_TRACE("mk_tune");
   if (!ctx) return MK_EINVAL;
   if (!bins || !target || !inout || !report || max_passes < 1)
     return mfail(ctx, MK_EINVAL, "mk_tune needs bins, a target, nodes, a report and max_passes >= 1");
