@@ -294,6 +294,10 @@ def test_other_fft_lengths(ctx, tiny, n_fft, layout):
     assert_field_close(g["eta"][:tot].cpu().numpy(), o["eta"], "eta")
     assert_flux_close(g["flux"][:tot].cpu().numpy(), o["flux"])
     assert_stats_close(st, so, check_fields=False)
+    # the tuning pass over the stored fields: teams of N/8 threads (several
+    # warps; at N = 2048 the whole CTA) stage the fields with bulk copies
+    st2 = ctx.flux_stats(w, g["sk"], len(ids), g["offsets"], g["delta"], g["eta"])
+    assert_stats_close(st2, so, check_fields=False)
 
 
 @pytest.mark.parametrize("n_fft", [256, 2048])
@@ -307,9 +311,12 @@ def test_segments_crossing_many_z_bins(ctx, tiny, n_fft):
     so = oracle.stats(w, o["j_lo"], o["offsets"], o["offsets_out"], o["flux"], o["delta"], o["eta"])
     assert np.count_nonzero(so["sums"][:, 0]) >= 10
     box = load(ctx, w, tiny["dev"]["d"], tiny["dev"]["e"], "padded")
-    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w, flags=mk.STATS | mk.STORE_FLUX)
+    st, g = ctx.run(box, mk.catalogue_tensor(pos, ids), len(ids), w,
+                    flags=mk.STATS | mk.STORE_FLUX | mk.STORE_FIELDS)
     assert_flux_close(g["flux"][:o["offsets"][-1]].cpu().numpy(), o["flux"])
     assert_stats_close(st, so)
+    # and the tuning pass over the stored fields, the same bin edges
+    assert_stats_close(ctx.flux_stats(w, g["sk"], len(ids), g["offsets"], g["delta"], g["eta"]), so)
 
 
 # ------------------------------------------------------------------ Gaussian-kernel interpolation (Sec. 2.3)
